@@ -1,0 +1,371 @@
+"""Pins of the CPU oracle against things other than itself.
+
+The paper prints no worked example and no intermediate value, so the oracle is
+pinned by: values worked out by hand from the definitions (tests/golden), brute
+force over every monotone alignment (Section 4: paths cannot go upward or
+leftward), textbook special cases (LCS, Levenshtein), closed forms and
+invariants.  The last test plants plausible mistakes in a copy of the oracle
+and checks that these pins catch every one of them.
+"""
+import itertools
+import json
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1509_08639_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+DIAG, UP, LEFT = O.DIAG, O.UP, O.LEFT
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _dict_from_json(m):
+    return synth.dictionary_from_map({int(k): v for k, v in m.items()})
+
+
+# ---------------------------------------------------------------- scoring pins
+
+def check_score_hand_examples(L=None):
+    for name in ("score_hand_example.json", "score_hand_example_2.json",
+                 "score_hand_example_3.json"):
+        g = _gold(name)
+        od = O.OracleDict(_dict_from_json(g["dictionary"]), L)
+        b = synth.docs_from_lists(g["src"], g["tgt"])
+        M = O.score_matrix(od, *b.pair(0))
+        assert M.tolist() == g["M"], name
+
+
+def test_score_hand_examples():
+    check_score_hand_examples()
+
+
+def test_score_hand_example_full_path():
+    g = _gold("score_hand_example.json")
+    M = np.asarray(g["M"], np.int32)
+    r, H, D = O.nw(M, g["gap"])
+    assert r == g["nw_score"]
+    assert H.tolist() == g["nw_H"]
+    mv = O.traceback(D)
+    assert [list(t) for t in O.select(M, mv, 32768)] == g["selected_theta_32768"]
+    assert [list(t) for t in O.select(M, mv, 50000)] == g["selected_theta_50000"]
+
+
+def check_score_closed_forms(L=None):
+    # identical sentence with an identity dictionary: every feature is 1.0
+    ident = synth.dictionary_from_map({t: [t] for t in range(1, 20)})
+    od = O.OracleDict(ident, L)
+    sent = [3, 5, 5, 7, 11, 3, 2]
+    M = O.score_matrix(od, *synth.docs_from_lists([sent], [list(sent)]).pair(0))
+    assert M[0, 0] == 65536
+    # disjoint vocabularies: only the length term survives, 0.25 * min/max
+    for L1, L2 in [(3, 7), (7, 3), (5, 5), (1, 9), (13, 4)]:
+        src = [1 + (k % 5) for k in range(L1)]
+        tgt = [100 + k for k in range(L2)]
+        M = O.score_matrix(od, *synth.docs_from_lists([src], [tgt]).pair(0))
+        q_l = (min(L1, L2) * 65536) // max(L1, L2)
+        assert M[0, 0] == (16384 * q_l) >> 16, (L1, L2)
+    # empty target sentence: no overlap and no length agreement -> 0
+    M = O.score_matrix(od, *synth.docs_from_lists([[1, 2]], [[]]).pair(0))
+    assert M[0, 0] == 0
+    # two empty sentences count as equal length: 0.25
+    M = O.score_matrix(od, *synth.docs_from_lists([[]], [[]]).pair(0))
+    assert M[0, 0] == 16384
+    # source made only of unknown tokens: target coverage 0, source coverage 0
+    M = O.score_matrix(od, *synth.docs_from_lists([[500, 501]], [[500, 501]]).pair(0))
+    assert M[0, 0] == 16384
+
+
+def test_score_closed_forms():
+    check_score_closed_forms()
+
+
+def test_score_ignores_dictionary_key_order_and_token_order():
+    rng = np.random.default_rng(7)
+    w = synth.workload(1)
+    d = w.dictionary
+    perm = rng.permutation(d.n_keys)
+    cnt = np.diff(d.trans_off)
+    new_off = np.zeros(d.n_keys + 1, np.int64)
+    np.cumsum(cnt[perm], out=new_off[1:])
+    new_tr = np.concatenate([d.trans[d.trans_off[k]:d.trans_off[k + 1]] for k in perm])
+    d2 = synth.Dictionary(d.keys[perm].copy(), new_off.astype(np.int32), new_tr.astype(np.int32))
+    src, tgt = w.batch.pair(0)
+    M1 = O.score_matrix(O.OracleDict(d), src, tgt)
+    M2 = O.score_matrix(O.OracleDict(d2), src, tgt)
+    assert np.array_equal(M1, M2)
+    # shuffling the tokens inside every sentence changes no set and no length
+    so, st = src
+    st2 = st.copy()
+    for i in range(len(so) - 1):
+        seg = st2[so[i]:so[i + 1]]
+        rng.shuffle(seg)
+    M3 = O.score_matrix(O.OracleDict(d), (so, st2), tgt)
+    assert np.array_equal(M1, M3)
+
+
+# ---------------------------------------------------------------- NW pins
+
+def check_nw_hand_examples(L=None):
+    g = _gold("nw_hand_examples.json")
+    for ex in g["examples"]:
+        M = np.asarray(ex["M"], np.int32)
+        r, H, D = O.nw(M, ex["gap"], L)
+        assert r == ex["nw_score"], ex["name"]
+        assert H.tolist() == ex["H"], ex["name"]
+        assert D.tolist() == ex["D"], ex["name"]
+        assert O.traceback(D, L) == ex["reversed_moves"], ex["name"]
+        for key in ex:
+            if key.startswith("selected_theta_"):
+                th = key[len("selected_theta_"):]
+                th = -1 if th == "minus1" else int(th)
+                got = [list(t) for t in O.select(M, O.traceback(D, L), th, L)]
+                assert got == ex[key], (ex["name"], key)
+
+
+def test_nw_hand_examples():
+    check_nw_hand_examples()
+
+
+def test_brute_force_enumerates_delannoy_many_paths():
+    # the enumerator itself: path counts are the Delannoy numbers
+    for S, T in [(1, 1), (2, 3), (3, 3), (4, 2), (5, 5)]:
+        assert O.brute_force(np.zeros((S, T), np.int32), -1)[2] == O.delannoy(S, T)
+    assert O.delannoy(7, 7) == 48639
+
+
+def check_brute_force(L=None, sizes=None, reps=3, seed=1509):
+    rng = np.random.default_rng(seed)
+    sizes = sizes or [(S, T) for S in range(1, 6) for T in range(1, 6)]
+    for S, T in sizes:
+        for rep in range(reps):
+            if rep % 3 == 0:      # many ties
+                M = synth.random_matrix(rng, S, T, values=[0, 16384, 32768])
+                g = int(rng.choice([0, -16384, -32768]))
+            elif rep % 3 == 1:    # signed, few ties
+                M = synth.random_matrix(rng, S, T, lo=-65536, hi=65536)
+                g = -int(rng.integers(0, 65537))
+            else:                 # non-negative scores as produced by the scorer
+                M = synth.random_matrix(rng, S, T, lo=0, hi=65536)
+                g = -int(rng.integers(0, 131073))
+            best, canon, _ = O.brute_force(M, g)
+            r, H, D = O.nw(M, g, L)
+            assert r == best, (S, T, rep)
+            assert O.traceback(D, L) == canon, (S, T, rep)
+
+
+def test_brute_force_small():
+    check_brute_force()
+
+
+def test_brute_force_up_to_7():
+    check_brute_force(sizes=[(6, 6), (7, 5), (5, 7), (7, 7)], reps=2, seed=1510)
+
+
+def _lcs_brute(a, b):
+    # longest subsequence of a that is also a subsequence of b, by enumeration
+    def is_sub(x, y):
+        it = iter(y)
+        return all(c in it for c in x)
+    for k in range(min(len(a), len(b)), -1, -1):
+        for idx in itertools.combinations(range(len(a)), k):
+            if is_sub([a[i] for i in idx], b):
+                return k
+    return 0
+
+
+def _edit_brute(a, b):
+    # shortest edit script by breadth-first search over (prefix, prefix) states
+    from collections import deque
+    seen = {(0, 0): 0}
+    q = deque([(0, 0)])
+    while q:
+        i, j = q.popleft()
+        d = seen[(i, j)]
+        if i == len(a) and j == len(b):
+            return d
+        nxt = []
+        if i < len(a) and j < len(b):
+            nxt.append(((i + 1, j + 1), 0 if a[i] == b[j] else 1))
+        if i < len(a):
+            nxt.append(((i + 1, j), 1))
+        if j < len(b):
+            nxt.append(((i, j + 1), 1))
+        for st, c in nxt:
+            if c == 0 and (st not in seen or seen[st] > d):
+                seen[st] = d
+                q.appendleft(st)
+            elif c == 1 and st not in seen:
+                seen[st] = d + 1
+                q.append(st)
+    raise AssertionError
+
+
+def _eq_matrix(a, b, hit, miss):
+    return np.asarray([[hit if x == y else miss for y in b] for x in a], np.int32)
+
+
+def check_textbook_special_cases(L=None, n=40, seed=11):
+    g = _gold("nw_hand_examples.json")
+    e, l = g["edit_distance"], g["lcs"]
+    r, _, _ = O.nw(_eq_matrix(e["a"], e["b"], 0, -65536), -65536, L)
+    assert -r // 65536 == e["distance"]
+    r, _, _ = O.nw(_eq_matrix(l["a"], l["b"], 65536, 0), 0, L)
+    assert r // 65536 == l["length"]
+    rng = np.random.default_rng(seed)
+    for _ in range(n):
+        a = list(rng.integers(0, 3, rng.integers(1, 8)))
+        b = list(rng.integers(0, 3, rng.integers(1, 8)))
+        r, _, _ = O.nw(_eq_matrix(a, b, 65536, 0), 0, L)
+        assert r == 65536 * _lcs_brute(a, b)
+        r, _, _ = O.nw(_eq_matrix(a, b, 0, -65536), -65536, L)
+        assert r == -65536 * _edit_brute(a, b)
+
+
+def test_textbook_special_cases():
+    check_textbook_special_cases()
+
+
+def check_closed_forms(L=None, seed=3):
+    rng = np.random.default_rng(seed)
+    # single source sentence: either match exactly one target (best one) and
+    # skip the other T-1, or skip all T and the source sentence itself
+    for T in [1, 2, 5, 33]:
+        M = synth.random_matrix(rng, 1, T, lo=0, hi=65536)
+        for g in [0, -1000, -65536, -200000]:
+            r, _, _ = O.nw(M, g, L)
+            assert r == max(int(M.max()) + g * (T - 1), g * (T + 1))
+    # zero matrix: |S-T| gaps; the canonical path matches from the end and
+    # leaves the surplus sentences unmatched at the start
+    for S, T in [(1, 4), (4, 1), (3, 3), (2, 7), (9, 4)]:
+        g = -65536
+        r, _, D = O.nw(np.zeros((S, T), np.int32), g, L)
+        assert r == g * abs(S - T)
+        mv = O.traceback(D, L)
+        gap_move = LEFT if T > S else UP
+        assert mv == [DIAG] * min(S, T) + [gap_move] * abs(S - T)
+
+
+def test_closed_forms():
+    check_closed_forms()
+
+
+def _walk(mv, S, T):
+    i, j = S, T
+    cells = []
+    for m in mv:
+        if m == DIAG:
+            cells.append((i, j))
+            i, j = i - 1, j - 1
+        elif m == UP:
+            i -= 1
+        else:
+            j -= 1
+        assert i >= 0 and j >= 0
+    assert (i, j) == (0, 0)
+    return cells[::-1]
+
+
+def check_invariants(L=None, seed=5):
+    rng = np.random.default_rng(seed)
+    for S, T in [(50, 70), (70, 50), (1, 90), (64, 64), (33, 31)]:
+        M = synth.random_matrix(rng, S, T, lo=0, hi=65536)
+        for g in [0, -16384, -65536, -131072]:
+            r, H, D = O.nw(M, g, L)
+            mv = O.traceback(D, L)
+            cells = _walk(mv, S, T)
+            # score along the path equals the optimum
+            assert r == sum(int(M[i - 1, j - 1]) for i, j in cells) + g * (len(mv) - len(cells))
+            assert len(mv) - len(cells) == S + T - 2 * len(cells)
+            # strictly increasing in both coordinates (each sentence once)
+            assert all(a[0] < b[0] and a[1] < b[1] for a, b in zip(cells, cells[1:]))
+            # the optimum does not depend on which article is called the source
+            rt, _, _ = O.nw(np.ascontiguousarray(M.T), g, L)
+            assert rt == r
+            # thresholds only filter: selections nest
+            prev = None
+            for th in [0, 16384, 32768, 49152, 65536]:
+                sel = set(O.select(M, mv, th, L))
+                assert all(s > th for _, _, s in sel)
+                if prev is not None:
+                    assert sel <= prev
+                prev = sel
+
+
+def test_invariants():
+    check_invariants()
+
+
+def test_overflow_bound_holds_for_accepted_inputs():
+    # (S+T)|g| + min(S,T)*65536 < 2^31 keeps every H inside int32
+    S = T = 4000
+    g = -131072
+    assert (S + T) * abs(g) + min(S, T) * 65536 < 2 ** 31
+
+
+# ------------------------------------------------ planted mistakes are caught
+
+_MUTANTS = {
+    "diag tie loses to up": ("(diag == best) ? OR_DIAG : (up == best) ? OR_UP : OR_LEFT",
+                             "(up == best) ? OR_UP : (diag == best) ? OR_DIAG : OR_LEFT"),
+    "up/left tie swapped": ("(diag == best) ? OR_DIAG : (up == best) ? OR_UP : OR_LEFT",
+                            "(diag == best) ? OR_DIAG : (left == best) ? OR_LEFT : OR_UP"),
+    "gap dropped from up": ("int64_t up = h[(i - 1) * W + j] + g;",
+                            "int64_t up = h[(i - 1) * W + j];"),
+    "transposed score index": ("M[(int64_t)(i - 1) * T + (j - 1)];\n            int64_t up",
+                               "M[(int64_t)(j - 1) * T + (i - 1) < (int64_t)S * T ? (int64_t)(j - 1) * T + (i - 1) : 0];\n            int64_t up"),
+    "free end gaps on first row": ("h[j] = (int64_t)j * g;", "h[j] = 0;"),
+    "source/target counts swapped": ("int64_t q_t = tgt[j].m > 0 ? (a * 65536) / tgt[j].m : 0;",
+                                     "int64_t q_t = src[i].n > 0 ? (a * 65536) / src[i].n : 0;"),
+    "coverage from multiset": [("src[i].nu = sort_unique(src[i].U, w);",
+                                "src[i].nu = w; qsort(src[i].U, (size_t)w, sizeof(int32_t), cmp_i32);"),
+                               ("{ ++a; ++x; ++y; }", "{ ++a; ++x; }")],
+    "length term weight swapped": ("int64_t s = (49152 * ((q_t + q_s) / 2) + 16384 * q_l) / 65536;",
+                                   "int64_t s = (16384 * ((q_t + q_s) / 2) + 49152 * q_l) / 65536;"),
+    "threshold not strict": ("if (s > theta) {", "if (s >= theta) {"),
+    "unknown tokens not counted": ("src[i].n = sort_unique(src[i].X, L);",
+                                   "src[i].n = sort_unique(src[i].X, L); { int32_t w2 = 0; for (int32_t p = 0; p < src[i].n; ++p) { const int32_t *tr; if (dict_lookup(d, src[i].X[p], &tr)) src[i].X[w2++] = src[i].X[p]; } src[i].n = w2; }"),
+    "b counts translations not tokens": ("for (int32_t k = 0; k < c && !hit; ++k) hit = contains",
+                                         "for (int32_t k = 0; k < c; ++k) hit += contains"),
+}
+
+
+def _run_all_pins(L):
+    checks = [check_score_hand_examples, check_score_closed_forms, check_nw_hand_examples,
+              lambda L: check_brute_force(L, reps=3), check_textbook_special_cases,
+              check_closed_forms, check_invariants]
+    failed = []
+    for c in checks:
+        try:
+            c(L)
+        except AssertionError:
+            failed.append(c)
+    return failed
+
+
+@pytest.mark.parametrize("name", sorted(_MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    edits = _MUTANTS[name]
+    edits = edits if isinstance(edits, list) else [edits]
+    src = open(O._SRC).read()
+    for old, new in edits:
+        assert src.count(old) == 1, f"mutation anchor for {name!r} not unique in the oracle"
+        src = src.replace(old, new)
+    path = tmp_path / "mutant.c"
+    path.write_text(src)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", str(path), "-o", str(so)],
+                   check=True, capture_output=True)
+    L = O.load(str(so))
+    assert _run_all_pins(L), f"no pin caught the planted mistake {name!r}"
+
+
+def test_unmutated_oracle_passes_all_pins():
+    assert _run_all_pins(O.lib()) == []
