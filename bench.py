@@ -1,0 +1,431 @@
+"""Benchmark of the GB300 parallel-sentence miner.
+
+Default workload: 10,000 synthetic comparable-article pairs with lognormal
+sentence counts (median 60, clipped 5-800), 5-40-token sentences over a 200k
+Zipf vocabulary and a 200k-entry dictionary, gap -1.0, threshold 0.5 (Q16).
+
+One step = the whole mining path (score matrices, alignments, tracebacks,
+selection) over the batch.  `value` is article pairs/s with the batch resident
+in device memory; `e2e` is the same through the host-buffer C call (copies in
+and results out inside the timed region); `plain` mines one pair per call.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "article pairs/s & NW GCUPS, batched/served vs plain per-pair, 1 GB300; p50/p99"
+UNIT = "article pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", type=int, default=2, help="1..5 (parity cases); 2 is the bench")
+    ap.add_argument("--pairs", type=int, default=None, help="override the pair count")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--plain-pairs", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=5000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------- helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1509_08639_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, when it still
+    describes the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    k = d.get("kernels", {}).get(kernel)
+    if not k or d.get("source_hash") != kernel_source_hash():
+        return None
+    return k.get("dram_bytes_per_launch_full_workload")
+
+
+def cpu_baseline(w, budget_s=20.0):
+    """The oracle as it stands, on this host's cores, on a bounded sample."""
+    from oracle import oracle as O
+    od = O.OracleDict(w.dictionary)
+    S, T = w.batch.sizes()
+    rng = np.random.default_rng(99)
+    order = rng.permutation(w.batch.n_pairs)
+    threads = os.cpu_count() or 1
+    done_pairs, done_cells, t_used, k = 0, 0, 0.0, 0
+    chunk = max(threads * 4, 32)
+    while t_used < budget_s and k < len(order):
+        idx = order[k:k + chunk]
+        sub = w.batch.subset(idx)
+        t0 = time.perf_counter()
+        _, used = O.mine_batch(od, sub, w.settings, threads)
+        t_used += time.perf_counter() - t0
+        done_pairs += len(idx)
+        done_cells += int((S[idx] * T[idx]).sum())
+        k += chunk
+    return {"value": done_pairs / t_used, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"{done_pairs} random pairs of the same workload ({done_cells} cells), "
+                      f"{t_used:.1f} s, OpenMP over pairs",
+            "gcups": done_cells * len({g for g, _ in w.settings}) / t_used / 1e9}
+
+
+# --------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1509_08639_gb300 import synth
+    w = synth.workload(args.workload, n_pairs=args.pairs)
+    from oracle import oracle as O
+    od = O.OracleDict(w.dictionary)
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    S, T = w.batch.sizes()
+    sample = max(threads * 8, 64)
+    times, pairs = [], []
+    for step in range(args.warmup + args.steps):
+        idx = rng.choice(w.batch.n_pairs, min(sample, w.batch.n_pairs), replace=False)
+        sub = w.batch.subset(idx)
+        t0 = time.perf_counter()
+        _, used = O.mine_batch(od, sub, w.settings, threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            pairs.append(len(idx))
+    v = sum(pairs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w.name, "pairs": w.batch.n_pairs},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(used), "kind": "oracle",
+                             "sample": f"{sample} random pairs per step, OpenMP over pairs"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GB300 arm
+
+def serving_run(ctx, dh, rate, seconds):
+    """Poisson arrivals of 40x45 pairs with a 1% tail of 2000x2000 pairs."""
+    from paper_1509_08639_gb300 import synth
+    w5 = synth.workload(5, n_pairs=max(int(rate * seconds * 1.1) + 16, 64))
+    # the request pool uses its own dictionary: register it
+    dh5 = ctx.dict_create(w5.dictionary)
+    arrivals = synth.poisson_arrivals(rate, seconds)
+    n = len(arrivals)
+    docs = [w5.batch.pair(p % w5.batch.n_pairs) for p in range(n)]
+    lat = []
+    done = threading.Event()
+    got = [0]
+
+    def poller():
+        while got[0] < n:
+            for r in ctx.poll(1024, 20000):
+                lat.append(r[5])
+                got[0] += 1
+        done.set()
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for k in range(n):
+        now = time.perf_counter() - t0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        src, tgt = docs[k]
+        ctx.submit(dh5, src, tgt, w5.settings)
+    done.wait(120)
+    t1 = time.perf_counter() - t0
+    th.join(5)
+    lat = np.asarray(lat, np.float64) / 1e6
+    return {"offered_pairs_per_s": rate, "served_pairs_per_s": n / t1, "requests": n,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "workload": "40x45 pairs, 1% 2000x2000, Poisson arrivals"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_env()
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1509_08639_gb300 import mine, synth
+
+    # every rank mines its own batch (independent pairs: weak scaling)
+    w = synth.workload(args.workload, n_pairs=args.pairs,
+                       seed=None if rank == 0 else 1508 + args.workload + 1000 * rank)
+    b = w.batch
+    P = b.n_pairs
+    S, T = b.sizes()
+    n_set = len(w.settings)
+    n_gap = len({g for g, _ in w.settings})
+    cells = int((S * T).sum())
+    ctx = mine.Context(device=local)
+    dh = ctx.dict_create(w.dictionary)
+
+    # ---- device-resident inputs
+    sent = torch.from_numpy(b.sent_off).to(dev)
+    tok = torch.from_numpy(b.tokens).to(dev)
+    cap = max(int(n_set * np.minimum(S, T).sum()), 1)
+    nw = torch.zeros(P * n_set, dtype=torch.int32, device=dev)
+    ns = torch.zeros(P * n_set, dtype=torch.int32, device=dev)
+    sel = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    n_sent, n_tok = int(b.sent_off.shape[0] - 1), int(b.tokens.shape[0])
+
+    def step():
+        ctx.run_batch_device(dh, P, b.doc_off, sent, tok, n_sent, n_tok, w.settings,
+                             nw, ns, sel, cap, stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    ctx.check()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    ctx.profile_read()
+    launches0 = ctx.launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * P / (ms / 1e3)
+    gcups = ws * cells * n_gap / (ms / 1e3) / 1e9
+
+    # ---- end to end through the host-buffer call (pinned host memory)
+    pin_sent = torch.from_numpy(b.sent_off).pin_memory()
+    pin_tok = torch.from_numpy(b.tokens).pin_memory()
+    hdo = np.ascontiguousarray(b.doc_off)
+    g = np.asarray([s[0] for s in w.settings], np.int32)
+    th = np.asarray([s[1] for s in w.settings], np.int32)
+    bc = mine.BatchC(P, n_sent, n_tok, mine._ptr(hdo), pin_sent.data_ptr(), pin_tok.data_ptr())
+    sc = mine.SettingsC(n_set, mine._ptr(g), mine._ptr(th))
+    o_nw = torch.zeros(P * n_set, dtype=torch.int32).pin_memory().numpy()
+    o_ns = torch.zeros(P * n_set, dtype=torch.int32).pin_memory().numpy()
+    o_off = torch.zeros(P * n_set + 1, dtype=torch.int64).pin_memory().numpy()
+    o_sel = torch.zeros(cap * 3, dtype=torch.int32).pin_memory().numpy()
+    outs = (o_nw, o_ns, o_off, o_sel, cap)
+    for _ in range(args.warmup):
+        ctx.run_batch_raw(dh, bc, sc, outs)
+    io0 = ctx.io_bytes()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.run_batch_raw(dh, bc, sc, outs)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    io1 = ctx.io_bytes()
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    # device-resident results equal the host-call results
+    assert np.array_equal(nw.cpu().numpy(), o_nw) and np.array_equal(ns.cpu().numpy(), o_ns)
+
+    # ---- plain path: one pair per call
+    plain = None
+    if args.plain_pairs > 0:
+        idx = np.random.default_rng(3).choice(P, min(args.plain_pairs, P), replace=False)
+        subs = [b.subset([p]) for p in idx]
+        for sb in subs[:5]:
+            ctx.run_batch(dh, sb, w.settings)
+        t0 = time.perf_counter()
+        for sb in subs:
+            ctx.run_batch(dh, sb, w.settings)
+        dt = time.perf_counter() - t0
+        plain = {"value": len(subs) / dt, "unit": UNIT, "pairs": len(subs),
+                 "how": "one pair per mine_run_batch call (copy in, 4 kernels, copy out, sync)"}
+
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = serving_run(ctx, dh, args.serve_rate, args.serve_seconds)
+
+    # ---- roofline of the dominant kernel
+    hbm_peak, sm_mhz_max, peak_kind = peaks()
+    timed = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(timed, key=lambda k: timed[k][0])
+    per_launch_ms = {k: v[0] / v[1] for k, v in timed.items()}
+    src_tok = int((b.sent_off[b.doc_off[1:-1:2]].astype(np.int64) -
+                   b.sent_off[b.doc_off[0:-1:2]].astype(np.int64)).sum())
+    tgt_tok = n_tok - src_tok
+    # algorithmic work per launch (roofline)
+    score_bytes = 4 * cells + 4 * (src_tok + tgt_tok)          # M written + tokens read
+    align_ops = 4 * cells * n_gap                                 # 4 int ops per DP cell
+    alu_peak_tops = 152 * 128 * sm_mhz_max * 1e6 / 1e12           # int32 lane-ops/s
+    rl = {}
+    for k in ("k_score", "k_align"):
+        if k not in per_launch_ms:
+            continue
+        t = per_launch_ms[k] / 1e3
+        if k == "k_score":
+            a = score_bytes / t / 1e9
+            rl[k] = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": a / hbm_peak, "traffic": committed_traffic(k),
+                     "algorithmic_bytes": score_bytes, "ms": per_launch_ms[k]}
+        else:
+            a = align_ops / t / 1e12
+            rl[k] = {"bound": "alu", "achieved": a, "peak": alu_peak_tops, "unit": "Tops/s",
+                     "frac": a / alu_peak_tops, "traffic": committed_traffic(k),
+                     "algorithmic_ops": align_ops, "ms": per_launch_ms[k],
+                     "gcups": cells * n_gap / t / 1e9}
+    roof = dict(rl.get(dom, {}))
+    roof["kernel"] = dom
+    roof["peak_kind"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if roof.get("bound") == "hbm" \
+        else "derived: 152 SMs x 128 int32 lanes x max SM clock"
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": w.name, "pairs": P, "cells": cells, "settings": n_set,
+                   "tokens": n_tok, "l2": "inputs larger than L2 (tokens %d MB, score matrices %d MB)"
+                   % (4 * n_tok >> 20, 4 * cells >> 20), "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "gcups": gcups,
+        "e2e": {"value": ws * P / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": (io1[0] - io0[0]) // args.steps,
+                "d2h_bytes_per_step": (io1[1] - io0[1]) // args.steps},
+        "plain": plain,
+        "batched_vs_plain": (value / ws) / plain["value"] if plain else None,
+        "serving": serving,
+        "roofline": roof,
+        "roofline_kernels": rl,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in timed.items()},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * mine.h -- C ABI of the GB300 parallel-sentence miner.
+ *
+ * The problem statement follows Wolk & Marasek, "Tuned and GPU-accelerated
+ * parallel data mining from comparable corpora", Section 4: given a pair of
+ * comparable articles and the alignment model of a language pair, find the
+ * sentence pairs that are close translation matches.  The comparison is a
+ * Needleman-Wunsch global alignment over the sentence-pair score matrix M
+ * ("paths cannot go upward or leftward in the M matrix"), with two parameters:
+ * Threshold (confidence needed to accept an aligned pair) and Penalty (how
+ * much skipping ahead is allowed).  The paper's confidence is an SVM
+ * probability; this library replaces it by a deterministic fixed-point score
+ * from token overlap (through a bilingual dictionary) and sentence length.
+ *
+ * Definitions (all integers; Q16 means value = x * 65536; "/" is floor
+ * division of non-negative integers):
+ *   source sentence i: X_i distinct tokens, n_i = |X_i|, L_i token count,
+ *                      U_i = distinct union of dict(t) over t in X_i
+ *   target sentence j: V_j distinct tokens, m_j = |V_j|, L'_j token count
+ *   a = |U_i & V_j|, b = #{t in X_i : dict(t) & V_j non-empty}
+ *   q_t = m_j ? a*65536/m_j : 0      q_s = n_i ? b*65536/n_i : 0
+ *   q_l = max(L,L') ? min(L,L')*65536/max(L,L') : 65536
+ *   s(i,j) = (49152*((q_t+q_s)>>1) + 16384*q_l) >> 16      in [0, 65536]
+ *   H[0][0]=0, H[i][0]=i*g, H[0][j]=j*g,
+ *   H[i][j] = max(H[i-1][j-1]+s(i,j), H[i-1][j]+g, H[i][j-1]+g)
+ *   ties: the diagonal wins, then "up" (source sentence i unmatched), then
+ *   "left" (target sentence j unmatched); the path is traced back from (S,T)
+ *   following these choices.  nw_score = H[S][T].
+ *   selected pairs: diagonal steps (i,j) of the path with s(i,j) > threshold,
+ *   in increasing i, reported 0-based.
+ *
+ * Conventions.
+ *   - Every function returns 0 (MINE_OK) on success or a negative MINE_E* code.
+ *   - Pointers documented as "host" are ordinary host memory read during the
+ *     call only (the library copies what it keeps).  Pointers documented as
+ *     "device" are CUDA device pointers on the context's device.
+ *   - Limits (MINE_EINVAL beyond them): token IDs in [0, 2^30); at most
+ *     1024 tokens per sentence; at most 65535 sentences per article; at most
+ *     32 translations per dictionary key; gap <= 0; threshold in [0, 65536]
+ *     for mined pairs.  MINE_EOVERFLOW when (S+T)*|gap| + min(S,T)*max|s|
+ *     reaches 2^31 (H would leave int32).
+ *   - A context owns one CUDA device (the one current when mine_open is
+ *     called, or cfg->device) and may be used from several threads; calls on
+ *     one context are serialised internally.
+ */
+#ifndef MINE_H
+#define MINE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mine_q16;                 /* fixed point, value = x * 65536 */
+
+enum {
+    MINE_OK = 0,
+    MINE_EINVAL = -1,      /* null pointer, malformed CSR, value out of range */
+    MINE_ENOMEM = -2,      /* request larger than the device budget, or host/device allocation failed */
+    MINE_EAGAIN = -3,      /* queue full / nothing ready yet: retry */
+    MINE_EOVERFLOW = -4,   /* H would leave int32 (see Limits) */
+    MINE_ETIMEDOUT = -5,   /* a bounded device wait ran out */
+    MINE_EBUSY = -6,       /* dictionary still used by requests in flight */
+    MINE_ECUDA = -7        /* CUDA error; text via mine_last_error() */
+};
+
+#define MINE_MAX_SENT_TOKENS 1024
+#define MINE_MAX_SENTENCES   65535
+#define MINE_MAX_TRANS       32
+#define MINE_MAX_TOKEN_ID    ((1 << 30) - 1)
+
+typedef struct mine_ctx mine_ctx;         /* opaque */
+typedef struct mine_dict mine_dict;       /* opaque, device-resident */
+
+/* One article in CSR form (host memory).  Sentence k holds
+ * tokens[sent_off[k] .. sent_off[k+1]); sent_off[0] = 0, non-decreasing. */
+typedef struct {
+    const int32_t *sent_off;              /* [n_sent + 1] */
+    const int32_t *tokens;                /* [sent_off[n_sent]], each in [0, 2^30) */
+    int32_t n_sent;                       /* 0 .. 65535 */
+} mine_doc;
+
+typedef struct {
+    int64_t device_budget_bytes;          /* admission budget for requests in flight; 0 -> 8 GiB */
+    int32_t max_inflight;                 /* batches on the device at once (serving); 0 -> 3 */
+    int32_t device;                       /* CUDA device ordinal; -1 -> current device */
+    int32_t max_batch_pairs;              /* serving: pairs per batch at most; 0 -> 4096 */
+    int32_t batch_window_us;              /* serving: wait this long to fill a batch; 0 -> 200 */
+} mine_config;
+
+typedef struct {
+    int32_t src_sent;                     /* 0-based source sentence */
+    int32_t tgt_sent;                     /* 0-based target sentence */
+    mine_q16 score;                       /* s(i,j) */
+} mine_pair;
+
+typedef struct {
+    uint64_t ticket;                      /* from mine_submit / mine_submit_sweep */
+    int32_t status;                       /* MINE_OK or the request's error */
+    int32_t setting;                      /* index into the request's settings (0 for mine_submit) */
+    mine_q16 nw_score;                    /* H[S][T] for this setting's gap */
+    int32_t n_pairs;                      /* selected pairs */
+    mine_pair *pairs;                     /* owned by the library until mine_result_free */
+    int64_t latency_ns;                   /* submit -> result ready, for p50/p99 */
+} mine_result;
+
+/* Last error text of this thread (CUDA errors, validation details).  Never NULL. */
+const char *mine_last_error(void);
+
+/* Open a context: creates streams, the serving thread and the device arena.
+ * cfg may be NULL (defaults).  *out receives the context. */
+int mine_open(const mine_config *cfg, mine_ctx **out);
+
+/* Drain every request still in flight, free all dictionaries and device
+ * memory of the context, and destroy it.  ctx may be NULL (no-op). */
+int mine_close(mine_ctx *ctx);
+
+/* Bilingual dictionary (the "alignment model" of a language pair, Section 4).
+ * Host CSR: key keys[k] translates to trans[trans_off[k] .. trans_off[k+1]).
+ * Keys unique and in [0, 2^30); at most 32 translations per key (repeats
+ * inside one key's list are ignored); translations in [0, 2^30).  The data are
+ * copied into a device-resident open-addressed hash table that stays resident
+ * until mine_dict_destroy.  Tokens without an entry are legal (no
+ * translation). */
+int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_off,
+                     const int32_t *trans, int32_t n_keys, mine_dict **out);
+
+/* MINE_EBUSY while submitted requests that use it have not finished. */
+int mine_dict_destroy(mine_ctx *ctx, mine_dict *dict);
+
+/* Queue one article pair for mining with one (gap, threshold) setting.
+ * The documents are copied before the call returns.  The result arrives
+ * through mine_poll with the returned ticket.  Returns MINE_ENOMEM when the
+ * request alone exceeds the device budget, MINE_EOVERFLOW per Limits. */
+int mine_submit(mine_ctx *ctx, const mine_doc *src, const mine_doc *tgt, const mine_dict *dict,
+                mine_q16 gap, mine_q16 threshold, uint64_t *ticket);
+
+/* Like mine_submit with n settings (gaps[k], thresholds[k]) evaluated
+ * against ONE score matrix (the paper's tuning of Threshold and Penalty).
+ * One alignment is run per distinct gap; n results share the ticket and carry
+ * setting = k.  1 <= n <= 256. */
+int mine_submit_sweep(mine_ctx *ctx, const mine_doc *src, const mine_doc *tgt,
+                      const mine_dict *dict, int32_t n, const mine_q16 *gaps,
+                      const mine_q16 *thresholds, uint64_t *ticket);
+
+/* Collect up to max_out finished results into out[] (host array), waiting up
+ * to timeout_us microseconds (0: do not wait; <0: wait until at least one
+ * result is ready or nothing is in flight).  Returns the number written
+ * (>= 0) or a negative error. */
+int mine_poll(mine_ctx *ctx, mine_result *out, int32_t max_out, int32_t timeout_us);
+
+/* Release result->pairs; safe on a zeroed result. */
+void mine_result_free(mine_ctx *ctx, mine_result *result);
+
+/* Alignment only, synchronously, on a caller-supplied score matrix: M is a
+ * host S x T row-major int32 matrix of any sign.  Writes the selected pairs
+ * (s > threshold, increasing i) to out[] (host, capacity min(S,T)), their
+ * count to *n_out and H[S][T] to *nw_score.  Any int32 threshold is
+ * accepted here. */
+int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mine_q16 gap,
+                      mine_q16 threshold, mine_pair *out, int32_t *n_out, mine_q16 *nw_score);
+
+/* ---------------------------------------------------------------- batches
+ * A batch of P article pairs in packed CSR form: document 2p is the source
+ * article of pair p and document 2p+1 its target article; document d holds
+ * sentences doc_off[d] .. doc_off[d+1]) and sentence k holds tokens
+ * tokens[sent_off[k] .. sent_off[k+1]).  doc_off[0] = sent_off[0] = 0. */
+typedef struct {
+    int32_t n_pairs;                      /* P >= 0 */
+    int64_t n_sent;                       /* doc_off[2P] */
+    int64_t n_tok;                        /* sent_off[n_sent] */
+    const int32_t *doc_off;               /* [2P + 1] */
+    const int32_t *sent_off;              /* [n_sent + 1] */
+    const int32_t *tokens;                /* [n_tok] */
+} mine_batch;
+
+/* The same n settings (gaps[k], thresholds[k]) for every pair of a batch;
+ * host arrays, 1 <= n <= 256. */
+typedef struct {
+    int32_t n;
+    const mine_q16 *gaps;
+    const mine_q16 *thresholds;
+} mine_settings;
+
+/* Selected-pair capacity a batch can need: sum over pairs of
+ * n * min(S_p, T_p).  doc_off is a host array. */
+int64_t mine_batch_capacity(const int32_t *doc_off, int32_t n_pairs, int32_t n_settings);
+
+/* Mine a whole batch synchronously; every array is HOST memory (copies to
+ * and from the device happen inside the call).  Outputs, for pair p and
+ * setting k at r = p*n + k:
+ *   nw_score[r], n_sel[r]  (arrays of P*n),
+ *   sel_off[r] .. sel_off[r+1]  range of sel[] holding the selected pairs
+ *   (sel_off has P*n + 1 entries), sel[] of capacity sel_cap (>= the total;
+ *   mine_batch_capacity() is always enough).  MINE_EINVAL if sel_cap is too
+ *   small for the actual selection (nothing partial is reported). */
+int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                   const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
+                   int64_t *sel_off, mine_pair *sel, int64_t sel_cap);
+
+/* The same with the batch already in DEVICE memory and outputs in DEVICE
+ * memory, enqueued on `stream` (a cudaStream_t; NULL = the context's own
+ * stream) without a host round trip for the data.  doc_off_host is a host
+ * copy of batch->doc_off (used to plan the launch).  sel[] (device) receives
+ * pair p / setting k at sel[sel_base + k*min(S_p,T_p) ...] where sel_base is
+ * the exclusive prefix sum of n*min(S,T) over earlier pairs; n_sel and
+ * nw_score are device arrays of P*n.  sel_cap must be at least
+ * mine_batch_capacity().  The call returns once the work is enqueued; the
+ * caller synchronises the stream.  Internal scratch stays owned by the
+ * context and is reused by the next call on it. */
+int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                          const int32_t *doc_off_host, const mine_settings *settings,
+                          mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
+                          void *stream);
+
+/* Wait for all work of the context's device and report a device-side
+ * validation failure of the last mine_run_batch_device call (malformed
+ * sentence offsets, token IDs out of range) as MINE_EINVAL. */
+int mine_check(mine_ctx *ctx);
+
+/* Number of kernel launches the library has issued on this context so far
+ * (for launch accounting by callers). */
+int64_t mine_launch_count(mine_ctx *ctx);
+
+/* Bytes copied host->device and device->host so far by mine_run_batch calls
+ * on this context (inputs, launch plan, results). */
+int mine_io_bytes(mine_ctx *ctx, int64_t *h2d, int64_t *d2h);
+
+/* Per-kernel device timing: when enabled, every kernel the context launches
+ * is bracketed by CUDA events recorded on its own launch stream. */
+int mine_profile(mine_ctx *ctx, int32_t enable);
+
+/* Wait for the timed kernels, then write for kernel id k < n the summed
+ * device time in ms[k] and the number of timed launches in launches[k]
+ * (host arrays), and reset the sums.  Returns the number of kernel ids. */
+int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n);
+
+/* Name of kernel id k ("" when out of range). */
+const char *mine_kernel_name(int32_t id);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MINE_H */

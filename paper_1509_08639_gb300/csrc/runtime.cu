@@ -1,0 +1,1250 @@
+// runtime.cu -- host side of the miner: the C ABI of include/mine.h.
+//
+// Contexts own a stream, a growable scratch arena for the synchronous batch
+// calls, and a serving engine: a host thread that forms batches from
+// submitted article pairs (continuous batching), admits them against a fixed
+// device-memory pool (the budget), runs up to max_inflight batches at once on
+// their own streams, and hands results to mine_poll.
+#include "internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+using namespace mine;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(MINE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int ceil_log2_host(int64_t x)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < x) ++l;
+    return l;
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ buffers
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+int ensure_dev(DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap && b.p) return 0;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const size_t nb = std::max<size_t>(bytes + bytes / 4, 1 << 16);
+    CK(cudaMalloc(&b.p, nb));
+    b.cap = nb;
+    return 0;
+}
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~HostBuf()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+int ensure_host(HostBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap && b.p) return 0;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const size_t nb = std::max<size_t>(bytes + bytes / 4, 1 << 16);
+    CK(cudaMallocHost(&b.p, nb));
+    b.cap = nb;
+    return 0;
+}
+
+// ------------------------------------------------------------------ plan
+
+using Setting = std::pair<int32_t, int32_t>;   // (gap, threshold)
+
+struct Plan {
+    int32_t P = 0;
+    std::vector<PairPlan> pairs;
+    std::vector<ScoreItem> sitems;
+    std::vector<NwItem> nitems;
+    std::vector<int32_t> set_gap, set_thr, gap_val;
+    int64_t m_elems = 0, code_words = 0, match_words = 0, hrow_words = 0, sel_cap = 0;
+    int32_t R = 0;
+    int64_t n_sent = 0, n_tok = 0;
+};
+
+// Validate a pair's settings and add them to the plan; returns the number of
+// distinct gaps (their indices start at gap0).
+int add_settings(Plan &pl, const Setting *set, int n, int32_t S, int32_t T, int64_t max_abs_s,
+                 bool mined, int32_t &gap0, int32_t &ngap)
+{
+    if (n < 1 || n > 256) return fail(MINE_EINVAL, "settings count must be in [1, 256]");
+    gap0 = (int32_t)pl.gap_val.size();
+    for (int k = 0; k < n; ++k) {
+        const int32_t g = set[k].first, th = set[k].second;
+        if (g > 0) return fail(MINE_EINVAL, "gap must be <= 0");
+        if (mined && (th < 0 || th > 65536))
+            return fail(MINE_EINVAL, "threshold must be in [0, 65536]");
+        const int64_t bound = (int64_t)(S + T) * (-(int64_t)g) + (int64_t)std::min(S, T) * max_abs_s;
+        if (bound >= (int64_t(1) << 31))
+            return fail(MINE_EOVERFLOW, "(S+T)*|gap| + min(S,T)*max|s| reaches 2^31");
+        int gi = -1;
+        for (int q = gap0; q < (int)pl.gap_val.size(); ++q)
+            if (pl.gap_val[q] == g) gi = q;
+        if (gi < 0) {
+            gi = (int)pl.gap_val.size();
+            pl.gap_val.push_back(g);
+        }
+        pl.set_gap.push_back(gi);
+        pl.set_thr.push_back(th);
+    }
+    ngap = (int32_t)pl.gap_val.size() - gap0;
+    return 0;
+}
+
+// settings_of(p) -> (pointer, count) of pair p's settings
+template <class F>
+int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F settings_of,
+               int64_t max_abs_s, bool mined)
+{
+    pl = Plan();
+    pl.P = P;
+    pl.n_sent = n_sent;
+    if (P < 0) return fail(MINE_EINVAL, "negative pair count");
+    if (doc_off[0] != 0) return fail(MINE_EINVAL, "doc_off[0] must be 0");
+    for (int64_t d = 0; d < 2 * (int64_t)P; ++d) {
+        const int64_t n = (int64_t)doc_off[d + 1] - doc_off[d];
+        if (n < 0 || n > MINE_MAX_SENTENCES)
+            return fail(MINE_EINVAL, "article sentence count out of range at document " + std::to_string(d));
+    }
+    if ((int64_t)doc_off[2 * (int64_t)P] != n_sent)
+        return fail(MINE_EINVAL, "doc_off[2P] must equal n_sent");
+    pl.pairs.resize(P);
+    std::vector<int> bucketS(P), bucketC(P);
+    for (int32_t p = 0; p < P; ++p) {
+        PairPlan &pp = pl.pairs[p];
+        pp.s0 = doc_off[2 * p];
+        pp.S = doc_off[2 * p + 1] - pp.s0;
+        pp.t0 = doc_off[2 * p + 1];
+        pp.T = doc_off[2 * p + 2] - pp.t0;
+        const Setting *set;
+        int n;
+        settings_of(p, set, n);
+        pp.set0 = pl.R;
+        pp.nset = n;
+        int rc = add_settings(pl, set, n, pp.S, pp.T, max_abs_s, mined, pp.gap0, pp.ngap);
+        if (rc) return rc;
+        pl.R += n;
+        const int64_t Tp = (pp.T + 3) & ~3;
+        pp.m_off = pl.m_elems;
+        pl.m_elems += (int64_t)pp.S * Tp;
+        pp.sel_base = pl.sel_cap;
+        pl.sel_cap += (int64_t)n * std::min(pp.S, pp.T);
+        bucketS[p] = ceil_log2_host((int64_t)pp.T + 1);
+        bucketC[p] = ceil_log2_host((int64_t)pp.S * pp.T + 1);
+    }
+    // longest-first orders (counting sort on the bit length of the work)
+    auto order_by = [&](const std::vector<int> &key) {
+        std::vector<int> cnt(66, 0), ord(P);
+        for (int p = 0; p < P; ++p) cnt[65 - key[p]]++;
+        for (int k = 1; k < 66; ++k) cnt[k] += cnt[k - 1];
+        for (int p = P - 1; p >= 0; --p) ord[--cnt[65 - key[p]]] = p;
+        return ord;
+    };
+    for (int p : order_by(bucketS)) {
+        const PairPlan &pp = pl.pairs[p];
+        for (int r0 = 0; r0 < pp.S; r0 += 32) pl.sitems.push_back(ScoreItem{p, r0});
+    }
+    for (int p : order_by(bucketC)) {
+        const PairPlan &pp = pl.pairs[p];
+        const int64_t CW = (pp.T + 15) >> 4;
+        for (int g = 0; g < pp.ngap; ++g) {
+            NwItem it;
+            it.pair = p;
+            it.gap = pp.gap0 + g;
+            it.code_off = pl.code_words;
+            pl.code_words += (int64_t)pp.S * CW;
+            it.match_off = pl.match_words;
+            pl.match_words += std::min(pp.S, pp.T);
+            it.hrow_off = pl.hrow_words;
+            pl.hrow_words += (int64_t)pp.T + 1;
+            pl.nitems.push_back(it);
+        }
+    }
+    return 0;
+}
+
+// Byte layout of one batch's device region.
+struct Layout {
+    int64_t plan = 0, plan_bytes = 0;
+    int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
+    int64_t elems = 0, sinfo = 0, M = 0, codes = 0, matches = 0, hrow = 0;
+    int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
+    int64_t total = 0;
+    // offsets inside the plan blob
+    int64_t o_pairs = 0, o_sitems = 0, o_nitems = 0, o_setgap = 0, o_setthr = 0, o_gapval = 0;
+};
+
+Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel, bool scoring)
+{
+    Layout L;
+    int64_t o = 0;
+    auto take = [&](int64_t bytes) {
+        const int64_t at = o;
+        o = align_up(o + std::max<int64_t>(bytes, 0), 256);
+        return at;
+    };
+    int64_t q = 0;
+    auto sub = [&](int64_t bytes) {
+        const int64_t at = q;
+        q = align_up(q + bytes, 16);
+        return at;
+    };
+    L.o_pairs = sub(sizeof(PairPlan) * pl.pairs.size());
+    L.o_sitems = sub(sizeof(ScoreItem) * pl.sitems.size());
+    L.o_nitems = sub(sizeof(NwItem) * pl.nitems.size());
+    L.o_setgap = sub(4 * pl.set_gap.size());
+    L.o_setthr = sub(4 * pl.set_thr.size());
+    L.o_gapval = sub(4 * pl.gap_val.size());
+    L.plan_bytes = q;
+    L.plan = take(q);
+    if (copy_inputs) {
+        L.sent_off = take(4 * (pl.n_sent + 1));
+        L.tokens = take(4 * pl.n_tok + 16);
+    }
+    if (scoring) {
+        L.elems = take(4 * (pl.n_tok * kmax + 3 * pl.n_sent + 16));
+        L.sinfo = take(16 * pl.n_sent);
+    }
+    L.M = take(4 * pl.m_elems + 16);
+    L.codes = take(4 * pl.code_words + 16);
+    L.matches = take(4 * pl.match_words + 16);
+    L.hrow = take(4 * pl.hrow_words + 16);
+    L.counters = take(4 * 16);
+    L.nw = take(4 * (int64_t)pl.R);
+    L.nsel = take(4 * (int64_t)pl.R);
+    if (own_sel) L.sel = take(12 * pl.sel_cap + 16);
+    L.total = o;
+    return L;
+}
+
+void pack_plan(const Plan &pl, const Layout &L, char *dst)
+{
+    std::memcpy(dst + L.o_pairs, pl.pairs.data(), sizeof(PairPlan) * pl.pairs.size());
+    std::memcpy(dst + L.o_sitems, pl.sitems.data(), sizeof(ScoreItem) * pl.sitems.size());
+    std::memcpy(dst + L.o_nitems, pl.nitems.data(), sizeof(NwItem) * pl.nitems.size());
+    std::memcpy(dst + L.o_setgap, pl.set_gap.data(), 4 * pl.set_gap.size());
+    std::memcpy(dst + L.o_setthr, pl.set_thr.data(), 4 * pl.set_thr.size());
+    std::memcpy(dst + L.o_gapval, pl.gap_val.data(), 4 * pl.gap_val.size());
+}
+
+BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_t *sent_off,
+                       const int32_t *tokens, int32_t *sel)
+{
+    BatchDev b{};
+    char *plan = base + L.plan;
+    b.sent_off = sent_off;
+    b.tokens = tokens;
+    b.n_pairs = pl.P;
+    b.pairs = reinterpret_cast<const PairPlan *>(plan + L.o_pairs);
+    b.score_items = reinterpret_cast<const ScoreItem *>(plan + L.o_sitems);
+    b.n_score_items = (int32_t)pl.sitems.size();
+    b.nw_items = reinterpret_cast<const NwItem *>(plan + L.o_nitems);
+    b.n_nw_items = (int32_t)pl.nitems.size();
+    b.set_gap = reinterpret_cast<const int32_t *>(plan + L.o_setgap);
+    b.set_thr = reinterpret_cast<const int32_t *>(plan + L.o_setthr);
+    b.gap_val = reinterpret_cast<const int32_t *>(plan + L.o_gapval);
+    b.elems = reinterpret_cast<uint32_t *>(base + L.elems);
+    b.sinfo = reinterpret_cast<int4 *>(base + L.sinfo);
+    b.M = reinterpret_cast<int32_t *>(base + L.M);
+    b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
+    b.matches = reinterpret_cast<uint32_t *>(base + L.matches);
+    b.hrow = reinterpret_cast<int32_t *>(base + L.hrow);
+    b.counters = reinterpret_cast<int32_t *>(base + L.counters);
+    b.err = b.counters + 8;
+    b.nw_score = reinterpret_cast<int32_t *>(base + L.nw);
+    b.n_sel = reinterpret_cast<int32_t *>(base + L.nsel);
+    b.sel = sel ? sel : reinterpret_cast<int32_t *>(base + L.sel);
+    return b;
+}
+
+const char *device_err_text(int32_t e)
+{
+    switch (e) {
+    case ERR_DUP_KEY: return "duplicate dictionary key";
+    case ERR_BAD_OFFSETS: return "malformed sentence offsets (sent_off must start at 0, not decrease, end at n_tok, and give <= 1024 tokens per sentence)";
+    case ERR_BAD_TOKEN: return "token id outside [0, 2^30)";
+    default: return "device error";
+    }
+}
+
+// ------------------------------------------------------------------ pool
+
+// First-fit allocator over one device region: the serving budget.
+struct Pool {
+    char *base = nullptr;
+    int64_t size = 0;
+    std::map<int64_t, int64_t> free_;   // offset -> bytes
+    int64_t used = 0;
+
+    int64_t alloc(int64_t bytes)
+    {
+        bytes = align_up(bytes, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const int64_t off = it->first, rest = it->second - bytes;
+                free_.erase(it);
+                if (rest > 0) free_[off + bytes] = rest;
+                used += bytes;
+                return off;
+            }
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t bytes)
+    {
+        bytes = align_up(bytes, 256);
+        used -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ objects
+
+struct mine_dict {
+    DevDict d{};
+    void *slots_mem = nullptr;
+    void *trans_mem = nullptr;
+    std::atomic<int64_t> inflight{0};
+};
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<int32_t> src_off, src_tok, tgt_off, tgt_tok;
+    const mine_dict *dict = nullptr;
+    std::vector<Setting> settings;
+    int64_t footprint = 0;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    std::vector<Request> reqs;
+    int64_t pool_off = -1, pool_bytes = 0;
+    HostBuf pin_in, pin_out;
+    Plan plan;
+    Layout lay;
+    int64_t out_nw = 0, out_nsel = 0, out_sel = 0, out_err = 0;
+};
+
+}  // namespace
+
+struct mine_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::mutex api_mu;                 // synchronous calls
+    DevBuf arena;                      // scratch of the synchronous calls
+    HostBuf pin;                       // staging of the synchronous calls
+    std::atomic<int64_t> launches{0};
+    std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // synchronous host-buffer calls
+    // per-kernel timing (CUDA events on the launching stream)
+    std::mutex prof_mu;
+    bool prof_on = false;
+    struct Mark { int kid; cudaEvent_t a, b; };
+    std::vector<Mark> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    double prof_ms[KID_COUNT] = {0};
+    int64_t prof_n[KID_COUNT] = {0};
+    int64_t err_off = -1;              // offset of the last device batch's error word
+
+    // serving
+    mine_config cfg{};
+    Pool pool;
+    void *pool_mem = nullptr;
+    std::vector<std::unique_ptr<Slot>> slots;
+    std::mutex q_mu;
+    std::condition_variable q_cv;      // pending work / stop
+    std::condition_variable r_cv;      // results ready
+    std::deque<Request> pending;
+    std::deque<mine_result> ready;
+    int64_t in_flight_reqs = 0;        // submitted, not yet turned into results
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::thread worker;
+    std::vector<mine_dict *> dicts;
+};
+
+namespace {
+
+int set_device(mine_ctx *ctx)
+{
+    CK(cudaSetDevice(ctx->device));
+    return 0;
+}
+
+cudaEvent_t prof_event(mine_ctx *ctx)
+{
+    if (!ctx->prof_free.empty()) {
+        cudaEvent_t e = ctx->prof_free.back();
+        ctx->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch one kernel through `fn`, bracketed by events when profiling is on.
+template <class F>
+int timed_launch(mine_ctx *ctx, int kid, cudaStream_t st, F fn)
+{
+    std::unique_lock<std::mutex> lk(ctx->prof_mu, std::defer_lock);
+    bool on = false;
+    {
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        on = ctx->prof_on;
+    }
+    if (!on) return fn();
+    cudaEvent_t a, b;
+    {
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        a = prof_event(ctx);
+        b = prof_event(ctx);
+    }
+    cudaEventRecord(a, st);
+    const int n = fn();
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    if (n > 0) {
+        ctx->prof_pending.push_back({kid, a, b});
+    } else {
+        ctx->prof_free.push_back(a);
+        ctx->prof_free.push_back(b);
+    }
+    return n;
+}
+
+// Enqueue the kernels of one batch whose plan is already on the device.
+int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int64_t n_sent,
+                    int64_t n_tok, bool scoring, cudaStream_t st)
+{
+    int n = 0;
+    CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
+    if (scoring) {
+        n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
+        n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(b, dict->d, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(b, dict->d, ctx->num_sms, st); });
+    }
+    n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
+    CK(cudaGetLastError());
+    ctx->launches += n;
+    return 0;
+}
+
+int64_t request_footprint(const Plan &pl, int32_t kmax)
+{
+    return make_layout(pl, kmax, true, true, true).total;
+}
+
+}  // namespace
+
+static void serving_loop(mine_ctx *ctx);
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *mine_last_error(void) { return g_err.c_str(); }
+
+int64_t mine_launch_count(mine_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+int mine_open(const mine_config *cfg, mine_ctx **out)
+{
+    if (!out) return fail(MINE_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::unique_ptr<mine_ctx> ctx(new mine_ctx());
+    mine_config c{};
+    if (cfg) c = *cfg;
+    else c.device = -1;
+    if (c.device_budget_bytes <= 0) c.device_budget_bytes = int64_t(8) << 30;
+    if (c.max_inflight <= 0) c.max_inflight = 3;
+    if (c.max_batch_pairs <= 0) c.max_batch_pairs = 4096;
+    if (c.batch_window_us <= 0) c.batch_window_us = 200;
+    ctx->cfg = c;
+    if (c.device < 0) {
+        CK(cudaGetDevice(&ctx->device));
+    } else {
+        ctx->device = c.device;
+    }
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    CK(cudaMalloc(&ctx->pool_mem, (size_t)c.device_budget_bytes));
+    ctx->pool.base = static_cast<char *>(ctx->pool_mem);
+    ctx->pool.size = c.device_budget_bytes;
+    ctx->pool.free_[0] = c.device_budget_bytes;
+    for (int k = 0; k < c.max_inflight; ++k) {
+        std::unique_ptr<Slot> s(new Slot());
+        CK(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+        ctx->slots.push_back(std::move(s));
+    }
+    mine_ctx *raw = ctx.release();
+    raw->worker = std::thread(serving_loop, raw);
+    *out = raw;
+    return MINE_OK;
+}
+
+int mine_close(mine_ctx *ctx)
+{
+    if (!ctx) return MINE_OK;
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        ctx->stop = true;
+    }
+    ctx->q_cv.notify_all();
+    if (ctx->worker.joinable()) ctx->worker.join();
+    cudaSetDevice(ctx->device);
+    for (mine_result &r : ctx->ready) std::free(r.pairs);
+    ctx->ready.clear();
+    for (mine_dict *d : ctx->dicts) {
+        cudaFree(d->slots_mem);
+        cudaFree(d->trans_mem);
+        delete d;
+    }
+    for (auto &s : ctx->slots) {
+        cudaStreamDestroy(s->st);
+        cudaEventDestroy(s->ev);
+    }
+    ctx->slots.clear();
+    for (auto &m : ctx->prof_pending) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
+    cudaFree(ctx->pool_mem);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return MINE_OK;
+}
+
+int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_off,
+                     const int32_t *trans, int32_t n_keys, mine_dict **out)
+{
+    if (!ctx || !out || n_keys < 0 || (n_keys > 0 && (!keys || !trans_off)))
+        return fail(MINE_EINVAL, "null argument or negative key count");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    if (n_keys > 0 && trans_off[0] != 0) return fail(MINE_EINVAL, "trans_off[0] must be 0");
+    int kmax = 1;
+    for (int32_t k = 0; k < n_keys; ++k) {
+        if (keys[k] < 0 || keys[k] > MINE_MAX_TOKEN_ID) return fail(MINE_EINVAL, "key outside [0, 2^30)");
+        const int32_t c = trans_off[k + 1] - trans_off[k];
+        if (c < 0 || c > MINE_MAX_TRANS) return fail(MINE_EINVAL, "translation count outside [0, 32]");
+        kmax = std::max(kmax, (int)c);
+    }
+    const int64_t n_trans = n_keys > 0 ? trans_off[n_keys] : 0;
+    if (n_trans >= (int64_t(1) << 26)) return fail(MINE_EINVAL, "more than 2^26 translations");
+    if (n_trans > 0 && !trans) return fail(MINE_EINVAL, "trans is NULL");
+    for (int64_t k = 0; k < n_trans; ++k)
+        if (trans[k] < 0 || trans[k] > MINE_MAX_TOKEN_ID) return fail(MINE_EINVAL, "translation outside [0, 2^30)");
+    std::unique_ptr<mine_dict> d(new mine_dict());
+    d->d.log2 = std::max(4, ceil_log2_host(2 * (int64_t)n_keys));
+    d->d.kmax = kmax;
+    d->d.n_trans = n_trans;
+    const size_t slots_bytes = sizeof(int2) << d->d.log2;
+    CK(cudaMalloc(&d->slots_mem, slots_bytes));
+    CK(cudaMalloc(&d->trans_mem, 4 * (size_t)std::max<int64_t>(n_trans, 1)));
+    d->d.slots = static_cast<int2 *>(d->slots_mem);
+    d->d.trans = static_cast<int32_t *>(d->trans_mem);
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(d->slots_mem, 0xff, slots_bytes, st));
+    if (n_trans > 0) CK(cudaMemcpyAsync(d->trans_mem, trans, 4 * n_trans, cudaMemcpyHostToDevice, st));
+    if (n_keys > 0) {
+        void *tmp = nullptr;
+        const size_t kb = 4 * (size_t)n_keys, ob = 4 * ((size_t)n_keys + 1);
+        CK(cudaMalloc(&tmp, kb + ob + 16));
+        int32_t *dk = static_cast<int32_t *>(tmp);
+        int32_t *doff = dk + n_keys;
+        int32_t *derr = doff + n_keys + 1;
+        CK(cudaMemcpyAsync(dk, keys, kb, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(doff, trans_off, ob, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(derr, 0, 4, st));
+        ctx->launches += timed_launch(ctx, KID_DICT, st, [&] { return launch_dict_build(dk, doff, n_keys, d->d, derr, st); });
+        int32_t herr = 0;
+        CK(cudaMemcpyAsync(&herr, derr, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        cudaFree(tmp);
+        if (herr) {
+            cudaFree(d->slots_mem);
+            cudaFree(d->trans_mem);
+            return fail(MINE_EINVAL, device_err_text(herr));
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    mine_dict *raw = d.release();
+    {
+        std::lock_guard<std::mutex> q(ctx->q_mu);
+        ctx->dicts.push_back(raw);
+    }
+    *out = raw;
+    return MINE_OK;
+}
+
+int mine_dict_destroy(mine_ctx *ctx, mine_dict *dict)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    std::lock_guard<std::mutex> q(ctx->q_mu);
+    if (dict->inflight.load() > 0) return fail(MINE_EBUSY, "dictionary used by requests in flight");
+    auto it = std::find(ctx->dicts.begin(), ctx->dicts.end(), dict);
+    if (it == ctx->dicts.end()) return fail(MINE_EINVAL, "unknown dictionary");
+    ctx->dicts.erase(it);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(dict->slots_mem);
+    cudaFree(dict->trans_mem);
+    delete dict;
+    return MINE_OK;
+}
+
+int64_t mine_batch_capacity(const int32_t *doc_off, int32_t n_pairs, int32_t n_settings)
+{
+    if (!doc_off || n_pairs < 0 || n_settings < 0) return 0;
+    int64_t cap = 0;
+    for (int32_t p = 0; p < n_pairs; ++p) {
+        const int64_t S = doc_off[2 * p + 1] - doc_off[2 * p];
+        const int64_t T = doc_off[2 * p + 2] - doc_off[2 * p + 1];
+        cap += (int64_t)n_settings * std::max<int64_t>(0, std::min(S, T));
+    }
+    return cap;
+}
+
+static int check_settings(const mine_settings *s)
+{
+    if (!s || s->n < 1 || s->n > 256 || !s->gaps || !s->thresholds)
+        return fail(MINE_EINVAL, "settings must hold 1..256 (gap, threshold) pairs");
+    return 0;
+}
+
+static int check_batch(const mine_batch *b)
+{
+    if (!b || b->n_pairs < 0 || !b->doc_off || b->n_sent < 0 || b->n_tok < 0 ||
+        (b->n_sent > 0 && !b->sent_off) || (b->n_tok > 0 && !b->tokens))
+        return fail(MINE_EINVAL, "malformed batch");
+    if (b->n_tok >= (int64_t(1) << 31) || b->n_sent >= (int64_t(1) << 31))
+        return fail(MINE_EINVAL, "batch larger than 2^31 tokens or sentences");
+    return 0;
+}
+
+int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                   const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
+                   int64_t *sel_off, mine_pair *sel, int64_t sel_cap)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if ((rc = check_settings(settings))) return rc;
+    const int32_t P = batch->n_pairs;
+    const int n = settings->n;
+    if (P > 0 && (!nw_score || !n_sel || !sel_off)) return fail(MINE_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    std::vector<Setting> set(n);
+    for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
+    Plan pl;
+    rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true);
+    if (rc) return rc;
+    pl.n_tok = batch->n_tok;
+    sel_off[0] = 0;
+    if (P == 0) return MINE_OK;
+    const Layout L = make_layout(pl, dict->d.kmax, true, true, true);
+    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
+    const int64_t out_bytes = 8 * (int64_t)pl.R + 12 * pl.sel_cap + 64;
+    if ((rc = ensure_host(ctx->pin, L.plan_bytes + out_bytes))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr);
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return rc;
+    char *ho = hp + align_up(L.plan_bytes, 64);
+    int32_t *h_nw = reinterpret_cast<int32_t *>(ho);
+    int32_t *h_ns = h_nw + pl.R;
+    int32_t *h_err = h_ns + pl.R;
+    int32_t *h_sel = h_err + 4;
+    CK(cudaMemcpyAsync(h_nw, b.nw_score, 4 * pl.R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_ns, b.n_sel, 4 * pl.R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_sel, b.sel, 12 * pl.sel_cap, cudaMemcpyDeviceToHost, st));
+    ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
+    ctx->d2h_bytes += 8 * (int64_t)pl.R + 4 + 12 * pl.sel_cap;
+    CK(cudaStreamSynchronize(st));
+    if (*h_err) return fail(MINE_EINVAL, device_err_text(*h_err));
+    int64_t tot = 0;
+    for (int32_t r = 0; r < pl.R; ++r) tot += h_ns[r];
+    if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
+    int64_t o = 0;
+    for (int32_t p = 0; p < P; ++p) {
+        const PairPlan &pp = pl.pairs[p];
+        const int64_t cap = std::min(pp.S, pp.T);
+        for (int k = 0; k < n; ++k) {
+            const int64_t r = (int64_t)p * n + k;
+            nw_score[r] = h_nw[r];
+            n_sel[r] = h_ns[r];
+            sel_off[r] = o;
+            std::memcpy(sel + o, h_sel + 3 * (pp.sel_base + k * cap), 12 * (size_t)h_ns[r]);
+            o += h_ns[r];
+        }
+    }
+    sel_off[(int64_t)P * n] = o;
+    return MINE_OK;
+}
+
+int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                          const int32_t *doc_off_host, const mine_settings *settings,
+                          mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
+                          void *stream)
+{
+    if (!ctx || !dict || !doc_off_host) return fail(MINE_EINVAL, "null argument");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if ((rc = check_settings(settings))) return rc;
+    const int32_t P = batch->n_pairs;
+    const int n = settings->n;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    std::vector<Setting> set(n);
+    for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
+    Plan pl;
+    rc = build_plan(pl, P, doc_off_host, batch->n_sent,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true);
+    if (rc) return rc;
+    pl.n_tok = batch->n_tok;
+    if (P == 0) return MINE_OK;
+    if (sel_cap < pl.sel_cap || !sel || !nw_score || !n_sel)
+        return fail(MINE_EINVAL, "sel_cap below mine_batch_capacity() or null output");
+    const Layout L = make_layout(pl, dict->d.kmax, false, false, true);
+    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
+    if ((rc = ensure_host(ctx->pin, L.plan_bytes + 64))) return rc;
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    // the staging buffer may still feed the previous call's copy
+    CK(cudaStreamSynchronize(st));
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    BatchDev b = make_batchdev(pl, L, base, batch->sent_off, batch->tokens,
+                               reinterpret_cast<int32_t *>(sel));
+    b.nw_score = nw_score;
+    b.n_sel = n_sel;
+    ctx->err_off = L.counters + 4 * 8;
+    return enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st);
+}
+
+int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mine_q16 gap,
+                      mine_q16 threshold, mine_pair *out, int32_t *n_out, mine_q16 *nw_score)
+{
+    if (!ctx || !n_out || !nw_score || S < 0 || T < 0 || S > MINE_MAX_SENTENCES ||
+        T > MINE_MAX_SENTENCES || (S > 0 && T > 0 && !M))
+        return fail(MINE_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    int64_t maxabs = 0;
+    for (int64_t k = 0; k < (int64_t)S * T; ++k)
+        maxabs = std::max<int64_t>(maxabs, M[k] < 0 ? -(int64_t)M[k] : (int64_t)M[k]);
+    const int32_t doc_off[3] = {0, S, S + T};
+    const Setting set(gap, threshold);
+    Plan pl;
+    rc = build_plan(pl, 1, doc_off, (int64_t)S + T,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, maxabs, false);
+    if (rc) return rc;
+    if (std::min(S, T) > 0 && !out) return fail(MINE_EINVAL, "out is NULL");
+    const Layout L = make_layout(pl, 1, false, true, false);
+    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
+    const int64_t out_bytes = 8 + 12 * pl.sel_cap + 64;
+    if ((rc = ensure_host(ctx->pin, L.plan_bytes + out_bytes))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr);
+    if (S > 0 && T > 0) {
+        const int Tp = (T + 3) & ~3;
+        CK(cudaMemcpy2DAsync(b.M, 4 * (size_t)Tp, M, 4 * (size_t)T, 4 * (size_t)T, S,
+                             cudaMemcpyHostToDevice, st));
+    }
+    if ((rc = enqueue_kernels(ctx, b, nullptr, 0, 0, false, st))) return rc;
+    char *ho = hp + align_up(L.plan_bytes, 64);
+    int32_t *h = reinterpret_cast<int32_t *>(ho);
+    CK(cudaMemcpyAsync(h, b.nw_score, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h + 1, b.n_sel, 4, cudaMemcpyDeviceToHost, st));
+    if (pl.sel_cap > 0)
+        CK(cudaMemcpyAsync(h + 2, b.sel, 12 * pl.sel_cap, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *nw_score = h[0];
+    *n_out = h[1];
+    if (h[1] > 0) std::memcpy(out, h + 2, 12 * (size_t)h[1]);
+    return MINE_OK;
+}
+
+int mine_check(mine_ctx *ctx)
+{
+    if (!ctx) return fail(MINE_EINVAL, "null context");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    if (ctx->err_off >= 0 && ctx->arena.p) {
+        int32_t e = 0;
+        CK(cudaMemcpy(&e, static_cast<char *>(ctx->arena.p) + ctx->err_off, 4, cudaMemcpyDeviceToHost));
+        if (e) return fail(MINE_EINVAL, device_err_text(e));
+    }
+    return MINE_OK;
+}
+
+int mine_io_bytes(mine_ctx *ctx, int64_t *h2d, int64_t *d2h)
+{
+    if (!ctx || !h2d || !d2h) return fail(MINE_EINVAL, "null argument");
+    *h2d = ctx->h2d_bytes.load();
+    *d2h = ctx->d2h_bytes.load();
+    return MINE_OK;
+}
+
+int mine_profile(mine_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return fail(MINE_EINVAL, "null context");
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    ctx->prof_on = enable != 0;
+    return MINE_OK;
+}
+
+int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n)
+{
+    if (!ctx || n < 0 || (n > 0 && (!ms || !launches))) return fail(MINE_EINVAL, "bad argument");
+    std::vector<mine_ctx::Mark> marks;
+    {
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        marks.swap(ctx->prof_pending);
+    }
+    cudaSetDevice(ctx->device);
+    for (auto &m : marks) {
+        CK(cudaEventSynchronize(m.b));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, m.a, m.b));
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        ctx->prof_ms[m.kid] += t;
+        ctx->prof_n[m.kid] += 1;
+        ctx->prof_free.push_back(m.a);
+        ctx->prof_free.push_back(m.b);
+    }
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    for (int k = 0; k < n && k < KID_COUNT; ++k) {
+        ms[k] = ctx->prof_ms[k];
+        launches[k] = ctx->prof_n[k];
+    }
+    for (int k = 0; k < KID_COUNT; ++k) {
+        ctx->prof_ms[k] = 0;
+        ctx->prof_n[k] = 0;
+    }
+    return KID_COUNT;
+}
+
+const char *mine_kernel_name(int32_t id)
+{
+    static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score", "k_align"};
+    return (id >= 0 && id < KID_COUNT) ? names[id] : "";
+}
+
+// ------------------------------------------------------------------ serving
+
+static int copy_doc(const mine_doc *d, std::vector<int32_t> &off, std::vector<int32_t> &tok)
+{
+    if (!d || d->n_sent < 0 || d->n_sent > MINE_MAX_SENTENCES || (d->n_sent > 0 && !d->sent_off))
+        return fail(MINE_EINVAL, "malformed document");
+    if (d->n_sent == 0) {
+        off.assign(1, 0);
+        tok.clear();
+        return 0;
+    }
+    if (d->sent_off[0] != 0) return fail(MINE_EINVAL, "sent_off[0] must be 0");
+    for (int32_t k = 0; k < d->n_sent; ++k) {
+        const int64_t L = (int64_t)d->sent_off[k + 1] - d->sent_off[k];
+        if (L < 0 || L > MINE_MAX_SENT_TOKENS) return fail(MINE_EINVAL, "sentence length outside [0, 1024]");
+    }
+    const int64_t nt = d->sent_off[d->n_sent];
+    if (nt > 0 && !d->tokens) return fail(MINE_EINVAL, "tokens is NULL");
+    for (int64_t k = 0; k < nt; ++k)
+        if (d->tokens[k] < 0 || d->tokens[k] > MINE_MAX_TOKEN_ID) return fail(MINE_EINVAL, "token outside [0, 2^30)");
+    off.assign(d->sent_off, d->sent_off + d->n_sent + 1);
+    tok.assign(d->tokens, d->tokens + nt);
+    return 0;
+}
+
+int mine_submit_sweep(mine_ctx *ctx, const mine_doc *src, const mine_doc *tgt,
+                      const mine_dict *dict, int32_t n, const mine_q16 *gaps,
+                      const mine_q16 *thresholds, uint64_t *ticket)
+{
+    if (!ctx || !dict || !ticket || n < 1 || n > 256 || !gaps || !thresholds)
+        return fail(MINE_EINVAL, "bad argument");
+    Request rq;
+    int rc = copy_doc(src, rq.src_off, rq.src_tok);
+    if (rc) return rc;
+    if ((rc = copy_doc(tgt, rq.tgt_off, rq.tgt_tok))) return rc;
+    rq.dict = dict;
+    rq.settings.resize(n);
+    for (int k = 0; k < n; ++k) rq.settings[k] = Setting(gaps[k], thresholds[k]);
+    // footprint of the request alone (also validates gap/threshold/overflow)
+    const int32_t S = (int32_t)rq.src_off.size() - 1, T = (int32_t)rq.tgt_off.size() - 1;
+    const int32_t doc_off[3] = {0, S, S + T};
+    Plan pl;
+    rc = build_plan(pl, 1, doc_off, (int64_t)S + T,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = rq.settings.data(); cnt = n; },
+                    65536, true);
+    if (rc) return rc;
+    pl.n_tok = (int64_t)rq.src_tok.size() + (int64_t)rq.tgt_tok.size();
+    rq.footprint = request_footprint(pl, dict->d.kmax);
+    if (rq.footprint > ctx->pool.size) return fail(MINE_ENOMEM, "request alone exceeds the device budget");
+    rq.t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        if (ctx->stop) return fail(MINE_EINVAL, "context is closing");
+        rq.ticket = ctx->next_ticket++;
+        *ticket = rq.ticket;
+        const_cast<mine_dict *>(dict)->inflight++;
+        ctx->in_flight_reqs++;
+        ctx->pending.push_back(std::move(rq));
+    }
+    ctx->q_cv.notify_all();
+    return MINE_OK;
+}
+
+int mine_submit(mine_ctx *ctx, const mine_doc *src, const mine_doc *tgt, const mine_dict *dict,
+                mine_q16 gap, mine_q16 threshold, uint64_t *ticket)
+{
+    return mine_submit_sweep(ctx, src, tgt, dict, 1, &gap, &threshold, ticket);
+}
+
+int mine_poll(mine_ctx *ctx, mine_result *out, int32_t max_out, int32_t timeout_us)
+{
+    if (!ctx || (max_out > 0 && !out) || max_out < 0) return fail(MINE_EINVAL, "bad argument");
+    std::unique_lock<std::mutex> lk(ctx->q_mu);
+    auto have = [&] { return !ctx->ready.empty() || (timeout_us < 0 && ctx->in_flight_reqs == 0); };
+    if (timeout_us > 0) {
+        ctx->r_cv.wait_for(lk, std::chrono::microseconds(timeout_us), have);
+    } else if (timeout_us < 0) {
+        ctx->r_cv.wait(lk, have);
+    }
+    int got = 0;
+    while (got < max_out && !ctx->ready.empty()) {
+        out[got++] = ctx->ready.front();
+        ctx->ready.pop_front();
+    }
+    return got;
+}
+
+void mine_result_free(mine_ctx *, mine_result *result)
+{
+    if (!result) return;
+    std::free(result->pairs);
+    result->pairs = nullptr;
+    result->n_pairs = 0;
+}
+
+}  // extern "C"
+
+// The serving engine.  Batches are formed from the front of the pending
+// queue (same dictionary, at most max_batch_pairs, total footprint that fits
+// the free part of the budget pool), launched on a free slot's stream, and
+// harvested when their event completes.  While batches run, new arrivals
+// wait at most batch_window_us before they form the next batch, which runs
+// concurrently on another slot.
+namespace {
+
+void finish_slot(mine_ctx *ctx, Slot &s)
+{
+    const char *ho = static_cast<const char *>(s.pin_out.p);
+    const int32_t *h_nw = reinterpret_cast<const int32_t *>(ho + s.out_nw);
+    const int32_t *h_ns = reinterpret_cast<const int32_t *>(ho + s.out_nsel);
+    const int32_t *h_sel = reinterpret_cast<const int32_t *>(ho + s.out_sel);
+    const int32_t dev_err = *reinterpret_cast<const int32_t *>(ho + s.out_err);
+    const cudaError_t ce = cudaEventQuery(s.ev);
+    const auto now = std::chrono::steady_clock::now();
+    std::vector<mine_result> res;
+    for (size_t p = 0; p < s.reqs.size(); ++p) {
+        const Request &rq = s.reqs[p];
+        const PairPlan &pp = s.plan.pairs[p];
+        const int64_t cap = std::min(pp.S, pp.T);
+        for (int k = 0; k < pp.nset; ++k) {
+            mine_result r{};
+            r.ticket = rq.ticket;
+            r.setting = k;
+            r.latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(now - rq.t_submit).count();
+            if (ce != cudaSuccess) {
+                r.status = MINE_ECUDA;
+            } else if (dev_err) {
+                r.status = MINE_EINVAL;
+            } else {
+                const int64_t row = pp.set0 + k;
+                r.nw_score = h_nw[row];
+                r.n_pairs = h_ns[row];
+                if (r.n_pairs > 0) {
+                    r.pairs = static_cast<mine_pair *>(std::malloc(sizeof(mine_pair) * r.n_pairs));
+                    std::memcpy(r.pairs, h_sel + 3 * (pp.sel_base + k * cap), 12 * (size_t)r.n_pairs);
+                }
+            }
+            res.push_back(r);
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        for (auto &r : res) ctx->ready.push_back(r);
+        for (auto &rq : s.reqs) {
+            const_cast<mine_dict *>(rq.dict)->inflight--;
+            ctx->in_flight_reqs--;
+        }
+        ctx->pool.release(s.pool_off, s.pool_bytes);
+    }
+    s.reqs.clear();
+    s.busy = false;
+    ctx->r_cv.notify_all();
+}
+
+// Pack requests into one batch and launch it on slot s.  Returns 0 or an error.
+int launch_slot(mine_ctx *ctx, Slot &s)
+{
+    const int P = (int)s.reqs.size();
+    std::vector<int32_t> doc_off(2 * P + 1, 0);
+    int64_t n_sent = 0, n_tok = 0;
+    for (int p = 0; p < P; ++p) {
+        const Request &rq = s.reqs[p];
+        doc_off[2 * p + 1] = doc_off[2 * p] + (int32_t)rq.src_off.size() - 1;
+        doc_off[2 * p + 2] = doc_off[2 * p + 1] + (int32_t)rq.tgt_off.size() - 1;
+        n_tok += (int64_t)rq.src_tok.size() + (int64_t)rq.tgt_tok.size();
+    }
+    n_sent = doc_off[2 * P];
+    const mine_dict *dict = s.reqs[0].dict;
+    int rc = build_plan(s.plan, P, doc_off.data(), n_sent,
+                        [&](int32_t p, const Setting *&set, int &cnt) {
+                            set = s.reqs[p].settings.data();
+                            cnt = (int)s.reqs[p].settings.size();
+                        },
+                        65536, true);
+    if (rc) return rc;
+    s.plan.n_tok = n_tok;
+    s.lay = make_layout(s.plan, dict->d.kmax, true, true, true);
+    const Layout &L = s.lay;
+    if (L.total > s.pool_bytes) return fail(MINE_ENOMEM, "batch layout exceeds its budget region");
+    // host staging: plan | sent_off | tokens ; outputs: nw | nsel | err | sel
+    const int64_t in_bytes = align_up(L.plan_bytes, 64) + 4 * (n_sent + 1) + 4 * n_tok + 64;
+    if ((rc = ensure_host(s.pin_in, in_bytes))) return rc;
+    s.out_nw = 0;
+    s.out_nsel = align_up(4 * (int64_t)s.plan.R, 16);
+    s.out_err = s.out_nsel + align_up(4 * (int64_t)s.plan.R, 16);
+    s.out_sel = s.out_err + 16;
+    if ((rc = ensure_host(s.pin_out, s.out_sel + 12 * s.plan.sel_cap + 16))) return rc;
+    char *hi = static_cast<char *>(s.pin_in.p);
+    pack_plan(s.plan, L, hi);
+    int32_t *h_sent = reinterpret_cast<int32_t *>(hi + align_up(L.plan_bytes, 64));
+    int32_t *h_tok = h_sent + n_sent + 1;
+    int64_t so = 0, to = 0;
+    h_sent[0] = 0;
+    for (int p = 0; p < P; ++p) {
+        const Request &rq = s.reqs[p];
+        for (int side = 0; side < 2; ++side) {
+            const std::vector<int32_t> &off = side ? rq.tgt_off : rq.src_off;
+            const std::vector<int32_t> &tk = side ? rq.tgt_tok : rq.src_tok;
+            const int32_t base = (int32_t)to;
+            for (size_t k = 1; k < off.size(); ++k) h_sent[++so] = base + off[k];
+            std::memcpy(h_tok + to, tk.data(), 4 * tk.size());
+            to += (int64_t)tk.size();
+        }
+    }
+    char *base = ctx->pool.base + s.pool_off;
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    CK(cudaMemcpyAsync(base + L.plan, hi, L.plan_bytes, cudaMemcpyHostToDevice, s.st));
+    CK(cudaMemcpyAsync(d_sent, h_sent, 4 * (n_sent + 1), cudaMemcpyHostToDevice, s.st));
+    if (n_tok > 0) CK(cudaMemcpyAsync(d_tok, h_tok, 4 * n_tok, cudaMemcpyHostToDevice, s.st));
+    BatchDev b = make_batchdev(s.plan, L, base, d_sent, d_tok, nullptr);
+    if ((rc = enqueue_kernels(ctx, b, dict, n_sent, n_tok, true, s.st))) return rc;
+    char *ho = static_cast<char *>(s.pin_out.p);
+    CK(cudaMemcpyAsync(ho + s.out_nw, b.nw_score, 4 * s.plan.R, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(ho + s.out_nsel, b.n_sel, 4 * s.plan.R, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(ho + s.out_err, b.err, 4, cudaMemcpyDeviceToHost, s.st));
+    if (s.plan.sel_cap > 0)
+        CK(cudaMemcpyAsync(ho + s.out_sel, b.sel, 12 * s.plan.sel_cap, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaEventRecord(s.ev, s.st));
+    s.busy = true;
+    return 0;
+}
+
+}  // namespace
+
+static void serving_loop(mine_ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    const auto window = std::chrono::microseconds(ctx->cfg.batch_window_us);
+    for (;;) {
+        // harvest finished batches
+        int nbusy = 0;
+        Slot *oldest = nullptr;
+        for (auto &sp : ctx->slots) {
+            Slot &s = *sp;
+            if (s.busy && cudaEventQuery(s.ev) != cudaErrorNotReady) finish_slot(ctx, s);
+            if (s.busy) {
+                ++nbusy;
+                if (!oldest) oldest = &s;
+            }
+        }
+        Slot *free_slot = nullptr;
+        for (auto &sp : ctx->slots)
+            if (!sp->busy) {
+                free_slot = sp.get();
+                break;
+            }
+        std::unique_lock<std::mutex> lk(ctx->q_mu);
+        if (ctx->pending.empty()) {
+            if (ctx->stop && nbusy == 0) return;
+            if (nbusy > 0) {   // poll the running batches, wake early on new work
+                ctx->q_cv.wait_for(lk, std::chrono::microseconds(20),
+                                   [&] { return ctx->stop || !ctx->pending.empty(); });
+                continue;
+            }
+            ctx->q_cv.wait(lk, [&] { return ctx->stop || !ctx->pending.empty(); });
+            continue;
+        }
+        if (!free_slot) {
+            lk.unlock();
+            cudaEventSynchronize(oldest->ev);
+            continue;
+        }
+        // let a small batch grow while the device is busy
+        if (nbusy > 0 && (int)ctx->pending.size() < ctx->cfg.max_batch_pairs && !ctx->stop) {
+            const auto age = std::chrono::steady_clock::now() - ctx->pending.front().t_submit;
+            if (age < window) {
+                ctx->q_cv.wait_for(lk, window - age, [&] {
+                    return ctx->stop || (int)ctx->pending.size() >= ctx->cfg.max_batch_pairs;
+                });
+                continue;
+            }
+        }
+        // form the batch: same dictionary, fits the free budget
+        Slot &s = *free_slot;
+        int64_t bytes = 0;
+        const mine_dict *dict = ctx->pending.front().dict;
+        std::vector<Request> take;
+        while (!ctx->pending.empty() && (int)take.size() < ctx->cfg.max_batch_pairs &&
+               ctx->pending.front().dict == dict) {
+            const int64_t f = ctx->pending.front().footprint;
+            if (bytes + f > ctx->pool.size - ctx->pool.used) break;
+            bytes += f;
+            take.push_back(std::move(ctx->pending.front()));
+            ctx->pending.pop_front();
+        }
+        if (take.empty()) {   // budget held by running batches
+            lk.unlock();
+            if (oldest) cudaEventSynchronize(oldest->ev);
+            continue;
+        }
+        // the exact layout of the merged batch is a little smaller than the sum
+        const int64_t off = ctx->pool.alloc(bytes + (int64_t)take.size() * 4096);
+        if (off < 0) {
+            for (auto it = take.rbegin(); it != take.rend(); ++it) ctx->pending.push_front(std::move(*it));
+            lk.unlock();
+            if (oldest) cudaEventSynchronize(oldest->ev);
+            else std::this_thread::sleep_for(std::chrono::microseconds(50));
+            continue;
+        }
+        lk.unlock();
+        s.reqs = std::move(take);
+        s.pool_off = off;
+        s.pool_bytes = bytes + (int64_t)s.reqs.size() * 4096;
+        int rc = launch_slot(ctx, s);
+        if (rc) {
+            // report the failure on every request of the batch
+            std::lock_guard<std::mutex> q(ctx->q_mu);
+            for (auto &rq : s.reqs) {
+                for (size_t k = 0; k < rq.settings.size(); ++k) {
+                    mine_result r{};
+                    r.ticket = rq.ticket;
+                    r.setting = (int32_t)k;
+                    r.status = rc;
+                    ctx->ready.push_back(r);
+                }
+                const_cast<mine_dict *>(rq.dict)->inflight--;
+                ctx->in_flight_reqs--;
+            }
+            ctx->pool.release(s.pool_off, s.pool_bytes);
+            s.reqs.clear();
+            s.busy = false;
+            ctx->r_cv.notify_all();
+        }
+    }
+}

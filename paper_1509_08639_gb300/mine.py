@@ -1,0 +1,292 @@
+"""Thin Python binding of the miner's C ABI (include/mine.h).
+
+Argument marshalling only: every step of the mining path runs in the CUDA
+library.  Loading fails loudly when the compiled library is missing; there is
+no CPU fallback.  PyTorch is used only to hand device buffers and streams to
+the ``*_device`` entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+MINE_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EAGAIN", -4: "EOVERFLOW", -5: "ETIMEDOUT",
+          -6: "EBUSY", -7: "ECUDA"}
+
+
+class MineError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"mine error {ERRORS.get(code, code)}: {what}")
+
+
+class Doc(ctypes.Structure):
+    _fields_ = [("sent_off", ctypes.c_void_p), ("tokens", ctypes.c_void_p),
+                ("n_sent", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
+                ("batch_window_us", ctypes.c_int32)]
+
+
+class Pair(ctypes.Structure):
+    _fields_ = [("src_sent", ctypes.c_int32), ("tgt_sent", ctypes.c_int32),
+                ("score", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("setting", ctypes.c_int32), ("nw_score", ctypes.c_int32),
+                ("n_pairs", ctypes.c_int32), ("pairs", ctypes.POINTER(Pair)),
+                ("latency_ns", ctypes.c_int64)]
+
+
+class BatchC(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int32), ("n_sent", ctypes.c_int64),
+                ("n_tok", ctypes.c_int64), ("doc_off", ctypes.c_void_p),
+                ("sent_off", ctypes.c_void_p), ("tokens", ctypes.c_void_p)]
+
+
+class SettingsC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("gaps", ctypes.c_void_p),
+                ("thresholds", ctypes.c_void_p)]
+
+
+# every function of include/mine.h with its ctypes signature
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_L = ctypes.c_int64
+SIGNATURES = {
+    "mine_last_error": (ctypes.c_char_p, []),
+    "mine_open": (_I, [ctypes.POINTER(Config), ctypes.POINTER(_P)]),
+    "mine_close": (_I, [_P]),
+    "mine_dict_create": (_I, [_P, _P, _P, _P, _I, ctypes.POINTER(_P)]),
+    "mine_dict_destroy": (_I, [_P, _P]),
+    "mine_submit": (_I, [_P, ctypes.POINTER(Doc), ctypes.POINTER(Doc), _P, _I, _I,
+                         ctypes.POINTER(ctypes.c_uint64)]),
+    "mine_submit_sweep": (_I, [_P, ctypes.POINTER(Doc), ctypes.POINTER(Doc), _P, _I, _P, _P,
+                               ctypes.POINTER(ctypes.c_uint64)]),
+    "mine_poll": (_I, [_P, ctypes.POINTER(Result), _I, _I]),
+    "mine_result_free": (None, [_P, ctypes.POINTER(Result)]),
+    "mine_align_matrix": (_I, [_P, _P, _I, _I, _I, _I, _P, ctypes.POINTER(_I),
+                               ctypes.POINTER(_I)]),
+    "mine_batch_capacity": (_L, [_P, _I, _I]),
+    "mine_run_batch": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P, _P,
+                            _P, _P, _L]),
+    "mine_run_batch_device": (_I, [_P, _P, ctypes.POINTER(BatchC), _P,
+                                   ctypes.POINTER(SettingsC), _P, _P, _P, _L, _P]),
+    "mine_check": (_I, [_P]),
+    "mine_launch_count": (_L, [_P]),
+    "mine_io_bytes": (_I, [_P, ctypes.POINTER(_L), ctypes.POINTER(_L)]),
+    "mine_profile": (_I, [_P, _I]),
+    "mine_profile_read": (_I, [_P, _P, _P, _I]),
+    "mine_kernel_name": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmine.so (building it first if allowed).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"the miner's CUDA library is not built: {path}")
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else ctypes.c_void_p(0)
+
+
+def _c32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _check(rc, L=None):
+    if rc < 0:
+        L = L or load()
+        raise MineError(rc, L.mine_last_error().decode(errors="replace"))
+    return rc
+
+
+def make_doc(sent_off, tokens):
+    so, tk = _c32(sent_off), _c32(tokens)
+    return Doc(_ptr(so), _ptr(tk), so.shape[0] - 1), (so, tk)
+
+
+class Context:
+    """One miner context on one CUDA device."""
+
+    def __init__(self, budget_bytes: int = 0, max_inflight: int = 0, device: int = -1,
+                 max_batch_pairs: int = 0, batch_window_us: int = 0):
+        self.L = load()
+        cfg = Config(budget_bytes, max_inflight, device, max_batch_pairs, batch_window_us)
+        h = ctypes.c_void_p()
+        _check(self.L.mine_open(ctypes.byref(cfg), ctypes.byref(h)), self.L)
+        self.h = h
+        self._dicts = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mine_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --------------------------------------------------------------- dictionary
+    def dict_create(self, d):
+        keys, off, tr = _c32(d.keys), _c32(d.trans_off), _c32(d.trans)
+        h = ctypes.c_void_p()
+        _check(self.L.mine_dict_create(self.h, _ptr(keys), _ptr(off), _ptr(tr),
+                                       int(keys.shape[0]), ctypes.byref(h)), self.L)
+        self._dicts.append(h)
+        return h
+
+    def dict_destroy(self, h):
+        _check(self.L.mine_dict_destroy(self.h, h), self.L)
+        self._dicts.remove(h)
+
+    # --------------------------------------------------------------- batches
+    def run_batch(self, dict_h, batch, settings):
+        """Host buffers in and out.  Returns results[p][k] = (nw_score, [(i, j, s)])."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        P = (do.shape[0] - 1) // 2
+        n = len(settings)
+        g = _c32([s[0] for s in settings])
+        th = _c32([s[1] for s in settings])
+        bc = BatchC(P, so.shape[0] - 1, tk.shape[0], _ptr(do), _ptr(so), _ptr(tk))
+        sc = SettingsC(n, _ptr(g), _ptr(th))
+        cap = max(int(self.L.mine_batch_capacity(_ptr(do), P, n)), 1)
+        nw = np.zeros(P * n, np.int32)
+        ns = np.zeros(P * n, np.int32)
+        off = np.zeros(P * n + 1, np.int64)
+        sel = np.zeros((cap, 3), np.int32)
+        _check(self.L.mine_run_batch(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc),
+                                     _ptr(nw), _ptr(ns), _ptr(off), _ptr(sel), cap), self.L)
+        return unpack_results(P, n, nw, ns, off, sel)
+
+    def run_batch_raw(self, dict_h, bc, sc, outs):
+        """Host-buffer call with pre-built ctypes structs (benchmark path)."""
+        nw, ns, off, sel, cap = outs
+        return _check(self.L.mine_run_batch(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc),
+                                            _ptr(nw), _ptr(ns), _ptr(off), _ptr(sel), cap),
+                      self.L)
+
+    def run_batch_device(self, dict_h, n_pairs, doc_off_host, sent_off_dev, tokens_dev,
+                         n_sent, n_tok, settings, nw_dev, nsel_dev, sel_dev, sel_cap,
+                         stream=None):
+        """Device buffers (torch tensors or raw pointers) in and out, enqueued on stream."""
+        def dp(x):
+            return ctypes.c_void_p(x if isinstance(x, int) else x.data_ptr())
+        do = _c32(doc_off_host)
+        g = _c32([s[0] for s in settings])
+        th = _c32([s[1] for s in settings])
+        bc = BatchC(n_pairs, n_sent, n_tok, ctypes.c_void_p(0), dp(sent_off_dev), dp(tokens_dev))
+        sc = SettingsC(len(settings), _ptr(g), _ptr(th))
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else
+                             (stream.cuda_stream if stream is not None else 0))
+        return _check(self.L.mine_run_batch_device(self.h, dict_h, ctypes.byref(bc), _ptr(do),
+                                                   ctypes.byref(sc), dp(nw_dev), dp(nsel_dev),
+                                                   dp(sel_dev), int(sel_cap), st), self.L)
+
+    def check(self):
+        return _check(self.L.mine_check(self.h), self.L)
+
+    def launch_count(self) -> int:
+        return int(self.L.mine_launch_count(self.h))
+
+    def io_bytes(self):
+        """(host->device, device->host) bytes moved by run_batch calls so far."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.L.mine_io_bytes(self.h, ctypes.byref(a), ctypes.byref(b)), self.L)
+        return a.value, b.value
+
+    def profile(self, enable: bool = True):
+        _check(self.L.mine_profile(self.h, 1 if enable else 0), self.L)
+
+    def profile_read(self):
+        """{kernel name: (total device ms, timed launches)} since the last read."""
+        ms = np.zeros(16, np.float64)
+        n = np.zeros(16, np.int64)
+        k = _check(self.L.mine_profile_read(self.h, _ptr(ms), _ptr(n), 16), self.L)
+        return {self.L.mine_kernel_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(k)}
+
+    # --------------------------------------------------------------- alignment only
+    def align_matrix(self, M, gap, threshold):
+        M = _c32(M)
+        S, T = M.shape
+        out = (Pair * max(min(S, T), 1))()
+        n = ctypes.c_int32()
+        nw = ctypes.c_int32()
+        _check(self.L.mine_align_matrix(self.h, _ptr(M), S, T, int(gap), int(threshold),
+                                        ctypes.cast(out, ctypes.c_void_p), ctypes.byref(n),
+                                        ctypes.byref(nw)), self.L)
+        return nw.value, [(out[k].src_sent, out[k].tgt_sent, out[k].score) for k in range(n.value)]
+
+    # --------------------------------------------------------------- serving
+    def submit(self, dict_h, src, tgt, settings):
+        (ds, ks), (dt, kt) = make_doc(*src), make_doc(*tgt)
+        t = ctypes.c_uint64()
+        g = _c32([s[0] for s in settings])
+        th = _c32([s[1] for s in settings])
+        _check(self.L.mine_submit_sweep(self.h, ctypes.byref(ds), ctypes.byref(dt), dict_h,
+                                        len(settings), _ptr(g), _ptr(th), ctypes.byref(t)),
+               self.L)
+        return t.value
+
+    def poll(self, max_out=1024, timeout_us=0):
+        """[(ticket, setting, status, nw_score, [(i, j, s)], latency_ns)]"""
+        buf = (Result * max_out)()
+        n = _check(self.L.mine_poll(self.h, buf, max_out, int(timeout_us)), self.L)
+        out = []
+        for k in range(n):
+            r = buf[k]
+            pairs = [(r.pairs[q].src_sent, r.pairs[q].tgt_sent, r.pairs[q].score)
+                     for q in range(r.n_pairs)]
+            out.append((r.ticket, r.setting, r.status, r.nw_score, pairs, r.latency_ns))
+            self.L.mine_result_free(self.h, ctypes.byref(buf[k]))
+        return out
+
+
+def unpack_results(P, n, nw, ns, off, sel):
+    res = []
+    for p in range(P):
+        row = []
+        for k in range(n):
+            r = p * n + k
+            trip = sel[off[r]:off[r] + ns[r]]
+            row.append((int(nw[r]), [tuple(int(v) for v in t) for t in trip]))
+        res.append(row)
+    return res

@@ -1,0 +1,289 @@
+"""CUDA path vs CPU oracle, bit-exact (every value is an integer).
+
+All calls go through the C ABI (libmine.so).  Sizes span several tiles (32
+source rows x 32 target columns per score tile, 32-row alignment stripes,
+16-column direction words) and ragged tails; the full-size batch of 10,000
+lognormal pairs is run in the benchmark's launch configuration and sampled.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1509_08639_gb300 import mine, synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = mine.Context(device=0)
+    yield c
+    c.close()
+
+
+def oracle_results(w, batch=None, settings=None):
+    res, _ = O.mine_batch(O.OracleDict(w.dictionary), batch or w.batch,
+                          settings or w.settings, THREADS)
+    return res
+
+
+def assert_same(got, want, what):
+    assert len(got) == len(want), what
+    bad = [p for p in range(len(got)) if got[p] != want[p]]
+    assert not bad, f"{what}: {len(bad)} pairs differ, first {bad[:8]}: got {got[bad[0]]!r:.300} want {want[bad[0]]!r:.300}"
+
+
+def test_plain_40x45_pair(ctx):
+    w = synth.workload(1)
+    dh = ctx.dict_create(w.dictionary)
+    got = ctx.run_batch(dh, w.batch, w.settings)
+    assert_same(got, oracle_results(w), w.name)
+    assert len(got[0][0][1]) > 0
+
+
+def test_lognormal_batch_subset(ctx):
+    w = synth.workload(2, n_pairs=300)
+    dh = ctx.dict_create(w.dictionary)
+    got = ctx.run_batch(dh, w.batch, w.settings)
+    assert_same(got, oracle_results(w), w.name)
+
+
+def test_full_size_lognormal_batch_sampled(ctx):
+    """The 10,000-pair batch through the device entry point, as bench.py runs it."""
+    torch = pytest.importorskip("torch")
+    w = synth.workload(2)
+    b = w.batch
+    dh = ctx.dict_create(w.dictionary)
+    dev = torch.device("cuda:0")
+    sent = torch.from_numpy(b.sent_off).to(dev)
+    tok = torch.from_numpy(b.tokens).to(dev)
+    P, n = b.n_pairs, len(w.settings)
+    S, T = b.sizes()
+    cap = int(n * np.minimum(S, T).sum())
+    nw = torch.zeros(P * n, dtype=torch.int32, device=dev)
+    ns = torch.zeros(P * n, dtype=torch.int32, device=dev)
+    sel = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx.run_batch_device(dh, P, b.doc_off, sent, tok, int(b.sent_off.shape[0] - 1),
+                         int(b.tokens.shape[0]), w.settings, nw, ns, sel, cap, stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    nw, ns, sel = nw.cpu().numpy(), ns.cpu().numpy(), sel.cpu().numpy().reshape(-1, 3)
+    base = np.zeros(P + 1, np.int64)
+    np.cumsum(n * np.minimum(S, T), out=base[1:])
+    rng = np.random.default_rng(1510)
+    big = np.argsort(-(S * T))[:6]
+    sample = np.unique(np.concatenate([rng.choice(P, 60, replace=False), big]))
+    want = oracle_results(w, b.subset(sample))
+    for q, p in enumerate(sample):
+        got = (int(nw[p]), [tuple(int(v) for v in t) for t in sel[base[p]:base[p] + ns[p]]])
+        assert got == want[q][0], f"pair {p} ({S[p]}x{T[p]})"
+    # properties that hold for every pair of the batch
+    assert (ns >= 0).all() and (ns <= np.minimum(S, T)).all()
+    assert (nw <= 65536 * np.minimum(S, T) - 65536 * np.abs(S - T)).all()
+
+
+def _edge_batch(rng, d, sizes, vocab, lo=5, hi=30, empty_frac=0.0):
+    cdf = synth._zipf_cdf(vocab)
+    S = np.array([s for s, _ in sizes])
+    T = np.array([t for _, t in sizes])
+    b = synth.make_pairs(rng, cdf, d, S, T, np.full(len(sizes), 0.6), lo, hi)
+    if empty_frac:
+        docs = []
+        for dd in range(2 * b.n_pairs):
+            so, tk = b.doc(dd)
+            lens = np.diff(so)
+            keep = rng.random(lens.shape[0]) >= empty_frac
+            new_tok = np.concatenate([tk[so[k]:so[k + 1]] if keep[k] else tk[:0]
+                                      for k in range(lens.shape[0])]) if lens.shape[0] else tk[:0]
+            new_off = np.zeros(lens.shape[0] + 1, np.int64)
+            np.cumsum(np.where(keep, lens, 0), out=new_off[1:])
+            docs.append((new_off.astype(np.int32), new_tok))
+        b = synth.pack_docs(docs)
+    return b
+
+
+def test_tile_boundaries_and_degenerate_shapes(ctx):
+    rng = np.random.default_rng(77)
+    d = synth.make_dictionary(rng, 5000, 3)
+    edges = [0, 1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129]
+    sizes = [(s, t) for s in edges for t in edges]
+    w = synth.Workload("edges", _edge_batch(rng, d, sizes, 5000), d, [-65536], [32768],
+                       [(-65536, 32768), (-20000, 0), (0, 65536), (-131072, 50000)])
+    dh = ctx.dict_create(d)
+    got = ctx.run_batch(dh, w.batch, w.settings)
+    assert_same(got, oracle_results(w), "tile edges")
+
+
+def test_empty_sentences_and_long_sentences(ctx):
+    rng = np.random.default_rng(78)
+    d = synth.make_dictionary(rng, 3000, 4)
+    sizes = [(40, 45), (3, 100), (100, 3), (50, 50), (1, 1), (7, 0), (0, 7)]
+    b = _edge_batch(rng, d, sizes, 3000, empty_frac=0.3)
+    w = synth.Workload("empties", b, d, [], [], [(-65536, 32768), (-30000, 10000)])
+    dh = ctx.dict_create(d)
+    assert_same(ctx.run_batch(dh, b, w.settings), oracle_results(w), "empty sentences")
+    # sentences up to the 1024-token limit (columns no longer fit 32 per block)
+    b2 = _edge_batch(rng, d, [(20, 70), (70, 20), (33, 33)], 3000, lo=200, hi=1024)
+    w2 = synth.Workload("long", b2, d, [], [], [(-65536, 32768)])
+    assert_same(ctx.run_batch(dh, b2, w2.settings), oracle_results(w2), "long sentences")
+
+
+def test_unusual_dictionaries(ctx):
+    rng = np.random.default_rng(79)
+    # up to 32 translations per key, many shared translations, unknown tokens
+    V = 400
+    m = {}
+    for key in range(0, V, 2):          # odd IDs have no entry
+        k = int(rng.integers(1, 33))
+        m[key] = list(rng.choice(60, size=min(k, 60), replace=False))
+    d = synth.dictionary_from_map(m)
+    cdf = synth._zipf_cdf(V)
+    b = synth.make_pairs(rng, cdf, synth.make_dictionary(rng, V, 2),
+                         np.array([30, 64, 5]), np.array([41, 64, 90]), np.full(3, 0.5), 1, 60)
+    w = synth.Workload("dict", b, d, [], [], [(-65536, 32768), (-8192, 40000)])
+    dh = ctx.dict_create(d)
+    assert_same(ctx.run_batch(dh, b, w.settings), oracle_results(w), "dense dictionary")
+    # keys given in arbitrary order
+    perm = rng.permutation(d.n_keys)
+    cnt = np.diff(d.trans_off)
+    off = np.zeros(d.n_keys + 1, np.int64)
+    np.cumsum(cnt[perm], out=off[1:])
+    tr = np.concatenate([d.trans[d.trans_off[k]:d.trans_off[k + 1]] for k in perm])
+    d2 = synth.Dictionary(d.keys[perm].copy(), off.astype(np.int32), tr.astype(np.int32))
+    dh2 = ctx.dict_create(d2)
+    assert_same(ctx.run_batch(dh2, b, w.settings), oracle_results(w), "permuted keys")
+
+
+def test_align_matrix_any_sign(ctx):
+    rng = np.random.default_rng(80)
+    for S, T in [(1, 1), (1, 57), (57, 1), (31, 33), (64, 65), (100, 37), (129, 128), (300, 310)]:
+        for kind in range(3):
+            if kind == 0:
+                M = synth.random_matrix(rng, S, T, values=[0, 1, 2])      # many ties
+                g, th = -1, 0
+            elif kind == 1:
+                M = synth.random_matrix(rng, S, T, lo=-65536, hi=65536)
+                g, th = -int(rng.integers(0, 70000)), int(rng.integers(-65536, 65536))
+            else:
+                M = synth.random_matrix(rng, S, T, lo=0, hi=65536)
+                g, th = -65536, 32768
+            got = ctx.align_matrix(M, g, th)
+            assert got == O.align(M, [(g, th)])[0], (S, T, kind)
+
+
+def test_align_matrix_textbook_cases(ctx):
+    rng = np.random.default_rng(81)
+    for _ in range(20):
+        a = rng.integers(0, 4, rng.integers(1, 90))
+        b = rng.integers(0, 4, rng.integers(1, 90))
+        eq = a[:, None] == b[None, :]
+        lcs = np.where(eq, 65536, 0).astype(np.int32)
+        lev = np.where(eq, 0, -65536).astype(np.int32)
+        assert ctx.align_matrix(lcs, 0, 0) == O.align(lcs, [(0, 0)])[0]
+        assert ctx.align_matrix(lev, -65536, -1) == O.align(lev, [(-65536, -1)])[0]
+
+
+def test_tuning_sweep_64_settings(ctx):
+    w = synth.workload(4, n_pairs=400)
+    dh = ctx.dict_create(w.dictionary)
+    assert len(w.settings) == 64
+    got = ctx.run_batch(dh, w.batch, w.settings)
+    assert_same(got, oracle_results(w), w.name)
+    # thresholds only filter one path per gap: selections nest
+    for p in range(len(got)):
+        for gi in range(8):
+            sels = [set(got[p][gi * 8 + t][1]) for t in range(8)]
+            assert all(sels[t + 1] <= sels[t] for t in range(7))
+
+
+@pytest.mark.slow
+def test_long_documents_4000x4000(ctx):
+    w = synth.workload(3, n_pairs=2)
+    dh = ctx.dict_create(w.dictionary)
+    got = ctx.run_batch(dh, w.batch, w.settings)
+    assert_same(got, oracle_results(w), w.name)
+
+
+def test_serving_alone_and_in_the_mix(ctx):
+    w = synth.workload(5, n_pairs=300)
+    b = w.batch
+    S, T = b.sizes()
+    dh = ctx.dict_create(w.dictionary)
+    tickets = {}
+    for p in range(b.n_pairs):
+        src, tgt = b.pair(p)
+        settings = w.settings if p % 7 else [(-65536, 32768), (-32768, 49152), (-65536, 0)]
+        tickets[ctx.submit(dh, src, tgt, settings)] = (p, settings)
+    got = {}
+    while len(got) < sum(len(s) for _, s in tickets.values()):
+        for (t, k, status, nw, pairs, lat) in ctx.poll(256, 200000):
+            assert status == 0
+            assert lat > 0
+            got[(t, k)] = (nw, pairs)
+    od = O.OracleDict(w.dictionary)
+    rng = np.random.default_rng(5)
+    check = set(rng.choice(b.n_pairs, 40, replace=False).tolist()) | set(np.nonzero(S > 100)[0].tolist())
+    for t, (p, settings) in tickets.items():
+        if p not in check:
+            continue
+        sub = b.subset([p])
+        want, _ = O.mine_batch(od, sub, settings, THREADS)
+        alone = ctx.run_batch(dh, sub, settings)
+        for k in range(len(settings)):
+            assert got[(t, k)] == want[0][k] == alone[0][k], (p, k)
+
+
+def test_errors_are_reported(ctx):
+    w = synth.workload(1)
+    dh = ctx.dict_create(w.dictionary)
+    with pytest.raises(mine.MineError) as e:
+        ctx.run_batch(dh, w.batch, [(1, 0)])                 # gap > 0
+    assert e.value.code == -1
+    with pytest.raises(mine.MineError) as e:
+        ctx.run_batch(dh, w.batch, [(-1, 70000)])           # threshold > 1.0
+    assert e.value.code == -1
+    with pytest.raises(mine.MineError) as e:
+        ctx.align_matrix(np.full((4000, 4000), 65536, np.int32), -1 << 20, 0)
+    assert e.value.code == -4                              # H leaves int32
+    bad = synth.Batch(w.batch.doc_off, w.batch.sent_off.copy(), w.batch.tokens.copy())
+    bad.tokens[5] = 1 << 30                                 # token out of range
+    with pytest.raises(mine.MineError):
+        ctx.run_batch(dh, bad, w.settings)
+    bad2 = synth.Batch(w.batch.doc_off, w.batch.sent_off.copy(), w.batch.tokens)
+    bad2.sent_off[3] = bad2.sent_off[2] - 1                 # decreasing offsets
+    with pytest.raises(mine.MineError):
+        ctx.run_batch(dh, bad2, w.settings)
+    # the context still works after rejected input
+    assert ctx.run_batch(dh, w.batch, w.settings) == oracle_results(w)
+    # duplicate dictionary keys
+    d = synth.dictionary_from_map({1: [2], 3: [4]})
+    d.keys[1] = 1
+    with pytest.raises(mine.MineError):
+        ctx.dict_create(d)
+
+
+def test_budget_admission():
+    w = synth.workload(1)
+    src, tgt = w.batch.pair(0)
+    with mine.Context(budget_bytes=1 << 16) as small:
+        dh = small.dict_create(w.dictionary)
+        with pytest.raises(mine.MineError) as e:
+            small.submit(dh, src, tgt, w.settings)
+        assert e.value.code == -2
+    with mine.Context(budget_bytes=1 << 22, max_inflight=2, max_batch_pairs=3) as c:
+        dh = c.dict_create(w.dictionary)
+        ts = [c.submit(dh, src, tgt, w.settings) for _ in range(20)]
+        with pytest.raises(mine.MineError) as e:
+            c.dict_destroy(dh)                              # still in use
+        assert e.value.code in (-6,)
+        out = []
+        while len(out) < len(ts):
+            out += c.poll(64, 100000)
+        want = oracle_results(w)[0][0]
+        assert all(o[2] == 0 and (o[3], o[4]) == want for o in out)
+        c.dict_destroy(dh)
