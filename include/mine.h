@@ -201,8 +201,9 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
 
 /* The same with the batch already in DEVICE memory and outputs in DEVICE
  * memory, enqueued on `stream` (a cudaStream_t; NULL = the context's own
- * stream) without a host round trip for the data.  doc_off_host is a host
- * copy of batch->doc_off (used to plan the launch).  sel[] (device) receives
+ * stream) without a host round trip for the data.  batch->sent_off and
+ * batch->tokens are device pointers; batch->doc_off is not read (may be NULL):
+ * doc_off_host, a host copy of the document offsets, plans the launch.  sel[] (device) receives
  * pair p / setting k at sel[sel_base + k*min(S_p,T_p) ...] where sel_base is
  * the exclusive prefix sum of n*min(S,T) over earlier pairs; n_sel and
  * nw_score are device arrays of P*n.  sel_cap must be at least

@@ -770,8 +770,10 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
                           mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
                           void *stream)
 {
-    if (!ctx || !dict || !doc_off_host) return fail(MINE_EINVAL, "null argument");
-    int rc = check_batch(batch);
+    if (!ctx || !dict || !doc_off_host || !batch) return fail(MINE_EINVAL, "null argument");
+    mine_batch bh = *batch;          // only the host copy of doc_off is read
+    bh.doc_off = doc_off_host;
+    int rc = check_batch(&bh);
     if (rc) return rc;
     if ((rc = check_settings(settings))) return rc;
     const int32_t P = batch->n_pairs;
