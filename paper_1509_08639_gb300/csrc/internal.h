@@ -20,15 +20,17 @@ constexpr uint32_t ELEM_TOKEN = (1u << 30) - 1;
 constexpr int32_t ERR_DUP_KEY = 1;
 constexpr int32_t ERR_BAD_OFFSETS = 2;
 constexpr int32_t ERR_BAD_TOKEN = 3;
+constexpr int32_t ERR_TIMEOUT = 4;          // a bounded device wait ran out
 
 constexpr int kWarp = 32;
-constexpr int kColHashLog2 = 11;            // per-warp target-token table, 2048 slots
-constexpr int kColHashSlots = 1 << kColHashLog2;
+constexpr int kTile = 32;                   // score matrices are stored as 32 x 32 tiles
+constexpr int kTileElems = kTile * kTile;
+constexpr int kColHashSlots = 2048;         // per-warp target-token table of a column block
 constexpr int kColTokCap = kColHashSlots / 2;   // tokens per column block at most
-constexpr int kPrepHashLog2 = 12;           // per-warp dedupe tables of the prep kernel
-constexpr int kPrepHashSlots = 1 << kPrepHashLog2;
-constexpr int kPrepElemCap = kPrepHashSlots / 2;
+constexpr int kPrepSlots = 2048;            // per-warp dedupe table of the row preparation
+constexpr int kPrepCap = kPrepSlots / 2;
 constexpr int kMaxSentTokens = MINE_MAX_SENT_TOKENS;
+constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins (mbarrier try_wait / flags)
 
 // Resident dictionary: open-addressed table of (key, off << 6 | cnt), linear
 // probing, hash = key * 0x9E3779B1 >> (32 - log2).  Empty key = -1.
@@ -45,16 +47,21 @@ struct PairPlan {       // 48 bytes
     int32_t t0, T;      // target sentences [t0, t0+T)
     int32_t set0, nset; // settings rows [set0, set0+nset)
     int32_t gap0, ngap; // distinct gaps [gap0, gap0+ngap) of this pair
-    int64_t m_off;      // int32 offset of M (S rows, pitch Tp = round_up(T, 4))
+    int64_t m_off;      // int32 offset of M: ceil(S/32) x ceil(T/32) tiles of 32 x 32
     int64_t sel_base;   // mine_pair offset of the selection block (nset * min(S,T))
 };
+
+// Offset of cell (r, c) (0-based) of a tiled score matrix with TT column tiles.
+__host__ __device__ __forceinline__ int64_t m_cell(int64_t m_off, int TT, int r, int c)
+{
+    return m_off + ((int64_t)(r >> 5) * TT + (c >> 5)) * kTileElems + (r & 31) * kTile + (c & 31);
+}
 
 struct NwItem {         // one alignment: (pair, gap)
     int32_t pair;
     int32_t gap;        // global gap index
     int64_t code_off;   // uint32 offset of the direction codes (S rows x ceil(T/16) words)
     int64_t match_off;  // uint32 offset of the match list (min(S,T) entries)
-    int64_t hrow_off;   // int32 offset of the row buffer (T+1 entries)
 };
 
 struct ScoreItem {      // 32 source rows of one pair
@@ -66,6 +73,7 @@ struct BatchDev {
     // inputs
     const int32_t *sent_off;     // [n_sent+1]
     const int32_t *tokens;       // [n_tok]
+    int64_t n_tok;
     int32_t n_pairs;
     // plan
     const PairPlan *pairs;
@@ -73,17 +81,16 @@ struct BatchDev {
     int32_t n_score_items;
     const NwItem *nw_items;
     int32_t n_nw_items;
+    int32_t n_nw_big;            // items [0, n_nw_big) are aligned by a whole CTA
     const int32_t *set_gap;      // [R] global gap index of each setting row
     const int32_t *set_thr;      // [R]
     const int32_t *gap_val;      // [G]
     // scratch
-    uint32_t *elems;             // [n_tok * kmax]
-    int4 *sinfo;                 // [n_sent] (n_i, n_elem, |U_i|, 0) for source sentences
-    int32_t *M;                  // scores
+    uint32_t *elems;             // source elements (see elem_base)
+    int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
-    int32_t *hrow;               // alignment row buffers
-    int32_t *counters;           // [4] work-queue heads
+    int32_t *counters;           // [8] work-queue heads
     int32_t *err;                // error word (0 = fine)
     // outputs
     int32_t *nw_score;           // [R]
@@ -91,19 +98,23 @@ struct BatchDev {
     int32_t *sel;                // mine_pair triples
 };
 
+// A one-warp alignment keeps the whole previous stripe row in a ring of kRing
+// entries, so a pair with more than 32 source sentences and T >= kRing target
+// sentences is aligned by a whole CTA, as is every pair of kBigCells or more.
+constexpr int kRing = 512;
+constexpr int64_t kBigCells = 1 << 15;
+
 // launchers (kernels.cu); each returns the number of kernels launched
 int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_keys, DevDict d,
                       int32_t *err, cudaStream_t st);
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st);
-int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
+int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 
 // kernel identities for per-kernel timing
-enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
+enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_SCORE = 2, KID_ALIGN = 3, KID_TILE = 4,
                 KID_COUNT = 5 };
-int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
-int launch_compact(const int32_t *src, const int64_t *src_off, const int64_t *dst_off,
-                   const int32_t *counts, int32_t n_rows, int32_t *dst, cudaStream_t st);
 
 }  // namespace mine

@@ -8,20 +8,29 @@
 //
 // Kernels:
 //   k_dict_build  one thread per dictionary key -> open-addressed HBM table
-//   k_prep        one warp per source sentence: distinct tokens X_i and their
-//                 translations grouped per token, flagged FIRST (first copy of
-//                 a translation in U_i) and END (last translation of a token)
-//   k_score       one warp per 32 source rows of a pair; for each block of up
-//                 to 32 target sentences a per-warp shared-memory hash of the
-//                 block's target tokens maps token -> 32-bit column mask; each
-//                 lane (one source row) probes its elements and accumulates the
-//                 overlap counts of all 32 columns at once in bit-sliced
-//                 carry-save counters, then scores and stores its 32 cells
-//   k_align       one warp per (pair, gap): anti-diagonal wavefront over
-//                 stripes of 32 rows (lane = row, the cell above passed by
-//                 __shfl_up_sync, the row kept in registers), 2-bit direction
-//                 codes packed 16 per word, a warp-cooperative traceback and
-//                 the threshold selection of every setting sharing the gap
+//   k_validate    sentence offsets are sane (later kernels trust them)
+//   k_score       persistent; one warp per 32 source rows of a pair.
+//                 Row preparation: all tokens of the 32 rows are loaded at
+//                 once, deduplicated per row in a shared-memory hash, looked
+//                 up in the dictionary in parallel, and their translations
+//                 written grouped per token with FIRST (first copy of a
+//                 translation in U_i) and END (last translation of a token)
+//                 flags.  Scoring: for each block of up to 32 target
+//                 sentences (tokens staged by a TMA bulk copy, prefetched one
+//                 block ahead) a shared-memory hash maps token -> 32-bit
+//                 column mask; each lane (one source row) probes its elements
+//                 and accumulates the overlap counts of all 32 columns at once
+//                 in bit-sliced carry-save counters, then scores its 32 cells
+//                 into 32 x 32 tiles of M.
+//   k_align       persistent; large pairs are aligned by a whole CTA (8 warps
+//                 pipelined over stripes of 32 rows, the boundary row passed
+//                 through a shared-memory ring with bounded flag waits), small
+//                 pairs by one warp each.  Inside a stripe: anti-diagonal
+//                 wavefront, lane = row, the cell above passed by
+//                 __shfl_up_sync, score tiles staged by TMA bulk copies three
+//                 tiles deep, 2-bit directions packed 16 per word, then a
+//                 warp-cooperative traceback and the threshold selection of
+//                 every setting that shares the gap.
 #include "internal.h"
 
 #include <algorithm>
@@ -34,6 +43,11 @@ namespace {
 constexpr uint32_t kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t hmul(int32_t key) { return (uint32_t)key * 0x9E3779B1u; }
+
+__device__ __forceinline__ uint32_t hmul64(unsigned long long key)
+{
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32);
+}
 
 __device__ __forceinline__ int ceil_log2(int x)
 {
@@ -55,6 +69,80 @@ __device__ __forceinline__ uint32_t mul_q16(uint32_t x, uint64_t K)
     return (uint32_t)(((uint64_t)x * K) >> 32);
 }
 
+// ---------------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ uint32_t s2u(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s2u(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of transaction on the barrier.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s2u(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// TMA bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            s2u(dst)),
+        "l"(src), "r"(bytes), "r"(s2u(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(s2u(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity; gives up after kWaitLimit tries,
+// records ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err)
+{
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_test(bar, parity)) return true;
+    atomicCAS(err, 0, ERR_TIMEOUT);
+    return false;
+}
+
+// Spin until *flag >= v (shared memory, written by another warp of the CTA).
+__device__ __forceinline__ bool flag_wait_ge(const int32_t *flag, int32_t v, int32_t *err)
+{
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        if (*(volatile const int32_t *)flag >= v) return true;
+        __nanosleep(32);
+    }
+    atomicCAS(err, 0, ERR_TIMEOUT);
+    return false;
+}
+
 // ---------------------------------------------------------------- dictionary
 
 __device__ __forceinline__ int2 dict_find(const DevDict &d, int32_t key)
@@ -62,7 +150,7 @@ __device__ __forceinline__ int2 dict_find(const DevDict &d, int32_t key)
     const uint32_t mask = (1u << d.log2) - 1u;
     uint32_t h = hmul(key) >> (32 - d.log2);
     for (;;) {
-        int2 e = __ldg(&d.slots[h]);
+        const int2 e = __ldg(&d.slots[h]);
         if (e.x == key) return make_int2((int32_t)((uint32_t)e.y >> 6), e.y & 63);
         if (e.x == -1) return make_int2(0, 0);
         h = (h + 1) & mask;
@@ -80,12 +168,12 @@ __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__
         const int32_t cnt = trans_off[k + 1] - off;
         uint32_t h = hmul(key) >> (32 - d.log2);
         for (uint32_t probe = 0; probe <= mask; ++probe) {
-            int32_t old = atomicCAS(&d.slots[h].x, -1, key);
+            const int32_t old = atomicCAS(&d.slots[h].x, -1, key);
             if (old == -1) {
                 d.slots[h].y = (int32_t)(((uint32_t)off << 6) | (uint32_t)cnt);
                 break;
             }
-            if (old == key) {  // duplicate key
+            if (old == key) {
                 atomicCAS(err, 0, ERR_DUP_KEY);
                 break;
             }
@@ -94,17 +182,17 @@ __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__
     }
 }
 
-// ---------------------------------------------------------------- shared hash
+// ---------------------------------------------------------------- shared hashes
+// Open addressing, linear probing; callers keep the load factor <= 1/2, so
+// every probe sequence meets an empty slot.
 
-// Insert key into an open-addressed shared-memory set; true if it was new.
-// The caller keeps the load factor <= 1/2, so an empty slot always exists.
-__device__ __forceinline__ bool set_insert(int32_t *tab, int log2, int32_t key)
+__device__ __forceinline__ bool set_insert64(unsigned long long *tab, int log2, unsigned long long key)
 {
     const uint32_t mask = (1u << log2) - 1u;
-    uint32_t h = hmul(key) >> (32 - log2);
+    uint32_t h = hmul64(key) >> (32 - log2);
     for (;;) {
-        int32_t old = atomicCAS(&tab[h], -1, key);
-        if (old == -1) return true;
+        const unsigned long long old = atomicCAS(&tab[h], ~0ull, key);
+        if (old == ~0ull) return true;
         if (old == key) return false;
         h = (h + 1) & mask;
     }
@@ -115,7 +203,7 @@ __device__ __forceinline__ int slot_of(int32_t *keys, int log2, int32_t key)
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t h = hmul(key) >> (32 - log2);
     for (;;) {
-        int32_t old = atomicCAS(&keys[h], -1, key);
+        const int32_t old = atomicCAS(&keys[h], -1, key);
         if (old == -1 || old == key) return (int)h;
         h = (h + 1) & mask;
     }
@@ -134,157 +222,58 @@ __device__ __forceinline__ uint32_t probe_occ(const int32_t *keys, const uint32_
     }
 }
 
+// Element list of source sentence `sent` (first token at tok_off): 16-byte
+// aligned with room for L * kmax elements before the next sentence's list
+// (the buffer holds n_tok * kmax + 3 * n_sent + 16 words).
 __device__ __forceinline__ int64_t elem_base(int64_t tok_off, int64_t sent, int32_t kmax)
 {
-    // 16-byte aligned start with room for L * kmax elements before the next
-    // sentence's start (the buffer holds n_tok * kmax + 3 * n_sent + 16 words)
     return (tok_off * kmax + 3 * sent + 3) & ~(int64_t)3;
 }
 
-__device__ __forceinline__ int warp_excl_scan(int v, int lane, int *total)
+// ---------------------------------------------------------------- validation
+
+__global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent, int64_t n_tok,
+                           int32_t *err)
 {
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
-    }
-    *total = __shfl_sync(kFull, x, 31);
-    return x - v;
-}
-
-// ---------------------------------------------------------------- k_prep
-
-struct PrepSmem {
-    int32_t tab[kPrepHashSlots];
-    int32_t xs[kMaxSentTokens];      // distinct tokens, then packed (off << 6 | cnt)
-    int32_t goff[kMaxSentTokens];    // element offset of each token's group
-};
-
-constexpr int kPrepWarps = 4;
-
-__global__ void __launch_bounds__(kPrepWarps * 32)
-k_prep(BatchDev b, DevDict d)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    PrepSmem &sm = reinterpret_cast<PrepSmem *>(smem_raw)[wib];
-    const int kmax = d.kmax;
-    if (*(volatile int32_t *)b.err) return;
-
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(&b.counters[0], 1);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= b.n_score_items) break;
-        const ScoreItem si = b.score_items[item];
-        const PairPlan pp = b.pairs[si.pair];
-        const int rows = min(32, pp.S - si.row0);
-        for (int r = 0; r < rows; ++r) {
-            const int64_t s = (int64_t)pp.s0 + si.row0 + r;
-            const int32_t t_beg = b.sent_off[s];
-            const int L = b.sent_off[s + 1] - t_beg;
-            // 1. distinct tokens X_i
-            const int lg_a = max(6, ceil_log2(2 * L));
-            for (int k = lane; k < (1 << lg_a); k += 32) sm.tab[k] = -1;
-            __syncwarp();
-            int n_i = 0;
-            for (int k0 = 0; k0 < L; k0 += 32) {
-                const int k = k0 + lane;
-                bool is_new = false;
-                int32_t tok = 0;
-                if (k < L) {
-                    tok = b.tokens[t_beg + k];
-                    if ((uint32_t)tok > (uint32_t)ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    is_new = set_insert(sm.tab, lg_a, tok);
-                }
-                const uint32_t bal = __ballot_sync(kFull, is_new);
-                if (is_new) sm.xs[n_i + __popc(bal & ((1u << lane) - 1u))] = tok;
-                n_i += __popc(bal);
-            }
-            __syncwarp();
-            // 2. dictionary lookups, group offsets
-            int n_elem = 0;
-            for (int p0 = 0; p0 < n_i; p0 += 32) {
-                const int p = p0 + lane;
-                int cnt = 0;
-                int32_t packed = 0;
-                if (p < n_i) {
-                    const int2 oc = dict_find(d, sm.xs[p]);
-                    cnt = oc.y;
-                    packed = (int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y);
-                }
-                int tot;
-                const int off = warp_excl_scan(cnt, lane, &tot);
-                if (p < n_i) {
-                    sm.xs[p] = packed;
-                    sm.goff[p] = n_elem + off;
-                }
-                n_elem += tot;
-            }
-            __syncwarp();
-            // 3. elements with FIRST / END flags
-            uint32_t *out = b.elems + elem_base(t_beg, s, kmax);
-            int nU = 0;
-            if (n_elem <= kPrepElemCap) {
-                const int lg_b = max(6, ceil_log2(2 * n_elem));
-                for (int k = lane; k < (1 << lg_b); k += 32) sm.tab[k] = -1;
-                __syncwarp();
-                int firsts = 0;
-                for (int p = lane; p < n_i; p += 32) {
-                    const uint32_t pk = (uint32_t)sm.xs[p];
-                    const int off = (int)(pk >> 6), cnt = (int)(pk & 63u);
-                    const int go = sm.goff[p];
-                    for (int k = 0; k < cnt; ++k) {
-                        const int32_t u = __ldg(&d.trans[off + k]);
-                        const bool first = set_insert(sm.tab, lg_b, u);
-                        firsts += first;
-                        out[go + k] = (uint32_t)u | (first ? ELEM_FIRST : 0u) |
-                                      (k == cnt - 1 ? ELEM_END : 0u);
-                    }
-                }
-                nU = __reduce_add_sync(kFull, firsts);
-            } else {
-                // rare long element lists: write, then mark first copies by scanning
-                for (int p = lane; p < n_i; p += 32) {
-                    const uint32_t pk = (uint32_t)sm.xs[p];
-                    const int off = (int)(pk >> 6), cnt = (int)(pk & 63u);
-                    const int go = sm.goff[p];
-                    for (int k = 0; k < cnt; ++k)
-                        out[go + k] = (uint32_t)__ldg(&d.trans[off + k]) |
-                                      (k == cnt - 1 ? ELEM_END : 0u);
-                }
-                __syncwarp();
-                int firsts = 0;
-                for (int e = lane; e < n_elem; e += 32) {
-                    const uint32_t u = out[e] & ELEM_TOKEN;
-                    bool first = true;
-                    for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
-                    firsts += first;
-                    if (first) atomicOr(&out[e], ELEM_FIRST);
-                }
-                nU = __reduce_add_sync(kFull, firsts);
-            }
-            if (lane == 0) b.sinfo[s] = make_int4(n_i, n_elem, nU, 0);
-            __syncwarp();
-        }
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_sent;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = sent_off[k], b = sent_off[k + 1];
+        const bool bad = (k == 0 && a != 0) || (b < a) || (b - a > kMaxSentTokens) ||
+                         (k == n_sent - 1 && (int64_t)b != n_tok);
+        if (bad) atomicCAS(err, 0, ERR_BAD_OFFSETS);
     }
 }
 
 // ---------------------------------------------------------------- k_score
 
-struct ScoreSmem {
+constexpr int kSW = 4;   // warps per CTA
+
+struct PrepArea {
+    unsigned long long key[kPrepSlots];   // (token | translation) << 5 | row
+    int2 grp[kPrepCap];                   // (token, row) then (off << 6 | cnt, row | pos << 5)
+};
+
+struct ColArea {
     int32_t keys[kColHashSlots];
     uint32_t occ[kColHashSlots];
+    int32_t tok[2][kColTokCap + 8];       // TMA staging of two column blocks
+};
+
+struct alignas(16) ScoreWarpSmem {
+    union {
+        PrepArea prep;
+        ColArea col;
+    } u;
+    unsigned long long bar[2];
+    int32_t soff[2][33];
     uint64_t Km[32];        // reciprocal of m_j
     uint64_t KL[32];        // reciprocal of L'_j
     int32_t Lt[32];
     int32_t mcnt[32];
-    int32_t soff[33];
+    int32_t rtok[33];
+    int32_t rcnt[32], recnt[32], rU[32];
+    int32_t ngrp;
 };
-
-constexpr int kScoreWarps = 4;
 
 __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b,
                                     uint32_t c)
@@ -326,29 +315,37 @@ __device__ __forceinline__ uint32_t plane_value(const uint32_t (&P)[NPL], int co
     return v;
 }
 
-// One column block: accumulate, score, store.
+// Accumulate the overlap counts of one column block and score its cells
+// into row `lane` of the score tiles (mrow points at column tile 0).
 template <int NPL>
-__device__ __forceinline__ void score_block(const ScoreSmem &sm, int lg, const uint32_t *el,
+__device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, const uint32_t *el,
                                             int n_elem, int nE8, int ncols, bool row_ok,
-                                            uint64_t Ks, uint64_t KLs, int Ls, int32_t *mrow)
+                                            uint64_t Ks, uint64_t KLs, int Ls, int32_t *mrow,
+                                            int c0)
 {
+    const ColArea &cs = sm.u.col;
     uint32_t A[NPL], B[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) A[k] = B[k] = 0u;
     uint32_t hit = 0;
+    uint4 n0 = make_uint4(0, 0, 0, 0), n1 = make_uint4(0, 0, 0, 0);
+    if (0 < n_elem) {
+        n0 = *reinterpret_cast<const uint4 *>(el);
+        n1 = *reinterpret_cast<const uint4 *>(el + 4);
+    }
     for (int e0 = 0; e0 < nE8; e0 += 8) {
-        uint32_t xa[8], xb[8];
-        uint4 v0 = make_uint4(0, 0, 0, 0), v1 = make_uint4(0, 0, 0, 0);
-        if (e0 < n_elem) {
-            v0 = *reinterpret_cast<const uint4 *>(el + e0);
-            v1 = *reinterpret_cast<const uint4 *>(el + e0 + 4);
+        const uint4 v0 = n0, v1 = n1;
+        if (e0 + 8 < n_elem) {   // prefetch the next eight
+            n0 = *reinterpret_cast<const uint4 *>(el + e0 + 8);
+            n1 = *reinterpret_cast<const uint4 *>(el + e0 + 12);
         }
         const uint32_t ev[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint32_t xa[8], xb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const bool ok = (e0 + q) < n_elem;
             const uint32_t e = ok ? ev[q] : 0u;
-            const uint32_t o = ok ? probe_occ(sm.keys, sm.occ, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
+            const uint32_t o = ok ? probe_occ(cs.keys, cs.occ, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
             xa[q] = (e & ELEM_FIRST) ? o : 0u;
             hit |= o;
             xb[q] = (e & ELEM_END) ? hit : 0u;
@@ -358,142 +355,513 @@ __device__ __forceinline__ void score_block(const ScoreSmem &sm, int lg, const u
         add8<NPL>(B, xb);
     }
     if (!row_ok) return;
+    int32_t out[32];
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) {
-        if (jj < ncols) {
-            const uint32_t a = plane_value<NPL>(A, jj);
-            const uint32_t bb = plane_value<NPL>(B, jj);
-            const uint32_t q_t = mul_q16(a, sm.Km[jj]);
-            const uint32_t q_s = mul_q16(bb, Ks);
-            const int Lt = sm.Lt[jj];
-            uint32_t q_l;
-            if (Ls == 0 && Lt == 0) {
-                q_l = 65536u;
-            } else {
-                const uint32_t lmin = (uint32_t)min(Ls, Lt);
-                q_l = mul_q16(lmin, Ls >= Lt ? KLs : sm.KL[jj]);
+        const uint32_t a = plane_value<NPL>(A, jj);
+        const uint32_t bb = plane_value<NPL>(B, jj);
+        const uint32_t q_t = mul_q16(a, sm.Km[jj]);
+        const uint32_t q_s = mul_q16(bb, Ks);
+        const int Lt = sm.Lt[jj];
+        uint32_t q_l;
+        if (Ls == 0 && Lt == 0) {
+            q_l = 65536u;
+        } else {
+            const uint32_t lmin = (uint32_t)min(Ls, Lt);
+            q_l = mul_q16(lmin, Ls >= Lt ? KLs : sm.KL[jj]);
+        }
+        const uint32_t h = (q_t + q_s) >> 1;
+        out[jj] = (int32_t)((3u * h + q_l) >> 2);
+    }
+    if (ncols == 32 && (c0 & 31) == 0) {
+        // one whole row of one tile: eight 16-byte stores
+        int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            dst[q] = make_int4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            if (jj < ncols) {
+                const int c = c0 + jj;
+                mrow[(int64_t)(c >> 5) * kTileElems + (c & 31)] = out[jj];
             }
-            const uint32_t h = (q_t + q_s) >> 1;
-            mrow[jj] = (int32_t)((3u * h + q_l) >> 2);
         }
     }
 }
 
-__global__ void __launch_bounds__(kScoreWarps * 32)
+// Plan the column block starting at c0: widest run of <= 32 target sentences
+// whose tokens fit the table; stage its tokens with a TMA bulk copy into
+// buffer `buf` (the few tokens past the last 16-byte boundary of the token
+// array are copied by lanes).  Returns ncols (>= 1, or 0 on bad offsets).
+__device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, int buf,
+                                          int64_t tcol0, int c0, int T, int lane, int &ntok,
+                                          int &lead)
+{
+    const int32_t tok0 = b.sent_off[tcol0 + c0];
+    int cum = 0x7fffffff;
+    if (c0 + lane < T) cum = b.sent_off[tcol0 + c0 + lane + 1] - tok0;
+    const int ncols = __popc(__ballot_sync(kFull, cum <= kColTokCap));
+    if (ncols == 0) return 0;
+    ntok = __shfl_sync(kFull, cum, ncols - 1);
+    if (lane < ncols) sm.soff[buf][lane + 1] = cum;
+    if (lane == 0) sm.soff[buf][0] = 0;
+    const int64_t a0 = (int64_t)tok0 & ~(int64_t)3;
+    lead = (int)(tok0 - a0);
+    const int64_t end = (int64_t)tok0 + ntok;
+    const int64_t a1 = min((end + 3) & ~(int64_t)3, b.n_tok & ~(int64_t)3);
+    const uint32_t bytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
+    int32_t *dst = sm.u.col.tok[buf];
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        mbar_expect_tx(&sm.bar[buf], bytes);
+        if (bytes) bulk_g2s(dst, b.tokens + a0, bytes, &sm.bar[buf]);
+    }
+    // tail beyond the last full 16 bytes of the token array
+    const int64_t tail0 = max(a1, a0);
+    for (int64_t p = tail0 + lane; p < end; p += 32) dst[p - a0] = b.tokens[p];
+    return ncols;
+}
+
+__global__ void __launch_bounds__(kSW * 32)
 k_score(BatchDev b, DevDict d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    ScoreSmem &sm = reinterpret_cast<ScoreSmem *>(smem_raw)[wib];
+    ScoreWarpSmem &sm = reinterpret_cast<ScoreWarpSmem *>(smem_raw)[wib];
     const int kmax = d.kmax;
+    if (lane == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    uint32_t parity[2] = {0u, 0u};
     if (*(volatile int32_t *)b.err) return;
 
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(&b.counters[1], 1);
+        if (lane == 0) item = atomicAdd(&b.counters[0], 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_score_items) break;
         const ScoreItem si = b.score_items[item];
         const PairPlan pp = b.pairs[si.pair];
-        const int S = pp.S, T = pp.T;
-        const int Tp = (T + 3) & ~3;
-        const int r = si.row0 + lane;
-        const bool row_ok = r < S;
-        // this lane's source row
-        int n_i = 0, n_elem = 0, nU = 0, Ls = 0;
-        const uint32_t *el = b.elems;
-        if (row_ok) {
-            const int64_t s = (int64_t)pp.s0 + r;
-            const int4 inf = b.sinfo[s];
-            n_i = inf.x;
-            n_elem = inf.y;
-            nU = inf.z;
-            const int32_t tb = b.sent_off[s];
-            Ls = b.sent_off[s + 1] - tb;
-            el = b.elems + elem_base(tb, s, kmax);
+        const int T = pp.T;
+        const int TT = (T + 31) >> 5;
+        const int nrows = min(32, pp.S - si.row0);
+        const int64_t s_first = (int64_t)pp.s0 + si.row0;
+
+        // ------------------------------------------------ row preparation
+        int32_t a_tok = 0, e_tok = 0;
+        if (lane < nrows) {
+            a_tok = b.sent_off[s_first + lane];
+            e_tok = b.sent_off[s_first + lane + 1];
         }
+        const int32_t tA = __shfl_sync(kFull, a_tok, 0);
+        if (lane < nrows) sm.rtok[lane] = a_tok - tA;
+        if (lane == nrows - 1) sm.rtok[nrows] = e_tok - tA;
+        sm.rcnt[lane] = 0;
+        sm.recnt[lane] = 0;
+        sm.rU[lane] = 0;
+        __syncwarp();
+        PrepArea &pa = sm.u.prep;
+        for (int rA = 0; rA < nrows;) {
+            // rows [rA, rB) with at most kPrepCap tokens (one row always fits)
+            const int cand = rA + 1 + lane;
+            const bool okr = cand <= nrows && sm.rtok[cand] - sm.rtok[rA] <= kPrepCap;
+            const int rB = rA + __popc(__ballot_sync(kFull, okr));
+            const int tbase = sm.rtok[rA];
+            const int ntok = sm.rtok[rB] - tbase;
+            int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+            for (int k = lane; k < (1 << lg); k += 32) pa.key[k] = ~0ull;
+            if (lane == 0) sm.ngrp = 0;
+            __syncwarp();
+            int32_t tk[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int k = q * 32 + lane;
+                tk[q] = k < ntok ? b.tokens[tA + tbase + k] : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int k = q * 32 + lane;
+                if (k < ntok) {
+                    const int32_t tok = tk[q];
+                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    int lo = rA, hi = rB - 1;   // row: last r with rtok[r] <= tbase + k
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sm.rtok[mid] <= tbase + k) lo = mid; else hi = mid - 1;
+                    }
+                    const unsigned long long key =
+                        ((unsigned long long)(uint32_t)(tok & ELEM_TOKEN) << 5) | (uint32_t)lo;
+                    if (set_insert64(pa.key, lg, key)) {
+                        const int g = atomicAdd(&sm.ngrp, 1);
+                        pa.grp[g] = make_int2(tok & (int32_t)ELEM_TOKEN, lo);
+                        atomicAdd(&sm.rcnt[lo], 1);
+                    }
+                }
+            }
+            __syncwarp();
+            const int ng = sm.ngrp;
+            // dictionary lookups, four per lane in flight
+            for (int g0 = 0; g0 < ng; g0 += 128) {
+                int2 e[4];
+                int32_t tok[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int g = g0 + q * 32 + lane;
+                    tok[q] = g < ng ? pa.grp[g].x : -1;
+                    e[q] = make_int2(-1, 0);
+                    if (g < ng) e[q] = __ldg(&d.slots[hmul(tok[q]) >> (32 - d.log2)]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int g = g0 + q * 32 + lane;
+                    if (g < ng) {
+                        int2 oc;
+                        if (e[q].x == tok[q]) oc = make_int2((int32_t)((uint32_t)e[q].y >> 6), e[q].y & 63);
+                        else if (e[q].x == -1) oc = make_int2(0, 0);
+                        else oc = dict_find(d, tok[q]);
+                        const int r = pa.grp[g].y;
+                        const int pos = atomicAdd(&sm.recnt[r], oc.y);
+                        pa.grp[g] = make_int2((int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y),
+                                              r | (pos << 5));
+                    }
+                }
+            }
+            __syncwarp();
+            // translations, rows [eA, eB) with at most kPrepCap elements at once
+            for (int eA = rA; eA < rB;) {
+                const int v = (eA + lane < rB) ? sm.recnt[eA + lane] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const bool fits = (eA + lane < rB) && incl <= kPrepCap;
+                int eB = eA + __popc(__ballot_sync(kFull, fits));
+                const bool slow = (eB == eA);   // one row with more than kPrepCap elements
+                if (slow) eB = eA + 1;
+                const int nel = __shfl_sync(kFull, incl, eB - eA - 1);
+                lg = max(6, ceil_log2(2 * max(nel, 1)));
+                if (!slow) {
+                    for (int k = lane; k < (1 << lg); k += 32) pa.key[k] = ~0ull;
+                    __syncwarp();
+                }
+                for (int g = lane; g < ng; g += 32) {
+                    const int2 gr = pa.grp[g];
+                    const int r = gr.y & 31;
+                    if (r < eA || r >= eB) continue;
+                    const uint32_t pk = (uint32_t)gr.x;
+                    const int off = (int)(pk >> 6), cnt = (int)(pk & 63u);
+                    const int pos = gr.y >> 5;
+                    uint32_t *out = b.elems + elem_base(tA + sm.rtok[r], s_first + r, kmax) + pos;
+                    int firsts = 0;
+                    for (int k0 = 0; k0 < cnt; k0 += 4) {
+                        int32_t u[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) u[q] = (k0 + q < cnt) ? __ldg(&d.trans[off + k0 + q]) : 0;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int k = k0 + q;
+                            if (k < cnt) {
+                                bool first = false;
+                                if (!slow)
+                                    first = set_insert64(pa.key, lg,
+                                                         ((unsigned long long)(uint32_t)u[q] << 5) | (uint32_t)r);
+                                firsts += first;
+                                out[k] = (uint32_t)u[q] | (first ? ELEM_FIRST : 0u) |
+                                         (k == cnt - 1 ? ELEM_END : 0u);
+                            }
+                        }
+                    }
+                    if (firsts) atomicAdd(&sm.rU[r], firsts);
+                }
+                __syncwarp();
+                if (slow) {
+                    // mark first copies by scanning the written list
+                    uint32_t *out = b.elems + elem_base(tA + sm.rtok[eA], s_first + eA, kmax);
+                    int firsts = 0;
+                    for (int e = lane; e < nel; e += 32) {
+                        const uint32_t u = out[e] & ELEM_TOKEN;
+                        bool first = true;
+                        for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
+                        firsts += first;
+                        if (first) atomicOr(&out[e], ELEM_FIRST);
+                    }
+                    const int f = __reduce_add_sync(kFull, firsts);
+                    if (lane == 0) sm.rU[eA] = f;
+                    __syncwarp();
+                }
+                eA = eB;
+            }
+            rA = rB;
+        }
+        __syncwarp();
+
+        // ------------------------------------------------ scoring
+        const bool row_ok = lane < nrows;
+        const int n_i = row_ok ? sm.rcnt[lane] : 0;
+        const int n_elem = row_ok ? sm.recnt[lane] : 0;
+        const int nU = row_ok ? sm.rU[lane] : 0;
+        const int Ls = row_ok ? e_tok - a_tok : 0;
+        const uint32_t *el =
+            row_ok ? b.elems + elem_base(a_tok, s_first + lane, kmax) : b.elems;
         const uint64_t Ks = recip48((uint32_t)n_i);
         const uint64_t KLs = recip48((uint32_t)Ls);
-        const int nE8 = (__reduce_max_sync(kFull, (unsigned)n_elem) + 7) & ~7;
+        const int nE8 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 7) & ~7u);
         const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
         const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
-        int32_t *mrow = b.M + pp.m_off + (int64_t)r * Tp;
+        int32_t *mrow = b.M + pp.m_off + (int64_t)(si.row0 >> 5) * TT * kTileElems +
+                        (row_ok ? lane : 0) * kTile;
+        __syncwarp();   // the prep area is reused by the column tables below
 
-        for (int c0 = 0; c0 < T; ) {
-            // widest block of <= 32 columns whose tokens fit the table
-            const int64_t tcol = (int64_t)pp.t0 + c0;
-            const int32_t tok0 = b.sent_off[tcol];
-            int cum = 0x7fffffff;
-            if (c0 + lane < T) cum = b.sent_off[tcol + lane + 1] - tok0;
-            const int ncols = __popc(__ballot_sync(kFull, cum <= kColTokCap));
-            if (ncols == 0) {  // cannot happen for validated offsets
+        const int64_t tcol0 = pp.t0;
+        int cur = 0;
+        int c0 = 0, ntok = 0, lead = 0;
+        int ncols = T > 0 ? plan_block(b, sm, 0, tcol0, 0, T, lane, ntok, lead) : 0;
+        bool pending = T > 0 && ncols > 0;   // a copy in flight into buffer `cur`
+        while (c0 < T) {
+            if (ncols == 0) {
                 if (lane == 0) atomicCAS(b.err, 0, ERR_BAD_OFFSETS);
+                pending = false;
                 break;
             }
-            const int ntok = __shfl_sync(kFull, cum, ncols - 1);
-            // column offsets (relative to tok0) for the token -> column search
-            if (lane < ncols) sm.soff[lane + 1] = cum;
-            if (lane == 0) sm.soff[0] = 0;
-            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            for (int k = lane; k < (1 << lg); k += 32) {
-                sm.keys[k] = -1;
-                sm.occ[k] = 0u;
-            }
-            if (lane < 32) sm.mcnt[lane] = 0;
+            if (!mbar_wait(&sm.bar[cur], parity[cur], b.err)) return;
+            parity[cur] ^= 1u;
+            pending = false;
             __syncwarp();
-            // build: token -> slot, set the column bit, count distinct per column
+            const int32_t *tokp = sm.u.col.tok[cur] + lead;
+            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+            ColArea &ca = sm.u.col;
+            for (int k = lane; k < (1 << lg); k += 32) {
+                ca.keys[k] = -1;
+                ca.occ[k] = 0u;
+            }
+            sm.mcnt[lane] = 0;
+            __syncwarp();
             for (int k = lane; k < ntok; k += 32) {
-                const int32_t tok = b.tokens[tok0 + k];
-                if ((uint32_t)tok > (uint32_t)ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                const int32_t tok = tokp[k];
+                if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
                 int lo = 0, hi = ncols - 1;   // column: last c with soff[c] <= k
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (sm.soff[mid] <= k) lo = mid; else hi = mid - 1;
+                    if (sm.soff[cur][mid] <= k) lo = mid; else hi = mid - 1;
                 }
-                const int slot = slot_of(sm.keys, lg, tok);
+                const int slot = slot_of(ca.keys, lg, (int32_t)(tok & ELEM_TOKEN));
                 const uint32_t bit = 1u << lo;
-                const uint32_t old = atomicOr(&sm.occ[slot], bit);
+                const uint32_t old = atomicOr(&ca.occ[slot], bit);
                 if (!(old & bit)) atomicAdd(&sm.mcnt[lo], 1);
             }
             __syncwarp();
             int maxM = 0;
             if (lane < ncols) {
                 const int m = sm.mcnt[lane];
-                const int Lt = sm.soff[lane + 1] - sm.soff[lane];
+                const int Lt = sm.soff[cur][lane + 1] - sm.soff[cur][lane];
                 sm.Km[lane] = recip48((uint32_t)m);
                 sm.KL[lane] = recip48((uint32_t)Lt);
                 sm.Lt[lane] = Lt;
                 maxM = m;
             }
             maxM = (int)__reduce_max_sync(kFull, (unsigned)maxM);
-            __syncwarp();
-            const int bound = max(min(maxU, maxM), maxN);
-            int32_t *dst = mrow + c0;
-            if (bound < 64) {
-                score_block<6>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, dst);
-            } else if (bound < 256) {
-                score_block<8>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, dst);
-            } else {
-                score_block<11>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, dst);
+            // prefetch the next block into the other buffer while this one is scored
+            const int nc0 = c0 + ncols;
+            int n_ncols = 0, n_ntok = 0, n_lead = 0;
+            if (nc0 < T) {
+                n_ncols = plan_block(b, sm, cur ^ 1, tcol0, nc0, T, lane, n_ntok, n_lead);
+                pending = n_ncols > 0;
             }
             __syncwarp();
-            c0 += ncols;
+            const int bound = max(min(maxU, maxM), maxN);
+            if (bound < 64) {
+                score_block<6>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+            } else if (bound < 256) {
+                score_block<8>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+            } else {
+                score_block<11>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+            }
+            __syncwarp();
+            c0 = nc0;
+            ncols = n_ncols;
+            ntok = n_ntok;
+            lead = n_lead;
+            cur ^= 1;
         }
+        if (pending) {   // a block was staged but not used (bad offsets): let it land
+            mbar_wait(&sm.bar[cur], parity[cur], b.err);
+            parity[cur] ^= 1u;
+        }
+        if (*(volatile int32_t *)b.err) return;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- k_tile
+
+__global__ void k_tile(const int32_t *__restrict__ src, int32_t S, int32_t T, int32_t *__restrict__ dst)
+{
+    const int TT = (T + 31) >> 5;
+    const int64_t n = (int64_t)S * T;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(k / T), c = (int)(k % T);
+        dst[m_cell(0, TT, r, c)] = src[k];
     }
 }
 
 // ---------------------------------------------------------------- k_align
 
-constexpr int kAlignWarps = 4;
+constexpr int kAW = 8;      // warps per CTA (pipeline depth of a large alignment)
+constexpr int kMBuf = 3;    // score tiles in flight per warp
+
+struct AlignSmem {
+    int32_t tile[kAW][kMBuf][kTileElems];
+    int32_t ring[kAW][kRing];
+    unsigned long long bar[kAW][kMBuf];
+    int32_t prod[kAW];      // stream values published by warp w (its last rows)
+    int32_t cons[kAW];      // stream values warp w consumed from its predecessor
+    int32_t item;
+    int32_t hfinal;
+};
+
+struct WarpPipe {
+    int w, W;               // position in the pipeline and its width
+    int32_t *ring_mine, *ring_pred;
+    int32_t *prod_mine, *prod_pred, *cons_mine, *cons_succ;
+};
+
+// Fill H over the stripes w, w+W, ... of one pair and write the direction
+// codes.  Stripe s publishes its last row (lane 31) as the stream values
+// gen*T + j - 1 (gen = s / W) of its warp's ring; stripe s+1 consumes them.
+// Returns false if a bounded wait ran out.
+__device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const WarpPipe &wp,
+                              const NwItem &it, const PairPlan &pp, int lane,
+                              uint32_t (&uses)[kMBuf], int32_t &hfinal)
+{
+    const int S = pp.S, T = pp.T;
+    const int32_t g = b.gap_val[it.gap];
+    const int TT = (T + 31) >> 5;
+    const int TS = (S + 31) >> 5;
+    const int CW = (T + 15) >> 4;
+    uint32_t *codes = b.codes + it.code_off;
+    const int32_t *Mp = b.M + pp.m_off;
+    for (int s = wp.w; s < TS; s += wp.W) {
+        const int gen = s / wp.W;
+        const int i0 = 32 * s;
+        const int row = i0 + lane + 1;
+        const bool row_ok = row <= S;
+        const bool has_above = s > 0;
+        const bool has_below = s + 1 < TS;
+        const int64_t qp_base = has_above ? (int64_t)((s - 1) / wp.W) * T : 0;
+        const int64_t qm_base = (int64_t)gen * T;
+        uint32_t *cr = codes + (int64_t)(row - 1) * CW;
+        // first tiles of this stripe
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+            for (int k = 0; k < kMBuf && k < TT; ++k) {
+                mbar_expect_tx(&sm.bar[wib][k], kTileElems * 4);
+                bulk_g2s(sm.tile[wib][k], Mp + ((int64_t)s * TT + k) * kTileElems, kTileElems * 4,
+                         &sm.bar[wib][k]);
+            }
+        }
+        for (int k = 0; k < kMBuf && k < TT; ++k) uses[k]++;
+        int32_t h_left = row * g;          // H[row][j-1]
+        int32_t up_prev = (row - 1) * g;   // H[row-1][j-1]
+        int32_t h_out = 0;                 // value handed to the next lane
+        uint32_t word = 0;
+        const int nchunks = (T + 31 + 31) >> 5;
+        for (int c = 0; c < nchunks; ++c) {
+            if (c < TT) {
+                const int bb = c % kMBuf;
+                if (!mbar_wait(&sm.bar[wib][bb], (uses[bb] - 1) & 1u, b.err)) return false;
+            }
+            if (c >= 2 && c + 1 < TT) {
+                // tile c-2 is no longer read: refill its buffer with tile c+1
+                const int bb = (c + 1) % kMBuf;
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
+                    bulk_g2s(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems,
+                             kTileElems * 4, &sm.bar[wib][bb]);
+                }
+                uses[bb]++;
+            }
+            // the row above for columns 32c+1 .. 32c+32 (lane k holds column 32c+1+k)
+            const int jcol = 32 * c + 1 + lane;
+            int32_t up_val;
+            if (has_above) {
+                const int64_t need = qp_base + min(32 * c + 32, T);
+                if (!flag_wait_ge(wp.prod_pred, (int32_t)need, b.err)) return false;
+                up_val = jcol <= T ? wp.ring_pred[(qp_base + jcol - 1) & (kRing - 1)] : 0;
+                __syncwarp();
+                if (lane == 0) *(volatile int32_t *)wp.cons_mine = (int32_t)need;
+            } else {
+                up_val = jcol * g;
+            }
+            if (has_below) {
+                // lane 31 writes columns up to 32c+1 in this chunk: their ring
+                // slots must have been read by the successor
+                const int jmax = min(32 * c + 1, T);
+                if (jmax >= 1 &&
+                    !flag_wait_ge(wp.cons_succ, (int32_t)(qm_base + jmax - kRing), b.err))
+                    return false;
+            }
+#pragma unroll 4
+            for (int u = 0; u < 32; ++u) {
+                const int t = 32 * c + u;
+                const int j = t - lane + 1;
+                int32_t up_in = __shfl_up_sync(kFull, h_out, 1);
+                const int32_t from_ring = __shfl_sync(kFull, up_val, u);
+                if (lane == 0) up_in = from_ring;
+                if (row_ok && j >= 1 && j <= T) {
+                    const int cidx = j - 1;
+                    const int32_t sv = sm.tile[wib][(cidx >> 5) % kMBuf][lane * kTile + (cidx & 31)];
+                    const int32_t cd = up_prev + sv;
+                    const int32_t cu = up_in + g;
+                    const int32_t cl = h_left + g;
+                    const bool upw = cu >= cl;
+                    const int32_t cg = upw ? cu : cl;
+                    const bool dg = cd >= cg;
+                    const int32_t best = dg ? cd : cg;
+                    const uint32_t dir = dg ? DIR_DIAG : (upw ? DIR_UP : DIR_LEFT);
+                    word |= dir << (2 * (cidx & 15));
+                    if ((cidx & 15) == 15 || j == T) {
+                        cr[cidx >> 4] = word;
+                        word = 0;
+                    }
+                    if (lane == 31 && has_below) wp.ring_mine[(qm_base + cidx) & (kRing - 1)] = best;
+                    h_left = best;
+                    h_out = best;
+                    up_prev = up_in;
+                }
+            }
+            __syncwarp();
+            if (has_below && lane == 31) {
+                const int jdone = min(32 * c + 1, T);
+                if (jdone >= 1) {
+                    __threadfence_block();
+                    *(volatile int32_t *)wp.prod_mine = (int32_t)(qm_base + jdone);
+                }
+            }
+        }
+        if (s == TS - 1) hfinal = __shfl_sync(kFull, h_left, (S - 1) - i0);
+        __syncwarp();
+    }
+    return true;
+}
 
 __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPlan &pp,
                                                 int gap_idx, int32_t H, const uint32_t *matches,
                                                 int nm, int lane)
 {
     const int cap = min(pp.S, pp.T);
-    const int Tp = (pp.T + 3) & ~3;
-    const int32_t *Mp = b.M + pp.m_off;
+    const int TT = (pp.T + 31) >> 5;
     for (int k = 0; k < pp.nset; ++k) {
         const int row = pp.set0 + k;
         if (b.set_gap[row] != gap_idx) continue;
@@ -501,7 +869,7 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
         int32_t *out = b.sel + 3 * (pp.sel_base + (int64_t)k * cap);
         int cnt = 0;
         for (int c = 0; c < nm; c += 32) {
-            const int q = c + lane;                   // position in increasing-i order
+            const int q = c + lane;   // position in increasing-i order
             bool take = false;
             int i = 0, j = 0;
             int32_t sc = 0;
@@ -509,7 +877,7 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
                 const uint32_t ij = matches[nm - 1 - q];
                 i = (int)(ij >> 16);
                 j = (int)(ij & 0xffffu);
-                sc = Mp[(int64_t)(i - 1) * Tp + (j - 1)];
+                sc = b.M[m_cell(pp.m_off, TT, i - 1, j - 1)];
                 take = sc > thr;
             }
             const uint32_t bal = __ballot_sync(kFull, take);
@@ -528,153 +896,112 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
     }
 }
 
-__global__ void __launch_bounds__(kAlignWarps * 32)
+// Traceback from (S,T): blocks of 32 rows x 16 columns of codes held in
+// registers, one lane per row; then the selection.
+__device__ void trace_and_select(const BatchDev &b, const NwItem &it, const PairPlan &pp,
+                                 int32_t H, int lane)
+{
+    const int S = pp.S, T = pp.T;
+    uint32_t *matches = b.matches + it.match_off;
+    const uint32_t *codes = b.codes + it.code_off;
+    const int CW = (T + 15) >> 4;
+    int i = S, j = T, nm = 0;
+    while (i > 0 && j > 0) {
+        const int rb = max(1, i - 31);
+        const int w = (j - 1) >> 4;
+        uint32_t wd = 0;
+        if (rb + lane <= i) wd = codes[(int64_t)(rb + lane - 1) * CW + w];
+        do {
+            const uint32_t word = __shfl_sync(kFull, wd, i - rb);
+            const uint32_t dir = (word >> (2 * ((j - 1) & 15))) & 3u;
+            if (dir == DIR_DIAG) {
+                if (lane == 0) matches[nm] = ((uint32_t)i << 16) | (uint32_t)j;
+                ++nm;
+                --i;
+                --j;
+            } else if (dir == DIR_UP) {
+                --i;
+            } else {
+                --j;
+            }
+        } while (i >= rb && i > 0 && j > 0 && ((j - 1) >> 4) == w);
+    }
+    __syncwarp();
+    select_and_emit(b, pp, it.gap, H, matches, nm, lane);
+}
+
+__global__ void __launch_bounds__(kAW * 32)
 k_align(BatchDev b)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AlignSmem &sm = *reinterpret_cast<AlignSmem *>(smem_raw);
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int k = 0; k < kMBuf; ++k) mbar_init(&sm.bar[wib][k], 1);
+        fence_barrier_init();
+    }
+    uint32_t uses[kMBuf] = {0u, 0u, 0u};
+    __syncthreads();
     if (*(volatile int32_t *)b.err) return;
+
+    // large alignments: the whole CTA on one pair
+    for (;;) {
+        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[1], 1);
+        if (threadIdx.x < kAW) {
+            sm.prod[threadIdx.x] = 0;
+            sm.cons[threadIdx.x] = 0;
+        }
+        __syncthreads();
+        const int item = sm.item;
+        if (item >= b.n_nw_big) break;
+        const NwItem it = b.nw_items[item];
+        const PairPlan pp = b.pairs[it.pair];
+        WarpPipe wp;
+        wp.w = wib;
+        wp.W = kAW;
+        const int pred = (wib + kAW - 1) % kAW, succ = (wib + 1) % kAW;
+        wp.ring_mine = sm.ring[wib];
+        wp.ring_pred = sm.ring[pred];
+        wp.prod_mine = &sm.prod[wib];
+        wp.prod_pred = &sm.prod[pred];
+        wp.cons_mine = &sm.cons[wib];
+        wp.cons_succ = &sm.cons[succ];
+        int32_t hf = 0;
+        const bool ok = align_stripes(b, sm, wib, wp, it, pp, lane, uses, hf);
+        const int last_warp = (((pp.S + 31) >> 5) - 1) % kAW;
+        if (ok && wib == last_warp && lane == 0) sm.hfinal = hf;
+        __syncthreads();
+        if (*(volatile int32_t *)b.err) return;
+        if (wib == 0) trace_and_select(b, it, pp, sm.hfinal, lane);
+        __syncthreads();
+    }
+    // small alignments: one warp each
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(&b.counters[2], 1);
+        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[2], 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_nw_items) break;
         const NwItem it = b.nw_items[item];
         const PairPlan pp = b.pairs[it.pair];
-        const int S = pp.S, T = pp.T;
-        const int32_t g = b.gap_val[it.gap];
-        uint32_t *matches = b.matches + it.match_off;
-        if (S == 0 || T == 0) {
-            select_and_emit(b, pp, it.gap, (S + T) * g, matches, 0, lane);
+        if (pp.S == 0 || pp.T == 0) {
+            select_and_emit(b, pp, it.gap, (pp.S + pp.T) * b.gap_val[it.gap], nullptr, 0, lane);
             continue;
         }
-        const int Tp = (T + 3) & ~3;
-        const int CW = (T + 15) >> 4;
-        const int32_t *Mp = b.M + pp.m_off;
-        uint32_t *codes = b.codes + it.code_off;
-        int32_t *hrow = b.hrow + it.hrow_off;
-        for (int j = lane; j <= T; j += 32) hrow[j] = j * g;
-        __syncwarp();
-        int32_t Hfinal = 0;
-        for (int i0 = 0; i0 < S; i0 += 32) {
-            const int row = i0 + lane + 1;          // 1-based
-            const bool row_ok = row <= S;
-            const int32_t *mr = Mp + (int64_t)(row - 1) * Tp;
-            uint32_t *cr = codes + (int64_t)(row - 1) * CW;
-            int32_t h_left = row * g;               // H[row][j-1]
-            int32_t up_prev = (row - 1) * g;        // H[row-1][j-1]
-            int32_t h_out = 0;                      // value handed to the next lane
-            uint32_t word = 0;
-            const int nsteps = T + 31;
-            int32_t cur_s[8], cur_u[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = u - lane + 1;
-                const bool ok = row_ok && j >= 1 && j <= T;
-                cur_s[u] = ok ? __ldg(mr + j - 1) : 0;
-                cur_u[u] = (lane == 0 && j >= 1 && j <= T) ? hrow[j] : 0;
-            }
-            for (int t0 = 0; t0 < nsteps; t0 += 8) {
-                int32_t nxt_s[8], nxt_u[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = t0 + 8 + u - lane + 1;
-                    const bool ok = row_ok && j >= 1 && j <= T;
-                    nxt_s[u] = ok ? __ldg(mr + j - 1) : 0;
-                    nxt_u[u] = (lane == 0 && j >= 1 && j <= T) ? hrow[j] : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int t = t0 + u;
-                    const int j = t - lane + 1;
-                    int32_t up_in = __shfl_up_sync(kFull, h_out, 1);
-                    if (lane == 0) up_in = cur_u[u];
-                    if (t < nsteps && row_ok && j >= 1 && j <= T) {
-                        const int32_t cd = up_prev + cur_s[u];
-                        const int32_t cu = up_in + g;
-                        const int32_t cl = h_left + g;
-                        const bool upw = cu >= cl;
-                        const int32_t cg = upw ? cu : cl;
-                        const bool dg = cd >= cg;
-                        const int32_t best = dg ? cd : cg;
-                        const uint32_t dir = dg ? DIR_DIAG : (upw ? DIR_UP : DIR_LEFT);
-                        word |= dir << (2 * ((j - 1) & 15));
-                        if (((j - 1) & 15) == 15 || j == T) {
-                            cr[(j - 1) >> 4] = word;
-                            word = 0;
-                        }
-                        if (lane == 31) hrow[j] = best;
-                        h_left = best;
-                        h_out = best;
-                        up_prev = up_in;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    cur_s[u] = nxt_s[u];
-                    cur_u[u] = nxt_u[u];
-                }
-            }
-            const int last_lane = (S - 1 - i0) < 32 ? (S - 1 - i0) : 31;
-            Hfinal = __shfl_sync(kFull, h_left, last_lane);
-            __syncwarp();
-        }
-        // traceback: walk blocks of 32 rows x 16 columns of codes held in registers
-        int i = S, j = T, nm = 0;
-        while (i > 0 && j > 0) {
-            const int rb = max(1, i - 31);
-            const int w = (j - 1) >> 4;
-            uint32_t wd = 0;
-            if (rb + lane <= i) wd = codes[(int64_t)(rb + lane - 1) * CW + w];
-            do {
-                const uint32_t word = __shfl_sync(kFull, wd, i - rb);
-                const uint32_t dir = (word >> (2 * ((j - 1) & 15))) & 3u;
-                if (dir == DIR_DIAG) {
-                    if (lane == 0) matches[nm] = ((uint32_t)i << 16) | (uint32_t)j;
-                    ++nm;
-                    --i;
-                    --j;
-                } else if (dir == DIR_UP) {
-                    --i;
-                } else {
-                    --j;
-                }
-            } while (i >= rb && i > 0 && j > 0 && ((j - 1) >> 4) == w);
+        if (lane == 0) {
+            sm.prod[wib] = 0;
+            sm.cons[wib] = 0;
         }
         __syncwarp();
-        select_and_emit(b, pp, it.gap, Hfinal, matches, nm, lane);
-    }
-}
-
-// ---------------------------------------------------------------- validation
-
-// Sentence offsets must start at 0, never decrease, end at n_tok and give at
-// most MINE_MAX_SENT_TOKENS tokens per sentence; later kernels trust them.
-__global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent, int64_t n_tok,
-                           int32_t *err)
-{
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_sent;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = sent_off[k], b = sent_off[k + 1];
-        const bool bad = (k == 0 && a != 0) || (b < a) || (b - a > kMaxSentTokens) ||
-                         (k == n_sent - 1 && (int64_t)b != n_tok);
-        if (bad) atomicCAS(err, 0, ERR_BAD_OFFSETS);
-    }
-}
-
-// ---------------------------------------------------------------- compaction
-
-__global__ void k_compact(const int32_t *__restrict__ src, const int64_t *__restrict__ src_off,
-                          const int64_t *__restrict__ dst_off, const int32_t *__restrict__ counts,
-                          int32_t n_rows, int32_t *__restrict__ dst)
-{
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int r = warp; r < n_rows; r += nwarps) {
-        const int64_t n = 3 * (int64_t)counts[r];
-        const int32_t *s = src + 3 * src_off[r];
-        int32_t *d = dst + 3 * dst_off[r];
-        for (int64_t k = lane; k < n; k += 32) d[k] = s[k];
+        WarpPipe wp;
+        wp.w = 0;
+        wp.W = 1;
+        wp.ring_mine = wp.ring_pred = sm.ring[wib];
+        wp.prod_mine = wp.prod_pred = &sm.prod[wib];
+        wp.cons_mine = wp.cons_succ = &sm.cons[wib];
+        int32_t hf = 0;
+        if (!align_stripes(b, sm, wib, wp, it, pp, lane, uses, hf)) return;
+        trace_and_select(b, it, pp, hf, lane);
     }
 }
 
@@ -692,12 +1019,6 @@ int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_k
     return 1;
 }
 
-static int grid_for(int num_sms, int per_sm, int items, int warps_per_cta)
-{
-    const int need = (items + warps_per_cta - 1) / warps_per_cta;
-    return max(1, min(num_sms * per_sm, need));
-}
-
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st)
 {
@@ -708,38 +1029,36 @@ int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int3
     return 1;
 }
 
-int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
-{
-    if (b.n_score_items <= 0) return 0;
-    const size_t smem = sizeof(PrepSmem) * kPrepWarps;
-    cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_prep<<<grid_for(num_sms, 2, b.n_score_items, kPrepWarps), kPrepWarps * 32, smem, st>>>(b, d);
-    return 1;
-}
-
 int launch_score(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
-    const size_t smem = sizeof(ScoreSmem) * kScoreWarps;
+    const size_t smem = sizeof(ScoreWarpSmem) * kSW;
     cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_score<<<grid_for(num_sms, 3, b.n_score_items, kScoreWarps), kScoreWarps * 32, smem, st>>>(b, d);
+    const int need = (b.n_score_items + kSW - 1) / kSW;
+    const int grid = std::max(1, std::min(num_sms * 2, need));
+    k_score<<<grid, kSW * 32, smem, st>>>(b, d);
     return 1;
 }
 
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_nw_items <= 0) return 0;
-    k_align<<<grid_for(num_sms, 8, b.n_nw_items, kAlignWarps), kAlignWarps * 32, 0, st>>>(b);
+    const size_t smem = sizeof(AlignSmem);
+    cudaFuncSetAttribute(k_align, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int small = b.n_nw_items - b.n_nw_big;
+    const int need = std::max(b.n_nw_big, (small + kAW - 1) / kAW);
+    const int grid = std::max(1, std::min(num_sms * 2, need));
+    k_align<<<grid, kAW * 32, smem, st>>>(b);
     return 1;
 }
 
-int launch_compact(const int32_t *src, const int64_t *src_off, const int64_t *dst_off,
-                   const int32_t *counts, int32_t n_rows, int32_t *dst, cudaStream_t st)
+int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st)
 {
-    if (n_rows <= 0) return 0;
+    const int64_t n = (int64_t)S * T;
+    if (n <= 0) return 0;
     const int threads = 256;
-    const int blocks = min(4096, (n_rows * 32 + threads - 1) / threads);
-    k_compact<<<blocks, threads, 0, st>>>(src, src_off, dst_off, counts, n_rows, dst);
+    const int blocks = (int)std::min<int64_t>(4096, (n + threads - 1) / threads);
+    k_tile<<<blocks, threads, 0, st>>>(src, S, T, dst);
     return 1;
 }
 

@@ -104,8 +104,9 @@ struct Plan {
     std::vector<ScoreItem> sitems;
     std::vector<NwItem> nitems;
     std::vector<int32_t> set_gap, set_thr, gap_val;
-    int64_t m_elems = 0, code_words = 0, match_words = 0, hrow_words = 0, sel_cap = 0;
+    int64_t m_elems = 0, code_words = 0, match_words = 0, sel_cap = 0;
     int32_t R = 0;
+    int32_t n_big = 0;              // alignments [0, n_big) use a whole CTA
     int64_t n_sent = 0, n_tok = 0;
 };
 
@@ -171,9 +172,8 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         int rc = add_settings(pl, set, n, pp.S, pp.T, max_abs_s, mined, pp.gap0, pp.ngap);
         if (rc) return rc;
         pl.R += n;
-        const int64_t Tp = (pp.T + 3) & ~3;
         pp.m_off = pl.m_elems;
-        pl.m_elems += (int64_t)pp.S * Tp;
+        pl.m_elems += (int64_t)((pp.S + kTile - 1) / kTile) * ((pp.T + kTile - 1) / kTile) * kTileElems;
         pp.sel_base = pl.sel_cap;
         pl.sel_cap += (int64_t)n * std::min(pp.S, pp.T);
         bucketS[p] = ceil_log2_host((int64_t)pp.T + 1);
@@ -191,21 +191,26 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         const PairPlan &pp = pl.pairs[p];
         for (int r0 = 0; r0 < pp.S; r0 += 32) pl.sitems.push_back(ScoreItem{p, r0});
     }
-    for (int p : order_by(bucketC)) {
-        const PairPlan &pp = pl.pairs[p];
-        const int64_t CW = (pp.T + 15) >> 4;
-        for (int g = 0; g < pp.ngap; ++g) {
-            NwItem it;
-            it.pair = p;
-            it.gap = pp.gap0 + g;
-            it.code_off = pl.code_words;
-            pl.code_words += (int64_t)pp.S * CW;
-            it.match_off = pl.match_words;
-            pl.match_words += std::min(pp.S, pp.T);
-            it.hrow_off = pl.hrow_words;
-            pl.hrow_words += (int64_t)pp.T + 1;
-            pl.nitems.push_back(it);
+    // alignments: whole-CTA ones first, then one-warp ones, each longest first
+    const std::vector<int> ord = order_by(bucketC);
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int p : ord) {
+            const PairPlan &pp = pl.pairs[p];
+            const bool big = (int64_t)pp.S * pp.T >= kBigCells || (pp.S > kTile && pp.T >= kRing);
+            if (big != (pass == 0)) continue;
+            const int64_t CW = (pp.T + 15) >> 4;
+            for (int g = 0; g < pp.ngap; ++g) {
+                NwItem it;
+                it.pair = p;
+                it.gap = pp.gap0 + g;
+                it.code_off = pl.code_words;
+                pl.code_words += (int64_t)pp.S * CW;
+                it.match_off = pl.match_words;
+                pl.match_words += std::min(pp.S, pp.T);
+                pl.nitems.push_back(it);
+            }
         }
+        if (pass == 0) pl.n_big = (int32_t)pl.nitems.size();
     }
     return 0;
 }
@@ -214,7 +219,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
 struct Layout {
     int64_t plan = 0, plan_bytes = 0;
     int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
-    int64_t elems = 0, sinfo = 0, M = 0, codes = 0, matches = 0, hrow = 0;
+    int64_t elems = 0, M = 0, Mrow = 0, codes = 0, matches = 0;
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
     // offsets inside the plan blob
@@ -250,12 +255,15 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     }
     if (scoring) {
         L.elems = take(4 * (pl.n_tok * kmax + 3 * pl.n_sent + 16));
-        L.sinfo = take(16 * pl.n_sent);
+    } else {
+        // a caller-supplied row-major matrix is copied here, then tiled
+        int64_t rows = 0;
+        for (const PairPlan &pp : pl.pairs) rows += (int64_t)pp.S * pp.T;
+        L.Mrow = take(4 * rows + 16);
     }
     L.M = take(4 * pl.m_elems + 16);
     L.codes = take(4 * pl.code_words + 16);
     L.matches = take(4 * pl.match_words + 16);
-    L.hrow = take(4 * pl.hrow_words + 16);
     L.counters = take(4 * 16);
     L.nw = take(4 * (int64_t)pl.R);
     L.nsel = take(4 * (int64_t)pl.R);
@@ -281,21 +289,21 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     char *plan = base + L.plan;
     b.sent_off = sent_off;
     b.tokens = tokens;
+    b.n_tok = pl.n_tok;
     b.n_pairs = pl.P;
     b.pairs = reinterpret_cast<const PairPlan *>(plan + L.o_pairs);
     b.score_items = reinterpret_cast<const ScoreItem *>(plan + L.o_sitems);
     b.n_score_items = (int32_t)pl.sitems.size();
     b.nw_items = reinterpret_cast<const NwItem *>(plan + L.o_nitems);
     b.n_nw_items = (int32_t)pl.nitems.size();
+    b.n_nw_big = pl.n_big;
     b.set_gap = reinterpret_cast<const int32_t *>(plan + L.o_setgap);
     b.set_thr = reinterpret_cast<const int32_t *>(plan + L.o_setthr);
     b.gap_val = reinterpret_cast<const int32_t *>(plan + L.o_gapval);
     b.elems = reinterpret_cast<uint32_t *>(base + L.elems);
-    b.sinfo = reinterpret_cast<int4 *>(base + L.sinfo);
     b.M = reinterpret_cast<int32_t *>(base + L.M);
     b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
     b.matches = reinterpret_cast<uint32_t *>(base + L.matches);
-    b.hrow = reinterpret_cast<int32_t *>(base + L.hrow);
     b.counters = reinterpret_cast<int32_t *>(base + L.counters);
     b.err = b.counters + 8;
     b.nw_score = reinterpret_cast<int32_t *>(base + L.nw);
@@ -310,6 +318,7 @@ const char *device_err_text(int32_t e)
     case ERR_DUP_KEY: return "duplicate dictionary key";
     case ERR_BAD_OFFSETS: return "malformed sentence offsets (sent_off must start at 0, not decrease, end at n_tok, and give <= 1024 tokens per sentence)";
     case ERR_BAD_TOKEN: return "token id outside [0, 2^30)";
+    case ERR_TIMEOUT: return "a bounded device wait ran out";
     default: return "device error";
     }
 }
@@ -487,7 +496,6 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
     CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
     if (scoring) {
         n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
-        n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(b, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(b, dict->d, ctx->num_sms, st); });
     }
     n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
@@ -838,9 +846,9 @@ int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mi
     CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
     BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr);
     if (S > 0 && T > 0) {
-        const int Tp = (T + 3) & ~3;
-        CK(cudaMemcpy2DAsync(b.M, 4 * (size_t)Tp, M, 4 * (size_t)T, 4 * (size_t)T, S,
-                             cudaMemcpyHostToDevice, st));
+        int32_t *mrow = reinterpret_cast<int32_t *>(base + L.Mrow);
+        CK(cudaMemcpyAsync(mrow, M, 4 * (size_t)S * T, cudaMemcpyHostToDevice, st));
+        ctx->launches += timed_launch(ctx, KID_TILE, st, [&] { return launch_tile(mrow, S, T, b.M, st); });
     }
     if ((rc = enqueue_kernels(ctx, b, nullptr, 0, 0, false, st))) return rc;
     char *ho = hp + align_up(L.plan_bytes, 64);
@@ -920,7 +928,7 @@ int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n)
 
 const char *mine_kernel_name(int32_t id)
 {
-    static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score", "k_align"};
+    static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_score", "k_align", "k_tile"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
