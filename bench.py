@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--plain-pairs", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=5000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--only-device", action="store_true",
+                    help="time only the device-resident path (for profiler captures)")
     return ap.parse_args()
 
 
@@ -308,6 +310,14 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     ms = ev0.elapsed_time(ev1) / args.steps
+    if args.only_device:
+        if rank == 0:
+            print(json.dumps({"workload": w.name, "pairs": P, "ms_per_step": ms,
+                              "pairs_per_s": P / (ms / 1e3),
+                              "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}),
+                  flush=True)
+        ctx.close()
+        return
     if ws > 1:
         t = torch.tensor([ms], dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)

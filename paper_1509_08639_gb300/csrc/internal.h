@@ -27,8 +27,6 @@ constexpr int kTile = 32;                   // score matrices are stored as 32 x
 constexpr int kTileElems = kTile * kTile;
 constexpr int kColHashSlots = 2048;         // per-warp target-token table of a column block
 constexpr int kColTokCap = kColHashSlots / 2;   // tokens per column block at most
-constexpr int kPrepSlots = 2048;            // per-warp dedupe table of the row preparation
-constexpr int kPrepCap = kPrepSlots / 2;
 constexpr int kMaxSentTokens = MINE_MAX_SENT_TOKENS;
 constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins (mbarrier try_wait / flags)
 
@@ -90,6 +88,7 @@ struct BatchDev {
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
+    const uint64_t *recip;       // [kMaxSentTokens + 1]: ceil(2^48 / m), 0 for m = 0
     int32_t *counters;           // [8] work-queue heads
     int32_t *err;                // error word (0 = fine)
     // outputs

@@ -44,11 +44,6 @@ constexpr uint32_t kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t hmul(int32_t key) { return (uint32_t)key * 0x9E3779B1u; }
 
-__device__ __forceinline__ uint32_t hmul64(unsigned long long key)
-{
-    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32);
-}
-
 __device__ __forceinline__ int ceil_log2(int x)
 {
     int l = 0;
@@ -56,14 +51,10 @@ __device__ __forceinline__ int ceil_log2(int x)
     return l;
 }
 
-// ceil(2^48 / m) for 1 <= m < 2^16, 0 for m == 0.  For every 0 <= x <= m,
-// floor(x * 65536 / m) == (x * K) >> 32: the scaled reciprocal errs by less
-// than x / 2^32 <= 1/m, which cannot carry the quotient past an integer.
-__device__ __forceinline__ uint64_t recip48(uint32_t m)
-{
-    return m ? ((1ull << 48) + m - 1) / m : 0ull;
-}
-
+// floor(x * 65536 / m) for 0 <= x <= m <= 1024, given K = ceil(2^48 / m)
+// (the host-built reciprocal table; K = 0 for m = 0): the scaled reciprocal
+// errs by less than x / 2^32 <= 1/m, which cannot carry the quotient past an
+// integer.
 __device__ __forceinline__ uint32_t mul_q16(uint32_t x, uint64_t K)
 {
     return (uint32_t)(((uint64_t)x * K) >> 32);
@@ -186,18 +177,6 @@ __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__
 // Open addressing, linear probing; callers keep the load factor <= 1/2, so
 // every probe sequence meets an empty slot.
 
-__device__ __forceinline__ bool set_insert64(unsigned long long *tab, int log2, unsigned long long key)
-{
-    const uint32_t mask = (1u << log2) - 1u;
-    uint32_t h = hmul64(key) >> (32 - log2);
-    for (;;) {
-        const unsigned long long old = atomicCAS(&tab[h], ~0ull, key);
-        if (old == ~0ull) return true;
-        if (old == key) return false;
-        h = (h + 1) & mask;
-    }
-}
-
 __device__ __forceinline__ int slot_of(int32_t *keys, int log2, int32_t key)
 {
     const uint32_t mask = (1u << log2) - 1u;
@@ -247,31 +226,25 @@ __global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent,
 // ---------------------------------------------------------------- k_score
 
 constexpr int kSW = 4;   // warps per CTA
+constexpr int kPrepTok = 512;            // tokens (and translations) per preparation round
 
-struct PrepArea {
-    unsigned long long key[kPrepSlots];   // (token | translation) << 5 | row
-    int2 grp[kPrepCap];                   // (token, row) then (off << 6 | cnt, row | pos << 5)
-};
-
-struct ColArea {
-    int32_t keys[kColHashSlots];
-    uint32_t occ[kColHashSlots];
-    int32_t tok[2][kColTokCap + 8];       // TMA staging of two column blocks
-};
-
+// Per-warp shared memory.  One open-addressed table (tabk keys, tabv 32-bit
+// masks) serves, at different times: the row preparation (token -> mask of
+// the rows holding it; translation -> mask of the rows whose U_i holds it)
+// and the column blocks (target token -> mask of the columns holding it).
+// tok[] stages tokens by TMA; during the preparation tok[1] holds the group
+// list (token, row) -> (off << 6 | cnt, row | pos << 5).
 struct alignas(16) ScoreWarpSmem {
-    union {
-        PrepArea prep;
-        ColArea col;
-    } u;
+    int32_t tabk[kColHashSlots];
+    uint32_t tabv[kColHashSlots];
+    int32_t tok[2][kColTokCap + 8];          // TMA staging
     unsigned long long bar[2];
     int32_t soff[2][33];
     uint64_t Km[32];        // reciprocal of m_j
     uint64_t KL[32];        // reciprocal of L'_j
     int32_t Lt[32];
-    int32_t mcnt[32];
     int32_t rtok[33];
-    int32_t rcnt[32], recnt[32], rU[32];
+    int32_t recnt[32], rU[32];
     int32_t ngrp;
 };
 
@@ -306,6 +279,27 @@ __device__ __forceinline__ void add8(uint32_t (&P)[NPL], const uint32_t (&x)[8])
     }
 }
 
+// Counts of columns 8m .. 8m+7 from eight bit planes: gather byte m of every
+// plane into a 64-bit 8 x 8 bit matrix (row k = plane k) and transpose it;
+// byte c of (lo, hi) is then the count of column 8m + c.
+__device__ __forceinline__ void planes_to_bytes(const uint32_t (&P)[8], int m, uint32_t &lo,
+                                                uint32_t &hi)
+{
+    const uint32_t sel = (uint32_t)m | ((uint32_t)(m + 4) << 4);
+    const uint32_t t01 = __byte_perm(P[0], P[1], sel), t23 = __byte_perm(P[2], P[3], sel);
+    const uint32_t t45 = __byte_perm(P[4], P[5], sel), t67 = __byte_perm(P[6], P[7], sel);
+    lo = __byte_perm(t01, t23, 0x5410);
+    hi = __byte_perm(t45, t67, 0x5410);
+    uint32_t t;
+    t = (lo ^ (lo >> 7)) & 0x00AA00AAu;  lo ^= t ^ (t << 7);
+    t = (hi ^ (hi >> 7)) & 0x00AA00AAu;  hi ^= t ^ (t << 7);
+    t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo ^= t ^ (t << 14);
+    t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi ^= t ^ (t << 14);
+    t = (lo ^ (hi << 4)) & 0xF0F0F0F0u;
+    lo ^= t;
+    hi ^= t >> 4;
+}
+
 template <int NPL>
 __device__ __forceinline__ uint32_t plane_value(const uint32_t (&P)[NPL], int col)
 {
@@ -315,15 +309,32 @@ __device__ __forceinline__ uint32_t plane_value(const uint32_t (&P)[NPL], int co
     return v;
 }
 
+__device__ __forceinline__ int32_t cell_score(uint32_t a, uint32_t bb, uint64_t Km, uint64_t Ks,
+                                              int Ls, int Lt, uint64_t KLs, uint64_t KLt)
+{
+    const uint32_t q_t = mul_q16(a, Km);
+    const uint32_t q_s = mul_q16(bb, Ks);
+    uint32_t q_l;
+    if (Ls == 0 && Lt == 0) {
+        q_l = 65536u;
+    } else {
+        const uint32_t lmin = (uint32_t)min(Ls, Lt);
+        q_l = mul_q16(lmin, Ls >= Lt ? KLs : KLt);
+    }
+    const uint32_t h = (q_t + q_s) >> 1;
+    // (49152 * h + 16384 * q_l) >> 16 == (3h + q_l) >> 2
+    return (int32_t)((3u * h + q_l) >> 2);
+}
+
 // Accumulate the overlap counts of one column block and score its cells
 // into row `lane` of the score tiles (mrow points at column tile 0).
+// NPL <= 8: bit planes are turned into byte counts by 8 x 8 transposes.
 template <int NPL>
 __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, const uint32_t *el,
                                             int n_elem, int nE8, int ncols, bool row_ok,
                                             uint64_t Ks, uint64_t KLs, int Ls, int32_t *mrow,
                                             int c0)
 {
-    const ColArea &cs = sm.u.col;
     uint32_t A[NPL], B[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) A[k] = B[k] = 0u;
@@ -345,7 +356,7 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
         for (int q = 0; q < 8; ++q) {
             const bool ok = (e0 + q) < n_elem;
             const uint32_t e = ok ? ev[q] : 0u;
-            const uint32_t o = ok ? probe_occ(cs.keys, cs.occ, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
+            const uint32_t o = ok ? probe_occ(sm.tabk, sm.tabv, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
             xa[q] = (e & ELEM_FIRST) ? o : 0u;
             hit |= o;
             xb[q] = (e & ELEM_END) ? hit : 0u;
@@ -356,22 +367,35 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
     }
     if (!row_ok) return;
     int32_t out[32];
+    if constexpr (NPL <= 8) {
+        uint32_t A8[8], B8[8];
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-        const uint32_t a = plane_value<NPL>(A, jj);
-        const uint32_t bb = plane_value<NPL>(B, jj);
-        const uint32_t q_t = mul_q16(a, sm.Km[jj]);
-        const uint32_t q_s = mul_q16(bb, Ks);
-        const int Lt = sm.Lt[jj];
-        uint32_t q_l;
-        if (Ls == 0 && Lt == 0) {
-            q_l = 65536u;
-        } else {
-            const uint32_t lmin = (uint32_t)min(Ls, Lt);
-            q_l = mul_q16(lmin, Ls >= Lt ? KLs : sm.KL[jj]);
+        for (int k = 0; k < 8; ++k) {
+            A8[k] = k < NPL ? A[k] : 0u;
+            B8[k] = k < NPL ? B[k] : 0u;
         }
-        const uint32_t h = (q_t + q_s) >> 1;
-        out[jj] = (int32_t)((3u * h + q_l) >> 2);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (8 * m < ncols) {
+                uint32_t alo, ahi, blo, bhi;
+                planes_to_bytes(A8, m, alo, ahi);
+                planes_to_bytes(B8, m, blo, bhi);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int jj = 8 * m + c;
+                    const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
+                    const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
+                    out[jj] = cell_score(a, bb, sm.Km[jj], Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            if (jj < ncols)
+                out[jj] = cell_score(plane_value<NPL>(A, jj), plane_value<NPL>(B, jj), sm.Km[jj], Ks,
+                                     Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+        }
     }
     if (ncols == 32 && (c0 & 31) == 0) {
         // one whole row of one tile: eight 16-byte stores
@@ -390,10 +414,30 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
     }
 }
 
+// Stage tokens [tok0, tok0 + ntok) into dst with a TMA bulk copy (the bulk
+// part is 16-byte aligned; the few tokens past the last 16-byte boundary of
+// the token array are copied by lanes).  Returns the offset of tok0 in dst.
+__device__ __forceinline__ int stage_tokens(const BatchDev &b, int32_t *dst,
+                                            unsigned long long *bar, int64_t tok0, int ntok,
+                                            int lane)
+{
+    const int64_t a0 = tok0 & ~(int64_t)3;
+    const int64_t end = tok0 + ntok;
+    const int64_t a1 = min((end + 3) & ~(int64_t)3, b.n_tok & ~(int64_t)3);
+    const uint32_t bytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        mbar_expect_tx(bar, bytes);
+        if (bytes) bulk_g2s(dst, b.tokens + a0, bytes, bar);
+    }
+    for (int64_t p = max(a1, a0) + lane; p < end; p += 32) dst[p - a0] = b.tokens[p];
+    return (int)(tok0 - a0);
+}
+
 // Plan the column block starting at c0: widest run of <= 32 target sentences
-// whose tokens fit the table; stage its tokens with a TMA bulk copy into
-// buffer `buf` (the few tokens past the last 16-byte boundary of the token
-// array are copied by lanes).  Returns ncols (>= 1, or 0 on bad offsets).
+// whose tokens fit the table; stage its tokens into buffer `buf`.
+// Returns ncols (>= 1, or 0 on bad offsets).
 __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, int buf,
                                           int64_t tcol0, int c0, int T, int lane, int &ntok,
                                           int &lead)
@@ -406,22 +450,18 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, 
     ntok = __shfl_sync(kFull, cum, ncols - 1);
     if (lane < ncols) sm.soff[buf][lane + 1] = cum;
     if (lane == 0) sm.soff[buf][0] = 0;
-    const int64_t a0 = (int64_t)tok0 & ~(int64_t)3;
-    lead = (int)(tok0 - a0);
-    const int64_t end = (int64_t)tok0 + ntok;
-    const int64_t a1 = min((end + 3) & ~(int64_t)3, b.n_tok & ~(int64_t)3);
-    const uint32_t bytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
-    int32_t *dst = sm.u.col.tok[buf];
-    fence_proxy_async();
-    __syncwarp();
-    if (lane == 0) {
-        mbar_expect_tx(&sm.bar[buf], bytes);
-        if (bytes) bulk_g2s(dst, b.tokens + a0, bytes, &sm.bar[buf]);
-    }
-    // tail beyond the last full 16 bytes of the token array
-    const int64_t tail0 = max(a1, a0);
-    for (int64_t p = tail0 + lane; p < end; p += 32) dst[p - a0] = b.tokens[p];
+    lead = stage_tokens(b, sm.tok[buf], &sm.bar[buf], tok0, ntok, lane);
     return ncols;
+}
+
+__device__ __forceinline__ void warp_clear2(int32_t *keys, uint32_t *vals, int n, int lane)
+{
+    int4 *k4 = reinterpret_cast<int4 *>(keys);
+    uint4 *v4 = reinterpret_cast<uint4 *>(vals);
+    for (int q = lane; q < n / 4; q += 32) {
+        k4[q] = make_int4(-1, -1, -1, -1);
+        v4[q] = make_uint4(0, 0, 0, 0);
+    }
 }
 
 __global__ void __launch_bounds__(kSW * 32)
@@ -432,6 +472,7 @@ k_score(BatchDev b, DevDict d)
     const int wib = threadIdx.x >> 5;
     ScoreWarpSmem &sm = reinterpret_cast<ScoreWarpSmem *>(smem_raw)[wib];
     const int kmax = d.kmax;
+    const uint64_t *recip = b.recip;
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
@@ -462,45 +503,88 @@ k_score(BatchDev b, DevDict d)
         const int32_t tA = __shfl_sync(kFull, a_tok, 0);
         if (lane < nrows) sm.rtok[lane] = a_tok - tA;
         if (lane == nrows - 1) sm.rtok[nrows] = e_tok - tA;
-        sm.rcnt[lane] = 0;
         sm.recnt[lane] = 0;
         sm.rU[lane] = 0;
+        int n_i = 0;   // distinct tokens of this lane's row
         __syncwarp();
-        PrepArea &pa = sm.u.prep;
+        int2 *grp = reinterpret_cast<int2 *>(sm.tok[1]);   // <= kPrepTok groups
         for (int rA = 0; rA < nrows;) {
-            // rows [rA, rB) with at most kPrepCap tokens (one row always fits)
+            // rows [rA, rB) with at most kPrepTok tokens, or one longer row alone
             const int cand = rA + 1 + lane;
-            const bool okr = cand <= nrows && sm.rtok[cand] - sm.rtok[rA] <= kPrepCap;
-            const int rB = rA + __popc(__ballot_sync(kFull, okr));
+            const bool okr = cand <= nrows && sm.rtok[cand] - sm.rtok[rA] <= kPrepTok;
+            const int rB = rA + max(1, __popc(__ballot_sync(kFull, okr)));
             const int tbase = sm.rtok[rA];
             const int ntok = sm.rtok[rB] - tbase;
-            int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            for (int k = lane; k < (1 << lg); k += 32) pa.key[k] = ~0ull;
+            const int lead = stage_tokens(b, sm.tok[0], &sm.bar[0], (int64_t)tA + tbase, ntok, lane);
+            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+            warp_clear2(sm.tabk, sm.tabv, 1 << lg, lane);
             if (lane == 0) sm.ngrp = 0;
+            if (!mbar_wait(&sm.bar[0], parity[0], b.err)) return;
+            parity[0] ^= 1u;
             __syncwarp();
-            int32_t tk[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int k = q * 32 + lane;
-                tk[q] = k < ntok ? b.tokens[tA + tbase + k] : 0;
-            }
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int k = q * 32 + lane;
-                if (k < ntok) {
-                    const int32_t tok = tk[q];
+            const int32_t *stk = sm.tok[0] + lead;
+            if (ntok > kPrepTok) {
+                // one row of up to 1024 tokens: tokens spread over the lanes,
+                // translations written as they are found, first copies marked after
+                uint32_t *out = b.elems + elem_base(tA + tbase, s_first + rA, kmax);
+                int newc = 0;
+                for (int k = lane; k < ntok; k += 32) {
+                    const int32_t tok = stk[k];
                     if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    int lo = rA, hi = rB - 1;   // row: last r with rtok[r] <= tbase + k
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (sm.rtok[mid] <= tbase + k) lo = mid; else hi = mid - 1;
+                    const int slot = slot_of(sm.tabk, lg, tok & (int32_t)ELEM_TOKEN);
+                    if (!(atomicOr(&sm.tabv[slot], 1u) & 1u)) {
+                        ++newc;
+                        const int2 oc = dict_find(d, tok & (int32_t)ELEM_TOKEN);
+                        const int pos = atomicAdd(&sm.recnt[rA], oc.y);
+                        for (int q = 0; q < oc.y; ++q)
+                            out[pos + q] = (uint32_t)__ldg(&d.trans[oc.x + q]) |
+                                           (q == oc.y - 1 ? ELEM_END : 0u);
                     }
-                    const unsigned long long key =
-                        ((unsigned long long)(uint32_t)(tok & ELEM_TOKEN) << 5) | (uint32_t)lo;
-                    if (set_insert64(pa.key, lg, key)) {
+                }
+                const int nd = __reduce_add_sync(kFull, newc);
+                if (lane == rA) n_i = nd;
+                __syncwarp();
+                const int nel = sm.recnt[rA];
+                int firsts = 0;
+                if (nel <= kColHashSlots / 2) {
+                    const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
+                    warp_clear2(sm.tabk, sm.tabv, 1 << lgE, lane);
+                    __syncwarp();
+                    for (int e = lane; e < nel; e += 32) {
+                        const int32_t u = (int32_t)(out[e] & ELEM_TOKEN);
+                        const int slot = slot_of(sm.tabk, lgE, u);
+                        if (!(atomicOr(&sm.tabv[slot], 1u) & 1u)) {
+                            ++firsts;
+                            atomicOr(&out[e], ELEM_FIRST);
+                        }
+                    }
+                } else {
+                    for (int e = lane; e < nel; e += 32) {
+                        const uint32_t u = out[e] & ELEM_TOKEN;
+                        bool first = true;
+                        for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
+                        firsts += first;
+                        if (first) atomicOr(&out[e], ELEM_FIRST);
+                    }
+                }
+                const int f = __reduce_add_sync(kFull, firsts);
+                if (lane == 0) sm.rU[rA] = f;
+                __syncwarp();
+                rA = rB;
+                continue;
+            }
+            // distinct (row, token): the table maps a token to the mask of rows holding it
+            if (lane >= rA && lane < rB) {
+                const uint32_t bit = 1u << lane;
+                const int k1 = sm.rtok[lane + 1] - tbase;
+                for (int k = sm.rtok[lane] - tbase; k < k1; ++k) {
+                    const int32_t tok = stk[k];
+                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    const int slot = slot_of(sm.tabk, lg, tok & (int32_t)ELEM_TOKEN);
+                    if (!(atomicOr(&sm.tabv[slot], bit) & bit)) {
+                        ++n_i;
                         const int g = atomicAdd(&sm.ngrp, 1);
-                        pa.grp[g] = make_int2(tok & (int32_t)ELEM_TOKEN, lo);
-                        atomicAdd(&sm.rcnt[lo], 1);
+                        grp[g] = make_int2(tok & (int32_t)ELEM_TOKEN, lane);
                     }
                 }
             }
@@ -513,7 +597,7 @@ k_score(BatchDev b, DevDict d)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int g = g0 + q * 32 + lane;
-                    tok[q] = g < ng ? pa.grp[g].x : -1;
+                    tok[q] = g < ng ? grp[g].x : -1;
                     e[q] = make_int2(-1, 0);
                     if (g < ng) e[q] = __ldg(&d.slots[hmul(tok[q]) >> (32 - d.log2)]);
                 }
@@ -525,15 +609,16 @@ k_score(BatchDev b, DevDict d)
                         if (e[q].x == tok[q]) oc = make_int2((int32_t)((uint32_t)e[q].y >> 6), e[q].y & 63);
                         else if (e[q].x == -1) oc = make_int2(0, 0);
                         else oc = dict_find(d, tok[q]);
-                        const int r = pa.grp[g].y;
+                        const int r = grp[g].y;
                         const int pos = atomicAdd(&sm.recnt[r], oc.y);
-                        pa.grp[g] = make_int2((int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y),
-                                              r | (pos << 5));
+                        grp[g] = make_int2((int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y),
+                                           r | (pos << 5));
                     }
                 }
             }
             __syncwarp();
-            // translations, rows [eA, eB) with at most kPrepCap elements at once
+            // translations of rows [eA, eB), at most kPrepTok of them per round
+            // (or one row alone); the table maps a translation to a row mask
             for (int eA = rA; eA < rB;) {
                 const int v = (eA + lane < rB) ? sm.recnt[eA + lane] : 0;
                 int incl = v;
@@ -542,24 +627,24 @@ k_score(BatchDev b, DevDict d)
                     const int y = __shfl_up_sync(kFull, incl, o);
                     if (lane >= o) incl += y;
                 }
-                const bool fits = (eA + lane < rB) && incl <= kPrepCap;
-                int eB = eA + __popc(__ballot_sync(kFull, fits));
-                const bool slow = (eB == eA);   // one row with more than kPrepCap elements
-                if (slow) eB = eA + 1;
+                const bool fits = (eA + lane < rB) && incl <= kPrepTok;
+                const int eB = eA + max(1, __popc(__ballot_sync(kFull, fits)));
                 const int nel = __shfl_sync(kFull, incl, eB - eA - 1);
-                lg = max(6, ceil_log2(2 * max(nel, 1)));
-                if (!slow) {
-                    for (int k = lane; k < (1 << lg); k += 32) pa.key[k] = ~0ull;
+                const bool scan = nel > kColHashSlots / 2;   // only a single long row
+                const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
+                if (!scan) {
+                    warp_clear2(sm.tabk, sm.tabv, 1 << lgE, lane);
                     __syncwarp();
                 }
                 for (int g = lane; g < ng; g += 32) {
-                    const int2 gr = pa.grp[g];
+                    const int2 gr = grp[g];
                     const int r = gr.y & 31;
                     if (r < eA || r >= eB) continue;
                     const uint32_t pk = (uint32_t)gr.x;
                     const int off = (int)(pk >> 6), cnt = (int)(pk & 63u);
                     const int pos = gr.y >> 5;
                     uint32_t *out = b.elems + elem_base(tA + sm.rtok[r], s_first + r, kmax) + pos;
+                    const uint32_t bit = 1u << r;
                     int firsts = 0;
                     for (int k0 = 0; k0 < cnt; k0 += 4) {
                         int32_t u[4];
@@ -570,9 +655,10 @@ k_score(BatchDev b, DevDict d)
                             const int k = k0 + q;
                             if (k < cnt) {
                                 bool first = false;
-                                if (!slow)
-                                    first = set_insert64(pa.key, lg,
-                                                         ((unsigned long long)(uint32_t)u[q] << 5) | (uint32_t)r);
+                                if (!scan) {
+                                    const int slot = slot_of(sm.tabk, lgE, u[q]);
+                                    first = !(atomicOr(&sm.tabv[slot], bit) & bit);
+                                }
                                 firsts += first;
                                 out[k] = (uint32_t)u[q] | (first ? ELEM_FIRST : 0u) |
                                          (k == cnt - 1 ? ELEM_END : 0u);
@@ -582,7 +668,7 @@ k_score(BatchDev b, DevDict d)
                     if (firsts) atomicAdd(&sm.rU[r], firsts);
                 }
                 __syncwarp();
-                if (slow) {
+                if (scan) {
                     // mark first copies by scanning the written list
                     uint32_t *out = b.elems + elem_base(tA + sm.rtok[eA], s_first + eA, kmax);
                     int firsts = 0;
@@ -605,20 +691,20 @@ k_score(BatchDev b, DevDict d)
 
         // ------------------------------------------------ scoring
         const bool row_ok = lane < nrows;
-        const int n_i = row_ok ? sm.rcnt[lane] : 0;
         const int n_elem = row_ok ? sm.recnt[lane] : 0;
         const int nU = row_ok ? sm.rU[lane] : 0;
         const int Ls = row_ok ? e_tok - a_tok : 0;
+        if (!row_ok) n_i = 0;
         const uint32_t *el =
             row_ok ? b.elems + elem_base(a_tok, s_first + lane, kmax) : b.elems;
-        const uint64_t Ks = recip48((uint32_t)n_i);
-        const uint64_t KLs = recip48((uint32_t)Ls);
+        const uint64_t Ks = __ldg(&recip[n_i]);
+        const uint64_t KLs = __ldg(&recip[Ls]);
         const int nE8 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 7) & ~7u);
         const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
         const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
         int32_t *mrow = b.M + pp.m_off + (int64_t)(si.row0 >> 5) * TT * kTileElems +
                         (row_ok ? lane : 0) * kTile;
-        __syncwarp();   // the prep area is reused by the column tables below
+        __syncwarp();   // the preparation area is reused by the column tables below
 
         const int64_t tcol0 = pp.t0;
         int cur = 0;
@@ -631,43 +717,30 @@ k_score(BatchDev b, DevDict d)
                 pending = false;
                 break;
             }
+            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+            warp_clear2(sm.tabk, sm.tabv, 1 << lg, lane);
             if (!mbar_wait(&sm.bar[cur], parity[cur], b.err)) return;
             parity[cur] ^= 1u;
             pending = false;
             __syncwarp();
-            const int32_t *tokp = sm.u.col.tok[cur] + lead;
-            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            ColArea &ca = sm.u.col;
-            for (int k = lane; k < (1 << lg); k += 32) {
-                ca.keys[k] = -1;
-                ca.occ[k] = 0u;
-            }
-            sm.mcnt[lane] = 0;
-            __syncwarp();
-            for (int k = lane; k < ntok; k += 32) {
-                const int32_t tok = tokp[k];
-                if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                int lo = 0, hi = ncols - 1;   // column: last c with soff[c] <= k
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (sm.soff[cur][mid] <= k) lo = mid; else hi = mid - 1;
-                }
-                const int slot = slot_of(ca.keys, lg, (int32_t)(tok & ELEM_TOKEN));
-                const uint32_t bit = 1u << lo;
-                const uint32_t old = atomicOr(&ca.occ[slot], bit);
-                if (!(old & bit)) atomicAdd(&sm.mcnt[lo], 1);
-            }
-            __syncwarp();
-            int maxM = 0;
+            // lane c inserts the tokens of column c and counts its distinct ones
+            int m = 0, Lt = 0;
             if (lane < ncols) {
-                const int m = sm.mcnt[lane];
-                const int Lt = sm.soff[cur][lane + 1] - sm.soff[cur][lane];
-                sm.Km[lane] = recip48((uint32_t)m);
-                sm.KL[lane] = recip48((uint32_t)Lt);
+                const int k0 = sm.soff[cur][lane], k1 = sm.soff[cur][lane + 1];
+                const int32_t *tokp = sm.tok[cur] + lead;
+                const uint32_t bit = 1u << lane;
+                Lt = k1 - k0;
+                for (int k = k0; k < k1; ++k) {
+                    const int32_t tok = tokp[k];
+                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    const int slot = slot_of(sm.tabk, lg, tok & (int32_t)ELEM_TOKEN);
+                    m += !(atomicOr(&sm.tabv[slot], bit) & bit);
+                }
+                sm.Km[lane] = __ldg(&recip[m]);
+                sm.KL[lane] = __ldg(&recip[Lt]);
                 sm.Lt[lane] = Lt;
-                maxM = m;
             }
-            maxM = (int)__reduce_max_sync(kFull, (unsigned)maxM);
+            const int maxM = (int)__reduce_max_sync(kFull, (unsigned)m);
             // prefetch the next block into the other buffer while this one is scored
             const int nc0 = c0 + ncols;
             int n_ncols = 0, n_ntok = 0, n_lead = 0;
@@ -677,9 +750,7 @@ k_score(BatchDev b, DevDict d)
             }
             __syncwarp();
             const int bound = max(min(maxU, maxM), maxN);
-            if (bound < 64) {
-                score_block<6>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
-            } else if (bound < 256) {
+            if (bound < 256) {
                 score_block<8>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
             } else {
                 score_block<11>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);

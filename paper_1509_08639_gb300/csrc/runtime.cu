@@ -283,9 +283,10 @@ void pack_plan(const Plan &pl, const Layout &L, char *dst)
 }
 
 BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_t *sent_off,
-                       const int32_t *tokens, int32_t *sel)
+                       const int32_t *tokens, int32_t *sel, const uint64_t *recip)
 {
     BatchDev b{};
+    b.recip = recip;
     char *plan = base + L.plan;
     b.sent_off = sent_off;
     b.tokens = tokens;
@@ -425,6 +426,7 @@ struct mine_ctx {
     mine_config cfg{};
     Pool pool;
     void *pool_mem = nullptr;
+    uint64_t *recip = nullptr;         // device table of ceil(2^48 / m), m <= kMaxSentTokens
     std::vector<std::unique_ptr<Slot>> slots;
     std::mutex q_mu;
     std::condition_variable q_cv;      // pending work / stop
@@ -543,6 +545,14 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
     CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
     CK(cudaMalloc(&ctx->pool_mem, (size_t)c.device_budget_bytes));
+    {
+        // exact fixed-point reciprocals: floor(x * 65536 / m) == (x * K[m]) >> 32
+        // for 0 <= x <= m <= kMaxSentTokens (error of K below 1/m)
+        std::vector<uint64_t> K(kMaxSentTokens + 1, 0);
+        for (int m = 1; m <= kMaxSentTokens; ++m) K[m] = ((uint64_t(1) << 48) + m - 1) / m;
+        CK(cudaMalloc(&ctx->recip, sizeof(uint64_t) * K.size()));
+        CK(cudaMemcpy(ctx->recip, K.data(), sizeof(uint64_t) * K.size(), cudaMemcpyHostToDevice));
+    }
     ctx->pool.base = static_cast<char *>(ctx->pool_mem);
     ctx->pool.size = c.device_budget_bytes;
     ctx->pool.free_[0] = c.device_budget_bytes;
@@ -586,6 +596,7 @@ int mine_close(mine_ctx *ctx)
     }
     for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
     cudaFree(ctx->pool_mem);
+    cudaFree(ctx->recip);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
     return MINE_OK;
@@ -738,7 +749,7 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
     if (batch->n_tok > 0)
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
-    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr);
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip);
     if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return rc;
     char *ho = hp + align_up(L.plan_bytes, 64);
     int32_t *h_nw = reinterpret_cast<int32_t *>(ho);
@@ -809,7 +820,7 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
     char *base = static_cast<char *>(ctx->arena.p);
     CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
     BatchDev b = make_batchdev(pl, L, base, batch->sent_off, batch->tokens,
-                               reinterpret_cast<int32_t *>(sel));
+                               reinterpret_cast<int32_t *>(sel), ctx->recip);
     b.nw_score = nw_score;
     b.n_sel = n_sel;
     ctx->err_off = L.counters + 4 * 8;
@@ -844,7 +855,7 @@ int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mi
     char *base = static_cast<char *>(ctx->arena.p);
     cudaStream_t st = ctx->stream;
     CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
-    BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr);
+    BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr, ctx->recip);
     if (S > 0 && T > 0) {
         int32_t *mrow = reinterpret_cast<int32_t *>(base + L.Mrow);
         CK(cudaMemcpyAsync(mrow, M, 4 * (size_t)S * T, cudaMemcpyHostToDevice, st));
@@ -1142,7 +1153,7 @@ int launch_slot(mine_ctx *ctx, Slot &s)
     CK(cudaMemcpyAsync(base + L.plan, hi, L.plan_bytes, cudaMemcpyHostToDevice, s.st));
     CK(cudaMemcpyAsync(d_sent, h_sent, 4 * (n_sent + 1), cudaMemcpyHostToDevice, s.st));
     if (n_tok > 0) CK(cudaMemcpyAsync(d_tok, h_tok, 4 * n_tok, cudaMemcpyHostToDevice, s.st));
-    BatchDev b = make_batchdev(s.plan, L, base, d_sent, d_tok, nullptr);
+    BatchDev b = make_batchdev(s.plan, L, base, d_sent, d_tok, nullptr, ctx->recip);
     if ((rc = enqueue_kernels(ctx, b, dict, n_sent, n_tok, true, s.st))) return rc;
     char *ho = static_cast<char *>(s.pin_out.p);
     CK(cudaMemcpyAsync(ho + s.out_nw, b.nw_score, 4 * s.plan.R, cudaMemcpyDeviceToHost, s.st));
