@@ -177,28 +177,81 @@ __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__
 // Open addressing, linear probing; callers keep the load factor <= 1/2, so
 // every probe sequence meets an empty slot.
 
-__device__ __forceinline__ int slot_of(int32_t *keys, int log2, int32_t key)
+__device__ __forceinline__ int tab_slot_from(int2 *tab, uint32_t mask, uint32_t h, int32_t key)
 {
-    const uint32_t mask = (1u << log2) - 1u;
-    uint32_t h = hmul(key) >> (32 - log2);
     for (;;) {
-        const int32_t old = atomicCAS(&keys[h], -1, key);
-        if (old == -1 || old == key) return (int)h;
+        int32_t k = tab[h].x;
+        if (k == -1) {
+            k = atomicCAS(&tab[h].x, -1, key);
+            if (k == -1) return (int)h;
+        }
+        if (k == key) return (int)h;
         h = (h + 1) & mask;
     }
 }
 
-__device__ __forceinline__ uint32_t probe_occ(const int32_t *keys, const uint32_t *occ, int log2,
-                                              int32_t key)
+// Table entries are (key, 32-bit mask) pairs, so one 64-bit shared load
+// answers a probe.  Keys are written once (CAS from -1) and never change.
+__device__ __forceinline__ int tab_slot(int2 *tab, int log2, int32_t key)
 {
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t h = hmul(key) >> (32 - log2);
     for (;;) {
-        const int32_t k = keys[h];
-        if (k == key) return occ[h];
-        if (k == -1) return 0u;
+        int32_t k = tab[h].x;
+        if (k == -1) {
+            k = atomicCAS(&tab[h].x, -1, key);
+            if (k == -1) return (int)h;
+        }
+        if (k == key) return (int)h;
         h = (h + 1) & mask;
     }
+}
+
+// Slots of up to four keys with their first probes and CASes in flight together.
+__device__ __forceinline__ void tab_slot4(int2 *tab, int log2, const int32_t (&key)[4],
+                                          const bool (&ok)[4], int (&slot)[4])
+{
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t h[4];
+    int32_t k[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h[q] = hmul(key[q]) >> (32 - log2);
+        k[q] = ok[q] ? tab[h[q]].x : key[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (ok[q] && k[q] == -1) {
+            const int32_t o = atomicCAS(&tab[h[q]].x, -1, key[q]);
+            k[q] = (o == -1) ? key[q] : o;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (ok[q] && k[q] != key[q]) {
+            h[q] = (h[q] + 1) & mask;
+            h[q] = (uint32_t)tab_slot_from(tab, mask, h[q], key[q]);
+        }
+        slot[q] = (int)h[q];
+    }
+}
+
+__device__ __forceinline__ uint32_t probe_occ(const int2 *tab, int log2, int32_t key)
+{
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t h = hmul(key) >> (32 - log2);
+    for (;;) {
+        const int2 e = tab[h];
+        if (e.x == key) return (uint32_t)e.y;
+        if (e.x == -1) return 0u;
+        h = (h + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ void tab_clear(int2 *tab, int n, int lane)
+{
+    int4 *t4 = reinterpret_cast<int4 *>(tab);
+    for (int q = lane; q < n / 2; q += 32) t4[q] = make_int4(-1, 0, -1, 0);
 }
 
 // Element list of source sentence `sent` (first token at tok_off): 16-byte
@@ -228,15 +281,14 @@ __global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent,
 constexpr int kSW = 4;   // warps per CTA
 constexpr int kPrepTok = 512;            // tokens (and translations) per preparation round
 
-// Per-warp shared memory.  One open-addressed table (tabk keys, tabv 32-bit
-// masks) serves, at different times: the row preparation (token -> mask of
-// the rows holding it; translation -> mask of the rows whose U_i holds it)
-// and the column blocks (target token -> mask of the columns holding it).
-// tok[] stages tokens by TMA; during the preparation tok[1] holds the group
-// list (token, row) -> (off << 6 | cnt, row | pos << 5).
+// Per-warp shared memory.  One open-addressed table of (key, mask) entries
+// serves, at different times: the row preparation (token -> mask of the rows
+// holding it; translation -> mask of the rows whose U_i holds it) and the
+// column blocks (target token -> mask of the columns holding it).  tok[]
+// stages tokens by TMA; during the preparation tok[1] holds the group list
+// (token, row) -> (off << 6 | cnt, row | pos << 5).
 struct alignas(16) ScoreWarpSmem {
-    int32_t tabk[kColHashSlots];
-    uint32_t tabv[kColHashSlots];
+    int2 tab[kColHashSlots];
     int32_t tok[2][kColTokCap + 8];          // TMA staging
     unsigned long long bar[2];
     int32_t soff[2][33];
@@ -356,7 +408,7 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
         for (int q = 0; q < 8; ++q) {
             const bool ok = (e0 + q) < n_elem;
             const uint32_t e = ok ? ev[q] : 0u;
-            const uint32_t o = ok ? probe_occ(sm.tabk, sm.tabv, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
+            const uint32_t o = ok ? probe_occ(sm.tab, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
             xa[q] = (e & ELEM_FIRST) ? o : 0u;
             hit |= o;
             xb[q] = (e & ELEM_END) ? hit : 0u;
@@ -416,16 +468,19 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
 
 // Stage tokens [tok0, tok0 + ntok) into dst with a TMA bulk copy (the bulk
 // part is 16-byte aligned; the few tokens past the last 16-byte boundary of
-// the token array are copied by lanes).  Returns the offset of tok0 in dst.
+// the token array are copied by lanes, which sets `generic`).  A buffer that
+// generic stores wrote before gets a proxy fence first.  Returns the offset
+// of tok0 in dst.
 __device__ __forceinline__ int stage_tokens(const BatchDev &b, int32_t *dst,
                                             unsigned long long *bar, int64_t tok0, int ntok,
-                                            int lane)
+                                            int lane, bool &generic)
 {
     const int64_t a0 = tok0 & ~(int64_t)3;
     const int64_t end = tok0 + ntok;
     const int64_t a1 = min((end + 3) & ~(int64_t)3, b.n_tok & ~(int64_t)3);
     const uint32_t bytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
-    fence_proxy_async();
+    if (generic) fence_proxy_async();
+    generic = max(a1, a0) < end;
     __syncwarp();
     if (lane == 0) {
         mbar_expect_tx(bar, bytes);
@@ -440,7 +495,7 @@ __device__ __forceinline__ int stage_tokens(const BatchDev &b, int32_t *dst,
 // Returns ncols (>= 1, or 0 on bad offsets).
 __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, int buf,
                                           int64_t tcol0, int c0, int T, int lane, int &ntok,
-                                          int &lead)
+                                          int &lead, bool &generic)
 {
     const int32_t tok0 = b.sent_off[tcol0 + c0];
     int cum = 0x7fffffff;
@@ -450,19 +505,46 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, 
     ntok = __shfl_sync(kFull, cum, ncols - 1);
     if (lane < ncols) sm.soff[buf][lane + 1] = cum;
     if (lane == 0) sm.soff[buf][0] = 0;
-    lead = stage_tokens(b, sm.tok[buf], &sm.bar[buf], tok0, ntok, lane);
+    lead = stage_tokens(b, sm.tok[buf], &sm.bar[buf], tok0, ntok, lane, generic);
     return ncols;
 }
 
-__device__ __forceinline__ void warp_clear2(int32_t *keys, uint32_t *vals, int n, int lane)
+// Insert the keys key[lo..hi) of one lane (4 at a time, first probes and
+// atomics in flight together) with `bit` into the table; returns how many
+// set their bit for the first time.  When `grp` is given, each first-time
+// key is appended to it with `tag`.
+__device__ __forceinline__ int tab_insert_run(int2 *tab, int lg, const int32_t *keys, int lo,
+                                             int hi, uint32_t bit, int32_t *err, int2 *grp,
+                                             int32_t *ngrp, int tag)
 {
-    int4 *k4 = reinterpret_cast<int4 *>(keys);
-    uint4 *v4 = reinterpret_cast<uint4 *>(vals);
-    for (int q = lane; q < n / 4; q += 32) {
-        k4[q] = make_int4(-1, -1, -1, -1);
-        v4[q] = make_uint4(0, 0, 0, 0);
+    int fresh = 0;
+    for (int k0 = lo; k0 < hi; k0 += 4) {
+        int32_t key[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ok[q] = k0 + q < hi;
+            const int32_t t = ok[q] ? keys[k0 + q] : 0;
+            if ((uint32_t)t > ELEM_TOKEN) atomicCAS(err, 0, ERR_BAD_TOKEN);
+            key[q] = t & (int32_t)ELEM_TOKEN;
+        }
+        int slot[4];
+        tab_slot4(tab, lg, key, ok, slot);
+        uint32_t old[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) old[q] = ok[q] ? atomicOr((uint32_t *)&tab[slot[q]].y, bit) : bit;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!(old[q] & bit)) {
+                ++fresh;
+                if (grp) grp[atomicAdd(ngrp, 1)] = make_int2(key[q], tag);
+            }
+        }
     }
+    return fresh;
 }
+
+constexpr int kPrepElem = kColHashSlots / 2;   // translations per dedupe round
 
 __global__ void __launch_bounds__(kSW * 32)
 k_score(BatchDev b, DevDict d)
@@ -480,6 +562,7 @@ k_score(BatchDev b, DevDict d)
     }
     __syncwarp();
     uint32_t parity[2] = {0u, 0u};
+    bool generic[2] = {false, false};   // generic stores wrote into tok[buf] since its last copy
     if (*(volatile int32_t *)b.err) return;
 
     for (;;) {
@@ -493,6 +576,13 @@ k_score(BatchDev b, DevDict d)
         const int TT = (T + 31) >> 5;
         const int nrows = min(32, pp.S - si.row0);
         const int64_t s_first = (int64_t)pp.s0 + si.row0;
+        const int64_t tcol0 = pp.t0;
+        // the first column block's offsets, fetched early
+        int32_t ctok0 = 0, ccum = 0x7fffffff;
+        if (T > 0) {
+            ctok0 = b.sent_off[tcol0];
+            if (lane < T) ccum = b.sent_off[tcol0 + lane + 1];
+        }
 
         // ------------------------------------------------ row preparation
         int32_t a_tok = 0, e_tok = 0;
@@ -515,9 +605,10 @@ k_score(BatchDev b, DevDict d)
             const int rB = rA + max(1, __popc(__ballot_sync(kFull, okr)));
             const int tbase = sm.rtok[rA];
             const int ntok = sm.rtok[rB] - tbase;
-            const int lead = stage_tokens(b, sm.tok[0], &sm.bar[0], (int64_t)tA + tbase, ntok, lane);
+            const int lead =
+                stage_tokens(b, sm.tok[0], &sm.bar[0], (int64_t)tA + tbase, ntok, lane, generic[0]);
             const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            warp_clear2(sm.tabk, sm.tabv, 1 << lg, lane);
+            tab_clear(sm.tab, 1 << lg, lane);
             if (lane == 0) sm.ngrp = 0;
             if (!mbar_wait(&sm.bar[0], parity[0], b.err)) return;
             parity[0] ^= 1u;
@@ -531,8 +622,8 @@ k_score(BatchDev b, DevDict d)
                 for (int k = lane; k < ntok; k += 32) {
                     const int32_t tok = stk[k];
                     if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    const int slot = slot_of(sm.tabk, lg, tok & (int32_t)ELEM_TOKEN);
-                    if (!(atomicOr(&sm.tabv[slot], 1u) & 1u)) {
+                    const int slot = tab_slot(sm.tab, lg, tok & (int32_t)ELEM_TOKEN);
+                    if (!(atomicOr((uint32_t *)&sm.tab[slot].y, 1u) & 1u)) {
                         ++newc;
                         const int2 oc = dict_find(d, tok & (int32_t)ELEM_TOKEN);
                         const int pos = atomicAdd(&sm.recnt[rA], oc.y);
@@ -546,14 +637,14 @@ k_score(BatchDev b, DevDict d)
                 __syncwarp();
                 const int nel = sm.recnt[rA];
                 int firsts = 0;
-                if (nel <= kColHashSlots / 2) {
+                if (nel <= kPrepElem) {
                     const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
-                    warp_clear2(sm.tabk, sm.tabv, 1 << lgE, lane);
+                    tab_clear(sm.tab, 1 << lgE, lane);
                     __syncwarp();
                     for (int e = lane; e < nel; e += 32) {
                         const int32_t u = (int32_t)(out[e] & ELEM_TOKEN);
-                        const int slot = slot_of(sm.tabk, lgE, u);
-                        if (!(atomicOr(&sm.tabv[slot], 1u) & 1u)) {
+                        const int slot = tab_slot(sm.tab, lgE, u);
+                        if (!(atomicOr((uint32_t *)&sm.tab[slot].y, 1u) & 1u)) {
                             ++firsts;
                             atomicOr(&out[e], ELEM_FIRST);
                         }
@@ -574,20 +665,10 @@ k_score(BatchDev b, DevDict d)
                 continue;
             }
             // distinct (row, token): the table maps a token to the mask of rows holding it
-            if (lane >= rA && lane < rB) {
-                const uint32_t bit = 1u << lane;
-                const int k1 = sm.rtok[lane + 1] - tbase;
-                for (int k = sm.rtok[lane] - tbase; k < k1; ++k) {
-                    const int32_t tok = stk[k];
-                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    const int slot = slot_of(sm.tabk, lg, tok & (int32_t)ELEM_TOKEN);
-                    if (!(atomicOr(&sm.tabv[slot], bit) & bit)) {
-                        ++n_i;
-                        const int g = atomicAdd(&sm.ngrp, 1);
-                        grp[g] = make_int2(tok & (int32_t)ELEM_TOKEN, lane);
-                    }
-                }
-            }
+            if (lane >= rA && lane < rB)
+                n_i += tab_insert_run(sm.tab, lg, stk, sm.rtok[lane] - tbase,
+                                      sm.rtok[lane + 1] - tbase, 1u << lane, b.err, grp,
+                                      &sm.ngrp, lane);
             __syncwarp();
             const int ng = sm.ngrp;
             // dictionary lookups, four per lane in flight
@@ -617,7 +698,7 @@ k_score(BatchDev b, DevDict d)
                 }
             }
             __syncwarp();
-            // translations of rows [eA, eB), at most kPrepTok of them per round
+            // translations of rows [eA, eB), at most kPrepElem of them per round
             // (or one row alone); the table maps a translation to a row mask
             for (int eA = rA; eA < rB;) {
                 const int v = (eA + lane < rB) ? sm.recnt[eA + lane] : 0;
@@ -627,13 +708,13 @@ k_score(BatchDev b, DevDict d)
                     const int y = __shfl_up_sync(kFull, incl, o);
                     if (lane >= o) incl += y;
                 }
-                const bool fits = (eA + lane < rB) && incl <= kPrepTok;
+                const bool fits = (eA + lane < rB) && incl <= kPrepElem;
                 const int eB = eA + max(1, __popc(__ballot_sync(kFull, fits)));
                 const int nel = __shfl_sync(kFull, incl, eB - eA - 1);
-                const bool scan = nel > kColHashSlots / 2;   // only a single long row
+                const bool scan = nel > kPrepElem;   // only a single row with many translations
                 const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
                 if (!scan) {
-                    warp_clear2(sm.tabk, sm.tabv, 1 << lgE, lane);
+                    tab_clear(sm.tab, 1 << lgE, lane);
                     __syncwarp();
                 }
                 for (int g = lane; g < ng; g += 32) {
@@ -648,17 +729,25 @@ k_score(BatchDev b, DevDict d)
                     int firsts = 0;
                     for (int k0 = 0; k0 < cnt; k0 += 4) {
                         int32_t u[4];
+                        bool ok[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) u[q] = (k0 + q < cnt) ? __ldg(&d.trans[off + k0 + q]) : 0;
+                        for (int q = 0; q < 4; ++q) {
+                            ok[q] = k0 + q < cnt;
+                            u[q] = ok[q] ? __ldg(&d.trans[off + k0 + q]) : 0;
+                        }
+                        uint32_t old[4] = {bit, bit, bit, bit};
+                        if (!scan) {
+                            int slot[4];
+                            tab_slot4(sm.tab, lgE, u, ok, slot);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (ok[q]) old[q] = atomicOr((uint32_t *)&sm.tab[slot[q]].y, bit);
+                        }
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int k = k0 + q;
-                            if (k < cnt) {
-                                bool first = false;
-                                if (!scan) {
-                                    const int slot = slot_of(sm.tabk, lgE, u[q]);
-                                    first = !(atomicOr(&sm.tabv[slot], bit) & bit);
-                                }
+                            if (ok[q]) {
+                                const bool first = !(old[q] & bit);
                                 firsts += first;
                                 out[k] = (uint32_t)u[q] | (first ? ELEM_FIRST : 0u) |
                                          (k == cnt - 1 ? ELEM_END : 0u);
@@ -687,6 +776,7 @@ k_score(BatchDev b, DevDict d)
             }
             rA = rB;
         }
+        generic[1] = true;   // the group list lived in tok[1]
         __syncwarp();
 
         // ------------------------------------------------ scoring
@@ -704,12 +794,21 @@ k_score(BatchDev b, DevDict d)
         const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
         int32_t *mrow = b.M + pp.m_off + (int64_t)(si.row0 >> 5) * TT * kTileElems +
                         (row_ok ? lane : 0) * kTile;
-        __syncwarp();   // the preparation area is reused by the column tables below
+        __syncwarp();   // the preparation table is reused by the column tables below
 
-        const int64_t tcol0 = pp.t0;
         int cur = 0;
-        int c0 = 0, ntok = 0, lead = 0;
-        int ncols = T > 0 ? plan_block(b, sm, 0, tcol0, 0, T, lane, ntok, lead) : 0;
+        int c0 = 0, ntok = 0, lead = 0, ncols = 0;
+        if (T > 0) {
+            // first block from the offsets fetched at the start of the item
+            const int cum = ccum - ctok0;
+            ncols = __popc(__ballot_sync(kFull, lane < T && cum <= kColTokCap));
+            if (ncols > 0) {
+                ntok = __shfl_sync(kFull, cum, ncols - 1);
+                if (lane < ncols) sm.soff[0][lane + 1] = cum;
+                if (lane == 0) sm.soff[0][0] = 0;
+                lead = stage_tokens(b, sm.tok[0], &sm.bar[0], ctok0, ntok, lane, generic[0]);
+            }
+        }
         bool pending = T > 0 && ncols > 0;   // a copy in flight into buffer `cur`
         while (c0 < T) {
             if (ncols == 0) {
@@ -718,36 +817,28 @@ k_score(BatchDev b, DevDict d)
                 break;
             }
             const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            warp_clear2(sm.tabk, sm.tabv, 1 << lg, lane);
+            tab_clear(sm.tab, 1 << lg, lane);
+            // prefetch the next block into the other buffer while this one is built and scored
+            const int nc0 = c0 + ncols;
+            int n_ncols = 0, n_ntok = 0, n_lead = 0;
+            if (nc0 < T)
+                n_ncols = plan_block(b, sm, cur ^ 1, tcol0, nc0, T, lane, n_ntok, n_lead,
+                                     generic[cur ^ 1]);
             if (!mbar_wait(&sm.bar[cur], parity[cur], b.err)) return;
             parity[cur] ^= 1u;
-            pending = false;
             __syncwarp();
             // lane c inserts the tokens of column c and counts its distinct ones
-            int m = 0, Lt = 0;
+            int m = 0;
             if (lane < ncols) {
                 const int k0 = sm.soff[cur][lane], k1 = sm.soff[cur][lane + 1];
-                const int32_t *tokp = sm.tok[cur] + lead;
-                const uint32_t bit = 1u << lane;
-                Lt = k1 - k0;
-                for (int k = k0; k < k1; ++k) {
-                    const int32_t tok = tokp[k];
-                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    const int slot = slot_of(sm.tabk, lg, tok & (int32_t)ELEM_TOKEN);
-                    m += !(atomicOr(&sm.tabv[slot], bit) & bit);
-                }
+                const int Lt = k1 - k0;
+                m = tab_insert_run(sm.tab, lg, sm.tok[cur] + lead, k0, k1, 1u << lane, b.err,
+                                   nullptr, nullptr, 0);
                 sm.Km[lane] = __ldg(&recip[m]);
                 sm.KL[lane] = __ldg(&recip[Lt]);
                 sm.Lt[lane] = Lt;
             }
             const int maxM = (int)__reduce_max_sync(kFull, (unsigned)m);
-            // prefetch the next block into the other buffer while this one is scored
-            const int nc0 = c0 + ncols;
-            int n_ncols = 0, n_ntok = 0, n_lead = 0;
-            if (nc0 < T) {
-                n_ncols = plan_block(b, sm, cur ^ 1, tcol0, nc0, T, lane, n_ntok, n_lead);
-                pending = n_ncols > 0;
-            }
             __syncwarp();
             const int bound = max(min(maxU, maxM), maxN);
             if (bound < 256) {
@@ -756,6 +847,7 @@ k_score(BatchDev b, DevDict d)
                 score_block<11>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
             }
             __syncwarp();
+            pending = nc0 < T && n_ncols > 0;
             c0 = nc0;
             ncols = n_ncols;
             ntok = n_ntok;
@@ -830,8 +922,7 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
         const int64_t qp_base = has_above ? (int64_t)((s - 1) / wp.W) * T : 0;
         const int64_t qm_base = (int64_t)gen * T;
         uint32_t *cr = codes + (int64_t)(row - 1) * CW;
-        // first tiles of this stripe
-        fence_proxy_async();
+        // first tiles of this stripe (buffers only ever read by generic loads)
         __syncwarp();
         if (lane == 0) {
             for (int k = 0; k < kMBuf && k < TT; ++k) {
@@ -854,7 +945,6 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
             if (c >= 2 && c + 1 < TT) {
                 // tile c-2 is no longer read: refill its buffer with tile c+1
                 const int bb = (c + 1) % kMBuf;
-                fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
                     mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
