@@ -109,7 +109,9 @@ typedef struct {
 const char *mine_last_error(void);
 
 /* Open a context: creates streams, the serving thread and the device arena.
- * cfg may be NULL (defaults).  *out receives the context. */
+ * Besides the budget pool, the context keeps about 40 MB of device scratch
+ * (tables for sentences longer than 512 tokens) per concurrently running
+ * batch.  cfg may be NULL (defaults).  *out receives the context. */
 int mine_open(const mine_config *cfg, mine_ctx **out);
 
 /* Drain every request still in flight, free all dictionaries and device

@@ -25,10 +25,14 @@ constexpr int32_t ERR_TIMEOUT = 4;          // a bounded device wait ran out
 constexpr int kWarp = 32;
 constexpr int kTile = 32;                   // score matrices are stored as 32 x 32 tiles
 constexpr int kTileElems = kTile * kTile;
-constexpr int kColHashSlots = 2048;         // per-warp target-token table of a column block
+constexpr int kColHashSlots = 1024;         // per-warp target-token table of a column block
 constexpr int kColTokCap = kColHashSlots / 2;   // tokens per column block at most
 constexpr int kMaxSentTokens = MINE_MAX_SENT_TOKENS;
 constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins (mbarrier try_wait / flags)
+constexpr int kScoreWarps = 4;              // warps per CTA of the score kernel
+constexpr int kScoreCtasPerSm = 4;          // its resident CTAs per SM (grid = SMs x this)
+// per-warp global table of the score kernel: 2 * kMaxSentTokens (key, mask) entries
+constexpr int64_t kScoreScratchPerWarp = 2 * (int64_t)kMaxSentTokens * 8;
 
 // Resident dictionary: open-addressed table of (key, off << 6 | cnt), linear
 // probing, hash = key * 0x9E3779B1 >> (32 - log2).  Empty key = -1.
@@ -89,6 +93,7 @@ struct BatchDev {
     uint32_t *codes;             // directions
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
     const uint64_t *recip;       // [kMaxSentTokens + 1]: ceil(2^48 / m), 0 for m = 0
+    int2 *gscratch;              // per-warp tables for sentences longer than the shared ones
     int32_t *counters;           // [8] work-queue heads
     int32_t *err;                // error word (0 = fine)
     // outputs

@@ -278,8 +278,11 @@ __global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent,
 
 // ---------------------------------------------------------------- k_score
 
-constexpr int kSW = 4;   // warps per CTA
-constexpr int kPrepTok = 512;            // tokens (and translations) per preparation round
+constexpr int kSW = kScoreWarps;
+// tokens per preparation round: the group list (one entry per distinct
+// (row, token)) lives in the second staging buffer, which holds
+// (kColTokCap + 8) / 2 int2 entries
+constexpr int kPrepTok = kColTokCap / 2;
 
 // Per-warp shared memory.  One open-addressed table of (key, mask) entries
 // serves, at different times: the row preparation (token -> mask of the rows
@@ -382,7 +385,8 @@ __device__ __forceinline__ int32_t cell_score(uint32_t a, uint32_t bb, uint64_t 
 // into row `lane` of the score tiles (mrow points at column tile 0).
 // NPL <= 8: bit planes are turned into byte counts by 8 x 8 transposes.
 template <int NPL>
-__device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, const uint32_t *el,
+__device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 *tab, int lg,
+                                            const uint32_t *el,
                                             int n_elem, int nE8, int ncols, bool row_ok,
                                             uint64_t Ks, uint64_t KLs, int Ls, int32_t *mrow,
                                             int c0)
@@ -408,7 +412,7 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
         for (int q = 0; q < 8; ++q) {
             const bool ok = (e0 + q) < n_elem;
             const uint32_t e = ok ? ev[q] : 0u;
-            const uint32_t o = ok ? probe_occ(sm.tab, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
+            const uint32_t o = ok ? probe_occ(tab, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
             xa[q] = (e & ELEM_FIRST) ? o : 0u;
             hit |= o;
             xb[q] = (e & ELEM_END) ? hit : 0u;
@@ -418,7 +422,7 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
         add8<NPL>(B, xb);
     }
     if (!row_ok) return;
-    int32_t out[32];
+    const bool whole = ncols == 32 && (c0 & 31) == 0;   // one whole row of one tile
     if constexpr (NPL <= 8) {
         uint32_t A8[8], B8[8];
 #pragma unroll
@@ -432,36 +436,36 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, int lg, con
                 uint32_t alo, ahi, blo, bhi;
                 planes_to_bytes(A8, m, alo, ahi);
                 planes_to_bytes(B8, m, blo, bhi);
+                int32_t v[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int jj = 8 * m + c;
                     const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
                     const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
-                    out[jj] = cell_score(a, bb, sm.Km[jj], Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+                    v[c] = cell_score(a, bb, sm.Km[jj], Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+                }
+                if (whole) {
+                    int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
+                    dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+                    dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int jj = 8 * m + c;
+                        if (jj < ncols) {
+                            const int col = c0 + jj;
+                            mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v[c];
+                        }
+                    }
                 }
             }
         }
     } else {
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-            if (jj < ncols)
-                out[jj] = cell_score(plane_value<NPL>(A, jj), plane_value<NPL>(B, jj), sm.Km[jj], Ks,
-                                     Ls, sm.Lt[jj], KLs, sm.KL[jj]);
-        }
-    }
-    if (ncols == 32 && (c0 & 31) == 0) {
-        // one whole row of one tile: eight 16-byte stores
-        int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            dst[q] = make_int4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-    } else {
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-            if (jj < ncols) {
-                const int c = c0 + jj;
-                mrow[(int64_t)(c >> 5) * kTileElems + (c & 31)] = out[jj];
-            }
+        for (int jj = 0; jj < ncols; ++jj) {
+            const int32_t v = cell_score(plane_value<NPL>(A, jj), plane_value<NPL>(B, jj), sm.Km[jj],
+                                         Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+            const int col = c0 + jj;
+            mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v;
         }
     }
 }
@@ -493,19 +497,28 @@ __device__ __forceinline__ int stage_tokens(const BatchDev &b, int32_t *dst,
 // Plan the column block starting at c0: widest run of <= 32 target sentences
 // whose tokens fit the table; stage its tokens into buffer `buf`.
 // Returns ncols (>= 1, or 0 on bad offsets).
+// A single column longer than kColTokCap becomes an unstaged block (staged =
+// false) whose tokens are read from global memory into the per-warp global
+// table.  tok0 receives the block's first token index.
 __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, int buf,
                                           int64_t tcol0, int c0, int T, int lane, int &ntok,
-                                          int &lead, bool &generic)
+                                          int &lead, bool &generic, bool &staged, int64_t &tok0)
 {
-    const int32_t tok0 = b.sent_off[tcol0 + c0];
+    tok0 = b.sent_off[tcol0 + c0];
     int cum = 0x7fffffff;
-    if (c0 + lane < T) cum = b.sent_off[tcol0 + c0 + lane + 1] - tok0;
-    const int ncols = __popc(__ballot_sync(kFull, cum <= kColTokCap));
-    if (ncols == 0) return 0;
+    if (c0 + lane < T) cum = b.sent_off[tcol0 + c0 + lane + 1] - (int32_t)tok0;
+    int ncols = __popc(__ballot_sync(kFull, cum <= kColTokCap));
+    staged = ncols > 0;
+    if (!staged) {
+        const int first = __shfl_sync(kFull, cum, 0);
+        if (c0 >= T || first < 0 || first > kMaxSentTokens) return 0;
+        ncols = 1;
+    }
     ntok = __shfl_sync(kFull, cum, ncols - 1);
     if (lane < ncols) sm.soff[buf][lane + 1] = cum;
     if (lane == 0) sm.soff[buf][0] = 0;
-    lead = stage_tokens(b, sm.tok[buf], &sm.bar[buf], tok0, ntok, lane, generic);
+    lead = 0;
+    if (staged) lead = stage_tokens(b, sm.tok[buf], &sm.bar[buf], tok0, ntok, lane, generic);
     return ncols;
 }
 
@@ -545,6 +558,39 @@ __device__ __forceinline__ int tab_insert_run(int2 *tab, int lg, const int32_t *
 }
 
 constexpr int kPrepElem = kColHashSlots / 2;   // translations per dedupe round
+static_assert(2 * kPrepTok <= kColTokCap + 8, "group list must fit the staging buffer");
+constexpr int kGTabSlots = 2 * kMaxSentTokens;   // per-warp global table for long sentences
+
+// Mark the first copy of every translation in out[0..nel) (one row) with
+// ELEM_FIRST, using the per-warp global table, or a scan when even that is
+// too small.  Returns the number of first copies (|U_i|).
+__device__ int mark_first_copies(uint32_t *out, int nel, int2 *gtab, int lane)
+{
+    int firsts = 0;
+    if (nel <= kGTabSlots / 2) {
+        const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
+        tab_clear(gtab, 1 << lgE, lane);
+        __syncwarp();
+        for (int e = lane; e < nel; e += 32) {
+            const int slot = tab_slot(gtab, lgE, (int32_t)(out[e] & ELEM_TOKEN));
+            if (!(atomicOr((uint32_t *)&gtab[slot].y, 1u) & 1u)) {
+                ++firsts;
+                atomicOr(&out[e], ELEM_FIRST);
+            }
+        }
+    } else {
+        for (int e = lane; e < nel; e += 32) {
+            const uint32_t u = out[e] & ELEM_TOKEN;
+            bool first = true;
+            for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
+            firsts += first;
+            if (first) atomicOr(&out[e], ELEM_FIRST);
+        }
+    }
+    const int f = __reduce_add_sync(kFull, firsts);
+    __syncwarp();
+    return f;
+}
 
 __global__ void __launch_bounds__(kSW * 32)
 k_score(BatchDev b, DevDict d)
@@ -553,6 +599,7 @@ k_score(BatchDev b, DevDict d)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     ScoreWarpSmem &sm = reinterpret_cast<ScoreWarpSmem *>(smem_raw)[wib];
+    int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * kSW + wib) * kGTabSlots;
     const int kmax = d.kmax;
     const uint64_t *recip = b.recip;
     if (lane == 0) {
@@ -577,12 +624,6 @@ k_score(BatchDev b, DevDict d)
         const int nrows = min(32, pp.S - si.row0);
         const int64_t s_first = (int64_t)pp.s0 + si.row0;
         const int64_t tcol0 = pp.t0;
-        // the first column block's offsets, fetched early
-        int32_t ctok0 = 0, ccum = 0x7fffffff;
-        if (T > 0) {
-            ctok0 = b.sent_off[tcol0];
-            if (lane < T) ccum = b.sent_off[tcol0 + lane + 1];
-        }
 
         // ------------------------------------------------ row preparation
         int32_t a_tok = 0, e_tok = 0;
@@ -605,25 +646,20 @@ k_score(BatchDev b, DevDict d)
             const int rB = rA + max(1, __popc(__ballot_sync(kFull, okr)));
             const int tbase = sm.rtok[rA];
             const int ntok = sm.rtok[rB] - tbase;
-            const int lead =
-                stage_tokens(b, sm.tok[0], &sm.bar[0], (int64_t)tA + tbase, ntok, lane, generic[0]);
-            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            tab_clear(sm.tab, 1 << lg, lane);
-            if (lane == 0) sm.ngrp = 0;
-            if (!mbar_wait(&sm.bar[0], parity[0], b.err)) return;
-            parity[0] ^= 1u;
-            __syncwarp();
-            const int32_t *stk = sm.tok[0] + lead;
             if (ntok > kPrepTok) {
-                // one row of up to 1024 tokens: tokens spread over the lanes,
-                // translations written as they are found, first copies marked after
+                // one row of up to 1024 tokens, read from global memory, deduplicated
+                // in the per-warp global table; translations written as found
+                const int32_t *gtk = b.tokens + tA + tbase;
                 uint32_t *out = b.elems + elem_base(tA + tbase, s_first + rA, kmax);
+                const int lgT = max(6, ceil_log2(2 * ntok));
+                tab_clear(gtab, 1 << lgT, lane);
+                __syncwarp();
                 int newc = 0;
                 for (int k = lane; k < ntok; k += 32) {
-                    const int32_t tok = stk[k];
+                    const int32_t tok = gtk[k];
                     if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    const int slot = tab_slot(sm.tab, lg, tok & (int32_t)ELEM_TOKEN);
-                    if (!(atomicOr((uint32_t *)&sm.tab[slot].y, 1u) & 1u)) {
+                    const int slot = tab_slot(gtab, lgT, tok & (int32_t)ELEM_TOKEN);
+                    if (!(atomicOr((uint32_t *)&gtab[slot].y, 1u) & 1u)) {
                         ++newc;
                         const int2 oc = dict_find(d, tok & (int32_t)ELEM_TOKEN);
                         const int pos = atomicAdd(&sm.recnt[rA], oc.y);
@@ -635,35 +671,21 @@ k_score(BatchDev b, DevDict d)
                 const int nd = __reduce_add_sync(kFull, newc);
                 if (lane == rA) n_i = nd;
                 __syncwarp();
-                const int nel = sm.recnt[rA];
-                int firsts = 0;
-                if (nel <= kPrepElem) {
-                    const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
-                    tab_clear(sm.tab, 1 << lgE, lane);
-                    __syncwarp();
-                    for (int e = lane; e < nel; e += 32) {
-                        const int32_t u = (int32_t)(out[e] & ELEM_TOKEN);
-                        const int slot = tab_slot(sm.tab, lgE, u);
-                        if (!(atomicOr((uint32_t *)&sm.tab[slot].y, 1u) & 1u)) {
-                            ++firsts;
-                            atomicOr(&out[e], ELEM_FIRST);
-                        }
-                    }
-                } else {
-                    for (int e = lane; e < nel; e += 32) {
-                        const uint32_t u = out[e] & ELEM_TOKEN;
-                        bool first = true;
-                        for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
-                        firsts += first;
-                        if (first) atomicOr(&out[e], ELEM_FIRST);
-                    }
-                }
-                const int f = __reduce_add_sync(kFull, firsts);
+                const int f = mark_first_copies(out, sm.recnt[rA], gtab, lane);
                 if (lane == 0) sm.rU[rA] = f;
                 __syncwarp();
                 rA = rB;
                 continue;
             }
+            const int lead =
+                stage_tokens(b, sm.tok[0], &sm.bar[0], (int64_t)tA + tbase, ntok, lane, generic[0]);
+            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+            tab_clear(sm.tab, 1 << lg, lane);
+            if (lane == 0) sm.ngrp = 0;
+            if (!mbar_wait(&sm.bar[0], parity[0], b.err)) return;
+            parity[0] ^= 1u;
+            __syncwarp();
+            const int32_t *stk = sm.tok[0] + lead;
             // distinct (row, token): the table maps a token to the mask of rows holding it
             if (lane >= rA && lane < rB)
                 n_i += tab_insert_run(sm.tab, lg, stk, sm.rtok[lane] - tbase,
@@ -698,8 +720,9 @@ k_score(BatchDev b, DevDict d)
                 }
             }
             __syncwarp();
-            // translations of rows [eA, eB), at most kPrepElem of them per round
-            // (or one row alone); the table maps a translation to a row mask
+            // translations of rows [eA, eB), at most kPrepElem of them per round;
+            // one row with more goes alone (global table or scan, first copies
+            // marked after writing); the table maps a translation to a row mask
             for (int eA = rA; eA < rB;) {
                 const int v = (eA + lane < rB) ? sm.recnt[eA + lane] : 0;
                 int incl = v;
@@ -711,9 +734,9 @@ k_score(BatchDev b, DevDict d)
                 const bool fits = (eA + lane < rB) && incl <= kPrepElem;
                 const int eB = eA + max(1, __popc(__ballot_sync(kFull, fits)));
                 const int nel = __shfl_sync(kFull, incl, eB - eA - 1);
-                const bool scan = nel > kPrepElem;   // only a single row with many translations
+                const bool alone = nel > kPrepElem;
                 const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
-                if (!scan) {
+                if (!alone) {
                     tab_clear(sm.tab, 1 << lgE, lane);
                     __syncwarp();
                 }
@@ -736,7 +759,7 @@ k_score(BatchDev b, DevDict d)
                             u[q] = ok[q] ? __ldg(&d.trans[off + k0 + q]) : 0;
                         }
                         uint32_t old[4] = {bit, bit, bit, bit};
-                        if (!scan) {
+                        if (!alone) {
                             int slot[4];
                             tab_slot4(sm.tab, lgE, u, ok, slot);
 #pragma unroll
@@ -757,18 +780,9 @@ k_score(BatchDev b, DevDict d)
                     if (firsts) atomicAdd(&sm.rU[r], firsts);
                 }
                 __syncwarp();
-                if (scan) {
-                    // mark first copies by scanning the written list
+                if (alone) {
                     uint32_t *out = b.elems + elem_base(tA + sm.rtok[eA], s_first + eA, kmax);
-                    int firsts = 0;
-                    for (int e = lane; e < nel; e += 32) {
-                        const uint32_t u = out[e] & ELEM_TOKEN;
-                        bool first = true;
-                        for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
-                        firsts += first;
-                        if (first) atomicOr(&out[e], ELEM_FIRST);
-                    }
-                    const int f = __reduce_add_sync(kFull, firsts);
+                    const int f = mark_first_copies(out, nel, gtab, lane);
                     if (lane == 0) sm.rU[eA] = f;
                     __syncwarp();
                 }
@@ -798,42 +812,40 @@ k_score(BatchDev b, DevDict d)
 
         int cur = 0;
         int c0 = 0, ntok = 0, lead = 0, ncols = 0;
-        if (T > 0) {
-            // first block from the offsets fetched at the start of the item
-            const int cum = ccum - ctok0;
-            ncols = __popc(__ballot_sync(kFull, lane < T && cum <= kColTokCap));
-            if (ncols > 0) {
-                ntok = __shfl_sync(kFull, cum, ncols - 1);
-                if (lane < ncols) sm.soff[0][lane + 1] = cum;
-                if (lane == 0) sm.soff[0][0] = 0;
-                lead = stage_tokens(b, sm.tok[0], &sm.bar[0], ctok0, ntok, lane, generic[0]);
-            }
-        }
-        bool pending = T > 0 && ncols > 0;   // a copy in flight into buffer `cur`
+        bool staged = false;
+        int64_t tok0 = 0;
+        if (T > 0)
+            ncols = plan_block(b, sm, 0, tcol0, 0, T, lane, ntok, lead, generic[0], staged, tok0);
+        bool pending = ncols > 0 && staged;   // a copy in flight into buffer `cur`
         while (c0 < T) {
             if (ncols == 0) {
                 if (lane == 0) atomicCAS(b.err, 0, ERR_BAD_OFFSETS);
-                pending = false;
                 break;
             }
+            int2 *tab = staged ? sm.tab : gtab;
             const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            tab_clear(sm.tab, 1 << lg, lane);
+            tab_clear(tab, 1 << lg, lane);
             // prefetch the next block into the other buffer while this one is built and scored
             const int nc0 = c0 + ncols;
             int n_ncols = 0, n_ntok = 0, n_lead = 0;
+            bool n_staged = false;
+            int64_t n_tok0 = 0;
             if (nc0 < T)
                 n_ncols = plan_block(b, sm, cur ^ 1, tcol0, nc0, T, lane, n_ntok, n_lead,
-                                     generic[cur ^ 1]);
-            if (!mbar_wait(&sm.bar[cur], parity[cur], b.err)) return;
-            parity[cur] ^= 1u;
+                                     generic[cur ^ 1], n_staged, n_tok0);
+            if (staged) {
+                if (!mbar_wait(&sm.bar[cur], parity[cur], b.err)) return;
+                parity[cur] ^= 1u;
+            }
+            pending = n_ncols > 0 && n_staged;
             __syncwarp();
             // lane c inserts the tokens of column c and counts its distinct ones
+            const int32_t *tks = staged ? sm.tok[cur] + lead : b.tokens + tok0;
             int m = 0;
             if (lane < ncols) {
                 const int k0 = sm.soff[cur][lane], k1 = sm.soff[cur][lane + 1];
                 const int Lt = k1 - k0;
-                m = tab_insert_run(sm.tab, lg, sm.tok[cur] + lead, k0, k1, 1u << lane, b.err,
-                                   nullptr, nullptr, 0);
+                m = tab_insert_run(tab, lg, tks, k0, k1, 1u << lane, b.err, nullptr, nullptr, 0);
                 sm.Km[lane] = __ldg(&recip[m]);
                 sm.KL[lane] = __ldg(&recip[Lt]);
                 sm.Lt[lane] = Lt;
@@ -842,16 +854,17 @@ k_score(BatchDev b, DevDict d)
             __syncwarp();
             const int bound = max(min(maxU, maxM), maxN);
             if (bound < 256) {
-                score_block<8>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+                score_block<8>(sm, tab, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
             } else {
-                score_block<11>(sm, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+                score_block<11>(sm, tab, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
             }
             __syncwarp();
-            pending = nc0 < T && n_ncols > 0;
             c0 = nc0;
             ncols = n_ncols;
             ntok = n_ntok;
             lead = n_lead;
+            staged = n_staged;
+            tok0 = n_tok0;
             cur ^= 1;
         }
         if (pending) {   // a block was staged but not used (bad offsets): let it land
@@ -1196,7 +1209,7 @@ int launch_score(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t 
     const size_t smem = sizeof(ScoreWarpSmem) * kSW;
     cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int need = (b.n_score_items + kSW - 1) / kSW;
-    const int grid = std::max(1, std::min(num_sms * 2, need));
+    const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSm, need));
     k_score<<<grid, kSW * 32, smem, st>>>(b, d);
     return 1;
 }

@@ -283,10 +283,11 @@ void pack_plan(const Plan &pl, const Layout &L, char *dst)
 }
 
 BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_t *sent_off,
-                       const int32_t *tokens, int32_t *sel, const uint64_t *recip)
+                       const int32_t *tokens, int32_t *sel, const uint64_t *recip, void *gscratch)
 {
     BatchDev b{};
     b.recip = recip;
+    b.gscratch = static_cast<int2 *>(gscratch);
     char *plan = base + L.plan;
     b.sent_off = sent_off;
     b.tokens = tokens;
@@ -399,6 +400,7 @@ struct Slot {
     Plan plan;
     Layout lay;
     int64_t out_nw = 0, out_nsel = 0, out_sel = 0, out_err = 0;
+    void *gscratch = nullptr;          // score-kernel tables for long sentences
 };
 
 }  // namespace
@@ -427,6 +429,8 @@ struct mine_ctx {
     Pool pool;
     void *pool_mem = nullptr;
     uint64_t *recip = nullptr;         // device table of ceil(2^48 / m), m <= kMaxSentTokens
+    void *gscratch = nullptr;          // score-kernel tables for long sentences (synchronous calls)
+    size_t gscratch_bytes = 0;
     std::vector<std::unique_ptr<Slot>> slots;
     std::mutex q_mu;
     std::condition_variable q_cv;      // pending work / stop
@@ -556,10 +560,14 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     ctx->pool.base = static_cast<char *>(ctx->pool_mem);
     ctx->pool.size = c.device_budget_bytes;
     ctx->pool.free_[0] = c.device_budget_bytes;
+    // one set of per-warp long-sentence tables per batch that can run at once
+    ctx->gscratch_bytes = (size_t)ctx->num_sms * kScoreCtasPerSm * kScoreWarps * kScoreScratchPerWarp;
+    CK(cudaMalloc(&ctx->gscratch, ctx->gscratch_bytes));
     for (int k = 0; k < c.max_inflight; ++k) {
         std::unique_ptr<Slot> s(new Slot());
         CK(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+        CK(cudaMalloc(&s->gscratch, ctx->gscratch_bytes));
         ctx->slots.push_back(std::move(s));
     }
     mine_ctx *raw = ctx.release();
@@ -588,7 +596,9 @@ int mine_close(mine_ctx *ctx)
     for (auto &s : ctx->slots) {
         cudaStreamDestroy(s->st);
         cudaEventDestroy(s->ev);
+        cudaFree(s->gscratch);
     }
+    cudaFree(ctx->gscratch);
     ctx->slots.clear();
     for (auto &m : ctx->prof_pending) {
         cudaEventDestroy(m.a);
@@ -749,7 +759,7 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
     if (batch->n_tok > 0)
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
-    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip);
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
     if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return rc;
     char *ho = hp + align_up(L.plan_bytes, 64);
     int32_t *h_nw = reinterpret_cast<int32_t *>(ho);
@@ -820,7 +830,7 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
     char *base = static_cast<char *>(ctx->arena.p);
     CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
     BatchDev b = make_batchdev(pl, L, base, batch->sent_off, batch->tokens,
-                               reinterpret_cast<int32_t *>(sel), ctx->recip);
+                               reinterpret_cast<int32_t *>(sel), ctx->recip, ctx->gscratch);
     b.nw_score = nw_score;
     b.n_sel = n_sel;
     ctx->err_off = L.counters + 4 * 8;
@@ -855,7 +865,7 @@ int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mi
     char *base = static_cast<char *>(ctx->arena.p);
     cudaStream_t st = ctx->stream;
     CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
-    BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr, ctx->recip);
+    BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr, ctx->recip, ctx->gscratch);
     if (S > 0 && T > 0) {
         int32_t *mrow = reinterpret_cast<int32_t *>(base + L.Mrow);
         CK(cudaMemcpyAsync(mrow, M, 4 * (size_t)S * T, cudaMemcpyHostToDevice, st));
@@ -1153,7 +1163,7 @@ int launch_slot(mine_ctx *ctx, Slot &s)
     CK(cudaMemcpyAsync(base + L.plan, hi, L.plan_bytes, cudaMemcpyHostToDevice, s.st));
     CK(cudaMemcpyAsync(d_sent, h_sent, 4 * (n_sent + 1), cudaMemcpyHostToDevice, s.st));
     if (n_tok > 0) CK(cudaMemcpyAsync(d_tok, h_tok, 4 * n_tok, cudaMemcpyHostToDevice, s.st));
-    BatchDev b = make_batchdev(s.plan, L, base, d_sent, d_tok, nullptr, ctx->recip);
+    BatchDev b = make_batchdev(s.plan, L, base, d_sent, d_tok, nullptr, ctx->recip, s.gscratch);
     if ((rc = enqueue_kernels(ctx, b, dict, n_sent, n_tok, true, s.st))) return rc;
     char *ho = static_cast<char *>(s.pin_out.p);
     CK(cudaMemcpyAsync(ho + s.out_nw, b.nw_score, 4 * s.plan.R, cudaMemcpyDeviceToHost, s.st));
