@@ -28,7 +28,9 @@ constexpr int kTileElems = kTile * kTile;
 constexpr int kColHashSlots = 1024;         // per-warp target-token table of a column block
 constexpr int kColTokCap = kColHashSlots / 2;   // tokens per column block at most
 constexpr int kMaxSentTokens = MINE_MAX_SENT_TOKENS;
-constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins (mbarrier try_wait / flags)
+constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins on shared-memory flags
+constexpr uint32_t kWaitHintNs = 100000;     // mbarrier try_wait suspend-time hint (100 us)
+constexpr uint32_t kMbarTries = 20000;       // try_wait attempts before giving up (<= ~2 s)
 constexpr int kScoreWarps = 4;              // warps per CTA of the score kernel
 constexpr int kScoreCtasPerSm = 4;          // its resident CTAs per SM (grid = SMs x this)
 // per-warp global table of the score kernel: 2 * kMaxSentTokens (key, mask) entries
@@ -89,6 +91,8 @@ struct BatchDev {
     const int32_t *gap_val;      // [G]
     // scratch
     uint32_t *elems;             // source elements (see elem_base)
+    int4 *sinfo;                 // [n_sent] (n_i, #elements, |U_i|, 0) of source sentences
+    int32_t kmax;                // largest translation count of the dictionary
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
@@ -113,12 +117,13 @@ int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_k
                       int32_t *err, cudaStream_t st);
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st);
-int launch_score(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 
 // kernel identities for per-kernel timing
-enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_SCORE = 2, KID_ALIGN = 3, KID_TILE = 4,
-                KID_COUNT = 5 };
+enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
+                KID_TILE = 5, KID_COUNT = 6 };
 
 }  // namespace mine

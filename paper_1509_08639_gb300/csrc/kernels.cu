@@ -101,23 +101,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Test the phase; a thread whose phase is incomplete may be suspended for up
+// to kWaitHintNs before the test returns false (no busy spinning).
 __device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(s2u(bar)), "r"(parity)
+        : "r"(s2u(bar)), "r"(parity), "r"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
 
-// Wait for the phase with the given parity; gives up after kWaitLimit tries,
-// records ERR_TIMEOUT and returns false.
+// Wait for the phase with the given parity; gives up after kMbarTries tests
+// (at most about kMbarTries * kWaitHintNs), records ERR_TIMEOUT and returns
+// false.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err)
 {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+    for (uint32_t it = 0; it < kMbarTries; ++it)
         if (mbar_test(bar, parity)) return true;
     atomicCAS(err, 0, ERR_TIMEOUT);
     return false;
@@ -276,31 +279,283 @@ __global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent,
     }
 }
 
-// ---------------------------------------------------------------- k_score
+// ---------------------------------------------------------------- row preparation
 
 constexpr int kSW = kScoreWarps;
-// tokens per preparation round: the group list (one entry per distinct
-// (row, token)) lives in the second staging buffer, which holds
-// (kColTokCap + 8) / 2 int2 entries
-constexpr int kPrepTok = kColTokCap / 2;
+constexpr int kPrepTok = 256;                    // tokens per preparation round
+constexpr int kPrepElem = kColHashSlots / 2;     // translations per dedupe round
+constexpr int kGTabSlots = 2 * kMaxSentTokens;   // per-warp global table for long sentences
 
-// Per-warp shared memory.  One open-addressed table of (key, mask) entries
-// serves, at different times: the row preparation (token -> mask of the rows
-// holding it; translation -> mask of the rows whose U_i holds it) and the
-// column blocks (target token -> mask of the columns holding it).  tok[]
-// stages tokens by TMA; during the preparation tok[1] holds the group list
-// (token, row) -> (off << 6 | cnt, row | pos << 5).
+// Per-warp shared memory of k_prep.  The table maps a source token to the
+// mask of rows holding it, then a translation to the mask of rows whose U_i
+// holds it.  grp lists the distinct (row, token) pairs of a round, then
+// their dictionary entries (off << 6 | cnt, row | pos << 5).
+struct alignas(16) PrepWarpSmem {
+    int2 tab[kColHashSlots];
+    int32_t tok[kPrepTok + 8];                   // TMA staging of a round's tokens
+    int2 grp[kPrepTok];
+    unsigned long long bar;
+    int32_t rtok[33];
+    int32_t recnt[32], rU[32];
+    int32_t ngrp;
+};
+
+// Set `bit` in the mask of `key`; true when it was not set before.
+__device__ __forceinline__ bool tab_set(int2 *tab, int lg, int32_t key, uint32_t bit)
+{
+    const int slot = tab_slot(tab, lg, key);
+    return !(atomicOr((uint32_t *)&tab[slot].y, bit) & bit);
+}
+
+// Stage tokens [tok0, tok0 + ntok) into dst with a TMA bulk copy (the bulk
+// part is 16-byte aligned; the few tokens past the last 16-byte boundary of
+// the token array are copied by lanes, which sets `generic`).  A buffer that
+// generic stores wrote before gets a proxy fence first.  Returns the offset
+// of tok0 in dst.
+__device__ __forceinline__ int stage_tokens(const BatchDev &b, int32_t *dst,
+                                            unsigned long long *bar, int64_t tok0, int ntok,
+                                            int lane, bool &generic)
+{
+    const int64_t a0 = tok0 & ~(int64_t)3;
+    const int64_t end = tok0 + ntok;
+    const int64_t a1 = min((end + 3) & ~(int64_t)3, b.n_tok & ~(int64_t)3);
+    const uint32_t bytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
+    if (generic) fence_proxy_async();
+    generic = max(a1, a0) < end;
+    __syncwarp();
+    if (lane == 0) {
+        mbar_expect_tx(bar, bytes);
+        if (bytes) bulk_g2s(dst, b.tokens + a0, bytes, bar);
+    }
+    for (int64_t p = max(a1, a0) + lane; p < end; p += 32) dst[p - a0] = b.tokens[p];
+    return (int)(tok0 - a0);
+}
+
+// Mark the first copy of every translation in out[0..nel) (one row) with
+// ELEM_FIRST, using the per-warp global table, or a scan when even that is
+// too small.  Returns the number of first copies (|U_i|).
+__device__ int mark_first_copies(uint32_t *out, int nel, int2 *gtab, int lane)
+{
+    int firsts = 0;
+    if (nel <= kGTabSlots / 2) {
+        const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
+        tab_clear(gtab, 1 << lgE, lane);
+        __syncwarp();
+        for (int e = lane; e < nel; e += 32) {
+            const int slot = tab_slot(gtab, lgE, (int32_t)(out[e] & ELEM_TOKEN));
+            if (!(atomicOr((uint32_t *)&gtab[slot].y, 1u) & 1u)) {
+                ++firsts;
+                atomicOr(&out[e], ELEM_FIRST);
+            }
+        }
+    } else {
+        for (int e = lane; e < nel; e += 32) {
+            const uint32_t u = out[e] & ELEM_TOKEN;
+            bool first = true;
+            for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
+            firsts += first;
+            if (first) atomicOr(&out[e], ELEM_FIRST);
+        }
+    }
+    const int f = __reduce_add_sync(kFull, firsts);
+    __syncwarp();
+    return f;
+}
+
+// One warp per 32 source rows of a pair: distinct tokens X_i (n_i), their
+// translations grouped per token with FIRST / END flags (U_i), written to the
+// row's element list, and (n_i, #elements, |U_i|) to sinfo.
+__global__ void __launch_bounds__(kSW * 32)
+k_prep(BatchDev b, DevDict d)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    PrepWarpSmem &sm = reinterpret_cast<PrepWarpSmem *>(smem_raw)[wib];
+    int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * kSW + wib) * kGTabSlots;
+    const int kmax = d.kmax;
+    if (lane == 0) {
+        mbar_init(&sm.bar, 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0u;
+    bool generic = false;
+    if (*(volatile int32_t *)b.err) return;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&b.counters[0], 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= b.n_score_items) break;
+        const ScoreItem si = b.score_items[item];
+        const PairPlan pp = b.pairs[si.pair];
+        const int nrows = min(32, pp.S - si.row0);
+        const int64_t s_first = (int64_t)pp.s0 + si.row0;
+        int32_t a_tok = 0, e_tok = 0;
+        if (lane < nrows) {
+            a_tok = b.sent_off[s_first + lane];
+            e_tok = b.sent_off[s_first + lane + 1];
+        }
+        const int32_t tA = __shfl_sync(kFull, a_tok, 0);
+        if (lane < nrows) sm.rtok[lane] = a_tok - tA;
+        if (lane == nrows - 1) sm.rtok[nrows] = e_tok - tA;
+        sm.recnt[lane] = 0;
+        sm.rU[lane] = 0;
+        int n_i = 0;   // distinct tokens of this lane's row
+        __syncwarp();
+        for (int rA = 0; rA < nrows;) {
+            // rows [rA, rB) with at most kPrepTok tokens, or one longer row alone
+            const int cand = rA + 1 + lane;
+            const bool okr = cand <= nrows && sm.rtok[cand] - sm.rtok[rA] <= kPrepTok;
+            const int rB = rA + max(1, __popc(__ballot_sync(kFull, okr)));
+            const int tbase = sm.rtok[rA];
+            const int ntok = sm.rtok[rB] - tbase;
+            if (ntok > kPrepTok) {
+                // one long row, read from global memory, deduplicated in the
+                // per-warp global table; translations written as found
+                const int32_t *gtk = b.tokens + tA + tbase;
+                uint32_t *out = b.elems + elem_base(tA + tbase, s_first + rA, kmax);
+                const int lgT = max(6, ceil_log2(2 * ntok));
+                tab_clear(gtab, 1 << lgT, lane);
+                __syncwarp();
+                int newc = 0;
+                for (int k = lane; k < ntok; k += 32) {
+                    const int32_t tok = gtk[k];
+                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    if (tab_set(gtab, lgT, tok & (int32_t)ELEM_TOKEN, 1u)) {
+                        ++newc;
+                        const int2 oc = dict_find(d, tok & (int32_t)ELEM_TOKEN);
+                        const int pos = atomicAdd(&sm.recnt[rA], oc.y);
+                        for (int q = 0; q < oc.y; ++q)
+                            out[pos + q] = (uint32_t)__ldg(&d.trans[oc.x + q]) |
+                                           (q == oc.y - 1 ? ELEM_END : 0u);
+                    }
+                }
+                const int nd = __reduce_add_sync(kFull, newc);
+                if (lane == rA) n_i = nd;
+                __syncwarp();
+                const int f = mark_first_copies(out, sm.recnt[rA], gtab, lane);
+                if (lane == 0) sm.rU[rA] = f;
+                __syncwarp();
+                rA = rB;
+                continue;
+            }
+            const int lead = stage_tokens(b, sm.tok, &sm.bar, (int64_t)tA + tbase, ntok, lane, generic);
+            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+            tab_clear(sm.tab, 1 << lg, lane);
+            if (lane == 0) sm.ngrp = 0;
+            if (!mbar_wait(&sm.bar, parity, b.err)) return;
+            parity ^= 1u;
+            __syncwarp();
+            // distinct (row, token): lane r walks the tokens of row r
+            if (lane >= rA && lane < rB) {
+                const uint32_t bit = 1u << lane;
+                const int32_t *stk = sm.tok + lead - tbase;
+                const int k1 = sm.rtok[lane + 1];
+                for (int k = sm.rtok[lane]; k < k1; ++k) {
+                    const int32_t tok = stk[k];
+                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    if (tab_set(sm.tab, lg, tok & (int32_t)ELEM_TOKEN, bit)) {
+                        ++n_i;
+                        sm.grp[atomicAdd(&sm.ngrp, 1)] = make_int2(tok & (int32_t)ELEM_TOKEN, lane);
+                    }
+                }
+            }
+            __syncwarp();
+            const int ng = sm.ngrp;
+            // dictionary lookups, two per lane in flight
+            for (int g0 = 0; g0 < ng; g0 += 64) {
+                int2 e[2];
+                int32_t tok[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int g = g0 + q * 32 + lane;
+                    tok[q] = g < ng ? sm.grp[g].x : -1;
+                    e[q] = make_int2(-1, 0);
+                    if (g < ng) e[q] = __ldg(&d.slots[hmul(tok[q]) >> (32 - d.log2)]);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int g = g0 + q * 32 + lane;
+                    if (g < ng) {
+                        int2 oc;
+                        if (e[q].x == tok[q]) oc = make_int2((int32_t)((uint32_t)e[q].y >> 6), e[q].y & 63);
+                        else if (e[q].x == -1) oc = make_int2(0, 0);
+                        else oc = dict_find(d, tok[q]);
+                        const int r = sm.grp[g].y;
+                        const int pos = atomicAdd(&sm.recnt[r], oc.y);
+                        sm.grp[g] = make_int2((int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y),
+                                              r | (pos << 5));
+                    }
+                }
+            }
+            __syncwarp();
+            // translations of rows [eA, eB), at most kPrepElem of them per round;
+            // one row with more goes alone (global table or scan)
+            for (int eA = rA; eA < rB;) {
+                const int v = (eA + lane < rB) ? sm.recnt[eA + lane] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const bool fits = (eA + lane < rB) && incl <= kPrepElem;
+                const int eB = eA + max(1, __popc(__ballot_sync(kFull, fits)));
+                const int nel = __shfl_sync(kFull, incl, eB - eA - 1);
+                const bool alone = nel > kPrepElem;
+                const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
+                if (!alone) {
+                    tab_clear(sm.tab, 1 << lgE, lane);
+                    __syncwarp();
+                }
+                for (int g = lane; g < ng; g += 32) {
+                    const int2 gr = sm.grp[g];
+                    const int r = gr.y & 31;
+                    if (r < eA || r >= eB) continue;
+                    const uint32_t pk = (uint32_t)gr.x;
+                    const int off = (int)(pk >> 6), cnt = (int)(pk & 63u);
+                    uint32_t *out = b.elems + elem_base(tA + sm.rtok[r], s_first + r, kmax) + (gr.y >> 5);
+                    const uint32_t bit = 1u << r;
+                    int firsts = 0;
+                    for (int k = 0; k < cnt; ++k) {
+                        const int32_t u = __ldg(&d.trans[off + k]);
+                        const bool first = !alone && tab_set(sm.tab, lgE, u, bit);
+                        firsts += first;
+                        out[k] = (uint32_t)u | (first ? ELEM_FIRST : 0u) | (k == cnt - 1 ? ELEM_END : 0u);
+                    }
+                    if (firsts) atomicAdd(&sm.rU[r], firsts);
+                }
+                __syncwarp();
+                if (alone) {
+                    uint32_t *out = b.elems + elem_base(tA + sm.rtok[eA], s_first + eA, kmax);
+                    const int f = mark_first_copies(out, nel, gtab, lane);
+                    if (lane == 0) sm.rU[eA] = f;
+                    __syncwarp();
+                }
+                eA = eB;
+            }
+            rA = rB;
+        }
+        __syncwarp();
+        if (lane < nrows) b.sinfo[s_first + lane] = make_int4(n_i, sm.recnt[lane], sm.rU[lane], 0);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- k_score
+
+// Per-warp shared memory of k_score: the column-block table (target token ->
+// mask of the block's columns holding it) and two TMA staging buffers.
 struct alignas(16) ScoreWarpSmem {
     int2 tab[kColHashSlots];
-    int32_t tok[2][kColTokCap + 8];          // TMA staging
+    int32_t tok[2][kColTokCap + 8];
     unsigned long long bar[2];
     int32_t soff[2][33];
     uint64_t Km[32];        // reciprocal of m_j
     uint64_t KL[32];        // reciprocal of L'_j
     int32_t Lt[32];
-    int32_t rtok[33];
-    int32_t recnt[32], rU[32];
-    int32_t ngrp;
 };
 
 __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b,
@@ -309,29 +564,6 @@ __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, 
     const uint32_t u = a ^ b;
     carry = (a & b) | (u & c);
     sum = u ^ c;
-}
-
-// Add eight 32-lane bit vectors x[0..7] to the bit-sliced counter P (plane k
-// holds bit k of 32 counts): carry-save adders for the three low planes, a
-// ripple for the rest (Harley-Seal).
-template <int NPL>
-__device__ __forceinline__ void add8(uint32_t (&P)[NPL], const uint32_t (&x)[8])
-{
-    uint32_t t1a, t1b, t2a, t2b, t4;
-    csa(t1a, P[0], P[0], x[0], x[1]);
-    csa(t1b, P[0], P[0], x[2], x[3]);
-    csa(t2a, P[1], P[1], t1a, t1b);
-    csa(t1a, P[0], P[0], x[4], x[5]);
-    csa(t1b, P[0], P[0], x[6], x[7]);
-    csa(t2b, P[1], P[1], t1a, t1b);
-    csa(t4, P[2], P[2], t2a, t2b);
-    uint32_t c = t4;
-#pragma unroll
-    for (int k = 3; k < NPL; ++k) {
-        const uint32_t n = P[k] & c;
-        P[k] ^= c;
-        c = n;
-    }
 }
 
 // Counts of columns 8m .. 8m+7 from eight bit planes: gather byte m of every
@@ -381,45 +613,71 @@ __device__ __forceinline__ int32_t cell_score(uint32_t a, uint32_t bb, uint64_t 
     return (int32_t)((3u * h + q_l) >> 2);
 }
 
+// Column mask of `key` in the block table: two slots are read at once; the
+// rare longer probe sequences continue in a loop.
+__device__ __forceinline__ uint32_t probe2(const int2 *tab, uint32_t mask, int lg, int32_t key)
+{
+    uint32_t h = hmul(key) >> (32 - lg);
+    const int2 e0 = tab[h];
+    if (e0.x == key) return (uint32_t)e0.y;
+    if (e0.x == -1) return 0u;
+    h = (h + 1) & mask;
+    for (;;) {
+        const int2 e = tab[h];
+        if (e.x == key) return (uint32_t)e.y;
+        if (e.x == -1) return 0u;
+        h = (h + 1) & mask;
+    }
+}
+
+// Add two 32-lane bit vectors to the bit-sliced counter P: a carry-save
+// adder for plane 0, then a ripple.
+template <int NPL>
+__device__ __forceinline__ void add2(uint32_t (&P)[NPL], uint32_t x, uint32_t y)
+{
+    uint32_t c;
+    csa(c, P[0], P[0], x, y);
+#pragma unroll
+    for (int k = 1; k < NPL; ++k) {
+        const uint32_t n = P[k] & c;
+        P[k] ^= c;
+        c = n;
+    }
+}
+
 // Accumulate the overlap counts of one column block and score its cells
 // into row `lane` of the score tiles (mrow points at column tile 0).
 // NPL <= 8: bit planes are turned into byte counts by 8 x 8 transposes.
 template <int NPL>
 __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 *tab, int lg,
-                                            const uint32_t *el,
-                                            int n_elem, int nE8, int ncols, bool row_ok,
-                                            uint64_t Ks, uint64_t KLs, int Ls, int32_t *mrow,
-                                            int c0)
+                                         const uint32_t *el, int n_elem, int nE2, int ncols,
+                                         bool row_ok, uint64_t Ks, uint64_t KLs, int Ls,
+                                         int32_t *mrow, int c0)
 {
     uint32_t A[NPL], B[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) A[k] = B[k] = 0u;
+    const uint32_t mask = (1u << lg) - 1u;
     uint32_t hit = 0;
-    uint4 n0 = make_uint4(0, 0, 0, 0), n1 = make_uint4(0, 0, 0, 0);
-    if (0 < n_elem) {
-        n0 = *reinterpret_cast<const uint4 *>(el);
-        n1 = *reinterpret_cast<const uint4 *>(el + 4);
-    }
-    for (int e0 = 0; e0 < nE8; e0 += 8) {
-        const uint4 v0 = n0, v1 = n1;
-        if (e0 + 8 < n_elem) {   // prefetch the next eight
-            n0 = *reinterpret_cast<const uint4 *>(el + e0 + 8);
-            n1 = *reinterpret_cast<const uint4 *>(el + e0 + 12);
-        }
-        const uint32_t ev[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        uint32_t xa[8], xb[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const bool ok = (e0 + q) < n_elem;
-            const uint32_t e = ok ? ev[q] : 0u;
-            const uint32_t o = ok ? probe_occ(tab, lg, (int32_t)(e & ELEM_TOKEN)) : 0u;
-            xa[q] = (e & ELEM_FIRST) ? o : 0u;
-            hit |= o;
-            xb[q] = (e & ELEM_END) ? hit : 0u;
-            hit = (e & ELEM_END) ? 0u : hit;
-        }
-        add8<NPL>(A, xa);
-        add8<NPL>(B, xb);
+    uint2 nx = make_uint2(0, 0);
+    if (0 < n_elem) nx = *reinterpret_cast<const uint2 *>(el);
+    for (int e0 = 0; e0 < nE2; e0 += 2) {
+        const uint2 v = nx;
+        if (e0 + 2 < n_elem) nx = *reinterpret_cast<const uint2 *>(el + e0 + 2);   // prefetch
+        const uint32_t ea = e0 < n_elem ? v.x : 0u;
+        const uint32_t eb = e0 + 1 < n_elem ? v.y : 0u;
+        const uint32_t oa = ea ? probe2(tab, mask, lg, (int32_t)(ea & ELEM_TOKEN)) : 0u;
+        const uint32_t ob = eb ? probe2(tab, mask, lg, (int32_t)(eb & ELEM_TOKEN)) : 0u;
+        const uint32_t xa0 = (ea & ELEM_FIRST) ? oa : 0u;
+        hit |= oa;
+        const uint32_t xb0 = (ea & ELEM_END) ? hit : 0u;
+        hit = (ea & ELEM_END) ? 0u : hit;
+        const uint32_t xa1 = (eb & ELEM_FIRST) ? ob : 0u;
+        hit |= ob;
+        const uint32_t xb1 = (eb & ELEM_END) ? hit : 0u;
+        hit = (eb & ELEM_END) ? 0u : hit;
+        add2<NPL>(A, xa0, xa1);
+        add2<NPL>(B, xb0, xb1);
     }
     if (!row_ok) return;
     const bool whole = ncols == 32 && (c0 & 31) == 0;   // one whole row of one tile
@@ -430,32 +688,30 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
             A8[k] = k < NPL ? A[k] : 0u;
             B8[k] = k < NPL ? B[k] : 0u;
         }
+#pragma unroll 1
+        for (int m = 0; m < 4 && 8 * m < ncols; ++m) {
+            uint32_t alo, ahi, blo, bhi;
+            planes_to_bytes(A8, m, alo, ahi);
+            planes_to_bytes(B8, m, blo, bhi);
+            int32_t v[8];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            if (8 * m < ncols) {
-                uint32_t alo, ahi, blo, bhi;
-                planes_to_bytes(A8, m, alo, ahi);
-                planes_to_bytes(B8, m, blo, bhi);
-                int32_t v[8];
+            for (int c = 0; c < 8; ++c) {
+                const int jj = 8 * m + c;
+                const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
+                const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
+                v[c] = cell_score(a, bb, sm.Km[jj], Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+            }
+            if (whole) {
+                int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
+                dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+                dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+            } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int jj = 8 * m + c;
-                    const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
-                    const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
-                    v[c] = cell_score(a, bb, sm.Km[jj], Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
-                }
-                if (whole) {
-                    int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
-                    dst[0] = make_int4(v[0], v[1], v[2], v[3]);
-                    dst[1] = make_int4(v[4], v[5], v[6], v[7]);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int jj = 8 * m + c;
-                        if (jj < ncols) {
-                            const int col = c0 + jj;
-                            mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v[c];
-                        }
+                    if (jj < ncols) {
+                        const int col = c0 + jj;
+                        mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v[c];
                     }
                 }
             }
@@ -470,36 +726,11 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
     }
 }
 
-// Stage tokens [tok0, tok0 + ntok) into dst with a TMA bulk copy (the bulk
-// part is 16-byte aligned; the few tokens past the last 16-byte boundary of
-// the token array are copied by lanes, which sets `generic`).  A buffer that
-// generic stores wrote before gets a proxy fence first.  Returns the offset
-// of tok0 in dst.
-__device__ __forceinline__ int stage_tokens(const BatchDev &b, int32_t *dst,
-                                            unsigned long long *bar, int64_t tok0, int ntok,
-                                            int lane, bool &generic)
-{
-    const int64_t a0 = tok0 & ~(int64_t)3;
-    const int64_t end = tok0 + ntok;
-    const int64_t a1 = min((end + 3) & ~(int64_t)3, b.n_tok & ~(int64_t)3);
-    const uint32_t bytes = a1 > a0 ? (uint32_t)(4 * (a1 - a0)) : 0u;
-    if (generic) fence_proxy_async();
-    generic = max(a1, a0) < end;
-    __syncwarp();
-    if (lane == 0) {
-        mbar_expect_tx(bar, bytes);
-        if (bytes) bulk_g2s(dst, b.tokens + a0, bytes, bar);
-    }
-    for (int64_t p = max(a1, a0) + lane; p < end; p += 32) dst[p - a0] = b.tokens[p];
-    return (int)(tok0 - a0);
-}
-
 // Plan the column block starting at c0: widest run of <= 32 target sentences
-// whose tokens fit the table; stage its tokens into buffer `buf`.
-// Returns ncols (>= 1, or 0 on bad offsets).
-// A single column longer than kColTokCap becomes an unstaged block (staged =
-// false) whose tokens are read from global memory into the per-warp global
-// table.  tok0 receives the block's first token index.
+// whose tokens fit the table; stage its tokens into buffer `buf`.  A single
+// column longer than kColTokCap becomes an unstaged block (staged = false)
+// read from global memory into the per-warp global table.  Returns ncols
+// (>= 1, or 0 on bad offsets); tok0 receives the block's first token index.
 __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, int buf,
                                           int64_t tcol0, int c0, int T, int lane, int &ntok,
                                           int &lead, bool &generic, bool &staged, int64_t &tok0)
@@ -522,86 +753,16 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, 
     return ncols;
 }
 
-// Insert the keys key[lo..hi) of one lane (4 at a time, first probes and
-// atomics in flight together) with `bit` into the table; returns how many
-// set their bit for the first time.  When `grp` is given, each first-time
-// key is appended to it with `tag`.
-__device__ __forceinline__ int tab_insert_run(int2 *tab, int lg, const int32_t *keys, int lo,
-                                             int hi, uint32_t bit, int32_t *err, int2 *grp,
-                                             int32_t *ngrp, int tag)
-{
-    int fresh = 0;
-    for (int k0 = lo; k0 < hi; k0 += 4) {
-        int32_t key[4];
-        bool ok[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            ok[q] = k0 + q < hi;
-            const int32_t t = ok[q] ? keys[k0 + q] : 0;
-            if ((uint32_t)t > ELEM_TOKEN) atomicCAS(err, 0, ERR_BAD_TOKEN);
-            key[q] = t & (int32_t)ELEM_TOKEN;
-        }
-        int slot[4];
-        tab_slot4(tab, lg, key, ok, slot);
-        uint32_t old[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) old[q] = ok[q] ? atomicOr((uint32_t *)&tab[slot[q]].y, bit) : bit;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!(old[q] & bit)) {
-                ++fresh;
-                if (grp) grp[atomicAdd(ngrp, 1)] = make_int2(key[q], tag);
-            }
-        }
-    }
-    return fresh;
-}
-
-constexpr int kPrepElem = kColHashSlots / 2;   // translations per dedupe round
-static_assert(2 * kPrepTok <= kColTokCap + 8, "group list must fit the staging buffer");
-constexpr int kGTabSlots = 2 * kMaxSentTokens;   // per-warp global table for long sentences
-
-// Mark the first copy of every translation in out[0..nel) (one row) with
-// ELEM_FIRST, using the per-warp global table, or a scan when even that is
-// too small.  Returns the number of first copies (|U_i|).
-__device__ int mark_first_copies(uint32_t *out, int nel, int2 *gtab, int lane)
-{
-    int firsts = 0;
-    if (nel <= kGTabSlots / 2) {
-        const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
-        tab_clear(gtab, 1 << lgE, lane);
-        __syncwarp();
-        for (int e = lane; e < nel; e += 32) {
-            const int slot = tab_slot(gtab, lgE, (int32_t)(out[e] & ELEM_TOKEN));
-            if (!(atomicOr((uint32_t *)&gtab[slot].y, 1u) & 1u)) {
-                ++firsts;
-                atomicOr(&out[e], ELEM_FIRST);
-            }
-        }
-    } else {
-        for (int e = lane; e < nel; e += 32) {
-            const uint32_t u = out[e] & ELEM_TOKEN;
-            bool first = true;
-            for (int q = 0; q < e && first; ++q) first = (out[q] & ELEM_TOKEN) != u;
-            firsts += first;
-            if (first) atomicOr(&out[e], ELEM_FIRST);
-        }
-    }
-    const int f = __reduce_add_sync(kFull, firsts);
-    __syncwarp();
-    return f;
-}
-
 __global__ void __launch_bounds__(kSW * 32)
-k_score(BatchDev b, DevDict d)
+k_score(BatchDev b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     ScoreWarpSmem &sm = reinterpret_cast<ScoreWarpSmem *>(smem_raw)[wib];
     int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * kSW + wib) * kGTabSlots;
-    const int kmax = d.kmax;
     const uint64_t *recip = b.recip;
+    const int kmax = b.kmax;
     if (lane == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
@@ -614,7 +775,7 @@ k_score(BatchDev b, DevDict d)
 
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(&b.counters[0], 1);
+        if (lane == 0) item = atomicAdd(&b.counters[1], 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_score_items) break;
         const ScoreItem si = b.score_items[item];
@@ -624,191 +785,24 @@ k_score(BatchDev b, DevDict d)
         const int nrows = min(32, pp.S - si.row0);
         const int64_t s_first = (int64_t)pp.s0 + si.row0;
         const int64_t tcol0 = pp.t0;
-
-        // ------------------------------------------------ row preparation
+        const bool row_ok = lane < nrows;
+        int4 inf = make_int4(0, 0, 0, 0);
         int32_t a_tok = 0, e_tok = 0;
-        if (lane < nrows) {
+        if (row_ok) {
+            inf = b.sinfo[s_first + lane];
             a_tok = b.sent_off[s_first + lane];
             e_tok = b.sent_off[s_first + lane + 1];
         }
-        const int32_t tA = __shfl_sync(kFull, a_tok, 0);
-        if (lane < nrows) sm.rtok[lane] = a_tok - tA;
-        if (lane == nrows - 1) sm.rtok[nrows] = e_tok - tA;
-        sm.recnt[lane] = 0;
-        sm.rU[lane] = 0;
-        int n_i = 0;   // distinct tokens of this lane's row
-        __syncwarp();
-        int2 *grp = reinterpret_cast<int2 *>(sm.tok[1]);   // <= kPrepTok groups
-        for (int rA = 0; rA < nrows;) {
-            // rows [rA, rB) with at most kPrepTok tokens, or one longer row alone
-            const int cand = rA + 1 + lane;
-            const bool okr = cand <= nrows && sm.rtok[cand] - sm.rtok[rA] <= kPrepTok;
-            const int rB = rA + max(1, __popc(__ballot_sync(kFull, okr)));
-            const int tbase = sm.rtok[rA];
-            const int ntok = sm.rtok[rB] - tbase;
-            if (ntok > kPrepTok) {
-                // one row of up to 1024 tokens, read from global memory, deduplicated
-                // in the per-warp global table; translations written as found
-                const int32_t *gtk = b.tokens + tA + tbase;
-                uint32_t *out = b.elems + elem_base(tA + tbase, s_first + rA, kmax);
-                const int lgT = max(6, ceil_log2(2 * ntok));
-                tab_clear(gtab, 1 << lgT, lane);
-                __syncwarp();
-                int newc = 0;
-                for (int k = lane; k < ntok; k += 32) {
-                    const int32_t tok = gtk[k];
-                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    const int slot = tab_slot(gtab, lgT, tok & (int32_t)ELEM_TOKEN);
-                    if (!(atomicOr((uint32_t *)&gtab[slot].y, 1u) & 1u)) {
-                        ++newc;
-                        const int2 oc = dict_find(d, tok & (int32_t)ELEM_TOKEN);
-                        const int pos = atomicAdd(&sm.recnt[rA], oc.y);
-                        for (int q = 0; q < oc.y; ++q)
-                            out[pos + q] = (uint32_t)__ldg(&d.trans[oc.x + q]) |
-                                           (q == oc.y - 1 ? ELEM_END : 0u);
-                    }
-                }
-                const int nd = __reduce_add_sync(kFull, newc);
-                if (lane == rA) n_i = nd;
-                __syncwarp();
-                const int f = mark_first_copies(out, sm.recnt[rA], gtab, lane);
-                if (lane == 0) sm.rU[rA] = f;
-                __syncwarp();
-                rA = rB;
-                continue;
-            }
-            const int lead =
-                stage_tokens(b, sm.tok[0], &sm.bar[0], (int64_t)tA + tbase, ntok, lane, generic[0]);
-            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            tab_clear(sm.tab, 1 << lg, lane);
-            if (lane == 0) sm.ngrp = 0;
-            if (!mbar_wait(&sm.bar[0], parity[0], b.err)) return;
-            parity[0] ^= 1u;
-            __syncwarp();
-            const int32_t *stk = sm.tok[0] + lead;
-            // distinct (row, token): the table maps a token to the mask of rows holding it
-            if (lane >= rA && lane < rB)
-                n_i += tab_insert_run(sm.tab, lg, stk, sm.rtok[lane] - tbase,
-                                      sm.rtok[lane + 1] - tbase, 1u << lane, b.err, grp,
-                                      &sm.ngrp, lane);
-            __syncwarp();
-            const int ng = sm.ngrp;
-            // dictionary lookups, four per lane in flight
-            for (int g0 = 0; g0 < ng; g0 += 128) {
-                int2 e[4];
-                int32_t tok[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int g = g0 + q * 32 + lane;
-                    tok[q] = g < ng ? grp[g].x : -1;
-                    e[q] = make_int2(-1, 0);
-                    if (g < ng) e[q] = __ldg(&d.slots[hmul(tok[q]) >> (32 - d.log2)]);
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int g = g0 + q * 32 + lane;
-                    if (g < ng) {
-                        int2 oc;
-                        if (e[q].x == tok[q]) oc = make_int2((int32_t)((uint32_t)e[q].y >> 6), e[q].y & 63);
-                        else if (e[q].x == -1) oc = make_int2(0, 0);
-                        else oc = dict_find(d, tok[q]);
-                        const int r = grp[g].y;
-                        const int pos = atomicAdd(&sm.recnt[r], oc.y);
-                        grp[g] = make_int2((int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y),
-                                           r | (pos << 5));
-                    }
-                }
-            }
-            __syncwarp();
-            // translations of rows [eA, eB), at most kPrepElem of them per round;
-            // one row with more goes alone (global table or scan, first copies
-            // marked after writing); the table maps a translation to a row mask
-            for (int eA = rA; eA < rB;) {
-                const int v = (eA + lane < rB) ? sm.recnt[eA + lane] : 0;
-                int incl = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const bool fits = (eA + lane < rB) && incl <= kPrepElem;
-                const int eB = eA + max(1, __popc(__ballot_sync(kFull, fits)));
-                const int nel = __shfl_sync(kFull, incl, eB - eA - 1);
-                const bool alone = nel > kPrepElem;
-                const int lgE = max(6, ceil_log2(2 * max(nel, 1)));
-                if (!alone) {
-                    tab_clear(sm.tab, 1 << lgE, lane);
-                    __syncwarp();
-                }
-                for (int g = lane; g < ng; g += 32) {
-                    const int2 gr = grp[g];
-                    const int r = gr.y & 31;
-                    if (r < eA || r >= eB) continue;
-                    const uint32_t pk = (uint32_t)gr.x;
-                    const int off = (int)(pk >> 6), cnt = (int)(pk & 63u);
-                    const int pos = gr.y >> 5;
-                    uint32_t *out = b.elems + elem_base(tA + sm.rtok[r], s_first + r, kmax) + pos;
-                    const uint32_t bit = 1u << r;
-                    int firsts = 0;
-                    for (int k0 = 0; k0 < cnt; k0 += 4) {
-                        int32_t u[4];
-                        bool ok[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            ok[q] = k0 + q < cnt;
-                            u[q] = ok[q] ? __ldg(&d.trans[off + k0 + q]) : 0;
-                        }
-                        uint32_t old[4] = {bit, bit, bit, bit};
-                        if (!alone) {
-                            int slot[4];
-                            tab_slot4(sm.tab, lgE, u, ok, slot);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                if (ok[q]) old[q] = atomicOr((uint32_t *)&sm.tab[slot[q]].y, bit);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int k = k0 + q;
-                            if (ok[q]) {
-                                const bool first = !(old[q] & bit);
-                                firsts += first;
-                                out[k] = (uint32_t)u[q] | (first ? ELEM_FIRST : 0u) |
-                                         (k == cnt - 1 ? ELEM_END : 0u);
-                            }
-                        }
-                    }
-                    if (firsts) atomicAdd(&sm.rU[r], firsts);
-                }
-                __syncwarp();
-                if (alone) {
-                    uint32_t *out = b.elems + elem_base(tA + sm.rtok[eA], s_first + eA, kmax);
-                    const int f = mark_first_copies(out, nel, gtab, lane);
-                    if (lane == 0) sm.rU[eA] = f;
-                    __syncwarp();
-                }
-                eA = eB;
-            }
-            rA = rB;
-        }
-        generic[1] = true;   // the group list lived in tok[1]
-        __syncwarp();
-
-        // ------------------------------------------------ scoring
-        const bool row_ok = lane < nrows;
-        const int n_elem = row_ok ? sm.recnt[lane] : 0;
-        const int nU = row_ok ? sm.rU[lane] : 0;
-        const int Ls = row_ok ? e_tok - a_tok : 0;
-        if (!row_ok) n_i = 0;
-        const uint32_t *el =
-            row_ok ? b.elems + elem_base(a_tok, s_first + lane, kmax) : b.elems;
+        const int n_i = inf.x, n_elem = inf.y, nU = inf.z;
+        const int Ls = e_tok - a_tok;
+        const uint32_t *el = row_ok ? b.elems + elem_base(a_tok, s_first + lane, kmax) : b.elems;
         const uint64_t Ks = __ldg(&recip[n_i]);
         const uint64_t KLs = __ldg(&recip[Ls]);
-        const int nE8 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 7) & ~7u);
+        const int nE2 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 1) & ~1u);
         const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
         const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
         int32_t *mrow = b.M + pp.m_off + (int64_t)(si.row0 >> 5) * TT * kTileElems +
                         (row_ok ? lane : 0) * kTile;
-        __syncwarp();   // the preparation table is reused by the column tables below
 
         int cur = 0;
         int c0 = 0, ntok = 0, lead = 0, ncols = 0;
@@ -844,19 +838,23 @@ k_score(BatchDev b, DevDict d)
             int m = 0;
             if (lane < ncols) {
                 const int k0 = sm.soff[cur][lane], k1 = sm.soff[cur][lane + 1];
-                const int Lt = k1 - k0;
-                m = tab_insert_run(tab, lg, tks, k0, k1, 1u << lane, b.err, nullptr, nullptr, 0);
+                const uint32_t bit = 1u << lane;
+                for (int k = k0; k < k1; ++k) {
+                    const int32_t tok = tks[k];
+                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    m += tab_set(tab, lg, tok & (int32_t)ELEM_TOKEN, bit);
+                }
                 sm.Km[lane] = __ldg(&recip[m]);
-                sm.KL[lane] = __ldg(&recip[Lt]);
-                sm.Lt[lane] = Lt;
+                sm.KL[lane] = __ldg(&recip[k1 - k0]);
+                sm.Lt[lane] = k1 - k0;
             }
             const int maxM = (int)__reduce_max_sync(kFull, (unsigned)m);
             __syncwarp();
             const int bound = max(min(maxU, maxM), maxN);
             if (bound < 256) {
-                score_block<8>(sm, tab, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+                score_block<8>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
             } else {
-                score_block<11>(sm, tab, lg, el, n_elem, nE8, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+                score_block<11>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
             }
             __syncwarp();
             c0 = nc0;
@@ -1121,7 +1119,7 @@ k_align(BatchDev b)
 
     // large alignments: the whole CTA on one pair
     for (;;) {
-        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[1], 1);
+        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[2], 1);
         if (threadIdx.x < kAW) {
             sm.prod[threadIdx.x] = 0;
             sm.cons[threadIdx.x] = 0;
@@ -1153,7 +1151,7 @@ k_align(BatchDev b)
     // small alignments: one warp each
     for (;;) {
         int item = 0;
-        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[2], 1);
+        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[3], 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_nw_items) break;
         const NwItem it = b.nw_items[item];
@@ -1203,14 +1201,25 @@ int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int3
     return 1;
 }
 
-int launch_score(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
+int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
+{
+    if (b.n_score_items <= 0) return 0;
+    const size_t smem = sizeof(PrepWarpSmem) * kSW;
+    cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int need = (b.n_score_items + kSW - 1) / kSW;
+    const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSm, need));
+    k_prep<<<grid, kSW * 32, smem, st>>>(b, d);
+    return 1;
+}
+
+int launch_score(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
     const size_t smem = sizeof(ScoreWarpSmem) * kSW;
     cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int need = (b.n_score_items + kSW - 1) / kSW;
     const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSm, need));
-    k_score<<<grid, kSW * 32, smem, st>>>(b, d);
+    k_score<<<grid, kSW * 32, smem, st>>>(b);
     return 1;
 }
 
