@@ -664,10 +664,12 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
     for (int e0 = 0; e0 < nE2; e0 += 2) {
         const uint2 v = nx;
         if (e0 + 2 < n_elem) nx = *reinterpret_cast<const uint2 *>(el + e0 + 2);   // prefetch
-        const uint32_t ea = e0 < n_elem ? v.x : 0u;
-        const uint32_t eb = e0 + 1 < n_elem ? v.y : 0u;
-        const uint32_t oa = ea ? probe2(tab, mask, lg, (int32_t)(ea & ELEM_TOKEN)) : 0u;
-        const uint32_t ob = eb ? probe2(tab, mask, lg, (int32_t)(eb & ELEM_TOKEN)) : 0u;
+        // validity comes from the index: token 0 without flags is a real element
+        const bool va = e0 < n_elem, vb = e0 + 1 < n_elem;
+        const uint32_t ea = va ? v.x : 0u;
+        const uint32_t eb = vb ? v.y : 0u;
+        const uint32_t oa = va ? probe2(tab, mask, lg, (int32_t)(ea & ELEM_TOKEN)) : 0u;
+        const uint32_t ob = vb ? probe2(tab, mask, lg, (int32_t)(eb & ELEM_TOKEN)) : 0u;
         const uint32_t xa0 = (ea & ELEM_FIRST) ? oa : 0u;
         hit |= oa;
         const uint32_t xb0 = (ea & ELEM_END) ? hit : 0u;
