@@ -163,6 +163,25 @@ void mine_result_free(mine_ctx *ctx, mine_result *result);
 int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mine_q16 gap,
                       mine_q16 threshold, mine_pair *out, int32_t *n_out, mine_q16 *nw_score);
 
+/* Alignment of a caller-supplied matrix that allocates no device memory.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory when they call in (a process whose memory manager owns the
+ * device heap, code that must not touch the allocator for latency, or code
+ * running while allocation would fail or synchronize).  It computes what
+ * mine_align_matrix computes, with the same host arguments, on the current
+ * CUDA device and on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream), which it synchronizes before returning.  No context is needed.
+ * Scratch lives in one static device array of about 8.3 MB that every GPU
+ * loading this library holds until the process exits, so S and T are limited
+ * to 1024 (MINE_EINVAL beyond).  The first call on a device looks up the
+ * array's device address for that device; make that first call before any
+ * stream capture.  Every call shares the array (a call clears what must start
+ * at zero), so calls that overlap on the GPU, from several threads or
+ * streams, race: serialize them.  Calls no cudaMalloc or cudaFree. */
+int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T, mine_q16 gap,
+                              mine_q16 threshold, mine_pair *out, int32_t *n_out,
+                              mine_q16 *nw_score, void *stream);
+
 /* ---------------------------------------------------------------- batches
  * A batch of P article pairs in packed CSR form: document 2p is the source
  * article of pair p and document 2p+1 its target article; document d holds

@@ -122,6 +122,9 @@ int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 
+// Record the text returned by mine_last_error() for this thread (runtime.cu).
+void set_last_error(const char *msg);
+
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_COUNT = 6 };

@@ -372,6 +372,8 @@ struct Pool {
 
 }  // namespace
 
+void mine::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 // ------------------------------------------------------------------ objects
 
 struct mine_dict {

@@ -83,6 +83,8 @@ SIGNATURES = {
     "mine_run_batch_device": (_I, [_P, _P, ctypes.POINTER(BatchC), _P,
                                    ctypes.POINTER(SettingsC), _P, _P, _P, _L, _P]),
     "mine_check": (_I, [_P]),
+    "mine_align_matrix_noalloc": (_I, [_P, _I, _I, _I, _I, _P, ctypes.POINTER(_I),
+                                       ctypes.POINTER(_I), _P]),
     "mine_launch_count": (_L, [_P]),
     "mine_io_bytes": (_I, [_P, ctypes.POINTER(_L), ctypes.POINTER(_L)]),
     "mine_profile": (_I, [_P, _I]),
@@ -278,6 +280,24 @@ class Context:
             out.append((r.ticket, r.setting, r.status, r.nw_score, pairs, r.latency_ns))
             self.L.mine_result_free(self.h, ctypes.byref(buf[k]))
         return out
+
+
+def align_matrix_noalloc(M, gap, threshold, stream=None):
+    """Alignment of a host matrix without device allocation (current device).
+
+    Returns (nw_score, [(i, j, s)]) like Context.align_matrix."""
+    L = load()
+    M = _c32(M)
+    S, T = M.shape
+    out = (Pair * max(min(S, T), 1))()
+    n = ctypes.c_int32()
+    nw = ctypes.c_int32()
+    st = ctypes.c_void_p(stream if isinstance(stream, int) else
+                         (stream.cuda_stream if stream is not None else 0))
+    _check(L.mine_align_matrix_noalloc(_ptr(M), S, T, int(gap), int(threshold),
+                                       ctypes.cast(out, ctypes.c_void_p), ctypes.byref(n),
+                                       ctypes.byref(nw), st), L)
+    return nw.value, [(out[k].src_sent, out[k].tgt_sent, out[k].score) for k in range(n.value)]
 
 
 def unpack_results(P, n, nw, ns, off, sel):
