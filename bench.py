@@ -56,6 +56,27 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(workload: int, rank: int):
+    """Seed of the batch a rank mines: rank 0 mines the standard batch, every
+    other rank its own independent batch of the same shape (weak scaling)."""
+    return None if rank == 0 else 1508 + workload + 1000 * rank
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """The slowest rank's value (time-like quantities)."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 # --------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -259,8 +280,7 @@ def main():
     from paper_1509_08639_gb300 import mine, synth
 
     # every rank mines its own batch (independent pairs: weak scaling)
-    w = synth.workload(args.workload, n_pairs=args.pairs,
-                       seed=None if rank == 0 else 1508 + args.workload + 1000 * rank)
+    w = synth.workload(args.workload, n_pairs=args.pairs, seed=rank_seed(args.workload, rank))
     b = w.batch
     P = b.n_pairs
     S, T = b.sizes()
@@ -309,7 +329,7 @@ def main():
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
     ctx.profile(False)
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, ws)
     if args.only_device:
         if rank == 0:
             print(json.dumps({"workload": w.name, "pairs": P, "ms_per_step": ms,
@@ -318,11 +338,7 @@ def main():
                   flush=True)
         ctx.close()
         return
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * P / (ms / 1e3)
+    value = whole_job_rate(P, ws, ms / 1e3)
     gcups = ws * cells * n_gap / (ms / 1e3) / 1e9
 
     # ---- end to end through the host-buffer call (pinned host memory)
@@ -345,12 +361,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.run_batch_raw(dh, bc, sc, outs)
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, ws)
     io1 = ctx.io_bytes()
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
     # device-resident results equal the host-call results
     assert np.array_equal(nw.cpu().numpy(), o_nw) and np.array_equal(ns.cpu().numpy(), o_ns)
 
@@ -417,7 +429,7 @@ def main():
                    "tokens": n_tok, "l2": "inputs larger than L2 (tokens %d MB, score matrices %d MB)"
                    % (4 * n_tok >> 20, 4 * cells >> 20), "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "gcups": gcups,
-        "e2e": {"value": ws * P / e2e_s, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(P, ws, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": (io1[0] - io0[0]) // args.steps,
                 "d2h_bytes_per_step": (io1[1] - io0[1]) // args.steps},
         "plain": plain,
