@@ -8,8 +8,9 @@
 
 namespace mine {
 
-// Direction codes of the alignment (2 bits per cell, 16 cells per uint32).
-enum : uint32_t { DIR_DIAG = 0, DIR_UP = 1, DIR_LEFT = 2 };
+// Direction codes of the alignment (2 bits per cell, 16 cells per uint32;
+// code 2 is unused).
+enum : uint32_t { DIR_DIAG = 0, DIR_UP = 1, DIR_LEFT = 3 };
 
 // Source-element flag bits (token IDs are < 2^30, so the two top bits are free).
 constexpr uint32_t ELEM_FIRST = 1u << 31;   // first occurrence of this translation in U_i
@@ -96,6 +97,7 @@ struct BatchDev {
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
+    int32_t *hfin;               // [n_nw_items] H[S][T] of each alignment
     const uint64_t *recip;       // [kMaxSentTokens + 1]: ceil(2^48 / m), 0 for m = 0
     int2 *gscratch;              // per-warp tables for sentences longer than the shared ones
     int32_t *counters;           // [8] work-queue heads
@@ -120,6 +122,7 @@ int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int3
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
+int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 
 // Record the text returned by mine_last_error() for this thread (runtime.cu).
@@ -127,6 +130,6 @@ void set_last_error(const char *msg);
 
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
-                KID_TILE = 5, KID_COUNT = 6 };
+                KID_TILE = 5, KID_TRACE = 6, KID_COUNT = 7 };
 
 }  // namespace mine

@@ -901,7 +901,6 @@ struct AlignSmem {
     int32_t prod[kAW];      // stream values published by warp w (its last rows)
     int32_t cons[kAW];      // stream values warp w consumed from its predecessor
     int32_t item;
-    int32_t hfinal;
 };
 
 struct WarpPipe {
@@ -910,13 +909,53 @@ struct WarpPipe {
     int32_t *prod_mine, *prod_pred, *cons_mine, *cons_succ;
 };
 
+// One chunk of 32 wavefront steps of a stripe.  At step u lane L is at
+// column cidx = 32c + u - L; its score comes from tile c-1 (u < L) or tile c
+// (base_prev / base_cur already point at column u = 0 of the lane's row).
+// Direction codes are shifted into `word` (two bits per cell, the oldest in
+// the low bits) and stored when a 16-column word is complete.  GUARD = false
+// for chunks in which every lane is inside the matrix.
+template <bool GUARD>
+__device__ __forceinline__ void stripe_chunk(int c, int lane, int T, bool row_ok, int32_t g,
+                                             int32_t up_val, const int32_t *base_prev,
+                                             const int32_t *base_cur, uint32_t flush,
+                                             uint32_t *cr, int32_t *ring, int32_t qm,
+                                             bool publish, int32_t &h_left, int32_t &up_prev,
+                                             int32_t &h_out, uint32_t &word)
+{
+#pragma unroll 8
+    for (int u = 0; u < 32; ++u) {
+        int32_t up_in = __shfl_up_sync(kFull, h_out, 1);
+        const int32_t from_above = __shfl_sync(kFull, up_val, u);
+        up_in = (lane == 0) ? from_above : up_in;
+        const int cidx = 32 * c + u - lane;
+        const bool valid = !GUARD || (row_ok && cidx >= 0 && cidx < T);
+        if (valid) {
+            const int32_t sv = (u < lane ? base_prev : base_cur)[u];
+            const int32_t cd = up_prev + sv;
+            const int32_t cu = up_in + g;
+            const int32_t cl = h_left + g;
+            const int32_t cg = max(cu, cl);
+            const int32_t best = max(cd, cg);
+            const uint32_t code = cd >= cg ? DIR_DIAG : (cu >= cl ? DIR_UP : DIR_LEFT);
+            word = __funnelshift_r(word, code, 2);
+            if ((flush >> u) & 1u) cr[cidx >> 4] = word;
+            if (publish) ring[(qm + cidx) & (kRing - 1)] = best;
+            h_left = best;
+            h_out = best;
+            up_prev = up_in;
+        }
+    }
+}
+
 // Fill H over the stripes w, w+W, ... of one pair and write the direction
 // codes.  Stripe s publishes its last row (lane 31) as the stream values
 // gen*T + j - 1 (gen = s / W) of its warp's ring; stripe s+1 consumes them.
-// Returns false if a bounded wait ran out.
+// The lane holding (S, T) writes H[S][T] to hfin.  Returns false if a
+// bounded wait ran out.
 __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const WarpPipe &wp,
-                              const NwItem &it, const PairPlan &pp, int lane,
-                              uint32_t (&uses)[kMBuf], int32_t &hfinal)
+                              int item, const NwItem &it, const PairPlan &pp, int lane,
+                              uint32_t (&uses)[kMBuf])
 {
     const int S = pp.S, T = pp.T;
     const int32_t g = b.gap_val[it.gap];
@@ -925,15 +964,19 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
     const int CW = (T + 15) >> 4;
     uint32_t *codes = b.codes + it.code_off;
     const int32_t *Mp = b.M + pp.m_off;
+    // flush steps of this lane: columns with (cidx & 15) == 15
+    const uint32_t f0 = (uint32_t)((lane + 15) & 15);
+    const uint32_t flush = (1u << f0) | (1u << (f0 + 16));
     for (int s = wp.w; s < TS; s += wp.W) {
         const int gen = s / wp.W;
         const int i0 = 32 * s;
         const int row = i0 + lane + 1;
         const bool row_ok = row <= S;
+        const bool full_stripe = i0 + 32 <= S;
         const bool has_above = s > 0;
         const bool has_below = s + 1 < TS;
-        const int64_t qp_base = has_above ? (int64_t)((s - 1) / wp.W) * T : 0;
-        const int64_t qm_base = (int64_t)gen * T;
+        const int32_t qp_base = has_above ? ((s - 1) / wp.W) * T : 0;
+        const int32_t qm_base = gen * T;
         uint32_t *cr = codes + (int64_t)(row - 1) * CW;
         // first tiles of this stripe (buffers only ever read by generic loads)
         __syncwarp();
@@ -950,14 +993,15 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
         int32_t h_out = 0;                 // value handed to the next lane
         uint32_t word = 0;
         const int nchunks = (T + 31 + 31) >> 5;
+        int b_cur = 0;                     // buffer of tile c (= c % kMBuf)
         for (int c = 0; c < nchunks; ++c) {
             if (c < TT) {
-                const int bb = c % kMBuf;
-                if (!mbar_wait(&sm.bar[wib][bb], (uses[bb] - 1) & 1u, b.err)) return false;
+                if (!mbar_wait(&sm.bar[wib][b_cur], (uses[b_cur] - 1) & 1u, b.err)) return false;
             }
+            const int b_prev = b_cur == 0 ? kMBuf - 1 : b_cur - 1;
             if (c >= 2 && c + 1 < TT) {
                 // tile c-2 is no longer read: refill its buffer with tile c+1
-                const int bb = (c + 1) % kMBuf;
+                const int bb = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
                 __syncwarp();
                 if (lane == 0) {
                     mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
@@ -970,11 +1014,11 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
             const int jcol = 32 * c + 1 + lane;
             int32_t up_val;
             if (has_above) {
-                const int64_t need = qp_base + min(32 * c + 32, T);
-                if (!flag_wait_ge(wp.prod_pred, (int32_t)need, b.err)) return false;
+                const int32_t need = qp_base + min(32 * c + 32, T);
+                if (!flag_wait_ge(wp.prod_pred, need, b.err)) return false;
                 up_val = jcol <= T ? wp.ring_pred[(qp_base + jcol - 1) & (kRing - 1)] : 0;
                 __syncwarp();
-                if (lane == 0) *(volatile int32_t *)wp.cons_mine = (int32_t)need;
+                if (lane == 0) *(volatile int32_t *)wp.cons_mine = need;
             } else {
                 up_val = jcol * g;
             }
@@ -982,49 +1026,32 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
                 // lane 31 writes columns up to 32c+1 in this chunk: their ring
                 // slots must have been read by the successor
                 const int jmax = min(32 * c + 1, T);
-                if (jmax >= 1 &&
-                    !flag_wait_ge(wp.cons_succ, (int32_t)(qm_base + jmax - kRing), b.err))
+                if (jmax >= 1 && !flag_wait_ge(wp.cons_succ, qm_base + jmax - kRing, b.err))
                     return false;
             }
-#pragma unroll 4
-            for (int u = 0; u < 32; ++u) {
-                const int t = 32 * c + u;
-                const int j = t - lane + 1;
-                int32_t up_in = __shfl_up_sync(kFull, h_out, 1);
-                const int32_t from_ring = __shfl_sync(kFull, up_val, u);
-                if (lane == 0) up_in = from_ring;
-                if (row_ok && j >= 1 && j <= T) {
-                    const int cidx = j - 1;
-                    const int32_t sv = sm.tile[wib][(cidx >> 5) % kMBuf][lane * kTile + (cidx & 31)];
-                    const int32_t cd = up_prev + sv;
-                    const int32_t cu = up_in + g;
-                    const int32_t cl = h_left + g;
-                    const bool upw = cu >= cl;
-                    const int32_t cg = upw ? cu : cl;
-                    const bool dg = cd >= cg;
-                    const int32_t best = dg ? cd : cg;
-                    const uint32_t dir = dg ? DIR_DIAG : (upw ? DIR_UP : DIR_LEFT);
-                    word |= dir << (2 * (cidx & 15));
-                    if ((cidx & 15) == 15 || j == T) {
-                        cr[cidx >> 4] = word;
-                        word = 0;
-                    }
-                    if (lane == 31 && has_below) wp.ring_mine[(qm_base + cidx) & (kRing - 1)] = best;
-                    h_left = best;
-                    h_out = best;
-                    up_prev = up_in;
-                }
-            }
+            const int32_t *base_prev = sm.tile[wib][b_prev] + lane * kTile + 32 - lane;
+            const int32_t *base_cur = sm.tile[wib][b_cur] + lane * kTile - lane;
+            const bool publish = has_below && lane == 31;
+            if (full_stripe && c >= 1 && 32 * (c + 1) <= T)
+                stripe_chunk<false>(c, lane, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
+                                    wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word);
+            else
+                stripe_chunk<true>(c, lane, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
+                                   wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word);
             __syncwarp();
-            if (has_below && lane == 31) {
+            if (publish) {
                 const int jdone = min(32 * c + 1, T);
                 if (jdone >= 1) {
                     __threadfence_block();
-                    *(volatile int32_t *)wp.prod_mine = (int32_t)(qm_base + jdone);
+                    *(volatile int32_t *)wp.prod_mine = qm_base + jdone;
                 }
             }
+            b_cur = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
         }
-        if (s == TS - 1) hfinal = __shfl_sync(kFull, h_left, (S - 1) - i0);
+        // a last word shorter than 16 columns: its codes sit in the high bits
+        const int tail = T & 15;
+        if (row_ok && tail) cr[(T - 1) >> 4] = word >> (2 * (16 - tail));
+        if (s == TS - 1 && row == S) b.hfin[item] = h_left;
         __syncwarp();
     }
     return true;
@@ -1141,14 +1168,9 @@ k_align(BatchDev b)
         wp.prod_pred = &sm.prod[pred];
         wp.cons_mine = &sm.cons[wib];
         wp.cons_succ = &sm.cons[succ];
-        int32_t hf = 0;
-        const bool ok = align_stripes(b, sm, wib, wp, it, pp, lane, uses, hf);
-        const int last_warp = (((pp.S + 31) >> 5) - 1) % kAW;
-        if (ok && wib == last_warp && lane == 0) sm.hfinal = hf;
+        align_stripes(b, sm, wib, wp, item, it, pp, lane, uses);
         __syncthreads();
         if (*(volatile int32_t *)b.err) return;
-        if (wib == 0) trace_and_select(b, it, pp, sm.hfinal, lane);
-        __syncthreads();
     }
     // small alignments: one warp each
     for (;;) {
@@ -1158,10 +1180,7 @@ k_align(BatchDev b)
         if (item >= b.n_nw_items) break;
         const NwItem it = b.nw_items[item];
         const PairPlan pp = b.pairs[it.pair];
-        if (pp.S == 0 || pp.T == 0) {
-            select_and_emit(b, pp, it.gap, (pp.S + pp.T) * b.gap_val[it.gap], nullptr, 0, lane);
-            continue;
-        }
+        if (pp.S == 0 || pp.T == 0) continue;   // nothing to fill; k_trace reports it
         if (lane == 0) {
             sm.prod[wib] = 0;
             sm.cons[wib] = 0;
@@ -1173,9 +1192,28 @@ k_align(BatchDev b)
         wp.ring_mine = wp.ring_pred = sm.ring[wib];
         wp.prod_mine = wp.prod_pred = &sm.prod[wib];
         wp.cons_mine = wp.cons_succ = &sm.cons[wib];
-        int32_t hf = 0;
-        if (!align_stripes(b, sm, wib, wp, it, pp, lane, uses, hf)) return;
-        trace_and_select(b, it, pp, hf, lane);
+        if (!align_stripes(b, sm, wib, wp, item, it, pp, lane, uses)) return;
+    }
+}
+
+// Traceback and selection of every alignment, one warp each.
+__global__ void __launch_bounds__(128)
+k_trace(BatchDev b)
+{
+    const int lane = threadIdx.x & 31;
+    if (*(volatile int32_t *)b.err) return;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&b.counters[4], 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= b.n_nw_items) break;
+        const NwItem it = b.nw_items[item];
+        const PairPlan pp = b.pairs[it.pair];
+        if (pp.S == 0 || pp.T == 0) {
+            select_and_emit(b, pp, it.gap, (pp.S + pp.T) * b.gap_val[it.gap], nullptr, 0, lane);
+            continue;
+        }
+        trace_and_select(b, it, pp, b.hfin[item], lane);
     }
 }
 
@@ -1234,6 +1272,15 @@ int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)
     const int need = std::max(b.n_nw_big, (small + kAW - 1) / kAW);
     const int grid = std::max(1, std::min(num_sms * 2, need));
     k_align<<<grid, kAW * 32, smem, st>>>(b);
+    return 1;
+}
+
+int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    if (b.n_nw_items <= 0) return 0;
+    const int need = (b.n_nw_items + 3) / 4;
+    const int grid = std::max(1, std::min(num_sms * 8, need));
+    k_trace<<<grid, 128, 0, st>>>(b);
     return 1;
 }
 

@@ -28,7 +28,7 @@ constexpr int64_t kOffMrow = kOffM + kTilesMax * kTileElems;              // row
 constexpr int64_t kOffCodes = kOffMrow + (int64_t)kNoAllocMaxDim * kNoAllocMaxDim;
 constexpr int64_t kOffMatch = kOffCodes + (int64_t)kNoAllocMaxDim * (kNoAllocMaxDim / 16);
 constexpr int64_t kOffSel = kOffMatch + kNoAllocMaxDim;
-constexpr int64_t kOffOut = kOffSel + 3 * kNoAllocMaxDim;                 // nw_score, n_sel
+constexpr int64_t kOffOut = kOffSel + 3 * kNoAllocMaxDim;                 // nw_score, n_sel, hfin
 constexpr int64_t kOffPlan = kOffOut + 64;                                // PairPlan, NwItem, settings
 constexpr int64_t kOffCounters = kOffPlan + 64;
 constexpr int64_t kScratchWords = kOffCounters + 64;
@@ -70,6 +70,7 @@ __global__ void k_noalloc_setup(int32_t *scratch, int32_t S, int32_t T, int32_t 
     for (int k = 0; k < 64; ++k) scratch[kOffCounters + k] = 0;
     scratch[kOffOut] = 0;
     scratch[kOffOut + 1] = 0;
+    scratch[kOffOut + 2] = 0;
 }
 
 struct DeviceScratch {
@@ -160,7 +161,9 @@ extern "C" int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T
     b.nw_score = sc + kOffOut;
     b.n_sel = sc + kOffOut + 1;
     b.sel = sc + kOffSel;
+    b.hfin = sc + kOffOut + 2;
     launch_align(b, ds.num_sms, st);
+    launch_trace(b, ds.num_sms, st);
     if (cudaGetLastError() != cudaSuccess) return fail_na(MINE_ECUDA, "kernel launch failed");
     int32_t head[2] = {0, 0}, derr = 0;
     if (cudaMemcpyAsync(head, sc + kOffOut, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -219,7 +219,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
 struct Layout {
     int64_t plan = 0, plan_bytes = 0;
     int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
-    int64_t elems = 0, sinfo = 0, M = 0, Mrow = 0, codes = 0, matches = 0;
+    int64_t elems = 0, sinfo = 0, M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
     // offsets inside the plan blob
@@ -265,6 +265,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     L.M = take(4 * pl.m_elems + 16);
     L.codes = take(4 * pl.code_words + 16);
     L.matches = take(4 * pl.match_words + 16);
+    L.hfin = take(4 * (int64_t)pl.nitems.size() + 16);
     L.counters = take(4 * 16);
     L.nw = take(4 * (int64_t)pl.R);
     L.nsel = take(4 * (int64_t)pl.R);
@@ -308,6 +309,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.M = reinterpret_cast<int32_t *>(base + L.M);
     b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
     b.matches = reinterpret_cast<uint32_t *>(base + L.matches);
+    b.hfin = reinterpret_cast<int32_t *>(base + L.hfin);
     b.counters = reinterpret_cast<int32_t *>(base + L.counters);
     b.err = b.counters + 8;
     b.nw_score = reinterpret_cast<int32_t *>(base + L.nw);
@@ -512,6 +514,7 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
     n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
+    n += timed_launch(ctx, KID_TRACE, st, [&] { return launch_trace(b, ctx->num_sms, st); });
     CK(cudaGetLastError());
     ctx->launches += n;
     return 0;
@@ -956,7 +959,8 @@ int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n)
 
 const char *mine_kernel_name(int32_t id)
 {
-    static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score", "k_align", "k_tile"};
+    static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
+                                           "k_align", "k_tile", "k_trace"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
