@@ -93,6 +93,7 @@ struct BatchDev {
     // scratch
     uint32_t *elems;             // source elements (see elem_base)
     int4 *sinfo;                 // [n_sent] (n_i, #elements, |U_i|, 0) of source sentences
+    int32_t *row_order;          // [n_sent] per pair, source rows by element count (longest first)
     int32_t kmax;                // largest translation count of the dictionary
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
@@ -120,6 +121,7 @@ int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_k
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st);
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
@@ -130,6 +132,6 @@ void set_last_error(const char *msg);
 
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
-                KID_TILE = 5, KID_TRACE = 6, KID_COUNT = 7 };
+                KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_COUNT = 8 };
 
 }  // namespace mine

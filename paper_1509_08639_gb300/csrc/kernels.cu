@@ -294,9 +294,10 @@ struct alignas(16) PrepWarpSmem {
     int2 tab[kColHashSlots];
     int32_t tok[kPrepTok + 8];                   // TMA staging of a round's tokens
     int2 grp[kPrepTok];
+    uint8_t rowmap[kPrepTok];                    // row of each staged token
     unsigned long long bar;
     int32_t rtok[33];
-    int32_t recnt[32], rU[32];
+    int32_t rcnt[32], recnt[32], rU[32];
     int32_t ngrp;
 };
 
@@ -400,9 +401,9 @@ k_prep(BatchDev b, DevDict d)
         const int32_t tA = __shfl_sync(kFull, a_tok, 0);
         if (lane < nrows) sm.rtok[lane] = a_tok - tA;
         if (lane == nrows - 1) sm.rtok[nrows] = e_tok - tA;
+        sm.rcnt[lane] = 0;
         sm.recnt[lane] = 0;
         sm.rU[lane] = 0;
-        int n_i = 0;   // distinct tokens of this lane's row
         __syncwarp();
         for (int rA = 0; rA < nrows;) {
             // rows [rA, rB) with at most kPrepTok tokens, or one longer row alone
@@ -433,7 +434,7 @@ k_prep(BatchDev b, DevDict d)
                     }
                 }
                 const int nd = __reduce_add_sync(kFull, newc);
-                if (lane == rA) n_i = nd;
+                if (lane == 0) sm.rcnt[rA] = nd;
                 __syncwarp();
                 const int f = mark_first_copies(out, sm.recnt[rA], gtab, lane);
                 if (lane == 0) sm.rU[rA] = f;
@@ -448,17 +449,23 @@ k_prep(BatchDev b, DevDict d)
             if (!mbar_wait(&sm.bar, parity, b.err)) return;
             parity ^= 1u;
             __syncwarp();
-            // distinct (row, token): lane r walks the tokens of row r
+            // row of every staged token (each lane marks its row's range)
             if (lane >= rA && lane < rB) {
-                const uint32_t bit = 1u << lane;
-                const int32_t *stk = sm.tok + lead - tbase;
-                const int k1 = sm.rtok[lane + 1];
-                for (int k = sm.rtok[lane]; k < k1; ++k) {
+                const int k1 = sm.rtok[lane + 1] - tbase;
+                for (int k = sm.rtok[lane] - tbase; k < k1; ++k) sm.rowmap[k] = (uint8_t)lane;
+            }
+            __syncwarp();
+            // distinct (row, token), all lanes over the tokens: the table maps a
+            // token to the mask of rows holding it
+            {
+                const int32_t *stk = sm.tok + lead;
+                for (int k = lane; k < ntok; k += 32) {
                     const int32_t tok = stk[k];
                     if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    if (tab_set(sm.tab, lg, tok & (int32_t)ELEM_TOKEN, bit)) {
-                        ++n_i;
-                        sm.grp[atomicAdd(&sm.ngrp, 1)] = make_int2(tok & (int32_t)ELEM_TOKEN, lane);
+                    const int r = sm.rowmap[k];
+                    if (tab_set(sm.tab, lg, tok & (int32_t)ELEM_TOKEN, 1u << r)) {
+                        atomicAdd(&sm.rcnt[r], 1);
+                        sm.grp[atomicAdd(&sm.ngrp, 1)] = make_int2(tok & (int32_t)ELEM_TOKEN, r);
                     }
                 }
             }
@@ -539,7 +546,59 @@ k_prep(BatchDev b, DevDict d)
             rA = rB;
         }
         __syncwarp();
-        if (lane < nrows) b.sinfo[s_first + lane] = make_int4(n_i, sm.recnt[lane], sm.rU[lane], 0);
+        if (lane < nrows) b.sinfo[s_first + lane] = make_int4(sm.rcnt[lane], sm.recnt[lane], sm.rU[lane], 0);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- k_order
+
+// Per pair, the source rows sorted by element count, longest first (counting
+// sort on min(count, 1023); ties in any order), written to row_order[s0 ..
+// s0+S).  One warp per pair.
+__global__ void __launch_bounds__(256)
+k_order(BatchDev b)
+{
+    __shared__ int32_t hist_all[8][1024];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int32_t *hist = hist_all[wib];
+    if (*(volatile int32_t *)b.err) return;
+    for (int p = (blockIdx.x * 8 + wib); p < b.n_pairs; p += gridDim.x * 8) {
+        const PairPlan pp = b.pairs[p];
+        const int S = pp.S;
+        int32_t *ord = b.row_order + pp.s0;
+        if (S <= 32) {
+            if (lane < S) ord[lane] = lane;
+            continue;
+        }
+        for (int k = lane; k < 1024; k += 32) hist[k] = 0;
+        __syncwarp();
+        for (int r = lane; r < S; r += 32) {
+            const int key = 1023 - min(b.sinfo[(int64_t)pp.s0 + r].y, 1023);
+            atomicAdd(&hist[key], 1);
+        }
+        __syncwarp();
+        // exclusive scan of 1024 buckets: 32 per lane, then across lanes
+        int run = 0;
+        for (int k = 0; k < 32; ++k) {
+            const int v = hist[lane * 32 + k];
+            hist[lane * 32 + k] = run;
+            run += v;
+        }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int base = incl - run;
+        for (int k = 0; k < 32; ++k) hist[lane * 32 + k] += base;
+        __syncwarp();
+        for (int r = lane; r < S; r += 32) {
+            const int key = 1023 - min(b.sinfo[(int64_t)pp.s0 + r].y, 1023);
+            ord[atomicAdd(&hist[key], 1)] = r;
+        }
         __syncwarp();
     }
 }
@@ -556,6 +615,8 @@ struct alignas(16) ScoreWarpSmem {
     uint64_t Km[32];        // reciprocal of m_j
     uint64_t KL[32];        // reciprocal of L'_j
     int32_t Lt[32];
+    int32_t mcnt[32];       // m_j of the block being built
+    uint8_t colmap[kColTokCap];   // column of each staged token
 };
 
 __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b,
@@ -613,21 +674,25 @@ __device__ __forceinline__ int32_t cell_score(uint32_t a, uint32_t bb, uint64_t 
     return (int32_t)((3u * h + q_l) >> 2);
 }
 
-// Column mask of `key` in the block table: two slots are read at once; the
-// rare longer probe sequences continue in a loop.
-__device__ __forceinline__ uint32_t probe2(const int2 *tab, uint32_t mask, int lg, int32_t key)
+// Column mask of `key` in the block table (valid lanes only).  The first
+// slot settles almost every probe without a branch; lanes whose key sits
+// further along continue in a loop that the warp enters only when needed.
+__device__ __forceinline__ uint32_t probe2(const int2 *tab, uint32_t mask, int lg, int32_t key,
+                                           bool valid)
 {
     uint32_t h = hmul(key) >> (32 - lg);
-    const int2 e0 = tab[h];
-    if (e0.x == key) return (uint32_t)e0.y;
-    if (e0.x == -1) return 0u;
-    h = (h + 1) & mask;
-    for (;;) {
-        const int2 e = tab[h];
-        if (e.x == key) return (uint32_t)e.y;
-        if (e.x == -1) return 0u;
-        h = (h + 1) & mask;
+    const int2 e0 = valid ? tab[h] : make_int2(key, 0);
+    uint32_t o = e0.x == key ? (uint32_t)e0.y : 0u;
+    bool more = e0.x != key && e0.x != -1;
+    if (__any_sync(kFull, more)) {
+        while (more) {
+            h = (h + 1) & mask;
+            const int2 e = tab[h];
+            o = e.x == key ? (uint32_t)e.y : 0u;
+            more = e.x != key && e.x != -1;
+        }
     }
+    return o;
 }
 
 // Add two 32-lane bit vectors to the bit-sliced counter P: a carry-save
@@ -668,8 +733,8 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
         const bool va = e0 < n_elem, vb = e0 + 1 < n_elem;
         const uint32_t ea = va ? v.x : 0u;
         const uint32_t eb = vb ? v.y : 0u;
-        const uint32_t oa = va ? probe2(tab, mask, lg, (int32_t)(ea & ELEM_TOKEN)) : 0u;
-        const uint32_t ob = vb ? probe2(tab, mask, lg, (int32_t)(eb & ELEM_TOKEN)) : 0u;
+        const uint32_t oa = probe2(tab, mask, lg, (int32_t)(ea & ELEM_TOKEN), va);
+        const uint32_t ob = probe2(tab, mask, lg, (int32_t)(eb & ELEM_TOKEN), vb);
         const uint32_t xa0 = (ea & ELEM_FIRST) ? oa : 0u;
         hit |= oa;
         const uint32_t xb0 = (ea & ELEM_END) ? hit : 0u;
@@ -785,26 +850,28 @@ k_score(BatchDev b)
         const int T = pp.T;
         const int TT = (T + 31) >> 5;
         const int nrows = min(32, pp.S - si.row0);
-        const int64_t s_first = (int64_t)pp.s0 + si.row0;
         const int64_t tcol0 = pp.t0;
         const bool row_ok = lane < nrows;
+        // rows are taken in the pair's order of element counts, so the 32
+        // rows of one item have lists of similar length
+        const int r = row_ok ? b.row_order[(int64_t)pp.s0 + si.row0 + lane] : 0;
+        const int64_t s_row = (int64_t)pp.s0 + r;
         int4 inf = make_int4(0, 0, 0, 0);
         int32_t a_tok = 0, e_tok = 0;
         if (row_ok) {
-            inf = b.sinfo[s_first + lane];
-            a_tok = b.sent_off[s_first + lane];
-            e_tok = b.sent_off[s_first + lane + 1];
+            inf = b.sinfo[s_row];
+            a_tok = b.sent_off[s_row];
+            e_tok = b.sent_off[s_row + 1];
         }
         const int n_i = inf.x, n_elem = inf.y, nU = inf.z;
         const int Ls = e_tok - a_tok;
-        const uint32_t *el = row_ok ? b.elems + elem_base(a_tok, s_first + lane, kmax) : b.elems;
+        const uint32_t *el = row_ok ? b.elems + elem_base(a_tok, s_row, kmax) : b.elems;
         const uint64_t Ks = __ldg(&recip[n_i]);
         const uint64_t KLs = __ldg(&recip[Ls]);
         const int nE2 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 1) & ~1u);
         const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
         const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
-        int32_t *mrow = b.M + pp.m_off + (int64_t)(si.row0 >> 5) * TT * kTileElems +
-                        (row_ok ? lane : 0) * kTile;
+        int32_t *mrow = b.M + pp.m_off + (int64_t)(r >> 5) * TT * kTileElems + (r & 31) * kTile;
 
         int cur = 0;
         int c0 = 0, ntok = 0, lead = 0, ncols = 0;
@@ -835,20 +902,29 @@ k_score(BatchDev b)
             }
             pending = n_ncols > 0 && n_staged;
             __syncwarp();
-            // lane c inserts the tokens of column c and counts its distinct ones
+            // column of every staged token, then all lanes insert the block's
+            // tokens (token -> column mask) and count each column's distinct ones
             const int32_t *tks = staged ? sm.tok[cur] + lead : b.tokens + tok0;
+            sm.mcnt[lane] = 0;
+            if (staged && lane < ncols) {
+                const int k1 = sm.soff[cur][lane + 1];
+                for (int k = sm.soff[cur][lane]; k < k1; ++k) sm.colmap[k] = (uint8_t)lane;
+            }
+            __syncwarp();
+            for (int k = lane; k < ntok; k += 32) {
+                const int32_t tok = tks[k];
+                if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                const int col = staged ? sm.colmap[k] : 0;
+                if (tab_set(tab, lg, tok & (int32_t)ELEM_TOKEN, 1u << col)) atomicAdd(&sm.mcnt[col], 1);
+            }
+            __syncwarp();
             int m = 0;
             if (lane < ncols) {
-                const int k0 = sm.soff[cur][lane], k1 = sm.soff[cur][lane + 1];
-                const uint32_t bit = 1u << lane;
-                for (int k = k0; k < k1; ++k) {
-                    const int32_t tok = tks[k];
-                    if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    m += tab_set(tab, lg, tok & (int32_t)ELEM_TOKEN, bit);
-                }
+                m = sm.mcnt[lane];
+                const int Lt = sm.soff[cur][lane + 1] - sm.soff[cur][lane];
                 sm.Km[lane] = __ldg(&recip[m]);
-                sm.KL[lane] = __ldg(&recip[k1 - k0]);
-                sm.Lt[lane] = k1 - k0;
+                sm.KL[lane] = __ldg(&recip[Lt]);
+                sm.Lt[lane] = Lt;
             }
             const int maxM = (int)__reduce_max_sync(kFull, (unsigned)m);
             __syncwarp();
@@ -1249,6 +1325,14 @@ int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t s
     const int need = (b.n_score_items + kSW - 1) / kSW;
     const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSm, need));
     k_prep<<<grid, kSW * 32, smem, st>>>(b, d);
+    return 1;
+}
+
+int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    if (b.n_pairs <= 0) return 0;
+    const int grid = std::max(1, std::min(num_sms * 4, (b.n_pairs + 7) / 8));
+    k_order<<<grid, 256, 0, st>>>(b);
     return 1;
 }
 

@@ -219,7 +219,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
 struct Layout {
     int64_t plan = 0, plan_bytes = 0;
     int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
-    int64_t elems = 0, sinfo = 0, M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
+    int64_t elems = 0, sinfo = 0, order = 0, M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
     // offsets inside the plan blob
@@ -256,6 +256,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     if (scoring) {
         L.elems = take(4 * (pl.n_tok * kmax + 3 * pl.n_sent + 16));
         L.sinfo = take(16 * pl.n_sent);
+        L.order = take(4 * pl.n_sent + 16);
     } else {
         // a caller-supplied row-major matrix is copied here, then tiled
         int64_t rows = 0;
@@ -306,6 +307,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.gap_val = reinterpret_cast<const int32_t *>(plan + L.o_gapval);
     b.elems = reinterpret_cast<uint32_t *>(base + L.elems);
     b.sinfo = reinterpret_cast<int4 *>(base + L.sinfo);
+    b.row_order = reinterpret_cast<int32_t *>(base + L.order);
     b.M = reinterpret_cast<int32_t *>(base + L.M);
     b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
     b.matches = reinterpret_cast<uint32_t *>(base + L.matches);
@@ -511,6 +513,7 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         BatchDev bd = b;
         bd.kmax = dict->d.kmax;
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
     n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
@@ -960,7 +963,7 @@ int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n)
 const char *mine_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
-                                           "k_align", "k_tile", "k_trace"};
+                                           "k_align", "k_tile", "k_trace", "k_order"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
