@@ -33,7 +33,17 @@ constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins on shared-memory fl
 constexpr uint32_t kWaitHintNs = 100000;     // mbarrier try_wait suspend-time hint (100 us)
 constexpr uint32_t kMbarTries = 20000;       // try_wait attempts before giving up (<= ~2 s)
 constexpr int kScoreWarps = 4;              // warps per CTA of the score kernel
-constexpr int kScoreCtasPerSm = 4;          // its resident CTAs per SM (grid = SMs x this)
+constexpr int kScoreCtasPerSm = 4;          // CTAs per SM of the preparation kernel (grid = SMs x this)
+constexpr int kScoreWarpsScore = 2;         // warps per CTA of the score kernel (64 rows per item)
+constexpr int kScoreCtasPerSmScore = 6;     // its resident CTAs per SM
+constexpr int kBlkTokCap = 1536;            // tokens of one staged 32-column block at most
+static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kScoreWarps * kScoreCtasPerSm,
+              "the per-warp global tables are allocated for the preparation kernel's grid");
+// Target articles with at most kDirect distinct tokens are scored through
+// dense document ids (a direct-indexed column mask per id); entry kZeroEnt of
+// that mask array is never set.
+constexpr int kDirect = 8192;
+constexpr uint32_t kZeroEnt = kDirect;
 // per-warp global table of the score kernel: 2 * kMaxSentTokens (key, mask) entries
 constexpr int64_t kScoreScratchPerWarp = 2 * (int64_t)kMaxSentTokens * 8;
 
@@ -69,7 +79,7 @@ struct NwItem {         // one alignment: (pair, gap)
     int64_t match_off;  // uint32 offset of the match list (min(S,T) entries)
 };
 
-struct ScoreItem {      // 32 source rows of one pair
+struct ScoreItem {      // 32 (preparation) or 64 (scoring) source rows of one pair
     int32_t pair;
     int32_t row0;
 };
@@ -82,7 +92,9 @@ struct BatchDev {
     int32_t n_pairs;
     // plan
     const PairPlan *pairs;
-    const ScoreItem *score_items;
+    const ScoreItem *prep_items;     // 32 rows each
+    int32_t n_prep_items;
+    const ScoreItem *score_items;    // 64 rows each
     int32_t n_score_items;
     const NwItem *nw_items;
     int32_t n_nw_items;
@@ -94,6 +106,9 @@ struct BatchDev {
     uint32_t *elems;             // source elements (see elem_base)
     int4 *sinfo;                 // [n_sent] (n_i, #elements, |U_i|, 0) of source sentences
     int32_t *row_order;          // [n_sent] per pair, source rows by element count (longest first)
+    uint16_t *tdoc;              // [n_tok + 32] document id of each target token
+    int32_t *pdoc;               // [n_pairs] distinct target tokens D, or -1 (token-keyed path)
+    const int32_t *dorder;       // [n_pairs] pairs by article size, longest first
     int32_t kmax;                // largest translation count of the dictionary
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
@@ -121,6 +136,7 @@ int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_k
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st);
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_doc(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
@@ -132,6 +148,7 @@ void set_last_error(const char *msg);
 
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
-                KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_COUNT = 8 };
+                KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
+                KID_COUNT = 9 };
 
 }  // namespace mine

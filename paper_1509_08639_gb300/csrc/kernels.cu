@@ -282,6 +282,7 @@ __global__ void k_validate(const int32_t *__restrict__ sent_off, int64_t n_sent,
 // ---------------------------------------------------------------- row preparation
 
 constexpr int kSW = kScoreWarps;
+constexpr int kSWS = kScoreWarpsScore;
 constexpr int kPrepTok = 256;                    // tokens per preparation round
 constexpr int kPrepElem = kColHashSlots / 2;     // translations per dedupe round
 constexpr int kGTabSlots = 2 * kMaxSentTokens;   // per-warp global table for long sentences
@@ -388,8 +389,8 @@ k_prep(BatchDev b, DevDict d)
         int item = 0;
         if (lane == 0) item = atomicAdd(&b.counters[0], 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= b.n_score_items) break;
-        const ScoreItem si = b.score_items[item];
+        if (item >= b.n_prep_items) break;
+        const ScoreItem si = b.prep_items[item];
         const PairPlan pp = b.pairs[si.pair];
         const int nrows = min(32, pp.S - si.row0);
         const int64_t s_first = (int64_t)pp.s0 + si.row0;
@@ -551,6 +552,161 @@ k_prep(BatchDev b, DevDict d)
     }
 }
 
+// ---------------------------------------------------------------- k_doc
+
+constexpr int kDocThreads = 256;
+constexpr int kDocSlots = 2 * kDirect;     // document table: at most ~53% full
+constexpr int kDocLog2 = 14;
+static_assert((1 << kDocLog2) == kDocSlots, "document table size");
+
+struct alignas(16) DocSmem {
+    int32_t key[kDocSlots];
+    uint16_t dval[kDocSlots];
+    int32_t nd;
+    int32_t item;
+};
+
+// Document id of target token `tok`, or -1 when the article lacks it.
+__device__ __forceinline__ int doc_find(const int32_t *key, const uint16_t *dval, int32_t tok)
+{
+    uint32_t h = hmul(tok) >> (32 - kDocLog2);
+    for (;;) {   // ends: the table always has empty slots
+        const int32_t k = key[h];
+        if (k == tok) return dval[h];
+        if (k == -1) return -1;
+        h = (h + 1) & (kDocSlots - 1);
+    }
+}
+
+__device__ __forceinline__ void doc_insert(DocSmem &sm, int32_t tok)
+{
+    uint32_t h = hmul(tok) >> (32 - kDocLog2);
+    for (;;) {
+        const int32_t old = atomicCAS(&sm.key[h], -1, tok);
+        if (old == -1) {
+            sm.dval[h] = (uint16_t)min(atomicAdd(&sm.nd, 1), 65535);
+            return;
+        }
+        if (old == tok) return;
+        h = (h + 1) & (kDocSlots - 1);
+    }
+}
+
+// Keep, of one source row's element list, the translations the target
+// article holds, in place: (id | FIRST), END on the last kept translation of
+// each source token.  Returns the kept count; nf receives the kept FIRSTs.
+__device__ __forceinline__ int compact_row(const DocSmem &sm, uint32_t *el, int n, int &nf)
+{
+    int w = 0;
+    nf = 0;
+    uint32_t pend = 0;
+    bool has = false;
+    uint4 nx = make_uint4(0u, 0u, 0u, 0u);
+    if (0 < n) nx = *reinterpret_cast<const uint4 *>(el);
+    for (int k = 0; k < n; k += 4) {
+        const uint4 v = nx;
+        // read ahead: writes so far stay below index k + 4
+        if (k + 4 < n) nx = *reinterpret_cast<const uint4 *>(el + k + 4);
+        const uint32_t ev[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (k + q >= n) break;
+            const uint32_t e = ev[q];
+            const int d = doc_find(sm.key, sm.dval, (int32_t)(e & ELEM_TOKEN));
+            if (d >= 0) {
+                if (has) el[w++] = pend;
+                pend = (uint32_t)d | (e & ELEM_FIRST);
+                nf += (e & ELEM_FIRST) ? 1 : 0;
+                has = true;
+            }
+            if ((e & ELEM_END) && has) {
+                el[w++] = pend | ELEM_END;
+                has = false;
+            }
+        }
+    }
+    if (has) el[w++] = pend | ELEM_END;
+    return w;
+}
+
+// One CTA per pair (largest first).  The distinct tokens of the target
+// article get dense ids 0..D-1.  When D <= kDirect every target token's id
+// goes to tdoc and each source row's element list is compacted in place to
+// the translations the target article holds, with (n_i, #kept, #kept FIRST)
+// in sinfo; pdoc[p] = D.  An article with more distinct tokens gets
+// pdoc[p] = -1 and is scored on the token-keyed path.
+__global__ void __launch_bounds__(kDocThreads)
+k_doc(BatchDev b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DocSmem &sm = *reinterpret_cast<DocSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (*(volatile int32_t *)b.err) return;
+    for (;;) {
+        __syncthreads();   // the previous pair is done with the table
+        if (tid == 0) {
+            sm.item = atomicAdd(&b.counters[5], 1);
+            sm.nd = 0;
+        }
+        int4 *kz = reinterpret_cast<int4 *>(sm.key);
+        for (int k = tid; k < kDocSlots / 4; k += kDocThreads) kz[k] = make_int4(-1, -1, -1, -1);
+        __syncthreads();
+        const int item = sm.item;
+        if (item >= b.n_pairs) break;
+        const int p = b.dorder[item];
+        const PairPlan pp = b.pairs[p];
+        const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
+        // 1. distinct target tokens -> dense ids, four loads in flight per
+        //    thread; stops once the ids cannot all fit
+        for (int32_t k = ta + tid; k < tb; k += 4 * kDocThreads) {
+            if (*(volatile int32_t *)&sm.nd > kDirect) break;
+            int32_t tk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t kk = k + q * kDocThreads;
+                tk[q] = kk < tb ? b.tokens[kk] : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (k + q * kDocThreads >= tb) break;
+                if ((uint32_t)tk[q] > ELEM_TOKEN) {
+                    atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    continue;
+                }
+                doc_insert(sm, tk[q]);
+            }
+        }
+        __syncthreads();
+        const int D = sm.nd;
+        if (tid == 0) b.pdoc[p] = D <= kDirect ? D : -1;
+        if (D > kDirect) continue;
+        // 2. id of every target token
+        for (int32_t k = ta + tid; k < tb; k += 4 * kDocThreads) {
+            int32_t tk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t kk = k + q * kDocThreads;
+                tk[q] = kk < tb ? b.tokens[kk] : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t kk = k + q * kDocThreads;
+                if (kk < tb)
+                    b.tdoc[kk] = (uint16_t)max(doc_find(sm.key, sm.dval, tk[q] & (int32_t)ELEM_TOKEN), 0);
+            }
+        }
+        // 3. source rows: keep the translations the target article holds
+        for (int r = tid; r < pp.S; r += kDocThreads) {
+            const int64_t si = (int64_t)pp.s0 + r;
+            const int4 inf = b.sinfo[si];
+            uint32_t *el = b.elems + elem_base(b.sent_off[si], si, b.kmax);
+            int nf;
+            const int w = compact_row(sm, el, inf.y, nf);
+            b.sinfo[si] = make_int4(inf.x, w, nf, 0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- k_order
 
 // Per pair, the source rows sorted by element count, longest first (counting
@@ -605,18 +761,41 @@ k_order(BatchDev b)
 
 // ---------------------------------------------------------------- k_score
 
-// Per-warp shared memory of k_score: the column-block table (target token ->
-// mask of the block's columns holding it) and two TMA staging buffers.
-struct alignas(16) ScoreWarpSmem {
+// Per-warp buffers of the token-keyed path: the column-block table (target
+// token -> mask of the block's columns holding it), two TMA staging buffers,
+// the column of each staged token and the block's column data.
+struct alignas(16) KeyedWarp {
     int2 tab[kColHashSlots];
     int32_t tok[2][kColTokCap + 8];
-    unsigned long long bar[2];
+    uint8_t colmap[kColTokCap];
     int32_t soff[2][33];
     uint64_t Km[32];        // reciprocal of m_j
     uint64_t KL[32];        // reciprocal of L'_j
     int32_t Lt[32];
     int32_t mcnt[32];       // m_j of the block being built
-    uint8_t colmap[kColTokCap];   // column of each staged token
+};
+
+// CTA buffers of the document-id path: a column mask per document id (entry
+// kZeroEnt stays zero), the TMA-staged ids of one block's tokens and the
+// block's column data.
+struct alignas(16) DirectCta {
+    uint32_t mask[kDirect + 16];
+    uint16_t ids[kBlkTokCap + 32];
+    uint64_t Km[32];
+    uint64_t KL[32];
+    int32_t Lt[32];
+};
+
+// Shared memory of one k_score CTA (kSWS warps).  The mbarriers stay outside
+// the union: both paths write it with generic stores.
+struct alignas(16) ScoreSmem {
+    union {
+        KeyedWarp kw[kSWS];
+        DirectCta d;
+    };
+    unsigned long long bar[kSWS][2];   // token-keyed path, per warp
+    unsigned long long dbar;           // document-id path
+    int32_t item;
 };
 
 __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b,
@@ -710,11 +889,17 @@ __device__ __forceinline__ void add2(uint32_t (&P)[NPL], uint32_t x, uint32_t y)
     }
 }
 
+template <int NPL>
+__device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
+                                         const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
+                                         uint64_t Ks, uint64_t KLs, int Ls, int ncols,
+                                         int32_t *mrow, int c0);
+
 // Accumulate the overlap counts of one column block and score its cells
 // into row `lane` of the score tiles (mrow points at column tile 0).
 // NPL <= 8: bit planes are turned into byte counts by 8 x 8 transposes.
 template <int NPL>
-__device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 *tab, int lg,
+__device__ __forceinline__ void score_block(const KeyedWarp &sm, const int2 *tab, int lg,
                                          const uint32_t *el, int n_elem, int nE2, int ncols,
                                          bool row_ok, uint64_t Ks, uint64_t KLs, int Ls,
                                          int32_t *mrow, int c0)
@@ -747,6 +932,19 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
         add2<NPL>(B, xb0, xb1);
     }
     if (!row_ok) return;
+    emit_row<NPL>(A, B, sm.Km, sm.KL, sm.Lt, Ks, KLs, Ls, ncols, mrow, c0);
+}
+
+// Score the cells of one row and one column block from its bit-sliced counts
+// A (|U_i and X_j|) and B (source tokens with a translation in X_j) into the
+// row's score tiles (mrow points at column tile 0).  NPL <= 8: bit planes are
+// turned into byte counts by 8 x 8 transposes.
+template <int NPL>
+__device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
+                                         const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
+                                         uint64_t Ks, uint64_t KLs, int Ls, int ncols,
+                                         int32_t *mrow, int c0)
+{
     const bool whole = ncols == 32 && (c0 & 31) == 0;   // one whole row of one tile
     if constexpr (NPL <= 8) {
         uint32_t A8[8], B8[8];
@@ -766,7 +964,7 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
                 const int jj = 8 * m + c;
                 const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
                 const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
-                v[c] = cell_score(a, bb, sm.Km[jj], Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+                v[c] = cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
             }
             if (whole) {
                 int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
@@ -785,12 +983,279 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
         }
     } else {
         for (int jj = 0; jj < ncols; ++jj) {
-            const int32_t v = cell_score(plane_value<NPL>(A, jj), plane_value<NPL>(B, jj), sm.Km[jj],
-                                         Ks, Ls, sm.Lt[jj], KLs, sm.KL[jj]);
+            const int32_t v = cell_score(plane_value<NPL>(A, jj), plane_value<NPL>(B, jj), Km[jj],
+                                         Ks, Ls, Lt[jj], KLs, KL[jj]);
             const int col = c0 + jj;
             mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v;
         }
     }
+}
+
+// Add eight 32-lane bit vectors to the bit-sliced counter P (planes 0..2 are
+// the ones / twos / fours of a carry-save tree; the weight-8 carry ripples
+// into the planes above).
+template <int NPL>
+__device__ __forceinline__ void add8(uint32_t (&P)[NPL], const uint32_t (&x)[8])
+{
+    uint32_t t1, t2, f1, f2, e;
+    csa(t1, P[0], P[0], x[0], x[1]);
+    csa(t2, P[0], P[0], x[2], x[3]);
+    csa(f1, P[1], P[1], t1, t2);
+    csa(t1, P[0], P[0], x[4], x[5]);
+    csa(t2, P[0], P[0], x[6], x[7]);
+    csa(f2, P[1], P[1], t1, t2);
+    csa(e, P[2], P[2], f1, f2);
+#pragma unroll
+    for (int k = 3; k < NPL; ++k) {
+        const uint32_t n = P[k] & e;
+        P[k] ^= e;
+        e = n;
+    }
+}
+
+// Overlap counts of one row and one 32-column block on the document-id path:
+// the row's hit list (document id | FIRST | END of its token group) is read
+// eight entries at a time; each id's column mask comes from the block's mask
+// array.  A counts FIRST entries, B counts token groups with any hit.
+template <int NPL>
+__device__ __forceinline__ void direct_counts(const uint32_t *mask, const uint32_t *hl, int n_h,
+                                              int nIt, uint4 f0, uint4 f1, uint32_t (&A)[NPL],
+                                              uint32_t (&B)[NPL])
+{
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) A[k] = B[k] = 0u;
+    uint32_t hit = 0;
+    // entries 0..7 stay in registers for the whole item; later ones are read
+    // one step ahead
+    uint4 n0 = make_uint4(0u, 0u, 0u, 0u), n1 = n0;
+    if (8 < n_h) {
+        n0 = *reinterpret_cast<const uint4 *>(hl + 8);
+        n1 = *reinterpret_cast<const uint4 *>(hl + 12);
+    }
+#pragma unroll 1
+    for (int it = 0; it < nIt; ++it) {
+        const int k0 = it * 8;
+        uint4 v0 = f0, v1 = f1;
+        if (it > 0) {
+            v0 = n0;
+            v1 = n1;
+            if (k0 + 8 < n_h) {
+                n0 = *reinterpret_cast<const uint4 *>(hl + k0 + 8);
+                n1 = *reinterpret_cast<const uint4 *>(hl + k0 + 12);
+            }
+        }
+        const uint32_t ev[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint32_t xa[8], xb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const bool ok = k0 + q < n_h;
+            const uint32_t en = ok ? ev[q] : 0u;
+            const uint32_t m = mask[ok ? min(en & ELEM_TOKEN, (uint32_t)kZeroEnt) : (uint32_t)kZeroEnt];
+            xa[q] = (en & ELEM_FIRST) ? m : 0u;
+            hit |= m;
+            xb[q] = (en & ELEM_END) ? hit : 0u;
+            hit = (en & ELEM_END) ? 0u : hit;
+        }
+        add8<NPL>(A, xa);
+        add8<NPL>(B, xb);
+    }
+}
+
+// Stage the document ids of tokens [k0, k1) into ids[] (one bulk copy of the
+// 16-byte aligned range around them); returns the offset of k0 in ids[].
+__device__ __forceinline__ int stage_ids(const BatchDev &b, uint16_t *ids, unsigned long long *bar,
+                                         int32_t k0, int32_t k1, bool issue)
+{
+    const int32_t a0 = k0 & ~7, a1 = (k1 + 7) & ~7;   // the id array is padded past n_tok
+    if (issue) {
+        const uint32_t bytes = (uint32_t)(2 * (a1 - a0));
+        mbar_expect_tx(bar, bytes);
+        if (bytes) bulk_g2s(ids, b.tdoc + a0, bytes, bar);
+    }
+    return k0 - a0;
+}
+
+// One score item (up to 64 source rows) on the document-id path, block by
+// block (32 columns), by the whole CTA: the block's ids are staged by TMA
+// (one block ahead); threads 2j and 2j+1 set bit j in the mask of every id of
+// target sentence j and count m_j on the way; every warp counts the hits of
+// its 32 rows and scores their cells; the masks of ids [0, D) are cleared
+// again.  A block with more than kBlkTokCap tokens reads its ids from global
+// memory.  Returns false (on every thread) when a bounded wait ran out.
+__device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned long long *dbar,
+                                  uint32_t &dparity, const PairPlan &pp, int D, int tid, int nrows,
+                                  bool row_ok, const uint32_t *hl, int n_h, uint64_t Ks,
+                                  uint64_t KLs, int Ls, int32_t *mrow)
+{
+    const int T = pp.T;
+    const int maxH = (int)__reduce_max_sync(kFull, (unsigned)n_h);   // this warp's rows
+    const int nIt = (maxH + 7) >> 3;
+    uint4 f0 = make_uint4(0u, 0u, 0u, 0u), f1 = f0;
+    if (0 < n_h) {
+        f0 = *reinterpret_cast<const uint4 *>(hl);
+        f1 = *reinterpret_cast<const uint4 *>(hl + 4);
+    }
+    const int col = tid >> 1, half = tid & 1;
+    const int64_t t0 = pp.t0;
+    int32_t k0 = b.sent_off[t0], k1 = b.sent_off[t0 + min(32, T)];
+    bool staged = k1 - k0 <= kBlkTokCap;
+    int lead = staged ? stage_ids(b, sd.ids, dbar, k0, k1, tid == 0) : 0;
+    for (int c0 = 0; c0 < T; c0 += 32) {
+        const int ncols = min(32, T - c0);
+        const int64_t j0 = t0 + c0;
+        int32_t a = 0, e = 0;
+        if (col < ncols) {
+            a = b.sent_off[j0 + col];
+            e = b.sent_off[j0 + col + 1];
+        }
+        // next block's token range, read while this one is in flight
+        const bool more = c0 + 32 < T;
+        int32_t nk1 = 0;
+        if (more) nk1 = b.sent_off[j0 + 32 + min(32, T - c0 - 32)];
+        bool ok = true;
+        if (staged) {
+            ok = mbar_wait(dbar, dparity, b.err);
+            dparity ^= 1u;
+        }
+        if (!__syncthreads_and(ok)) return false;
+        const uint32_t bit = 1u << col;
+        int m = 0;
+        if (staged) {
+            const uint16_t *ids = sd.ids + lead - k0;
+            for (int32_t k = a + half; k < e; k += 2)
+                m += (atomicOr(&sd.mask[min((uint32_t)ids[k], kZeroEnt - 1)], bit) & bit) ? 0 : 1;
+        } else {
+            for (int32_t k = a + half; k < e; k += 2)
+                m += (atomicOr(&sd.mask[min((uint32_t)b.tdoc[k], kZeroEnt - 1)], bit) & bit) ? 0 : 1;
+        }
+        m += __shfl_xor_sync(kFull, m, 1);
+        if (half == 0 && col < ncols) {
+            sd.Km[col] = __ldg(&b.recip[m]);
+            sd.KL[col] = __ldg(&b.recip[e - a]);
+            sd.Lt[col] = e - a;
+        }
+        __syncthreads();
+        // the ids are in the masks now: stage the next block's
+        if (more) {
+            k0 = k1;
+            k1 = nk1;
+            staged = k1 - k0 <= kBlkTokCap;
+            if (staged) lead = stage_ids(b, sd.ids, dbar, k0, k1, tid == 0);
+        }
+        if (nrows > 0) {
+            if (maxH < 256) {
+                uint32_t A[8], B[8];
+                direct_counts<8>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
+                if (row_ok) emit_row<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0);
+            } else {
+                uint32_t A[11], B[11];
+                direct_counts<11>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
+                if (row_ok) emit_row<11>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0);
+            }
+        }
+        __syncthreads();
+        uint4 *mz = reinterpret_cast<uint4 *>(sd.mask);
+        for (int k = tid; k < (D + 3) >> 2; k += kSWS * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+    }
+    return true;
+}
+
+__device__ __forceinline__ int plan_block(const BatchDev &b, KeyedWarp &sm, unsigned long long *bar,
+                                          int buf, int64_t tcol0, int c0, int T, int lane, int &ntok,
+                                          int &lead, bool &generic, bool &staged, int64_t &tok0);
+
+// One score item on the token-keyed path, one warp for its 32 rows.
+// Returns false when a bounded wait ran out.
+__device__ bool score_item_keyed(const BatchDev &b, KeyedWarp &sm, unsigned long long *bar,
+                                 uint32_t (&parity)[2], bool (&generic)[2], int2 *gtab,
+                                 const PairPlan &pp, int lane, bool row_ok, const uint32_t *el,
+                                 int n_elem, int nU, int n_i, uint64_t Ks, uint64_t KLs, int Ls,
+                                 int32_t *mrow)
+{
+    const int T = pp.T;
+    const int64_t tcol0 = pp.t0;
+    const uint64_t *recip = b.recip;
+    const int nE2 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 1) & ~1u);
+    const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
+    const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
+    int cur = 0;
+    int c0 = 0, ntok = 0, lead = 0, ncols = 0;
+    bool staged = false;
+    int64_t tok0 = 0;
+    if (T > 0)
+        ncols = plan_block(b, sm, bar, 0, tcol0, 0, T, lane, ntok, lead, generic[0], staged, tok0);
+    bool pending = ncols > 0 && staged;   // a copy in flight into buffer `cur`
+    while (c0 < T) {
+        if (ncols == 0) {
+            if (lane == 0) atomicCAS(b.err, 0, ERR_BAD_OFFSETS);
+            break;
+        }
+        int2 *tab = staged ? sm.tab : gtab;
+        const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
+        tab_clear(tab, 1 << lg, lane);
+        // prefetch the next block into the other buffer while this one is built and scored
+        const int nc0 = c0 + ncols;
+        int n_ncols = 0, n_ntok = 0, n_lead = 0;
+        bool n_staged = false;
+        int64_t n_tok0 = 0;
+        if (nc0 < T)
+            n_ncols = plan_block(b, sm, bar, cur ^ 1, tcol0, nc0, T, lane, n_ntok, n_lead,
+                                 generic[cur ^ 1], n_staged, n_tok0);
+        if (staged) {
+            if (!mbar_wait(&bar[cur], parity[cur], b.err)) return false;
+            parity[cur] ^= 1u;
+        }
+        pending = n_ncols > 0 && n_staged;
+        __syncwarp();
+        // column of every staged token, then all lanes insert the block's
+        // tokens (token -> column mask) and count each column's distinct ones
+        const int32_t *tks = staged ? sm.tok[cur] + lead : b.tokens + tok0;
+        sm.mcnt[lane] = 0;
+        if (staged && lane < ncols) {
+            const int k1 = sm.soff[cur][lane + 1];
+            for (int k = sm.soff[cur][lane]; k < k1; ++k) sm.colmap[k] = (uint8_t)lane;
+        }
+        __syncwarp();
+        for (int k = lane; k < ntok; k += 32) {
+            const int32_t tok = tks[k];
+            if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+            const int col = staged ? sm.colmap[k] : 0;
+            if (tab_set(tab, lg, tok & (int32_t)ELEM_TOKEN, 1u << col)) atomicAdd(&sm.mcnt[col], 1);
+        }
+        __syncwarp();
+        int m = 0;
+        if (lane < ncols) {
+            m = sm.mcnt[lane];
+            const int Lt = sm.soff[cur][lane + 1] - sm.soff[cur][lane];
+            sm.Km[lane] = __ldg(&recip[m]);
+            sm.KL[lane] = __ldg(&recip[Lt]);
+            sm.Lt[lane] = Lt;
+        }
+        const int maxM = (int)__reduce_max_sync(kFull, (unsigned)m);
+        __syncwarp();
+        const int bound = max(min(maxU, maxM), maxN);
+        if (bound < 256) {
+            score_block<8>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+        } else {
+            score_block<11>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+        }
+        __syncwarp();
+        c0 = nc0;
+        ncols = n_ncols;
+        ntok = n_ntok;
+        lead = n_lead;
+        staged = n_staged;
+        tok0 = n_tok0;
+        cur ^= 1;
+    }
+    if (pending) {   // a block was staged but not used (bad offsets): let it land
+        const bool ok = mbar_wait(&bar[cur], parity[cur], b.err);
+        parity[cur] ^= 1u;
+        if (!ok) return false;
+    }
+    __syncwarp();
+    return true;
 }
 
 // Plan the column block starting at c0: widest run of <= 32 target sentences
@@ -798,8 +1263,8 @@ __device__ __forceinline__ void score_block(const ScoreWarpSmem &sm, const int2 
 // column longer than kColTokCap becomes an unstaged block (staged = false)
 // read from global memory into the per-warp global table.  Returns ncols
 // (>= 1, or 0 on bad offsets); tok0 receives the block's first token index.
-__device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, int buf,
-                                          int64_t tcol0, int c0, int T, int lane, int &ntok,
+__device__ __forceinline__ int plan_block(const BatchDev &b, KeyedWarp &sm, unsigned long long *bar,
+                                          int buf, int64_t tcol0, int c0, int T, int lane, int &ntok,
                                           int &lead, bool &generic, bool &staged, int64_t &tok0)
 {
     tok0 = b.sent_off[tcol0 + c0];
@@ -816,45 +1281,51 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, ScoreWarpSmem &sm, 
     if (lane < ncols) sm.soff[buf][lane + 1] = cum;
     if (lane == 0) sm.soff[buf][0] = 0;
     lead = 0;
-    if (staged) lead = stage_tokens(b, sm.tok[buf], &sm.bar[buf], tok0, ntok, lane, generic);
+    if (staged) lead = stage_tokens(b, sm.tok[buf], &bar[buf], tok0, ntok, lane, generic);
     return ncols;
 }
 
-__global__ void __launch_bounds__(kSW * 32)
+__global__ void __launch_bounds__(kSWS * 32)
 k_score(BatchDev b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    ScoreWarpSmem &sm = reinterpret_cast<ScoreWarpSmem *>(smem_raw)[wib];
-    int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * kSW + wib) * kGTabSlots;
+    ScoreSmem &S = *reinterpret_cast<ScoreSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int wib = tid >> 5;
+    KeyedWarp &kw = S.kw[wib];
+    unsigned long long *kbar = S.bar[wib];
+    int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * kSWS + wib) * kGTabSlots;
     const uint64_t *recip = b.recip;
     const int kmax = b.kmax;
     if (lane == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+        mbar_init(&kbar[0], 1);
+        mbar_init(&kbar[1], 1);
+        if (wib == 0) mbar_init(&S.dbar, 1);
         fence_barrier_init();
     }
-    __syncwarp();
-    uint32_t parity[2] = {0u, 0u};
-    bool generic[2] = {false, false};   // generic stores wrote into tok[buf] since its last copy
-    if (*(volatile int32_t *)b.err) return;
+    uint32_t parity[2] = {0u, 0u}, dparity = 0u;
+    bool generic[2] = {false, false};   // generic stores wrote into kw.tok[buf] since its last copy
+    bool mask_clean = false;            // S.d.mask is all zero
+    bool ok = true;
 
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(&b.counters[1], 1);
-        item = __shfl_sync(kFull, item, 0);
+        // every thread leaves together: on an error (here or in another CTA)
+        // or when the queue is empty
+        if (__syncthreads_or(!ok || *(volatile int32_t *)b.err != 0)) break;
+        if (tid == 0) S.item = atomicAdd(&b.counters[1], 1);
+        __syncthreads();
+        const int item = S.item;
         if (item >= b.n_score_items) break;
         const ScoreItem si = b.score_items[item];
         const PairPlan pp = b.pairs[si.pair];
-        const int T = pp.T;
-        const int TT = (T + 31) >> 5;
-        const int nrows = min(32, pp.S - si.row0);
-        const int64_t tcol0 = pp.t0;
+        const int TT = (pp.T + 31) >> 5;
+        // this warp's 32 rows, in the pair's order of element counts (the
+        // rows of one warp have lists of similar length)
+        const int row0 = si.row0 + 32 * wib;
+        const int nrows = max(0, min(32, pp.S - row0));
         const bool row_ok = lane < nrows;
-        // rows are taken in the pair's order of element counts, so the 32
-        // rows of one item have lists of similar length
-        const int r = row_ok ? b.row_order[(int64_t)pp.s0 + si.row0 + lane] : 0;
+        const int r = row_ok ? b.row_order[(int64_t)pp.s0 + row0 + lane] : 0;
         const int64_t s_row = (int64_t)pp.s0 + r;
         int4 inf = make_int4(0, 0, 0, 0);
         int32_t a_tok = 0, e_tok = 0;
@@ -868,87 +1339,29 @@ k_score(BatchDev b)
         const uint32_t *el = row_ok ? b.elems + elem_base(a_tok, s_row, kmax) : b.elems;
         const uint64_t Ks = __ldg(&recip[n_i]);
         const uint64_t KLs = __ldg(&recip[Ls]);
-        const int nE2 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 1) & ~1u);
-        const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
-        const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
         int32_t *mrow = b.M + pp.m_off + (int64_t)(r >> 5) * TT * kTileElems + (r & 31) * kTile;
 
-        int cur = 0;
-        int c0 = 0, ntok = 0, lead = 0, ncols = 0;
-        bool staged = false;
-        int64_t tok0 = 0;
-        if (T > 0)
-            ncols = plan_block(b, sm, 0, tcol0, 0, T, lane, ntok, lead, generic[0], staged, tok0);
-        bool pending = ncols > 0 && staged;   // a copy in flight into buffer `cur`
-        while (c0 < T) {
-            if (ncols == 0) {
-                if (lane == 0) atomicCAS(b.err, 0, ERR_BAD_OFFSETS);
-                break;
+        const int D = b.pdoc[si.pair];
+        if (D >= 0) {
+            // document-id path (the element list holds the row's hits)
+            if (!mask_clean) {
+                // the token-keyed path wrote these bytes with generic stores
+                uint4 *mz = reinterpret_cast<uint4 *>(S.d.mask);
+                for (int k = tid; k < (kDirect + 16) / 4; k += kSWS * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
+                fence_proxy_async();
+                __syncthreads();
+                mask_clean = true;
             }
-            int2 *tab = staged ? sm.tab : gtab;
-            const int lg = max(6, ceil_log2(2 * max(ntok, 1)));
-            tab_clear(tab, 1 << lg, lane);
-            // prefetch the next block into the other buffer while this one is built and scored
-            const int nc0 = c0 + ncols;
-            int n_ncols = 0, n_ntok = 0, n_lead = 0;
-            bool n_staged = false;
-            int64_t n_tok0 = 0;
-            if (nc0 < T)
-                n_ncols = plan_block(b, sm, cur ^ 1, tcol0, nc0, T, lane, n_ntok, n_lead,
-                                     generic[cur ^ 1], n_staged, n_tok0);
-            if (staged) {
-                if (!mbar_wait(&sm.bar[cur], parity[cur], b.err)) return;
-                parity[cur] ^= 1u;
-            }
-            pending = n_ncols > 0 && n_staged;
-            __syncwarp();
-            // column of every staged token, then all lanes insert the block's
-            // tokens (token -> column mask) and count each column's distinct ones
-            const int32_t *tks = staged ? sm.tok[cur] + lead : b.tokens + tok0;
-            sm.mcnt[lane] = 0;
-            if (staged && lane < ncols) {
-                const int k1 = sm.soff[cur][lane + 1];
-                for (int k = sm.soff[cur][lane]; k < k1; ++k) sm.colmap[k] = (uint8_t)lane;
-            }
-            __syncwarp();
-            for (int k = lane; k < ntok; k += 32) {
-                const int32_t tok = tks[k];
-                if ((uint32_t)tok > ELEM_TOKEN) atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                const int col = staged ? sm.colmap[k] : 0;
-                if (tab_set(tab, lg, tok & (int32_t)ELEM_TOKEN, 1u << col)) atomicAdd(&sm.mcnt[col], 1);
-            }
-            __syncwarp();
-            int m = 0;
-            if (lane < ncols) {
-                m = sm.mcnt[lane];
-                const int Lt = sm.soff[cur][lane + 1] - sm.soff[cur][lane];
-                sm.Km[lane] = __ldg(&recip[m]);
-                sm.KL[lane] = __ldg(&recip[Lt]);
-                sm.Lt[lane] = Lt;
-            }
-            const int maxM = (int)__reduce_max_sync(kFull, (unsigned)m);
-            __syncwarp();
-            const int bound = max(min(maxU, maxM), maxN);
-            if (bound < 256) {
-                score_block<8>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
-            } else {
-                score_block<11>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
-            }
-            __syncwarp();
-            c0 = nc0;
-            ncols = n_ncols;
-            ntok = n_ntok;
-            lead = n_lead;
-            staged = n_staged;
-            tok0 = n_tok0;
-            cur ^= 1;
+            // generic stores now cover the keyed staging buffers: fence before their next copy
+            generic[0] = generic[1] = true;
+            ok = score_item_direct(b, S.d, &S.dbar, dparity, pp, D, tid, nrows, row_ok, el, n_elem,
+                                   Ks, KLs, Ls, mrow);
+            continue;
         }
-        if (pending) {   // a block was staged but not used (bad offsets): let it land
-            mbar_wait(&sm.bar[cur], parity[cur], b.err);
-            parity[cur] ^= 1u;
-        }
-        if (*(volatile int32_t *)b.err) return;
-        __syncwarp();
+        mask_clean = false;
+        if (nrows > 0)
+            ok = score_item_keyed(b, kw, kbar, parity, generic, gtab, pp, lane, row_ok, el, n_elem,
+                                  nU, n_i, Ks, KLs, Ls, mrow);
     }
 }
 
@@ -1319,12 +1732,22 @@ int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int3
 
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
-    if (b.n_score_items <= 0) return 0;
+    if (b.n_prep_items <= 0) return 0;
     const size_t smem = sizeof(PrepWarpSmem) * kSW;
     cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int need = (b.n_score_items + kSW - 1) / kSW;
+    const int need = (b.n_prep_items + kSW - 1) / kSW;
     const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSm, need));
     k_prep<<<grid, kSW * 32, smem, st>>>(b, d);
+    return 1;
+}
+
+int launch_doc(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    if (b.n_pairs <= 0) return 0;
+    const size_t smem = sizeof(DocSmem);
+    cudaFuncSetAttribute(k_doc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::max(1, std::min(num_sms * 2, b.n_pairs));
+    k_doc<<<grid, kDocThreads, smem, st>>>(b);
     return 1;
 }
 
@@ -1339,11 +1762,11 @@ int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
-    const size_t smem = sizeof(ScoreWarpSmem) * kSW;
+    const size_t smem = sizeof(ScoreSmem);
     cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int need = (b.n_score_items + kSW - 1) / kSW;
-    const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSm, need));
-    k_score<<<grid, kSW * 32, smem, st>>>(b);
+    const int need = (b.n_score_items + kSWS - 1) / kSWS;
+    const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSmScore, need));
+    k_score<<<grid, kSWS * 32, smem, st>>>(b);
     return 1;
 }
 

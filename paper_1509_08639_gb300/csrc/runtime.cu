@@ -101,7 +101,9 @@ using Setting = std::pair<int32_t, int32_t>;   // (gap, threshold)
 struct Plan {
     int32_t P = 0;
     std::vector<PairPlan> pairs;
-    std::vector<ScoreItem> sitems;
+    std::vector<ScoreItem> pitems;  // 32-row items of the preparation kernel
+    std::vector<ScoreItem> sitems;  // 64-row items of the score kernel
+    std::vector<int32_t> dorder;    // pairs by sentence count, longest first
     std::vector<NwItem> nitems;
     std::vector<int32_t> set_gap, set_thr, gap_val;
     int64_t m_elems = 0, code_words = 0, match_words = 0, sel_cap = 0;
@@ -157,7 +159,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
     if ((int64_t)doc_off[2 * (int64_t)P] != n_sent)
         return fail(MINE_EINVAL, "doc_off[2P] must equal n_sent");
     pl.pairs.resize(P);
-    std::vector<int> bucketS(P), bucketC(P);
+    std::vector<int> bucketS(P), bucketC(P), bucketD(P);
     for (int32_t p = 0; p < P; ++p) {
         PairPlan &pp = pl.pairs[p];
         pp.s0 = doc_off[2 * p];
@@ -178,6 +180,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         pl.sel_cap += (int64_t)n * std::min(pp.S, pp.T);
         bucketS[p] = ceil_log2_host((int64_t)pp.T + 1);
         bucketC[p] = ceil_log2_host((int64_t)pp.S * pp.T + 1);
+        bucketD[p] = ceil_log2_host((int64_t)pp.S + pp.T + 1);
     }
     // longest-first orders (counting sort on the bit length of the work)
     auto order_by = [&](const std::vector<int> &key) {
@@ -187,9 +190,11 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         for (int p = P - 1; p >= 0; --p) ord[--cnt[65 - key[p]]] = p;
         return ord;
     };
+    pl.dorder = order_by(bucketD);
     for (int p : order_by(bucketS)) {
         const PairPlan &pp = pl.pairs[p];
-        for (int r0 = 0; r0 < pp.S; r0 += 32) pl.sitems.push_back(ScoreItem{p, r0});
+        for (int r0 = 0; r0 < pp.S; r0 += 32) pl.pitems.push_back(ScoreItem{p, r0});
+        for (int r0 = 0; r0 < pp.S; r0 += 64) pl.sitems.push_back(ScoreItem{p, r0});
     }
     // alignments: whole-CTA ones first, then one-warp ones, each longest first
     const std::vector<int> ord = order_by(bucketC);
@@ -219,11 +224,13 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
 struct Layout {
     int64_t plan = 0, plan_bytes = 0;
     int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
-    int64_t elems = 0, sinfo = 0, order = 0, M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
+    int64_t elems = 0, sinfo = 0, order = 0, tdoc = 0, pdoc = 0;
+    int64_t M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
     // offsets inside the plan blob
     int64_t o_pairs = 0, o_sitems = 0, o_nitems = 0, o_setgap = 0, o_setthr = 0, o_gapval = 0;
+    int64_t o_dorder = 0, o_pitems = 0;
 };
 
 Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel, bool scoring)
@@ -247,6 +254,8 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     L.o_setgap = sub(4 * pl.set_gap.size());
     L.o_setthr = sub(4 * pl.set_thr.size());
     L.o_gapval = sub(4 * pl.gap_val.size());
+    L.o_dorder = sub(4 * pl.dorder.size());
+    L.o_pitems = sub(sizeof(ScoreItem) * pl.pitems.size());
     L.plan_bytes = q;
     L.plan = take(q);
     if (copy_inputs) {
@@ -257,6 +266,8 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
         L.elems = take(4 * (pl.n_tok * kmax + 3 * pl.n_sent + 16));
         L.sinfo = take(16 * pl.n_sent);
         L.order = take(4 * pl.n_sent + 16);
+        L.tdoc = take(2 * pl.n_tok + 64);   // bulk copies round up past the end
+        L.pdoc = take(4 * (int64_t)pl.P + 16);
     } else {
         // a caller-supplied row-major matrix is copied here, then tiled
         int64_t rows = 0;
@@ -283,6 +294,8 @@ void pack_plan(const Plan &pl, const Layout &L, char *dst)
     std::memcpy(dst + L.o_setgap, pl.set_gap.data(), 4 * pl.set_gap.size());
     std::memcpy(dst + L.o_setthr, pl.set_thr.data(), 4 * pl.set_thr.size());
     std::memcpy(dst + L.o_gapval, pl.gap_val.data(), 4 * pl.gap_val.size());
+    std::memcpy(dst + L.o_dorder, pl.dorder.data(), 4 * pl.dorder.size());
+    std::memcpy(dst + L.o_pitems, pl.pitems.data(), sizeof(ScoreItem) * pl.pitems.size());
 }
 
 BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_t *sent_off,
@@ -297,6 +310,8 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.n_tok = pl.n_tok;
     b.n_pairs = pl.P;
     b.pairs = reinterpret_cast<const PairPlan *>(plan + L.o_pairs);
+    b.prep_items = reinterpret_cast<const ScoreItem *>(plan + L.o_pitems);
+    b.n_prep_items = (int32_t)pl.pitems.size();
     b.score_items = reinterpret_cast<const ScoreItem *>(plan + L.o_sitems);
     b.n_score_items = (int32_t)pl.sitems.size();
     b.nw_items = reinterpret_cast<const NwItem *>(plan + L.o_nitems);
@@ -308,6 +323,9 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.elems = reinterpret_cast<uint32_t *>(base + L.elems);
     b.sinfo = reinterpret_cast<int4 *>(base + L.sinfo);
     b.row_order = reinterpret_cast<int32_t *>(base + L.order);
+    b.tdoc = reinterpret_cast<uint16_t *>(base + L.tdoc);
+    b.pdoc = reinterpret_cast<int32_t *>(base + L.pdoc);
+    b.dorder = reinterpret_cast<const int32_t *>(plan + L.o_dorder);
     b.M = reinterpret_cast<int32_t *>(base + L.M);
     b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
     b.matches = reinterpret_cast<uint32_t *>(base + L.matches);
@@ -513,6 +531,7 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         BatchDev bd = b;
         bd.kmax = dict->d.kmax;
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_DOC, st, [&] { return launch_doc(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
@@ -963,7 +982,8 @@ int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n)
 const char *mine_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
-                                           "k_align", "k_tile", "k_trace", "k_order"};
+                                           "k_align", "k_tile", "k_trace", "k_order",
+                                           "k_doc"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
