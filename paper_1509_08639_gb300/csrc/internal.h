@@ -37,8 +37,13 @@ constexpr int kScoreCtasPerSm = 4;          // CTAs per SM of the preparation ke
 constexpr int kScoreWarpsScore = 2;         // warps per CTA of the score kernel (64 rows per item)
 constexpr int kScoreCtasPerSmScore = 6;     // its resident CTAs per SM
 constexpr int kBlkTokCap = 1536;            // tokens of one staged 32-column block at most
-static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kScoreWarps * kScoreCtasPerSm,
-              "the per-warp global tables are allocated for the preparation kernel's grid");
+constexpr int kPairPrepCtasPerSm = 2;       // CTAs (16 warps each) per SM of the pair preparation
+// per-warp global tables: enough for the largest grid of the three kernels using them
+constexpr int kGScratchWarpsPerSm = 32;
+static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kGScratchWarpsPerSm &&
+                  kScoreWarps * kScoreCtasPerSm <= kGScratchWarpsPerSm &&
+                  16 * kPairPrepCtasPerSm <= kGScratchWarpsPerSm,
+              "per-warp global tables");
 // Target articles with at most kDirect distinct tokens are scored through
 // dense document ids (a direct-indexed column mask per id); entry kZeroEnt of
 // that mask array is never set.
@@ -136,7 +141,7 @@ int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_k
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st);
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
-int launch_doc(const BatchDev &b, int num_sms, cudaStream_t st);
+int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);

@@ -391,6 +391,7 @@ k_prep(BatchDev b, DevDict d)
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_prep_items) break;
         const ScoreItem si = b.prep_items[item];
+        if (b.pdoc[si.pair] >= 0) continue;   // prepared by k_pairprep
         const PairPlan pp = b.pairs[si.pair];
         const int nrows = min(32, pp.S - si.row0);
         const int64_t s_first = (int64_t)pp.s0 + si.row0;
@@ -552,157 +553,262 @@ k_prep(BatchDev b, DevDict d)
     }
 }
 
-// ---------------------------------------------------------------- k_doc
+// ---------------------------------------------------------------- k_pairprep
 
-constexpr int kDocThreads = 256;
-constexpr int kDocSlots = 2 * kDirect;     // document table: at most ~53% full
-constexpr int kDocLog2 = 14;
-static_assert((1 << kDocLog2) == kDocSlots, "document table size");
+constexpr int kPPThreads = 512;
+constexpr int kPPWarps = kPPThreads / 32;
+constexpr int kDocSlotsMax = 2 * kDirect;          // document table: at most ~53% full
+constexpr int kDocWordsMax = kDocSlotsMax / 32;
+constexpr int kRowSetSlots = 128;                  // a row's source tokens, rows of <= 64 tokens
+constexpr int kRowSetBig = 2 * kMaxSentTokens;     // longer rows: per-warp table in global memory
+static_assert(kRowSetBig * 8 <= kScoreScratchPerWarp, "per-warp global table too small");
 
-struct alignas(16) DocSmem {
-    int32_t key[kDocSlots];
-    uint16_t dval[kDocSlots];
+struct alignas(16) PairPrepSmem {
+    int32_t key[kDocSlotsMax];                 // target tokens of the article
+    uint32_t occ[kDocWordsMax];                // occupied slots
+    uint16_t rank[kDocWordsMax];               // occupied slots before each word
+    uint32_t seen[kPPWarps][kDirect / 32];     // ids already kept in the warp's current row
+    int2 rset[kPPWarps][kRowSetSlots];         // (token, row stamp)
     int32_t nd;
     int32_t item;
 };
 
-// Document id of target token `tok`, or -1 when the article lacks it.
-__device__ __forceinline__ int doc_find(const int32_t *key, const uint16_t *dval, int32_t tok)
+// Document id of target token `tok` (the rank of its slot among the
+// occupied ones), or -1 when the article lacks it.
+__device__ __forceinline__ int doc_id(const PairPrepSmem &sm, int lg, int32_t tok)
 {
-    uint32_t h = hmul(tok) >> (32 - kDocLog2);
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hmul(tok) >> (32 - lg);
     for (;;) {   // ends: the table always has empty slots
-        const int32_t k = key[h];
-        if (k == tok) return dval[h];
+        const int32_t k = sm.key[h];
+        if (k == tok) {
+            const uint32_t w = h >> 5;
+            return (int)sm.rank[w] + __popc(sm.occ[w] & ((1u << (h & 31)) - 1u));
+        }
         if (k == -1) return -1;
-        h = (h + 1) & (kDocSlots - 1);
+        h = (h + 1) & mask;
     }
 }
 
-__device__ __forceinline__ void doc_insert(DocSmem &sm, int32_t tok)
+__device__ __forceinline__ void doc_insert(PairPrepSmem &sm, int lg, int32_t tok)
 {
-    uint32_t h = hmul(tok) >> (32 - kDocLog2);
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hmul(tok) >> (32 - lg);
+    volatile int32_t *key = sm.key;
     for (;;) {
-        const int32_t old = atomicCAS(&sm.key[h], -1, tok);
-        if (old == -1) {
-            sm.dval[h] = (uint16_t)min(atomicAdd(&sm.nd, 1), 65535);
-            return;
+        const int32_t k = key[h];
+        if (k == tok) return;
+        if (k == -1) {
+            const int32_t old = atomicCAS(&sm.key[h], -1, tok);
+            if (old == -1) {
+                atomicAdd(&sm.nd, 1);
+                return;
+            }
+            if (old == tok) return;
         }
-        if (old == tok) return;
-        h = (h + 1) & (kDocSlots - 1);
+        h = (h + 1) & mask;
     }
 }
 
-// Keep, of one source row's element list, the translations the target
-// article holds, in place: (id | FIRST), END on the last kept translation of
-// each source token.  Returns the kept count; nf receives the kept FIRSTs.
-__device__ __forceinline__ int compact_row(const DocSmem &sm, uint32_t *el, int n, int &nf)
+// Insert `tok` into a row set whose live entries carry `stamp`; true when
+// the token is new in this row.  Entries of earlier rows count as empty.
+__device__ __forceinline__ bool rset_insert(int2 *set, int lg, int32_t tok, int32_t stamp)
 {
-    int w = 0;
-    nf = 0;
-    uint32_t pend = 0;
-    bool has = false;
-    uint4 nx = make_uint4(0u, 0u, 0u, 0u);
-    if (0 < n) nx = *reinterpret_cast<const uint4 *>(el);
-    for (int k = 0; k < n; k += 4) {
-        const uint4 v = nx;
-        // read ahead: writes so far stay below index k + 4
-        if (k + 4 < n) nx = *reinterpret_cast<const uint4 *>(el + k + 4);
-        const uint32_t ev[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (k + q >= n) break;
-            const uint32_t e = ev[q];
-            const int d = doc_find(sm.key, sm.dval, (int32_t)(e & ELEM_TOKEN));
-            if (d >= 0) {
-                if (has) el[w++] = pend;
-                pend = (uint32_t)d | (e & ELEM_FIRST);
-                nf += (e & ELEM_FIRST) ? 1 : 0;
-                has = true;
-            }
-            if ((e & ELEM_END) && has) {
-                el[w++] = pend | ELEM_END;
-                has = false;
-            }
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hmul(tok) >> (32 - lg);
+    unsigned long long *s64 = reinterpret_cast<unsigned long long *>(set);
+    const unsigned long long mine = ((unsigned long long)(uint32_t)stamp << 32) | (uint32_t)tok;
+    unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(&s64[h]);
+    for (;;) {
+        if ((int32_t)(cur >> 32) != stamp) {
+            const unsigned long long old = atomicCAS(&s64[h], cur, mine);
+            if (old == cur) return true;
+            cur = old;   // taken meanwhile: look at it again
+            continue;
         }
+        if ((uint32_t)cur == (uint32_t)tok) return false;
+        h = (h + 1) & mask;
+        cur = *reinterpret_cast<volatile unsigned long long *>(&s64[h]);
     }
-    if (has) el[w++] = pend | ELEM_END;
-    return w;
 }
 
-// One CTA per pair (largest first).  The distinct tokens of the target
-// article get dense ids 0..D-1.  When D <= kDirect every target token's id
-// goes to tdoc and each source row's element list is compacted in place to
-// the translations the target article holds, with (n_i, #kept, #kept FIRST)
-// in sinfo; pdoc[p] = D.  An article with more distinct tokens gets
-// pdoc[p] = -1 and is scored on the token-keyed path.
-__global__ void __launch_bounds__(kDocThreads)
-k_doc(BatchDev b)
+// One CTA per pair (largest first), for every pair whose target article has
+// at most kDirect distinct tokens:
+//  1. the article's distinct tokens go into a shared table; their dense ids
+//     are the ranks of the occupied slots (pdoc[p] = D, the count);
+//  2. every target token's id goes to tdoc;
+//  3. one warp per source row: distinct tokens (n_i), their dictionary
+//     translations, of which only those the target article holds are kept,
+//     written as (id | FIRST | END) -- FIRST on the first copy of an id in the
+//     row, END on the last kept translation of each source token -- with
+//     (n_i, #kept, #kept FIRST) in sinfo.
+// A larger article gets pdoc[p] = -1 and is left to k_prep and the
+// token-keyed score path.
+__global__ void __launch_bounds__(kPPThreads)
+k_pairprep(BatchDev b, DevDict d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DocSmem &sm = *reinterpret_cast<DocSmem *>(smem_raw);
-    const int tid = threadIdx.x;
-    if (*(volatile int32_t *)b.err) return;
+    PairPrepSmem &sm = *reinterpret_cast<PairPrepSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    int2 *gset = b.gscratch + (int64_t)(blockIdx.x * kPPWarps + wib) * kGTabSlots;
+    bool gset_clean = false;
+    int32_t stamp = 0;
+    for (int k = tid; k < kPPWarps * (kDirect / 32); k += kPPThreads) (&sm.seen[0][0])[k] = 0u;
+    for (int k = tid; k < kPPWarps * kRowSetSlots; k += kPPThreads) (&sm.rset[0][0])[k] = make_int2(-1, 0);
+    const int kmax = b.kmax;
     for (;;) {
-        __syncthreads();   // the previous pair is done with the table
+        if (__syncthreads_or(*(volatile int32_t *)b.err != 0)) break;
         if (tid == 0) {
             sm.item = atomicAdd(&b.counters[5], 1);
             sm.nd = 0;
         }
-        int4 *kz = reinterpret_cast<int4 *>(sm.key);
-        for (int k = tid; k < kDocSlots / 4; k += kDocThreads) kz[k] = make_int4(-1, -1, -1, -1);
         __syncthreads();
         const int item = sm.item;
         if (item >= b.n_pairs) break;
         const int p = b.dorder[item];
         const PairPlan pp = b.pairs[p];
         const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
-        // 1. distinct target tokens -> dense ids, four loads in flight per
-        //    thread; stops once the ids cannot all fit
-        for (int32_t k = ta + tid; k < tb; k += 4 * kDocThreads) {
+        const int lg = min(max(ceil_log2(2 * max(tb - ta, 1)), 10), 14);
+        const int NS = 1 << lg;
+        int4 *kz = reinterpret_cast<int4 *>(sm.key);
+        for (int k = tid; k < NS / 4; k += kPPThreads) kz[k] = make_int4(-1, -1, -1, -1);
+        __syncthreads();
+        // 1. distinct target tokens; four loads in flight per thread; stops
+        //    once they cannot all get ids
+        for (int32_t k = ta + tid; k < tb; k += 4 * kPPThreads) {
             if (*(volatile int32_t *)&sm.nd > kDirect) break;
             int32_t tk[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int32_t kk = k + q * kDocThreads;
+                const int32_t kk = k + q * kPPThreads;
                 tk[q] = kk < tb ? b.tokens[kk] : -1;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (k + q * kDocThreads >= tb) break;
+                if (k + q * kPPThreads >= tb) break;
                 if ((uint32_t)tk[q] > ELEM_TOKEN) {
                     atomicCAS(b.err, 0, ERR_BAD_TOKEN);
                     continue;
                 }
-                doc_insert(sm, tk[q]);
+                doc_insert(sm, lg, tk[q]);
             }
         }
         __syncthreads();
         const int D = sm.nd;
         if (tid == 0) b.pdoc[p] = D <= kDirect ? D : -1;
         if (D > kDirect) continue;
+        const int NW = NS >> 5;
+        for (int w = wib; w < NW; w += kPPWarps)
+            sm.occ[w] = __ballot_sync(kFull, sm.key[32 * w + lane] != -1);
+        __syncthreads();
+        if (wib == 0) {
+            const int per = NW >> 5;   // NW >= 32
+            int run = 0;
+            for (int q = 0; q < per; ++q) run += __popc(sm.occ[lane * per + q]);
+            int incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int base = incl - run;
+            for (int q = 0; q < per; ++q) {
+                sm.rank[lane * per + q] = (uint16_t)base;
+                base += __popc(sm.occ[lane * per + q]);
+            }
+        }
+        __syncthreads();
         // 2. id of every target token
-        for (int32_t k = ta + tid; k < tb; k += 4 * kDocThreads) {
+        for (int32_t k = ta + tid; k < tb; k += 4 * kPPThreads) {
             int32_t tk[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int32_t kk = k + q * kDocThreads;
+                const int32_t kk = k + q * kPPThreads;
                 tk[q] = kk < tb ? b.tokens[kk] : 0;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int32_t kk = k + q * kDocThreads;
-                if (kk < tb)
-                    b.tdoc[kk] = (uint16_t)max(doc_find(sm.key, sm.dval, tk[q] & (int32_t)ELEM_TOKEN), 0);
+                const int32_t kk = k + q * kPPThreads;
+                if (kk < tb) b.tdoc[kk] = (uint16_t)max(doc_id(sm, lg, tk[q] & (int32_t)ELEM_TOKEN), 0);
             }
         }
-        // 3. source rows: keep the translations the target article holds
-        for (int r = tid; r < pp.S; r += kDocThreads) {
-            const int64_t si = (int64_t)pp.s0 + r;
-            const int4 inf = b.sinfo[si];
-            uint32_t *el = b.elems + elem_base(b.sent_off[si], si, b.kmax);
-            int nf;
-            const int w = compact_row(sm, el, inf.y, nf);
-            b.sinfo[si] = make_int4(inf.x, w, nf, 0);
+        // 3. source rows, one warp each
+        uint32_t *seen = sm.seen[wib];
+        for (int r = wib; r < pp.S; r += kPPWarps) {
+            const int64_t s = (int64_t)pp.s0 + r;
+            const int32_t a = b.sent_off[s], L = b.sent_off[s + 1] - a;
+            ++stamp;
+            int2 *set = sm.rset[wib];
+            int lgS = 7;
+            if (L > 64) {
+                set = gset;
+                lgS = 11;
+                if (!gset_clean) {
+                    int4 *gz = reinterpret_cast<int4 *>(gset);
+                    for (int k = lane; k < kRowSetBig / 2; k += 32) gz[k] = make_int4(-1, 0, -1, 0);
+                    __syncwarp();
+                    gset_clean = true;
+                }
+            }
+            uint32_t *el = b.elems + elem_base(a, s, kmax);
+            int n_i = 0, out = 0, nf = 0;
+            for (int c = 0; c < L; c += 32) {
+                const bool valid = c + lane < L;
+                int32_t tok = valid ? b.tokens[a + c + lane] : 0;
+                if ((uint32_t)tok > ELEM_TOKEN) {
+                    atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    tok &= (int32_t)ELEM_TOKEN;
+                }
+                const bool isnew = valid && rset_insert(set, lgS, tok, stamp);
+                n_i += __popc(__ballot_sync(kFull, isnew));
+                const int2 oc = isnew ? dict_find(d, tok) : make_int2(0, 0);
+                // the first four translations stay in registers
+                int id[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) id[q] = q < oc.y ? __ldg(&d.trans[oc.x + q]) : 0;
+                int kc = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    id[q] = q < oc.y ? doc_id(sm, lg, id[q]) : -1;
+                    kc += id[q] >= 0 ? 1 : 0;
+                }
+                for (int q = 4; q < oc.y; ++q) kc += doc_id(sm, lg, __ldg(&d.trans[oc.x + q])) >= 0 ? 1 : 0;
+                int incl = kc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int pos = out + incl - kc;
+                out += __shfl_sync(kFull, incl, 31);
+                int left = kc;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (id[q] >= 0) {
+                        const uint32_t bit = 1u << (id[q] & 31);
+                        const bool first = !(atomicOr(&seen[id[q] >> 5], bit) & bit);
+                        nf += first ? 1 : 0;
+                        --left;
+                        el[pos++] = (uint32_t)id[q] | (first ? ELEM_FIRST : 0u) | (left == 0 ? ELEM_END : 0u);
+                    }
+                }
+                for (int q = 4; q < oc.y; ++q) {
+                    const int idv = doc_id(sm, lg, __ldg(&d.trans[oc.x + q]));
+                    if (idv >= 0) {
+                        const uint32_t bit = 1u << (idv & 31);
+                        const bool first = !(atomicOr(&seen[idv >> 5], bit) & bit);
+                        nf += first ? 1 : 0;
+                        --left;
+                        el[pos++] = (uint32_t)idv | (first ? ELEM_FIRST : 0u) | (left == 0 ? ELEM_END : 0u);
+                    }
+                }
+            }
+            nf = (int)__reduce_add_sync(kFull, (unsigned)nf);
+            if (lane == 0) b.sinfo[s] = make_int4(n_i, out, nf, 0);
+            __syncwarp();
+            uint4 *sz = reinterpret_cast<uint4 *>(seen);
+            for (int k = lane; k < kDirect / 128; k += 32) sz[k] = make_uint4(0u, 0u, 0u, 0u);
+            __syncwarp();
         }
     }
 }
@@ -1741,13 +1847,13 @@ int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t s
     return 1;
 }
 
-int launch_doc(const BatchDev &b, int num_sms, cudaStream_t st)
+int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    const size_t smem = sizeof(DocSmem);
-    cudaFuncSetAttribute(k_doc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = std::max(1, std::min(num_sms * 2, b.n_pairs));
-    k_doc<<<grid, kDocThreads, smem, st>>>(b);
+    const size_t smem = sizeof(PairPrepSmem);
+    cudaFuncSetAttribute(k_pairprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::max(1, std::min(num_sms * kPairPrepCtasPerSm, b.n_pairs));
+    k_pairprep<<<grid, kPPThreads, smem, st>>>(b, d);
     return 1;
 }
 

@@ -530,8 +530,8 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
         BatchDev bd = b;
         bd.kmax = dict->d.kmax;
+        n += timed_launch(ctx, KID_DOC, st, [&] { return launch_pairprep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
-        n += timed_launch(ctx, KID_DOC, st, [&] { return launch_doc(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
@@ -593,7 +593,7 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     ctx->pool.size = c.device_budget_bytes;
     ctx->pool.free_[0] = c.device_budget_bytes;
     // one set of per-warp long-sentence tables per batch that can run at once
-    ctx->gscratch_bytes = (size_t)ctx->num_sms * kScoreCtasPerSm * kScoreWarps * kScoreScratchPerWarp;
+    ctx->gscratch_bytes = (size_t)ctx->num_sms * kGScratchWarpsPerSm * kScoreScratchPerWarp;
     CK(cudaMalloc(&ctx->gscratch, ctx->gscratch_bytes));
     for (int k = 0; k < c.max_inflight; ++k) {
         std::unique_ptr<Slot> s(new Slot());
@@ -983,7 +983,7 @@ const char *mine_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
-                                           "k_doc"};
+                                           "k_pairprep"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
