@@ -52,8 +52,9 @@ constexpr uint32_t kZeroEnt = kDirect;
 // per-warp global table of the score kernel: 2 * kMaxSentTokens (key, mask) entries
 constexpr int64_t kScoreScratchPerWarp = 2 * (int64_t)kMaxSentTokens * 8;
 
-// Resident dictionary: open-addressed table of (key, off << 6 | cnt), linear
-// probing, hash = key * 0x9E3779B1 >> (32 - log2).  Empty key = -1.
+// Resident dictionary: table of (key, off << 6 | cnt) slots in buckets of 8,
+// bucket = key * 0x9E3779B1 >> (35 - log2), overflow into the next bucket.
+// Empty key = -1.
 struct DevDict {
     int2 *slots;        // [1 << log2]
     int32_t *trans;     // translations

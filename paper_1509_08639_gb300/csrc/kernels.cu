@@ -139,39 +139,80 @@ __device__ __forceinline__ bool flag_wait_ge(const int32_t *flag, int32_t v, int
 
 // ---------------------------------------------------------------- dictionary
 
+// The dictionary table is made of buckets of 8 (key, off << 6 | cnt) slots
+// (64 bytes, read at once); a key lives in its hash bucket or, when that is
+// full, in the next ones.  Slots of a bucket fill in order, so a bucket with
+// an empty last slot ends every search.
+constexpr int kDictBucket = 8;
+
+__device__ __forceinline__ uint32_t dict_bucket(const DevDict &d, int32_t key)
+{
+    return hmul(key) >> (32 - (d.log2 - 3));
+}
+
+__device__ __forceinline__ void dict_load(const DevDict &d, uint32_t bk, int4 (&q)[4])
+{
+    const int4 *p = reinterpret_cast<const int4 *>(d.slots + (size_t)kDictBucket * bk);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = __ldg(p + i);
+}
+
+// (off, cnt) of `key` from its loaded bucket; `more` when the bucket is full
+// without it (the search goes on in the next bucket).
+__device__ __forceinline__ int2 dict_match(const int4 (&q)[4], int32_t key, bool &more)
+{
+    int32_t v = -1;
+    bool hit = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (q[i].x == key) { v = q[i].y; hit = true; }
+        if (q[i].z == key) { v = q[i].w; hit = true; }
+    }
+    more = !hit && q[3].z != -1;
+    return hit ? make_int2((int32_t)((uint32_t)v >> 6), v & 63) : make_int2(0, 0);
+}
+
 __device__ __forceinline__ int2 dict_find(const DevDict &d, int32_t key)
 {
-    const uint32_t mask = (1u << d.log2) - 1u;
-    uint32_t h = hmul(key) >> (32 - d.log2);
-    for (;;) {
-        const int2 e = __ldg(&d.slots[h]);
-        if (e.x == key) return make_int2((int32_t)((uint32_t)e.y >> 6), e.y & 63);
-        if (e.x == -1) return make_int2(0, 0);
-        h = (h + 1) & mask;
+    const uint32_t nbm = (1u << (d.log2 - 3)) - 1u;
+    uint32_t bk = dict_bucket(d, key);
+    for (;;) {   // ends: the table is at most half full
+        int4 q[4];
+        dict_load(d, bk, q);
+        bool more;
+        const int2 oc = dict_match(q, key, more);
+        if (!more) return oc;
+        bk = (bk + 1) & nbm;
     }
 }
 
 __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__restrict__ trans_off,
                              int32_t n_keys, DevDict d, int32_t *err)
 {
-    const uint32_t mask = (1u << d.log2) - 1u;
+    const uint32_t nbm = (1u << (d.log2 - 3)) - 1u;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_keys;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t key = keys[k];
         const int32_t off = trans_off[k];
         const int32_t cnt = trans_off[k + 1] - off;
-        uint32_t h = hmul(key) >> (32 - d.log2);
-        for (uint32_t probe = 0; probe <= mask; ++probe) {
-            const int32_t old = atomicCAS(&d.slots[h].x, -1, key);
-            if (old == -1) {
-                d.slots[h].y = (int32_t)(((uint32_t)off << 6) | (uint32_t)cnt);
-                break;
+        uint32_t bk = dict_bucket(d, key);
+        bool done = false;
+        for (uint32_t probe = 0; probe <= nbm && !done; ++probe) {
+            for (int sl = 0; sl < kDictBucket; ++sl) {
+                int2 *slot = d.slots + (size_t)kDictBucket * bk + sl;
+                const int32_t old = atomicCAS(&slot->x, -1, key);
+                if (old == -1) {
+                    slot->y = (int32_t)(((uint32_t)off << 6) | (uint32_t)cnt);
+                    done = true;
+                    break;
+                }
+                if (old == key) {
+                    atomicCAS(err, 0, ERR_DUP_KEY);
+                    done = true;
+                    break;
+                }
             }
-            if (old == key) {
-                atomicCAS(err, 0, ERR_DUP_KEY);
-                break;
-            }
-            h = (h + 1) & mask;
+            bk = (bk + 1) & nbm;
         }
     }
 }
@@ -473,25 +514,13 @@ k_prep(BatchDev b, DevDict d)
             }
             __syncwarp();
             const int ng = sm.ngrp;
-            // dictionary lookups, two per lane in flight
+            // dictionary lookups
             for (int g0 = 0; g0 < ng; g0 += 64) {
-                int2 e[2];
-                int32_t tok[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int g = g0 + q * 32 + lane;
-                    tok[q] = g < ng ? sm.grp[g].x : -1;
-                    e[q] = make_int2(-1, 0);
-                    if (g < ng) e[q] = __ldg(&d.slots[hmul(tok[q]) >> (32 - d.log2)]);
-                }
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int g = g0 + q * 32 + lane;
                     if (g < ng) {
-                        int2 oc;
-                        if (e[q].x == tok[q]) oc = make_int2((int32_t)((uint32_t)e[q].y >> 6), e[q].y & 63);
-                        else if (e[q].x == -1) oc = make_int2(0, 0);
-                        else oc = dict_find(d, tok[q]);
+                        const int2 oc = dict_find(d, sm.grp[g].x);
                         const int r = sm.grp[g].y;
                         const int pos = atomicAdd(&sm.recnt[r], oc.y);
                         sm.grp[g] = make_int2((int32_t)(((uint32_t)oc.x << 6) | (uint32_t)oc.y),
@@ -559,8 +588,7 @@ constexpr int kPPThreads = 512;
 constexpr int kPPWarps = kPPThreads / 32;
 constexpr int kDocSlotsMax = 2 * kDirect;          // document table: at most ~53% full
 constexpr int kDocWordsMax = kDocSlotsMax / 32;
-constexpr int kRowSetSlots = 128;                  // a row's source tokens, rows of <= 64 tokens
-constexpr int kRowSetBig = 2 * kMaxSentTokens;     // longer rows: per-warp table in global memory
+constexpr int kRowSetBig = 2 * kMaxSentTokens;     // rows of > 64 tokens: per-warp table in global memory
 static_assert(kRowSetBig * 8 <= kScoreScratchPerWarp, "per-warp global table too small");
 
 struct alignas(16) PairPrepSmem {
@@ -568,7 +596,7 @@ struct alignas(16) PairPrepSmem {
     uint32_t occ[kDocWordsMax];                // occupied slots
     uint16_t rank[kDocWordsMax];               // occupied slots before each word
     uint32_t seen[kPPWarps][kDirect / 32];     // ids already kept in the warp's current row
-    int2 rset[kPPWarps][kRowSetSlots];         // (token, row stamp)
+    int32_t cbuf[kPPWarps][64];                // distinct tokens of the row, compacted
     int32_t nd;
     int32_t item;
 };
@@ -632,6 +660,158 @@ __device__ __forceinline__ bool rset_insert(int2 *set, int lg, int32_t tok, int3
     }
 }
 
+// Distinct tokens of a row of L <= 64 tokens (t0: tokens 0..31, t1: 32..63,
+// one per lane), compacted into cb[0..n); returns n.
+__device__ __forceinline__ int distinct64(int32_t t0, int32_t t1, int L, int lane, int32_t *cb)
+{
+    const bool v0 = lane < L, v1 = 32 + lane < L;
+    const int32_t k0 = v0 ? t0 : -1 - lane;   // tokens are >= 0: sentinels never match one
+    // every lane takes part in the match (no short-circuit around it)
+    const uint32_t m0 = __match_any_sync(kFull, k0);
+    const bool lead0 = v0 && (__ffs(m0) - 1 == lane);
+    bool lead1 = false;
+    if (L > 32) {
+        const int32_t k1 = v1 ? t1 : -1 - lane;
+        const uint32_t m1 = __match_any_sync(kFull, k1);
+        lead1 = v1 && (__ffs(m1) - 1 == lane);
+        bool dup = false;
+        for (int q = 0; q < 32; ++q) dup |= __shfl_sync(kFull, k0, q) == k1;
+        lead1 = lead1 && !dup;
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t b0 = __ballot_sync(kFull, lead0), b1 = __ballot_sync(kFull, lead1);
+    const int n0 = __popc(b0);
+    if (lead0) cb[__popc(b0 & lt)] = t0;
+    if (lead1) cb[n0 + __popc(b1 & lt)] = t1;
+    __syncwarp();
+    return n0 + __popc(b1);
+}
+
+// Kept translations of one distinct source token per lane (first four given
+// in u, the rest read again): write them from position out + (earlier lanes'
+// kept count) as (id | FIRST | END); advances out by the warp's total.
+__device__ __forceinline__ void emit_kept(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm,
+                                          int lg, const int32_t (&u)[4], int2 oc, uint32_t *seen,
+                                          uint32_t *el, int &out, int &nf, int lane)
+{
+    int id[4];
+    int kc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        id[q] = q < oc.y ? doc_id(sm, lg, u[q]) : -1;
+        kc += id[q] >= 0 ? 1 : 0;
+    }
+    for (int q = 4; q < oc.y; ++q) kc += doc_id(sm, lg, __ldg(&d.trans[oc.x + q])) >= 0 ? 1 : 0;
+    int incl = kc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int pos = out + incl - kc;
+    out += __shfl_sync(kFull, incl, 31);
+    int left = kc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (id[q] >= 0) {
+            const uint32_t bit = 1u << (id[q] & 31);
+            const bool first = !(atomicOr(&seen[id[q] >> 5], bit) & bit);
+            nf += first ? 1 : 0;
+            --left;
+            el[pos++] = (uint32_t)id[q] | (first ? ELEM_FIRST : 0u) | (left == 0 ? ELEM_END : 0u);
+        }
+    }
+    for (int q = 4; q < oc.y; ++q) {
+        const int idv = doc_id(sm, lg, __ldg(&d.trans[oc.x + q]));
+        if (idv >= 0) {
+            const uint32_t bit = 1u << (idv & 31);
+            const bool first = !(atomicOr(&seen[idv >> 5], bit) & bit);
+            nf += first ? 1 : 0;
+            --left;
+            el[pos++] = (uint32_t)idv | (first ? ELEM_FIRST : 0u) | (left == 0 ? ELEM_END : 0u);
+        }
+    }
+}
+
+// One source row of <= 64 tokens: tokens, distinct tokens (warp match, no
+// table), dictionary buckets, translations, then the kept translations.
+__device__ void prep_row_short(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm, int lg,
+                               int64_t s, int32_t a, int32_t L, int lane, uint32_t *seen,
+                               int32_t *cb, int kmax)
+{
+    int32_t t0 = 0, t1 = 0;
+    if (lane < L) t0 = b.tokens[a + lane];
+    if (32 + lane < L) t1 = b.tokens[a + 32 + lane];
+    if (((uint32_t)t0 | (uint32_t)t1) > ELEM_TOKEN) {
+        atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+        t0 &= (int32_t)ELEM_TOKEN;
+        t1 &= (int32_t)ELEM_TOKEN;
+    }
+    const int n = distinct64(t0, t1, L, lane, cb);
+    uint32_t *el = b.elems + elem_base(a, s, kmax);
+    int out = 0, nf = 0;
+    for (int g = 0; 32 * g < n; ++g) {
+        const int k = 32 * g + lane;
+        const bool v = k < n;
+        const int32_t key = v ? cb[k] : 0;
+        int2 oc = make_int2(0, 0);
+        if (v) {
+            int4 q[4];
+            dict_load(d, dict_bucket(d, key), q);
+            bool more;
+            oc = dict_match(q, key, more);
+            if (more) oc = dict_find(d, key);
+        }
+        int32_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[q] = q < oc.y ? __ldg(&d.trans[oc.x + q]) : 0;
+        emit_kept(b, d, sm, lg, u, oc, seen, el, out, nf, lane);
+    }
+    nf = (int)__reduce_add_sync(kFull, (unsigned)nf);
+    if (lane == 0) b.sinfo[s] = make_int4(n, out, nf, 0);
+    __syncwarp();
+    uint4 *sz = reinterpret_cast<uint4 *>(seen);
+    for (int q = lane; q < kDirect / 128; q += 32) sz[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+}
+
+// One source row of any length (distinct tokens through a per-warp table in
+// global memory whose live entries carry the row's stamp).
+__device__ void prep_row_long(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm, int lg,
+                              int64_t s, int32_t a, int32_t L, int lane, int2 *gset,
+                              bool &gset_clean, int32_t stamp, uint32_t *seen)
+{
+    if (!gset_clean) {
+        int4 *gz = reinterpret_cast<int4 *>(gset);
+        for (int k = lane; k < kRowSetBig / 2; k += 32) gz[k] = make_int4(-1, 0, -1, 0);
+        __syncwarp();
+        gset_clean = true;
+    }
+    uint32_t *el = b.elems + elem_base(a, s, b.kmax);
+    int n_i = 0, out = 0, nf = 0;
+    for (int c = 0; c < L; c += 32) {
+        const bool valid = c + lane < L;
+        int32_t tok = valid ? b.tokens[a + c + lane] : 0;
+        if ((uint32_t)tok > ELEM_TOKEN) {
+            atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+            tok &= (int32_t)ELEM_TOKEN;
+        }
+        const bool isnew = valid && rset_insert(gset, 11, tok, stamp);
+        n_i += __popc(__ballot_sync(kFull, isnew));
+        const int2 oc = isnew ? dict_find(d, tok) : make_int2(0, 0);
+        int32_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[q] = q < oc.y ? __ldg(&d.trans[oc.x + q]) : 0;
+        emit_kept(b, d, sm, lg, u, oc, seen, el, out, nf, lane);
+    }
+    nf = (int)__reduce_add_sync(kFull, (unsigned)nf);
+    if (lane == 0) b.sinfo[s] = make_int4(n_i, out, nf, 0);
+    __syncwarp();
+    uint4 *sz = reinterpret_cast<uint4 *>(seen);
+    for (int q = lane; q < kDirect / 128; q += 32) sz[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+}
+
 // One CTA per pair (largest first), for every pair whose target article has
 // at most kDirect distinct tokens:
 //  1. the article's distinct tokens go into a shared table; their dense ids
@@ -644,7 +824,7 @@ __device__ __forceinline__ bool rset_insert(int2 *set, int lg, int32_t tok, int3
 //     (n_i, #kept, #kept FIRST) in sinfo.
 // A larger article gets pdoc[p] = -1 and is left to k_prep and the
 // token-keyed score path.
-__global__ void __launch_bounds__(kPPThreads)
+__global__ void __launch_bounds__(kPPThreads, kPairPrepCtasPerSm)
 k_pairprep(BatchDev b, DevDict d)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -654,7 +834,6 @@ k_pairprep(BatchDev b, DevDict d)
     bool gset_clean = false;
     int32_t stamp = 0;
     for (int k = tid; k < kPPWarps * (kDirect / 32); k += kPPThreads) (&sm.seen[0][0])[k] = 0u;
-    for (int k = tid; k < kPPWarps * kRowSetSlots; k += kPPThreads) (&sm.rset[0][0])[k] = make_int2(-1, 0);
     const int kmax = b.kmax;
     for (;;) {
         if (__syncthreads_or(*(volatile int32_t *)b.err != 0)) break;
@@ -733,82 +912,15 @@ k_pairprep(BatchDev b, DevDict d)
             }
         }
         // 3. source rows, one warp each
-        uint32_t *seen = sm.seen[wib];
-        for (int r = wib; r < pp.S; r += kPPWarps) {
-            const int64_t s = (int64_t)pp.s0 + r;
-            const int32_t a = b.sent_off[s], L = b.sent_off[s + 1] - a;
-            ++stamp;
-            int2 *set = sm.rset[wib];
-            int lgS = 7;
-            if (L > 64) {
-                set = gset;
-                lgS = 11;
-                if (!gset_clean) {
-                    int4 *gz = reinterpret_cast<int4 *>(gset);
-                    for (int k = lane; k < kRowSetBig / 2; k += 32) gz[k] = make_int4(-1, 0, -1, 0);
-                    __syncwarp();
-                    gset_clean = true;
-                }
-            }
-            uint32_t *el = b.elems + elem_base(a, s, kmax);
-            int n_i = 0, out = 0, nf = 0;
-            for (int c = 0; c < L; c += 32) {
-                const bool valid = c + lane < L;
-                int32_t tok = valid ? b.tokens[a + c + lane] : 0;
-                if ((uint32_t)tok > ELEM_TOKEN) {
-                    atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    tok &= (int32_t)ELEM_TOKEN;
-                }
-                const bool isnew = valid && rset_insert(set, lgS, tok, stamp);
-                n_i += __popc(__ballot_sync(kFull, isnew));
-                const int2 oc = isnew ? dict_find(d, tok) : make_int2(0, 0);
-                // the first four translations stay in registers
-                int id[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) id[q] = q < oc.y ? __ldg(&d.trans[oc.x + q]) : 0;
-                int kc = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    id[q] = q < oc.y ? doc_id(sm, lg, id[q]) : -1;
-                    kc += id[q] >= 0 ? 1 : 0;
-                }
-                for (int q = 4; q < oc.y; ++q) kc += doc_id(sm, lg, __ldg(&d.trans[oc.x + q])) >= 0 ? 1 : 0;
-                int incl = kc;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                int pos = out + incl - kc;
-                out += __shfl_sync(kFull, incl, 31);
-                int left = kc;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (id[q] >= 0) {
-                        const uint32_t bit = 1u << (id[q] & 31);
-                        const bool first = !(atomicOr(&seen[id[q] >> 5], bit) & bit);
-                        nf += first ? 1 : 0;
-                        --left;
-                        el[pos++] = (uint32_t)id[q] | (first ? ELEM_FIRST : 0u) | (left == 0 ? ELEM_END : 0u);
-                    }
-                }
-                for (int q = 4; q < oc.y; ++q) {
-                    const int idv = doc_id(sm, lg, __ldg(&d.trans[oc.x + q]));
-                    if (idv >= 0) {
-                        const uint32_t bit = 1u << (idv & 31);
-                        const bool first = !(atomicOr(&seen[idv >> 5], bit) & bit);
-                        nf += first ? 1 : 0;
-                        --left;
-                        el[pos++] = (uint32_t)idv | (first ? ELEM_FIRST : 0u) | (left == 0 ? ELEM_END : 0u);
-                    }
-                }
-            }
-            nf = (int)__reduce_add_sync(kFull, (unsigned)nf);
-            if (lane == 0) b.sinfo[s] = make_int4(n_i, out, nf, 0);
-            __syncwarp();
-            uint4 *sz = reinterpret_cast<uint4 *>(seen);
-            for (int k = lane; k < kDirect / 128; k += 32) sz[k] = make_uint4(0u, 0u, 0u, 0u);
-            __syncwarp();
+        for (int j = wib; j < pp.S; j += kPPWarps) {
+            const int64_t sj = (int64_t)pp.s0 + j;
+            int32_t v = 0;
+            if (lane < 2) v = b.sent_off[sj + lane];
+            const int32_t a = __shfl_sync(kFull, v, 0), L = __shfl_sync(kFull, v, 1) - a;
+            if (L > 64)
+                prep_row_long(b, d, sm, lg, sj, a, L, lane, gset, gset_clean, ++stamp, sm.seen[wib]);
+            else
+                prep_row_short(b, d, sm, lg, sj, a, L, lane, sm.seen[wib], sm.cbuf[wib], kmax);
         }
     }
 }

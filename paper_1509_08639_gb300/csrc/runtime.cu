@@ -667,7 +667,8 @@ int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_of
     for (int64_t k = 0; k < n_trans; ++k)
         if (trans[k] < 0 || trans[k] > MINE_MAX_TOKEN_ID) return fail(MINE_EINVAL, "translation outside [0, 2^30)");
     std::unique_ptr<mine_dict> d(new mine_dict());
-    d->d.log2 = std::max(4, ceil_log2_host(2 * (int64_t)n_keys));
+    // buckets of 8 slots, at most a quarter full on average
+    d->d.log2 = std::max(4, ceil_log2_host(4 * (int64_t)n_keys));
     d->d.kmax = kmax;
     d->d.n_trans = n_trans;
     const size_t slots_bytes = sizeof(int2) << d->d.log2;
