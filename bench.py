@@ -430,7 +430,7 @@ def main():
     src_tok = int((b.sent_off[b.doc_off[1:-1:2]].astype(np.int64) -
                    b.sent_off[b.doc_off[0:-1:2]].astype(np.int64)).sum())
     tgt_tok = n_tok - src_tok
-    # algorithmic work per launch (roofline)
+    # algorithmic work per launch: units of the launch x bytes (or int ops) per unit
     n_src_rows = int(S.sum())
     kept = kept_entries(w)
     prep_bytes = 4 * n_tok + 2 * tgt_tok + 4 * kept + 16 * n_src_rows   # tokens, ids, hit lists, row info
