@@ -87,6 +87,69 @@ def test_full_size_lognormal_batch_sampled(ctx):
     assert (nw <= 65536 * np.minimum(S, T) - 65536 * np.abs(S - T)).all()
 
 
+def test_device_batch_graph_replay(ctx):
+    """Repeating a device-buffer batch replays its captured graph: every
+    kernel runs again on the current contents of the input buffers, so new
+    tokens in the same buffers give the new results; a host-buffer call in
+    between, or per-kernel profiling, falls back to planning and launching."""
+    torch = pytest.importorskip("torch")
+    w = synth.workload(2, n_pairs=300)
+    b = w.batch
+    dh = ctx.dict_create(w.dictionary)
+    dev = torch.device("cuda:0")
+    sent = torch.from_numpy(b.sent_off).to(dev)
+    tok = torch.from_numpy(b.tokens).to(dev)
+    P, n = b.n_pairs, len(w.settings)
+    S, T = b.sizes()
+    cap = int(n * np.minimum(S, T).sum())
+    nw = torch.zeros(P * n, dtype=torch.int32, device=dev)
+    ns = torch.zeros(P * n, dtype=torch.int32, device=dev)
+    sel = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    base = np.zeros(P + 1, np.int64)
+    np.cumsum(n * np.minimum(S, T), out=base[1:])
+
+    def run_and_read():
+        nw.zero_()
+        ns.zero_()
+        sel.zero_()
+        c0 = ctx.launch_count()
+        ctx.run_batch_device(dh, P, b.doc_off, sent, tok, int(b.sent_off.shape[0] - 1),
+                             int(b.tokens.shape[0]), w.settings, nw, ns, sel, cap, stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        a, c, e = nw.cpu().numpy(), ns.cpu().numpy(), sel.cpu().numpy().reshape(-1, 3)
+        got = [[(int(a[p]), [tuple(int(v) for v in t) for t in e[base[p]:base[p] + c[p]]])]
+               for p in range(P)]
+        return got, ctx.launch_count() - c0
+
+    want = oracle_results(w)
+    first, n0 = run_and_read()
+    assert_same(first, want, "captured call")
+    for k in range(2):
+        again, n1 = run_and_read()
+        assert_same(again, want, f"replay {k}")
+        assert n1 == n0 > 0
+    # new contents in the same buffers
+    rng = np.random.default_rng(77)
+    tok2 = b.tokens.copy()
+    flip = rng.random(tok2.shape[0]) < 0.2
+    tok2[flip] = rng.integers(0, 200000, int(flip.sum()), dtype=np.int32)
+    b2 = synth.Batch(b.doc_off, b.sent_off, tok2)
+    tok.copy_(torch.from_numpy(tok2))
+    got2, _ = run_and_read()
+    assert_same(got2, oracle_results(w, b2), "replay on new tokens")
+    # a host-buffer call rewrites the context's scratch: the next call plans again
+    assert_same(ctx.run_batch(dh, b2, w.settings), oracle_results(w, b2), "host call")
+    got3, _ = run_and_read()
+    assert_same(got3, oracle_results(w, b2), "after a host call")
+    ctx.profile(True)
+    got4, _ = run_and_read()
+    ctx.profile(False)
+    ctx.profile_read()
+    assert_same(got4, oracle_results(w, b2), "profiled call")
+
+
 def _edge_batch(rng, d, sizes, vocab, lo=5, hi=30, empty_frac=0.0):
     cdf = synth._zipf_cdf(vocab)
     S = np.array([s for s, _ in sizes])
