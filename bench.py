@@ -327,6 +327,10 @@ def main():
     cells = int((S * T).sum())
     ctx = mine.Context(device=local)
     dh = ctx.dict_create(w.dictionary)
+    # alignment strategy per size bin, timed on this GPU
+    t_tune = time.perf_counter()
+    align_table = ctx.autotune()
+    t_tune = time.perf_counter() - t_tune
 
     # ---- device-resident inputs
     sent = torch.from_numpy(b.sent_off).to(dev)
@@ -493,6 +497,10 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "gpu_launches": launches,
+        "autotune": {"seconds": t_tune,
+                     "whole_cta_bins": [k for k, v in enumerate(align_table) if v == 1],
+                     "one_warp_bins": [k for k, v in enumerate(align_table) if v == 0],
+                     "bin": "ceil(log2(S*T+1)); other bins keep the built-in rule"},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

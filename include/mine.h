@@ -230,7 +230,12 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
  * nw_score are device arrays of P*n.  sel_cap must be at least
  * mine_batch_capacity().  The call returns once the work is enqueued; the
  * caller synchronises the stream.  Internal scratch stays owned by the
- * context and is reused by the next call on it. */
+ * context and is reused by the next call on it.
+ * The first call captures the plan upload and every kernel as a CUDA graph;
+ * a later call with the same dictionary, doc_off contents, settings, device
+ * pointers, sel_cap and stream replays that graph (every kernel runs again on
+ * the buffers' current contents) unless another call on the context has used
+ * its scratch since, or per-kernel profiling is on. */
 int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
                           const int32_t *doc_off_host, const mine_settings *settings,
                           mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
@@ -260,6 +265,24 @@ int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 
 /* Name of kernel id k ("" when out of range). */
 const char *mine_kernel_name(int32_t id);
+
+/* Autotuner of the alignment strategy per size bin.  Bin b holds the pairs
+ * with ceil(log2(S*T + 1)) == b, b < MINE_ALIGN_BINS.  For every bin of up to
+ * 2^17 cells this times, on the context's GPU, the alignment kernel over a
+ * batch of random square score matrices of that size aligned (a) one warp per
+ * alignment and (b) by a whole CTA of 8 pipelined warps, and records the
+ * faster; larger bins keep the built-in rule (whole CTA from 2^15 cells).
+ * A pair with S > 32 and T >= 512 is always aligned by a whole CTA (the
+ * one-warp form keeps one boundary row of at most 512 cells).  Runs
+ * synchronously on the context's stream and uses its scratch (about 70 MB).
+ * The strategy does not change any result, only the time.  No counterpart in
+ * the paper, whose single GPU NW (Section 5, Table 3) has no size classes. */
+#define MINE_ALIGN_BINS 40
+int mine_autotune(mine_ctx *ctx);
+
+/* Read (get != 0) or set the strategy table: tab[b] = 1 whole CTA, 0 one warp
+ * (where allowed), -1 built-in rule; n entries, n <= MINE_ALIGN_BINS. */
+int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get);
 
 #ifdef __cplusplus
 }

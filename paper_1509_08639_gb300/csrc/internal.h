@@ -135,6 +135,20 @@ struct BatchDev {
 // sentences is aligned by a whole CTA, as is every pair of kBigCells or more.
 constexpr int kRing = 512;
 constexpr int64_t kBigCells = 1 << 15;
+constexpr int kAlignBins = MINE_ALIGN_BINS;
+
+// Whole-CTA alignment for an S x T pair: forced when one warp cannot hold the
+// boundary row, else the tuned choice of its size bin (tab may be null; -1
+// entries keep the built-in rule).
+inline bool align_whole_cta(const int8_t *tab, int32_t S, int32_t T)
+{
+    if (S > kTile && T >= kRing) return true;
+    const int64_t c = (int64_t)S * T;
+    int bin = 0;
+    while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
+    if (tab && bin < kAlignBins && tab[bin] >= 0) return tab[bin] != 0;
+    return c >= kBigCells;
+}
 
 // launchers (kernels.cu); each returns the number of kernels launched
 int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_keys, DevDict d,
@@ -148,6 +162,7 @@ int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
+int launch_fill_scores(int32_t *M, int64_t n, uint32_t seed, cudaStream_t st);
 
 // Record the text returned by mine_last_error() for this thread (runtime.cu).
 void set_last_error(const char *msg);

@@ -2009,6 +2009,27 @@ int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st)
     return 1;
 }
 
+// Random scores in [0, 65536) for timing (a multiplicative hash of the index).
+__global__ void k_fill_scores(int32_t *__restrict__ M, int64_t n, uint32_t seed)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)k * 0x9E3779B1u ^ seed;
+        x ^= x >> 15;
+        x *= 0x2C1B3C6Du;
+        x ^= x >> 12;
+        M[k] = (int32_t)(x & 0xFFFFu);
+    }
+}
+
+int launch_fill_scores(int32_t *M, int64_t n, uint32_t seed, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    const int blocks = (int)std::min<int64_t>(4096, (n + 255) / 256);
+    k_fill_scores<<<blocks, 256, 0, st>>>(M, n, seed);
+    return 1;
+}
+
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st)
 {
     const int64_t n = (int64_t)S * T;

@@ -144,7 +144,7 @@ int add_settings(Plan &pl, const Setting *set, int n, int32_t S, int32_t T, int6
 // settings_of(p) -> (pointer, count) of pair p's settings
 template <class F>
 int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F settings_of,
-               int64_t max_abs_s, bool mined)
+               int64_t max_abs_s, bool mined, const int8_t *align_tab = nullptr)
 {
     pl = Plan();
     pl.P = P;
@@ -201,7 +201,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
     for (int pass = 0; pass < 2; ++pass) {
         for (int p : ord) {
             const PairPlan &pp = pl.pairs[p];
-            const bool big = (int64_t)pp.S * pp.T >= kBigCells || (pp.S > kTile && pp.T >= kRing);
+            const bool big = align_whole_cta(align_tab, pp.S, pp.T);
             if (big != (pass == 0)) continue;
             const int64_t CW = (pp.T + 15) >> 4;
             for (int g = 0; g < pp.ngap; ++g) {
@@ -451,6 +451,7 @@ struct mine_ctx {
     int64_t prof_n[KID_COUNT] = {0};
     int64_t err_off = -1;              // offset of the last device batch's error word
     uint64_t arena_gen = 0;            // bumped whenever a call rewrites arena / pin
+    int8_t align_tab[kAlignBins];      // alignment strategy per size bin (-1: built-in rule)
     uint64_t dict_serial = 0;
     // The last device-buffer batch as a CUDA graph (plan upload + kernels);
     // replayed when the next call repeats it byte for byte.
@@ -574,11 +575,106 @@ const char *mine_last_error(void) { return g_err.c_str(); }
 
 int64_t mine_launch_count(mine_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
 
+namespace {
+
+// Device time (ms, mean of three launches after a warm-up) of the alignment
+// kernel over P random side x side matrices, every pair aligned one warp
+// each (cta = 0) or by a whole CTA (cta = 1).
+int time_align(mine_ctx *ctx, int bin, int side, int32_t P, int cta, cudaEvent_t e0, cudaEvent_t e1,
+               float &ms)
+{
+    std::vector<int32_t> doc(2 * (size_t)P + 1);
+    for (size_t k = 0; k < doc.size(); ++k) doc[k] = (int32_t)k * side;
+    int8_t tab[kAlignBins];
+    std::fill(tab, tab + kAlignBins, (int8_t)-1);
+    tab[bin] = (int8_t)cta;
+    const Setting set(-65536, 0);
+    Plan pl;
+    int rc = build_plan(pl, P, doc.data(), (int64_t)doc.back(),
+                        [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, 65536, false, tab);
+    if (rc) return rc;
+    const Layout L = make_layout(pl, 1, false, true, false);
+    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
+    if ((rc = ensure_host(ctx->pin, L.plan_bytes + 64))) return rc;
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr, ctx->recip, ctx->gscratch);
+    launch_fill_scores(b.M, pl.m_elems, 0x5EEDu + (uint32_t)bin, st);
+    for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
+        if (rep == 1) CK(cudaEventRecord(e0, st));
+        ctx->launches += launch_align(b, ctx->num_sms, st);
+    }
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaGetLastError());
+    int32_t derr = 0;
+    CK(cudaMemcpy(&derr, b.err, 4, cudaMemcpyDeviceToHost));
+    if (derr) return fail(MINE_ETIMEDOUT, "a bounded device wait ran out while tuning");
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 3.0f;
+    return 0;
+}
+
+}  // namespace
+
+int mine_autotune(mine_ctx *ctx)
+{
+    if (!ctx) return fail(MINE_EINVAL, "null context");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    ++ctx->arena_gen;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(MINE_ECUDA, "cudaEventCreate failed");
+    }
+    int8_t tab[kAlignBins];
+    std::copy(ctx->align_tab, ctx->align_tab + kAlignBins, tab);
+    for (int bin = 6; bin <= 17 && rc == 0; ++bin) {
+        // square pairs whose cell count falls in the bin: 2^(bin-1) < side^2 + 1 <= 2^bin
+        int side = 1;
+        while ((int64_t)(side + 1) * (side + 1) + 1 <= (int64_t(1) << bin)) ++side;
+        const int64_t cells = (int64_t)side * side;
+        const int32_t P = (int32_t)std::min<int64_t>(8192, std::max<int64_t>(64, (int64_t(1) << 23) / cells));
+        float t[2] = {0.f, 0.f};
+        for (int cta = 0; cta < 2 && rc == 0; ++cta) rc = time_align(ctx, bin, side, P, cta, e0, e1, t[cta]);
+        if (rc == 0) tab[bin] = t[1] < t[0] ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::copy(tab, tab + kAlignBins, ctx->align_tab);
+    return MINE_OK;
+}
+
+int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get)
+{
+    if (!ctx || !tab || n < 0 || n > kAlignBins) return fail(MINE_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if (get) {
+        std::copy(ctx->align_tab, ctx->align_tab + n, tab);
+    } else {
+        for (int k = 0; k < n; ++k)
+            if (tab[k] < -1 || tab[k] > 1) return fail(MINE_EINVAL, "strategy entries are -1, 0 or 1");
+        std::copy(tab, tab + n, ctx->align_tab);
+        ++ctx->arena_gen;   // cached graphs hold plans of the old table
+    }
+    return MINE_OK;
+}
+
 int mine_open(const mine_config *cfg, mine_ctx **out)
 {
     if (!out) return fail(MINE_EINVAL, "out is NULL");
     *out = nullptr;
     std::unique_ptr<mine_ctx> ctx(new mine_ctx());
+    std::fill(ctx->align_tab, ctx->align_tab + kAlignBins, (int8_t)-1);
     mine_config c{};
     if (cfg) c = *cfg;
     else c.device = -1;
@@ -791,7 +887,8 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
     Plan pl;
     rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
-                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true);
+                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true,
+                    ctx->align_tab);
     if (rc) return rc;
     pl.n_tok = batch->n_tok;
     sel_off[0] = 0;
@@ -881,7 +978,8 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
     for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
     Plan pl;
     rc = build_plan(pl, P, doc_off_host, batch->n_sent,
-                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true);
+                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true,
+                    ctx->align_tab);
     if (rc) return rc;
     pl.n_tok = batch->n_tok;
     if (P == 0) return MINE_OK;
@@ -964,7 +1062,8 @@ int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mi
     const Setting set(gap, threshold);
     Plan pl;
     rc = build_plan(pl, 1, doc_off, (int64_t)S + T,
-                    [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, maxabs, false);
+                    [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, maxabs, false,
+                    ctx->align_tab);
     if (rc) return rc;
     if (std::min(S, T) > 0 && !out) return fail(MINE_EINVAL, "out is NULL");
     const Layout L = make_layout(pl, 1, false, true, false);
@@ -1239,7 +1338,7 @@ int launch_slot(mine_ctx *ctx, Slot &s)
                             set = s.reqs[p].settings.data();
                             cnt = (int)s.reqs[p].settings.size();
                         },
-                        65536, true);
+                        65536, true, ctx->align_tab);
     if (rc) return rc;
     s.plan.n_tok = n_tok;
     s.lay = make_layout(s.plan, dict->d.kmax, true, true, true);

@@ -90,7 +90,11 @@ SIGNATURES = {
     "mine_profile": (_I, [_P, _I]),
     "mine_profile_read": (_I, [_P, _P, _P, _I]),
     "mine_kernel_name": (ctypes.c_char_p, [_I]),
+    "mine_autotune": (_I, [_P]),
+    "mine_align_strategy": (_I, [_P, _P, _I, _I]),
 }
+
+ALIGN_BINS = 40
 
 _lib = None
 
@@ -237,6 +241,20 @@ class Context:
 
     def profile(self, enable: bool = True):
         _check(self.L.mine_profile(self.h, 1 if enable else 0), self.L)
+
+    def autotune(self):
+        """Time both alignment strategies per size bin on this GPU and keep
+        the faster; returns the strategy table."""
+        _check(self.L.mine_autotune(self.h), self.L)
+        return self.align_strategy()
+
+    def align_strategy(self, table=None):
+        """Get (table None) or set the per-bin strategy table: 1 whole CTA,
+        0 one warp where allowed, -1 built-in rule."""
+        t = np.full(ALIGN_BINS, -1, np.int8) if table is None else np.ascontiguousarray(table, np.int8)
+        _check(self.L.mine_align_strategy(self.h, _ptr(t), int(t.shape[0]), 1 if table is None else 0),
+               self.L)
+        return [int(v) for v in t]
 
     def profile_read(self):
         """{kernel name: (total device ms, timed launches)} since the last read."""

@@ -170,6 +170,32 @@ def _edge_batch(rng, d, sizes, vocab, lo=5, hi=30, empty_frac=0.0):
     return b
 
 
+def test_alignment_strategies_agree(ctx):
+    """Every pair aligned one warp each where allowed, then by a whole CTA
+    each, then by the autotuned table: the results never change."""
+    w = synth.workload(2, n_pairs=300)
+    dh = ctx.dict_create(w.dictionary)
+    want = oracle_results(w)
+    rng = np.random.default_rng(5)
+    sizes = [(s, t) for s in (1, 7, 31, 32, 33, 64, 100) for t in (1, 5, 32, 33, 200, 511, 512, 700)]
+    edge = _edge_batch(rng, w.dictionary, sizes, 200000, lo=5, hi=40)
+    want_e = oracle_results(w, edge)
+    old = ctx.align_strategy()
+    try:
+        for tab in ([0] * mine.ALIGN_BINS, [1] * mine.ALIGN_BINS):
+            ctx.align_strategy(tab)
+            assert ctx.align_strategy() == tab
+            assert_same(ctx.run_batch(dh, w.batch, w.settings), want, f"strategy {tab[0]}")
+            assert_same(ctx.run_batch(dh, edge, w.settings), want_e, f"edge sizes, strategy {tab[0]}")
+        ctx.align_strategy(old)
+        tuned = ctx.autotune()
+        assert all(v in (0, 1) for v in tuned[6:18])
+        assert tuned[:6] == old[:6] and tuned[18:] == old[18:]
+        assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned")
+    finally:
+        ctx.align_strategy(old)
+
+
 def test_tile_boundaries_and_degenerate_shapes(ctx):
     rng = np.random.default_rng(77)
     d = synth.make_dictionary(rng, 5000, 3)
