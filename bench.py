@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident path (for profiler captures)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in alignment strategy (no tuning launches before the run)")
     return ap.parse_args()
 
 
@@ -329,7 +331,7 @@ def main():
     dh = ctx.dict_create(w.dictionary)
     # alignment strategy per size bin, timed on this GPU
     t_tune = time.perf_counter()
-    align_table = ctx.autotune()
+    align_table = ctx.align_strategy() if args.no_autotune else ctx.autotune()
     t_tune = time.perf_counter() - t_tune
 
     # ---- device-resident inputs

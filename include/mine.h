@@ -241,6 +241,17 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
                           mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
                           void *stream);
 
+/* Single-precision scores (a float variant of the score of mine_run_batch):
+ * for every pair p of the host batch, its S_p x T_p matrix of
+ *   s = 0.375 (a/m_j + b/n_i) + 0.25 min(L,L')/max(L,L')
+ * with the features of the fixed-point score (Section 4: the confidence of a
+ * sentence pair; here token overlap and length) and correctly rounded float
+ * division, written row-major to out, pair after pair (out_len >= sum S*T
+ * floats, host memory owned by the caller).  Within 1e-5 of the same score in
+ * exact arithmetic.  No alignment runs.  Errors as mine_run_batch. */
+int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,
+                   int64_t out_len);
+
 /* Wait for all work of the context's device and report a device-side
  * validation failure of the last mine_run_batch_device call (malformed
  * sentence offsets, token IDs out of range) as MINE_EINVAL. */

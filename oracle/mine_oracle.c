@@ -31,6 +31,11 @@
  *           H[i][j] = max(H[i-1][j-1]+s(i,j), H[i-1][j]+g, H[i][j-1]+g),
  *           direction DIAG if the diagonal attains the max, else UP, else LEFT
  *           (first row LEFT, first column UP).
+ *   real    the same features with exact division, in double:
+ *           s = 0.75 * (a/m_j + b/n_i) / 2 + 0.25 * min(L,L')/max(L,L')
+ *           (a/m_j = 0 if m_j = 0, b/n_i = 0 if n_i = 0, ratio 1 if both are
+ *           empty) -- the reference of the single-precision score variant;
+ *           65536*s exceeds the fixed-point s by less than 2.375.
  *   path    from (S,T) follow the directions back to (0,0).
  *   select  every DIAG step (i,j) with s(i,j) > theta, in increasing i.
  * Arithmetic is int64 throughout, so nothing here can overflow for inputs the
@@ -150,9 +155,11 @@ typedef struct {
 } tgt_set;
 
 /* ------------------------------------------------------------------ score
- * Fills M (S x T, row-major, int32) with the fixed-point pair score. */
-void oracle_score_matrix(void *dict, const int32_t *src_off, const int32_t *src_tok, int32_t S,
-                         const int32_t *tgt_off, const int32_t *tgt_tok, int32_t T, int32_t *M)
+ * Fills M (S x T, row-major, int32) with the fixed-point pair score when M is
+ * not NULL, and Mr (double) with the real-valued score when Mr is not NULL. */
+static void score_matrix_impl(void *dict, const int32_t *src_off, const int32_t *src_tok, int32_t S,
+                              const int32_t *tgt_off, const int32_t *tgt_tok, int32_t T, int32_t *M,
+                              double *Mr)
 {
     const oracle_dict *d = (const oracle_dict *)dict;
     src_set *src = (src_set *)calloc((size_t)(S > 0 ? S : 1), sizeof(src_set));
@@ -211,12 +218,30 @@ void oracle_score_matrix(void *dict, const int32_t *src_off, const int32_t *src_
             int64_t lmax = src[i].L < tgt[j].L ? tgt[j].L : src[i].L;
             int64_t q_l = lmax > 0 ? (lmin * 65536) / lmax : 65536;
             int64_t s = (49152 * ((q_t + q_s) / 2) + 16384 * q_l) / 65536;
-            M[(int64_t)i * T + j] = (int32_t)s;
+            if (M) M[(int64_t)i * T + j] = (int32_t)s;
+            if (Mr) {
+                double rt = tgt[j].m > 0 ? (double)a / (double)tgt[j].m : 0.0;
+                double rs = src[i].n > 0 ? (double)b / (double)src[i].n : 0.0;
+                double rl = lmax > 0 ? (double)lmin / (double)lmax : 1.0;
+                Mr[(int64_t)i * T + j] = 0.75 * (rt + rs) / 2.0 + 0.25 * rl;
+            }
         }
     }
     for (int32_t i = 0; i < S; ++i) { free(src[i].X); free(src[i].U); }
     for (int32_t j = 0; j < T; ++j) free(tgt[j].V);
     free(src); free(tgt);
+}
+
+void oracle_score_matrix(void *dict, const int32_t *src_off, const int32_t *src_tok, int32_t S,
+                         const int32_t *tgt_off, const int32_t *tgt_tok, int32_t T, int32_t *M)
+{
+    score_matrix_impl(dict, src_off, src_tok, S, tgt_off, tgt_tok, T, M, NULL);
+}
+
+void oracle_score_matrix_f64(void *dict, const int32_t *src_off, const int32_t *src_tok, int32_t S,
+                             const int32_t *tgt_off, const int32_t *tgt_tok, int32_t T, double *Mr)
+{
+    score_matrix_impl(dict, src_off, src_tok, S, tgt_off, tgt_tok, T, NULL, Mr);
 }
 
 /* ------------------------------------------------------------------ NW

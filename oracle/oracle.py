@@ -52,6 +52,7 @@ def load(path: str):
     L.oracle_dict_new.argtypes = [P, P, P, i32]
     L.oracle_dict_free.argtypes = [P]
     L.oracle_score_matrix.argtypes = [P, P, P, i32, P, P, i32, P]
+    L.oracle_score_matrix_f64.argtypes = [P, P, P, i32, P, P, i32, P]
     L.oracle_nw.restype = ctypes.c_int64
     L.oracle_nw.argtypes = [P, i32, i32, i32, P, P]
     L.oracle_traceback.restype = i32
@@ -102,6 +103,17 @@ def score_matrix(od: OracleDict, src, tgt) -> np.ndarray:
     S, T = so.shape[0] - 1, to.shape[0] - 1
     M = np.zeros((S, T), np.int32)
     od.L.oracle_score_matrix(od.h, _p(so), _p(st), S, _p(to), _p(tt), T, _p(M))
+    return M
+
+
+def score_matrix_f64(od: OracleDict, src, tgt) -> np.ndarray:
+    """Real-valued pair score (exact division, double) of source sentence i,
+    target j: the reference of the single-precision score."""
+    so, st = _c32(src[0]), _c32(src[1])
+    to, tt = _c32(tgt[0]), _c32(tgt[1])
+    S, T = so.shape[0] - 1, to.shape[0] - 1
+    M = np.zeros((S, T), np.float64)
+    od.L.oracle_score_matrix_f64(od.h, _p(so), _p(st), S, _p(to), _p(tt), T, _p(M))
     return M
 
 

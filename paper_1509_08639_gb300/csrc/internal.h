@@ -122,6 +122,7 @@ struct BatchDev {
     int32_t *hfin;               // [n_nw_items] H[S][T] of each alignment
     const uint64_t *recip;       // [kMaxSentTokens + 1]: ceil(2^48 / m), 0 for m = 0
     int2 *gscratch;              // per-warp tables for sentences longer than the shared ones
+    int32_t f32;                 // score kernel writes single-precision scores (float bits) into M
     int32_t *counters;           // [8] work-queue heads
     int32_t *err;                // error word (0 = fine)
     // outputs

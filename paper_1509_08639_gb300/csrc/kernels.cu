@@ -1002,6 +1002,7 @@ struct alignas(16) DirectCta {
     uint64_t Km[32];
     uint64_t KL[32];
     int32_t Lt[32];
+    int32_t Mj[32];          // m_j (single-precision scores)
 };
 
 // Shared memory of one k_score CTA (kSWS warps).  The mbarriers stay outside
@@ -1071,6 +1072,18 @@ __device__ __forceinline__ int32_t cell_score(uint32_t a, uint32_t bb, uint64_t 
     return (int32_t)((3u * h + q_l) >> 2);
 }
 
+// Single-precision score of one cell from the same counts: the coverage and
+// length ratios by correctly rounded division, then 0.375 (q_t + q_s) +
+// 0.25 q_l (the fixed-point weights 49152/2 and 16384 over 65536).
+__device__ __forceinline__ float cell_score_f32(uint32_t a, uint32_t bb, int m, int n, int Ls, int Lt)
+{
+    const float rt = m > 0 ? __fdiv_rn((float)a, (float)m) : 0.f;
+    const float rs = n > 0 ? __fdiv_rn((float)bb, (float)n) : 0.f;
+    const int lmax = max(Ls, Lt);
+    const float rl = lmax > 0 ? __fdiv_rn((float)min(Ls, Lt), (float)lmax) : 1.f;
+    return 0.375f * (rt + rs) + 0.25f * rl;
+}
+
 // Column mask of `key` in the block table (valid lanes only).  The first
 // slot settles almost every probe without a branch; lanes whose key sits
 // further along continue in a loop that the warp enters only when needed.
@@ -1111,7 +1124,7 @@ template <int NPL>
 __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
                                          const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
                                          uint64_t Ks, uint64_t KLs, int Ls, int ncols,
-                                         int32_t *mrow, int c0);
+                                         int32_t *mrow, int c0, bool f32, const int32_t *Mj, int n_i);
 
 // Accumulate the overlap counts of one column block and score its cells
 // into row `lane` of the score tiles (mrow points at column tile 0).
@@ -1120,7 +1133,7 @@ template <int NPL>
 __device__ __forceinline__ void score_block(const KeyedWarp &sm, const int2 *tab, int lg,
                                          const uint32_t *el, int n_elem, int nE2, int ncols,
                                          bool row_ok, uint64_t Ks, uint64_t KLs, int Ls,
-                                         int32_t *mrow, int c0)
+                                         int32_t *mrow, int c0, bool f32, int n_i)
 {
     uint32_t A[NPL], B[NPL];
 #pragma unroll
@@ -1150,7 +1163,7 @@ __device__ __forceinline__ void score_block(const KeyedWarp &sm, const int2 *tab
         add2<NPL>(B, xb0, xb1);
     }
     if (!row_ok) return;
-    emit_row<NPL>(A, B, sm.Km, sm.KL, sm.Lt, Ks, KLs, Ls, ncols, mrow, c0);
+    emit_row<NPL>(A, B, sm.Km, sm.KL, sm.Lt, Ks, KLs, Ls, ncols, mrow, c0, f32, sm.mcnt, n_i);
 }
 
 // Score the cells of one row and one column block from its bit-sliced counts
@@ -1161,7 +1174,7 @@ template <int NPL>
 __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
                                          const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
                                          uint64_t Ks, uint64_t KLs, int Ls, int ncols,
-                                         int32_t *mrow, int c0)
+                                         int32_t *mrow, int c0, bool f32, const int32_t *Mj, int n_i)
 {
     const bool whole = ncols == 32 && (c0 & 31) == 0;   // one whole row of one tile
     if constexpr (NPL <= 8) {
@@ -1182,7 +1195,8 @@ __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_
                 const int jj = 8 * m + c;
                 const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
                 const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
-                v[c] = cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
+                v[c] = f32 ? __float_as_int(cell_score_f32(a, bb, Mj[jj], n_i, Ls, Lt[jj]))
+                           : cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
             }
             if (whole) {
                 int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
@@ -1201,8 +1215,9 @@ __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_
         }
     } else {
         for (int jj = 0; jj < ncols; ++jj) {
-            const int32_t v = cell_score(plane_value<NPL>(A, jj), plane_value<NPL>(B, jj), Km[jj],
-                                         Ks, Ls, Lt[jj], KLs, KL[jj]);
+            const uint32_t a = plane_value<NPL>(A, jj), bb = plane_value<NPL>(B, jj);
+            const int32_t v = f32 ? __float_as_int(cell_score_f32(a, bb, Mj[jj], n_i, Ls, Lt[jj]))
+                                  : cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
             const int col = c0 + jj;
             mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v;
         }
@@ -1302,7 +1317,7 @@ __device__ __forceinline__ int stage_ids(const BatchDev &b, uint16_t *ids, unsig
 // memory.  Returns false (on every thread) when a bounded wait ran out.
 __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned long long *dbar,
                                   uint32_t &dparity, const PairPlan &pp, int D, int tid, int nrows,
-                                  bool row_ok, const uint32_t *hl, int n_h, uint64_t Ks,
+                                  bool row_ok, const uint32_t *hl, int n_h, int n_i, uint64_t Ks,
                                   uint64_t KLs, int Ls, int32_t *mrow)
 {
     const int T = pp.T;
@@ -1351,6 +1366,7 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
             sd.Km[col] = __ldg(&b.recip[m]);
             sd.KL[col] = __ldg(&b.recip[e - a]);
             sd.Lt[col] = e - a;
+            sd.Mj[col] = m;
         }
         __syncthreads();
         // the ids are in the masks now: stage the next block's
@@ -1364,11 +1380,15 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
             if (maxH < 256) {
                 uint32_t A[8], B[8];
                 direct_counts<8>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
-                if (row_ok) emit_row<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0);
+                if (row_ok)
+                    emit_row<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0, sd.Mj,
+                                n_i);
             } else {
                 uint32_t A[11], B[11];
                 direct_counts<11>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
-                if (row_ok) emit_row<11>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0);
+                if (row_ok)
+                    emit_row<11>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
+                                 sd.Mj, n_i);
             }
         }
         __syncthreads();
@@ -1454,9 +1474,11 @@ __device__ bool score_item_keyed(const BatchDev &b, KeyedWarp &sm, unsigned long
         __syncwarp();
         const int bound = max(min(maxU, maxM), maxN);
         if (bound < 256) {
-            score_block<8>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+            score_block<8>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0,
+                           b.f32 != 0, n_i);
         } else {
-            score_block<11>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0);
+            score_block<11>(sm, tab, lg, el, n_elem, nE2, ncols, row_ok, Ks, KLs, Ls, mrow, c0,
+                            b.f32 != 0, n_i);
         }
         __syncwarp();
         c0 = nc0;
@@ -1573,7 +1595,7 @@ k_score(BatchDev b)
             // generic stores now cover the keyed staging buffers: fence before their next copy
             generic[0] = generic[1] = true;
             ok = score_item_direct(b, S.d, &S.dbar, dparity, pp, D, tid, nrows, row_ok, el, n_elem,
-                                   Ks, KLs, Ls, mrow);
+                                   n_i, Ks, KLs, Ls, mrow);
             continue;
         }
         mask_clean = false;

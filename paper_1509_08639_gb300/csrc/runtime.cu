@@ -538,7 +538,7 @@ int timed_launch(mine_ctx *ctx, int kid, cudaStream_t st, F fn)
 
 // Enqueue the kernels of one batch whose plan is already on the device.
 int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int64_t n_sent,
-                    int64_t n_tok, bool scoring, cudaStream_t st)
+                    int64_t n_tok, bool scoring, cudaStream_t st, bool aligning = true)
 {
     int n = 0;
     CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
@@ -551,8 +551,10 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
-    n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
-    n += timed_launch(ctx, KID_TRACE, st, [&] { return launch_trace(b, ctx->num_sms, st); });
+    if (aligning) {
+        n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_TRACE, st, [&] { return launch_trace(b, ctx->num_sms, st); });
+    }
     CK(cudaGetLastError());
     ctx->launches += n;
     return 0;
@@ -939,6 +941,60 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
         }
     }
     sel_off[(int64_t)P * n] = o;
+    return MINE_OK;
+}
+
+int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,
+                   int64_t out_len)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    const int32_t P = batch->n_pairs;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    ++ctx->arena_gen;
+    const Setting set(-65536, 0);
+    Plan pl;
+    rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, 65536, true,
+                    ctx->align_tab);
+    if (rc) return rc;
+    pl.n_tok = batch->n_tok;
+    int64_t cells = 0;
+    for (const PairPlan &pp : pl.pairs) cells += (int64_t)pp.S * pp.T;
+    if (out_len < cells || (cells > 0 && !out)) return fail(MINE_EINVAL, "out shorter than the sum of S*T");
+    if (P == 0 || cells == 0) return MINE_OK;
+    const Layout L = make_layout(pl, dict->d.kmax, true, true, true);
+    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
+    const int64_t m_bytes = 4 * pl.m_elems;
+    if ((rc = ensure_host(ctx->pin, align_up(L.plan_bytes, 64) + m_bytes + 64))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    b.f32 = 1;
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
+    int32_t *h_err = reinterpret_cast<int32_t *>(hp + align_up(L.plan_bytes, 64));
+    float *h_m = reinterpret_cast<float *>(h_err + 16);
+    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_m, b.M, m_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*h_err) return fail(MINE_EINVAL, device_err_text(*h_err));
+    // tiles -> row-major, pair after pair
+    int64_t o = 0;
+    for (const PairPlan &pp : pl.pairs) {
+        const int TT = (pp.T + kTile - 1) / kTile;
+        for (int i = 0; i < pp.S; ++i)
+            for (int j = 0; j < pp.T; ++j) out[o++] = h_m[m_cell(pp.m_off, TT, i, j)];
+    }
     return MINE_OK;
 }
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "mine_profile_read": (_I, [_P, _P, _P, _I]),
     "mine_kernel_name": (ctypes.c_char_p, [_I]),
     "mine_autotune": (_I, [_P]),
+    "mine_score_f32": (_I, [_P, _P, ctypes.POINTER(BatchC), _P, _L]),
     "mine_align_strategy": (_I, [_P, _P, _I, _I]),
 }
 
@@ -241,6 +242,21 @@ class Context:
 
     def profile(self, enable: bool = True):
         _check(self.L.mine_profile(self.h, 1 if enable else 0), self.L)
+
+    def score_f32(self, dict_h, batch):
+        """Single-precision score matrices of every pair (list of S x T float32 arrays)."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        S, T = batch.sizes()
+        cells = int((S * T).sum())
+        out = np.zeros(max(cells, 1), np.float32)
+        bc = BatchC(batch.n_pairs, int(so.shape[0] - 1), int(tk.shape[0]), _ptr(do), _ptr(so), _ptr(tk))
+        _check(self.L.mine_score_f32(self.h, dict_h, ctypes.byref(bc), _ptr(out), cells), self.L)
+        res, o = [], 0
+        for p in range(batch.n_pairs):
+            n = int(S[p] * T[p])
+            res.append(out[o:o + n].reshape(int(S[p]), int(T[p])))
+            o += n
+        return res
 
     def autotune(self):
         """Time both alignment strategies per size bin on this GPU and keep

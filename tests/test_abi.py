@@ -19,7 +19,7 @@ HEADER = os.path.join(ROOT, "include", "mine.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mine_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mine_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +38,7 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_function(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r" T (mine_[a-z_]+)$", out, flags=re.M))
+    exported = set(re.findall(r" T (mine_[a-z0-9_]+)$", out, flags=re.M))
     missing = [f for f in declared_functions() if f not in exported]
     assert not missing, missing
     # and the binding knows the signature of each of them

@@ -196,6 +196,31 @@ def test_alignment_strategies_agree(ctx):
         ctx.align_strategy(old)
 
 
+def test_single_precision_scores(ctx):
+    """Float scores within 1e-5 of the exact-arithmetic oracle on both score
+    paths (document ids, and the token-keyed path of a target article with
+    more than 8192 distinct tokens), including empty sentences."""
+    w = synth.workload(2, n_pairs=120)
+    w1 = synth.workload(1)
+    rng = np.random.default_rng(9)
+    src = [[int(x) for x in rng.integers(0, 200000, 30)] for _ in range(40)]
+    tgt = [[int(x) for x in rng.integers(0, 200000, 400)] for _ in range(30)]
+    big = synth.docs_from_lists(src, tgt)
+    edge = _edge_batch(rng, w.dictionary, [(1, 1), (33, 65), (64, 31), (5, 0), (0, 4)], 200000,
+                       empty_frac=0.2)
+    for dd, b in ((w.dictionary, w.batch), (w1.dictionary, w1.batch), (w.dictionary, big),
+                  (w.dictionary, edge)):
+        dh = ctx.dict_create(dd)
+        got = ctx.score_f32(dh, b)
+        od = O.OracleDict(dd)
+        for p in range(b.n_pairs):
+            want = O.score_matrix_f64(od, *b.pair(p))
+            assert got[p].shape == want.shape
+            if want.size:
+                err = np.abs(got[p].astype(np.float64) - want).max()
+                assert err <= 1e-5, (p, err)
+
+
 def test_tile_boundaries_and_degenerate_shapes(ctx):
     rng = np.random.default_rng(77)
     d = synth.make_dictionary(rng, 5000, 3)

@@ -87,6 +87,43 @@ def test_score_closed_forms():
     check_score_closed_forms()
 
 
+def test_score_real_hand_example():
+    g = _gold("score_real_hand_example.json")
+    base = _gold(g["same_inputs_as"])
+    od = O.OracleDict(_dict_from_json(base["dictionary"]))
+    b = synth.docs_from_lists(base["src"], base["tgt"])
+    M = O.score_matrix_f64(od, *b.pair(0))
+    want = np.array([[n / d for n, d in row] for row in g["M_num_den"]])
+    assert np.abs(M - want).max() < 1e-15
+
+
+def test_score_real_closed_forms():
+    ident = synth.dictionary_from_map({t: [t] for t in range(1, 20)})
+    od = O.OracleDict(ident)
+    sent = [3, 5, 5, 7, 11, 3, 2]
+    assert O.score_matrix_f64(od, *synth.docs_from_lists([sent], [list(sent)]).pair(0))[0, 0] == 1.0
+    for L1, L2 in [(3, 7), (7, 3), (5, 5), (1, 9), (13, 4)]:
+        src = [1 + (k % 5) for k in range(L1)]
+        tgt = [100 + k for k in range(L2)]
+        v = O.score_matrix_f64(od, *synth.docs_from_lists([src], [tgt]).pair(0))[0, 0]
+        assert abs(v - 0.25 * min(L1, L2) / max(L1, L2)) < 1e-15
+    assert O.score_matrix_f64(od, *synth.docs_from_lists([[1, 2]], [[]]).pair(0))[0, 0] == 0.0
+    assert O.score_matrix_f64(od, *synth.docs_from_lists([[]], [[]]).pair(0))[0, 0] == 0.25
+    assert O.score_matrix_f64(od, *synth.docs_from_lists([[500, 501]], [[500, 501]]).pair(0))[0, 0] == 0.25
+
+
+def test_score_real_matches_fixed_point_within_its_rounding():
+    """The fixed-point score floors three ratios and one weighted sum: 65536
+    times the exact score exceeds it by at least 0 and less than 2.375."""
+    w = synth.workload(2, n_pairs=40)
+    od = O.OracleDict(w.dictionary)
+    for p in range(w.batch.n_pairs):
+        src, tgt = w.batch.pair(p)
+        Mq = O.score_matrix(od, src, tgt).astype(np.float64)
+        Mr = O.score_matrix_f64(od, src, tgt) * 65536.0
+        assert (Mr - Mq >= -1e-9).all() and (Mr - Mq < 2.375).all(), p
+
+
 def test_score_ignores_dictionary_key_order_and_token_order():
     rng = np.random.default_rng(7)
     w = synth.workload(1)
