@@ -291,6 +291,13 @@ const char *mine_kernel_name(int32_t id);
 #define MINE_ALIGN_BINS 40
 int mine_autotune(mine_ctx *ctx);
 
+/* The same tuning on a batch of the caller's workload (host buffers as for
+ * mine_run_batch): its score matrices are computed once, then for every size
+ * bin present in it (largest pairs excepted, see above) the other strategy
+ * is tried on the whole batch's alignment, and kept when that is more than 3%
+ * faster.  Synchronous; uses the context's scratch. */
+int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch);
+
 /* Read (get != 0) or set the strategy table: tab[b] = 1 whole CTA, 0 one warp
  * (where allowed), -1 built-in rule; n entries, n <= MINE_ALIGN_BINS. */
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get);

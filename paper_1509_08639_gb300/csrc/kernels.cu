@@ -1120,11 +1120,22 @@ __device__ __forceinline__ void add2(uint32_t (&P)[NPL], uint32_t x, uint32_t y)
     }
 }
 
-template <int NPL>
+template <int NPL, bool F32>
 __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
                                          const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
                                          uint64_t Ks, uint64_t KLs, int Ls, int ncols,
-                                         int32_t *mrow, int c0, bool f32, const int32_t *Mj, int n_i);
+                                         int32_t *mrow, int c0, const int32_t *Mj, int n_i);
+
+// emit_row with the single-precision form chosen at run time (uniform per launch)
+template <int NPL>
+__device__ __forceinline__ void emit_row_any(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
+                                             const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
+                                             uint64_t Ks, uint64_t KLs, int Ls, int ncols, int32_t *mrow,
+                                             int c0, bool f32, const int32_t *Mj, int n_i)
+{
+    if (f32) emit_row<NPL, true>(A, B, Km, KL, Lt, Ks, KLs, Ls, ncols, mrow, c0, Mj, n_i);
+    else emit_row<NPL, false>(A, B, Km, KL, Lt, Ks, KLs, Ls, ncols, mrow, c0, Mj, n_i);
+}
 
 // Accumulate the overlap counts of one column block and score its cells
 // into row `lane` of the score tiles (mrow points at column tile 0).
@@ -1163,18 +1174,18 @@ __device__ __forceinline__ void score_block(const KeyedWarp &sm, const int2 *tab
         add2<NPL>(B, xb0, xb1);
     }
     if (!row_ok) return;
-    emit_row<NPL>(A, B, sm.Km, sm.KL, sm.Lt, Ks, KLs, Ls, ncols, mrow, c0, f32, sm.mcnt, n_i);
+    emit_row_any<NPL>(A, B, sm.Km, sm.KL, sm.Lt, Ks, KLs, Ls, ncols, mrow, c0, f32, sm.mcnt, n_i);
 }
 
 // Score the cells of one row and one column block from its bit-sliced counts
 // A (|U_i and X_j|) and B (source tokens with a translation in X_j) into the
 // row's score tiles (mrow points at column tile 0).  NPL <= 8: bit planes are
 // turned into byte counts by 8 x 8 transposes.
-template <int NPL>
+template <int NPL, bool F32>
 __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_t (&B)[NPL],
                                          const uint64_t *Km, const uint64_t *KL, const int32_t *Lt,
                                          uint64_t Ks, uint64_t KLs, int Ls, int ncols,
-                                         int32_t *mrow, int c0, bool f32, const int32_t *Mj, int n_i)
+                                         int32_t *mrow, int c0, const int32_t *Mj, int n_i)
 {
     const bool whole = ncols == 32 && (c0 & 31) == 0;   // one whole row of one tile
     if constexpr (NPL <= 8) {
@@ -1195,8 +1206,8 @@ __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_
                 const int jj = 8 * m + c;
                 const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
                 const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
-                v[c] = f32 ? __float_as_int(cell_score_f32(a, bb, Mj[jj], n_i, Ls, Lt[jj]))
-                           : cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
+                if constexpr (F32) v[c] = __float_as_int(cell_score_f32(a, bb, Mj[jj], n_i, Ls, Lt[jj]));
+                else v[c] = cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
             }
             if (whole) {
                 int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
@@ -1216,8 +1227,9 @@ __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_
     } else {
         for (int jj = 0; jj < ncols; ++jj) {
             const uint32_t a = plane_value<NPL>(A, jj), bb = plane_value<NPL>(B, jj);
-            const int32_t v = f32 ? __float_as_int(cell_score_f32(a, bb, Mj[jj], n_i, Ls, Lt[jj]))
-                                  : cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
+            int32_t v;
+            if constexpr (F32) v = __float_as_int(cell_score_f32(a, bb, Mj[jj], n_i, Ls, Lt[jj]));
+            else v = cell_score(a, bb, Km[jj], Ks, Ls, Lt[jj], KLs, KL[jj]);
             const int col = c0 + jj;
             mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v;
         }
@@ -1381,14 +1393,14 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
                 uint32_t A[8], B[8];
                 direct_counts<8>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
                 if (row_ok)
-                    emit_row<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0, sd.Mj,
-                                n_i);
+                    emit_row_any<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
+                                    sd.Mj, n_i);
             } else {
                 uint32_t A[11], B[11];
                 direct_counts<11>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
                 if (row_ok)
-                    emit_row<11>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
-                                 sd.Mj, n_i);
+                    emit_row_any<11>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
+                                     sd.Mj, n_i);
             }
         }
         __syncthreads();

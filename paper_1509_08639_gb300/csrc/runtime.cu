@@ -656,6 +656,111 @@ int mine_autotune(mine_ctx *ctx)
     return MINE_OK;
 }
 
+static int check_batch(const mine_batch *b);
+
+int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    const int32_t P = batch->n_pairs;
+    if (P == 0) return MINE_OK;
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    ++ctx->arena_gen;
+    const Setting set(-65536, 32768);
+    auto plan_with = [&](Plan &pl, const int8_t *tab) {
+        int r = build_plan(pl, P, batch->doc_off, batch->n_sent,
+                           [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, 65536, true, tab);
+        pl.n_tok = batch->n_tok;
+        return r;
+    };
+    int8_t tab[kAlignBins];
+    std::copy(ctx->align_tab, ctx->align_tab + kAlignBins, tab);
+    Plan pl;
+    if ((rc = plan_with(pl, tab))) return rc;
+    const Layout L = make_layout(pl, dict->d.kmax, true, true, true);
+    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
+    if ((rc = ensure_host(ctx->pin, L.plan_bytes + 64))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    pack_plan(pl, L, hp);
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    // the batch's score matrices, once
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(MINE_ECUDA, "cudaEventCreate failed");
+    }
+    // device time of the batch's alignment under a strategy table (the plan's
+    // alignment items change with it; score matrices and their layout do not)
+    auto time_with = [&](const int8_t *t, float &ms) -> int {
+        Plan q;
+        int r = plan_with(q, t);
+        if (r) return r;
+        CK(cudaStreamSynchronize(st));
+        pack_plan(q, L, hp);
+        CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+        BatchDev bq = make_batchdev(q, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaMemsetAsync(bq.counters, 0, 4 * 8, st));   // queue heads; keeps the error word
+            if (rep == 1) CK(cudaEventRecord(e0, st));
+            ctx->launches += launch_align(bq, ctx->num_sms, st);
+        }
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaGetLastError());
+        int32_t derr = 0;
+        CK(cudaMemcpy(&derr, bq.err, 4, cudaMemcpyDeviceToHost));
+        if (derr) return fail(derr == ERR_TIMEOUT ? MINE_ETIMEDOUT : MINE_EINVAL, device_err_text(derr));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 2.0f;
+        return 0;
+    };
+    // bins present in the batch whose pairs may take either strategy
+    bool present[kAlignBins] = {false};
+    for (const PairPlan &pp : pl.pairs) {
+        if (pp.S > kTile && pp.T >= kRing) continue;
+        const int64_t c = (int64_t)pp.S * pp.T;
+        int bin = 0;
+        while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
+        if (bin < kAlignBins) present[bin] = true;
+    }
+    float best = 0.f;
+    rc = time_with(tab, best);
+    for (int bin = 0; bin < kAlignBins && rc == 0; ++bin) {
+        if (!present[bin]) continue;
+        int8_t trial[kAlignBins];
+        std::copy(tab, tab + kAlignBins, trial);
+        // the strategy the bin has now, then the other one
+        const int64_t c_mid = bin > 0 ? (int64_t(1) << (bin - 1)) : 0;
+        const bool now = tab[bin] >= 0 ? tab[bin] != 0 : c_mid >= kBigCells;
+        trial[bin] = now ? 0 : 1;
+        float t = 0.f;
+        if ((rc = time_with(trial, t))) break;
+        if (t < 0.97f * best) {
+            best = t;
+            tab[bin] = trial[bin];
+        } else {
+            tab[bin] = now ? 1 : 0;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::copy(tab, tab + kAlignBins, ctx->align_tab);
+    return MINE_OK;
+}
+
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get)
 {
     if (!ctx || !tab || n < 0 || n > kAlignBins) return fail(MINE_EINVAL, "bad argument");

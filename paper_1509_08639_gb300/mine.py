@@ -91,6 +91,7 @@ SIGNATURES = {
     "mine_profile_read": (_I, [_P, _P, _P, _I]),
     "mine_kernel_name": (ctypes.c_char_p, [_I]),
     "mine_autotune": (_I, [_P]),
+    "mine_autotune_batch": (_I, [_P, _P, ctypes.POINTER(BatchC)]),
     "mine_score_f32": (_I, [_P, _P, ctypes.POINTER(BatchC), _P, _L]),
     "mine_align_strategy": (_I, [_P, _P, _I, _I]),
 }
@@ -262,6 +263,14 @@ class Context:
         """Time both alignment strategies per size bin on this GPU and keep
         the faster; returns the strategy table."""
         _check(self.L.mine_autotune(self.h), self.L)
+        return self.align_strategy()
+
+    def autotune_batch(self, dict_h, batch):
+        """Tune the per-bin alignment strategy on a batch of the workload;
+        returns the strategy table."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        bc = BatchC(batch.n_pairs, int(so.shape[0] - 1), int(tk.shape[0]), _ptr(do), _ptr(so), _ptr(tk))
+        _check(self.L.mine_autotune_batch(self.h, dict_h, ctypes.byref(bc)), self.L)
         return self.align_strategy()
 
     def align_strategy(self, table=None):

@@ -192,6 +192,10 @@ def test_alignment_strategies_agree(ctx):
         assert all(v in (0, 1) for v in tuned[6:18])
         assert tuned[:6] == old[:6] and tuned[18:] == old[18:]
         assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned")
+        ctx.align_strategy(old)
+        tuned = ctx.autotune_batch(dh, w.batch)
+        assert all(v in (-1, 0, 1) for v in tuned)
+        assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned on the batch")
     finally:
         ctx.align_strategy(old)
 
