@@ -88,7 +88,12 @@ struct NwItem {         // one alignment: (pair, gap)
 struct ScoreItem {      // 32 (preparation) or 64 (scoring) source rows of one pair
     int32_t pair;
     int32_t row0;
+    int32_t c0, c1;     // scoring: target columns [c0, c1)
 };
+
+// A score item covers at most this many target columns (long articles are cut
+// so that no item is much longer than the others).
+constexpr int kScoreColChunk = 256;
 
 struct BatchDev {
     // inputs
@@ -159,7 +164,8 @@ int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int3
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
-int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);
+int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);        // small articles
+int launch_score_wide(const BatchDev &b, int num_sms, cudaStream_t st);   // all other items
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
@@ -171,6 +177,6 @@ void set_last_error(const char *msg);
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
-                KID_COUNT = 9 };
+                KID_SCORE_WIDE = 9, KID_COUNT = 10 };
 
 }  // namespace mine

@@ -993,11 +993,12 @@ struct alignas(16) KeyedWarp {
     int32_t mcnt[32];       // m_j of the block being built
 };
 
-// CTA buffers of the document-id path: a column mask per document id (entry
-// kZeroEnt stays zero), the TMA-staged ids of one block's tokens and the
-// block's column data.
+// CTA buffers of the document-id path: a column mask per document id below
+// DIRECT (entry DIRECT stays zero), the TMA-staged ids of one block's tokens
+// and the block's column data.
+template <int DIRECT>
 struct alignas(16) DirectCta {
-    uint32_t mask[kDirect + 16];
+    uint32_t mask[DIRECT + 16];
     uint16_t ids[kBlkTokCap + 32];
     uint64_t Km[32];
     uint64_t KL[32];
@@ -1006,16 +1007,22 @@ struct alignas(16) DirectCta {
 };
 
 // Shared memory of one k_score CTA (kSWS warps).  The mbarriers stay outside
-// the union: both paths write it with generic stores.
+// the union: both paths write it with generic stores.  Without the
+// token-keyed path (KEYED false) the per-warp buffers are not needed.
+template <int DIRECT, bool KEYED>
 struct alignas(16) ScoreSmem {
     union {
-        KeyedWarp kw[kSWS];
-        DirectCta d;
+        KeyedWarp kw[KEYED ? kSWS : 1];
+        DirectCta<DIRECT> d;
     };
     unsigned long long bar[kSWS][2];   // token-keyed path, per warp
     unsigned long long dbar;           // document-id path
     int32_t item;
 };
+
+// The two score launches: articles with at most kDirectSmall distinct target
+// tokens (small mask array, more CTAs per SM), and all others.
+constexpr int kDirectSmall = 4096;
 
 __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b,
                                     uint32_t c)
@@ -1262,7 +1269,7 @@ __device__ __forceinline__ void add8(uint32_t (&P)[NPL], const uint32_t (&x)[8])
 // the row's hit list (document id | FIRST | END of its token group) is read
 // eight entries at a time; each id's column mask comes from the block's mask
 // array.  A counts FIRST entries, B counts token groups with any hit.
-template <int NPL>
+template <int NPL, int ZERO>
 __device__ __forceinline__ void direct_counts(const uint32_t *mask, const uint32_t *hl, int n_h,
                                               int nIt, uint4 f0, uint4 f1, uint32_t (&A)[NPL],
                                               uint32_t (&B)[NPL])
@@ -1295,7 +1302,7 @@ __device__ __forceinline__ void direct_counts(const uint32_t *mask, const uint32
         for (int q = 0; q < 8; ++q) {
             const bool ok = k0 + q < n_h;
             const uint32_t en = ok ? ev[q] : 0u;
-            const uint32_t m = mask[ok ? min(en & ELEM_TOKEN, (uint32_t)kZeroEnt) : (uint32_t)kZeroEnt];
+            const uint32_t m = mask[ok ? min(en & ELEM_TOKEN, (uint32_t)ZERO) : (uint32_t)ZERO];
             xa[q] = (en & ELEM_FIRST) ? m : 0u;
             hit |= m;
             xb[q] = (en & ELEM_END) ? hit : 0u;
@@ -1327,12 +1334,12 @@ __device__ __forceinline__ int stage_ids(const BatchDev &b, uint16_t *ids, unsig
 // its 32 rows and scores their cells; the masks of ids [0, D) are cleared
 // again.  A block with more than kBlkTokCap tokens reads its ids from global
 // memory.  Returns false (on every thread) when a bounded wait ran out.
-__device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned long long *dbar,
+template <int DIRECT>
+__device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsigned long long *dbar,
                                   uint32_t &dparity, const PairPlan &pp, int D, int tid, int nrows,
                                   bool row_ok, const uint32_t *hl, int n_h, int n_i, uint64_t Ks,
-                                  uint64_t KLs, int Ls, int32_t *mrow)
+                                  uint64_t KLs, int Ls, int32_t *mrow, int cbeg, int cend)
 {
-    const int T = pp.T;
     const int maxH = (int)__reduce_max_sync(kFull, (unsigned)n_h);   // this warp's rows
     const int nIt = (maxH + 7) >> 3;
     uint4 f0 = make_uint4(0u, 0u, 0u, 0u), f1 = f0;
@@ -1342,11 +1349,12 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
     }
     const int col = tid >> 1, half = tid & 1;
     const int64_t t0 = pp.t0;
-    int32_t k0 = b.sent_off[t0], k1 = b.sent_off[t0 + min(32, T)];
-    bool staged = k1 - k0 <= kBlkTokCap;
+    int32_t k0 = b.sent_off[t0 + cbeg], k1 = b.sent_off[t0 + cbeg + max(0, min(32, cend - cbeg))];
+    // a copy is issued only for a block the loop below consumes (and waits for)
+    bool staged = cbeg < cend && k1 - k0 <= kBlkTokCap;
     int lead = staged ? stage_ids(b, sd.ids, dbar, k0, k1, tid == 0) : 0;
-    for (int c0 = 0; c0 < T; c0 += 32) {
-        const int ncols = min(32, T - c0);
+    for (int c0 = cbeg; c0 < cend; c0 += 32) {
+        const int ncols = min(32, cend - c0);
         const int64_t j0 = t0 + c0;
         int32_t a = 0, e = 0;
         if (col < ncols) {
@@ -1354,9 +1362,9 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
             e = b.sent_off[j0 + col + 1];
         }
         // next block's token range, read while this one is in flight
-        const bool more = c0 + 32 < T;
+        const bool more = c0 + 32 < cend;
         int32_t nk1 = 0;
-        if (more) nk1 = b.sent_off[j0 + 32 + min(32, T - c0 - 32)];
+        if (more) nk1 = b.sent_off[j0 + 32 + min(32, cend - c0 - 32)];
         bool ok = true;
         if (staged) {
             ok = mbar_wait(dbar, dparity, b.err);
@@ -1368,10 +1376,10 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
         if (staged) {
             const uint16_t *ids = sd.ids + lead - k0;
             for (int32_t k = a + half; k < e; k += 2)
-                m += (atomicOr(&sd.mask[min((uint32_t)ids[k], kZeroEnt - 1)], bit) & bit) ? 0 : 1;
+                m += (atomicOr(&sd.mask[min((uint32_t)ids[k], (uint32_t)DIRECT - 1)], bit) & bit) ? 0 : 1;
         } else {
             for (int32_t k = a + half; k < e; k += 2)
-                m += (atomicOr(&sd.mask[min((uint32_t)b.tdoc[k], kZeroEnt - 1)], bit) & bit) ? 0 : 1;
+                m += (atomicOr(&sd.mask[min((uint32_t)b.tdoc[k], (uint32_t)DIRECT - 1)], bit) & bit) ? 0 : 1;
         }
         m += __shfl_xor_sync(kFull, m, 1);
         if (half == 0 && col < ncols) {
@@ -1391,13 +1399,13 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta &sd, unsigned lon
         if (nrows > 0) {
             if (maxH < 256) {
                 uint32_t A[8], B[8];
-                direct_counts<8>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
+                direct_counts<8, DIRECT>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
                 if (row_ok)
                     emit_row_any<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
                                     sd.Mj, n_i);
             } else {
                 uint32_t A[11], B[11];
-                direct_counts<11>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
+                direct_counts<11, DIRECT>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
                 if (row_ok)
                     emit_row_any<11>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
                                      sd.Mj, n_i);
@@ -1421,20 +1429,20 @@ __device__ bool score_item_keyed(const BatchDev &b, KeyedWarp &sm, unsigned long
                                  uint32_t (&parity)[2], bool (&generic)[2], int2 *gtab,
                                  const PairPlan &pp, int lane, bool row_ok, const uint32_t *el,
                                  int n_elem, int nU, int n_i, uint64_t Ks, uint64_t KLs, int Ls,
-                                 int32_t *mrow)
+                                 int32_t *mrow, int cbeg, int cend)
 {
-    const int T = pp.T;
+    const int T = cend;   // blocks end at the item's last column
     const int64_t tcol0 = pp.t0;
     const uint64_t *recip = b.recip;
     const int nE2 = (int)((__reduce_max_sync(kFull, (unsigned)n_elem) + 1) & ~1u);
     const int maxU = (int)__reduce_max_sync(kFull, (unsigned)nU);
     const int maxN = (int)__reduce_max_sync(kFull, (unsigned)n_i);
     int cur = 0;
-    int c0 = 0, ntok = 0, lead = 0, ncols = 0;
+    int c0 = cbeg, ntok = 0, lead = 0, ncols = 0;
     bool staged = false;
     int64_t tok0 = 0;
-    if (T > 0)
-        ncols = plan_block(b, sm, bar, 0, tcol0, 0, T, lane, ntok, lead, generic[0], staged, tok0);
+    if (c0 < T)
+        ncols = plan_block(b, sm, bar, 0, tcol0, c0, T, lane, ntok, lead, generic[0], staged, tok0);
     bool pending = ncols > 0 && staged;   // a copy in flight into buffer `cur`
     while (c0 < T) {
         if (ncols == 0) {
@@ -1537,11 +1545,15 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, KeyedWarp &sm, unsi
     return ncols;
 }
 
+// DIRECT = kDirectSmall: items of articles with at most that many distinct
+// target tokens (queue counters[1]); DIRECT = kDirect with KEYED: all other
+// items, document-id or token-keyed (queue counters[6]).
+template <int DIRECT, bool KEYED>
 __global__ void __launch_bounds__(kSWS * 32)
 k_score(BatchDev b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScoreSmem &S = *reinterpret_cast<ScoreSmem *>(smem_raw);
+    ScoreSmem<DIRECT, KEYED> &S = *reinterpret_cast<ScoreSmem<DIRECT, KEYED> *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int wib = tid >> 5;
@@ -1565,11 +1577,13 @@ k_score(BatchDev b)
         // every thread leaves together: on an error (here or in another CTA)
         // or when the queue is empty
         if (__syncthreads_or(!ok || *(volatile int32_t *)b.err != 0)) break;
-        if (tid == 0) S.item = atomicAdd(&b.counters[1], 1);
+        if (tid == 0) S.item = atomicAdd(&b.counters[KEYED ? 6 : 1], 1);
         __syncthreads();
         const int item = S.item;
         if (item >= b.n_score_items) break;
         const ScoreItem si = b.score_items[item];
+        const int D = b.pdoc[si.pair];
+        if (KEYED ? (D >= 0 && D <= kDirectSmall) : (D < 0 || D > kDirectSmall)) continue;   // the other launch's
         const PairPlan pp = b.pairs[si.pair];
         const int TT = (pp.T + 31) >> 5;
         // this warp's 32 rows, in the pair's order of element counts (the
@@ -1593,27 +1607,28 @@ k_score(BatchDev b)
         const uint64_t KLs = __ldg(&recip[Ls]);
         int32_t *mrow = b.M + pp.m_off + (int64_t)(r >> 5) * TT * kTileElems + (r & 31) * kTile;
 
-        const int D = b.pdoc[si.pair];
         if (D >= 0) {
             // document-id path (the element list holds the row's hits)
             if (!mask_clean) {
                 // the token-keyed path wrote these bytes with generic stores
                 uint4 *mz = reinterpret_cast<uint4 *>(S.d.mask);
-                for (int k = tid; k < (kDirect + 16) / 4; k += kSWS * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
+                for (int k = tid; k < (DIRECT + 16) / 4; k += kSWS * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
                 fence_proxy_async();
                 __syncthreads();
                 mask_clean = true;
             }
             // generic stores now cover the keyed staging buffers: fence before their next copy
             generic[0] = generic[1] = true;
-            ok = score_item_direct(b, S.d, &S.dbar, dparity, pp, D, tid, nrows, row_ok, el, n_elem,
-                                   n_i, Ks, KLs, Ls, mrow);
+            ok = score_item_direct<DIRECT>(b, S.d, &S.dbar, dparity, pp, D, tid, nrows, row_ok, el,
+                                           n_elem, n_i, Ks, KLs, Ls, mrow, si.c0, si.c1);
             continue;
         }
-        mask_clean = false;
-        if (nrows > 0)
-            ok = score_item_keyed(b, kw, kbar, parity, generic, gtab, pp, lane, row_ok, el, n_elem,
-                                  nU, n_i, Ks, KLs, Ls, mrow);
+        if constexpr (KEYED) {
+            mask_clean = false;
+            if (nrows > 0)
+                ok = score_item_keyed(b, kw, kbar, parity, generic, gtab, pp, lane, row_ok, el, n_elem,
+                                      nU, n_i, Ks, KLs, Ls, mrow, si.c0, si.c1);
+        }
     }
 }
 
@@ -2011,15 +2026,34 @@ int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
     return 1;
 }
 
+template <int DIRECT, bool KEYED>
+int launch_score_one(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    const size_t smem = sizeof(ScoreSmem<DIRECT, KEYED>);
+    static int per_sm = 0;   // resident CTAs per SM of this variant (queried once)
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_score<DIRECT, KEYED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<DIRECT, KEYED>, kSWS * 32, smem) !=
+                cudaSuccess || n < 1)
+            n = 1;
+        per_sm = std::min(n, kGScratchWarpsPerSm / kSWS);
+    }
+    const int grid = std::max(1, std::min(num_sms * per_sm, b.n_score_items));
+    k_score<DIRECT, KEYED><<<grid, kSWS * 32, smem, st>>>(b);
+    return 1;
+}
+
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
-    const size_t smem = sizeof(ScoreSmem);
-    cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int need = (b.n_score_items + kSWS - 1) / kSWS;
-    const int grid = std::max(1, std::min(num_sms * kScoreCtasPerSmScore, need));
-    k_score<<<grid, kSWS * 32, smem, st>>>(b);
-    return 1;
+    return launch_score_one<kDirectSmall, false>(b, num_sms, st);
+}
+
+int launch_score_wide(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    if (b.n_score_items <= 0) return 0;
+    return launch_score_one<kDirect, true>(b, num_sms, st);
 }
 
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)

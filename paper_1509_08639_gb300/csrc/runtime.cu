@@ -193,8 +193,10 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
     pl.dorder = order_by(bucketD);
     for (int p : order_by(bucketS)) {
         const PairPlan &pp = pl.pairs[p];
-        for (int r0 = 0; r0 < pp.S; r0 += 32) pl.pitems.push_back(ScoreItem{p, r0});
-        for (int r0 = 0; r0 < pp.S; r0 += 64) pl.sitems.push_back(ScoreItem{p, r0});
+        for (int r0 = 0; r0 < pp.S; r0 += 32) pl.pitems.push_back(ScoreItem{p, r0, 0, 0});
+        for (int r0 = 0; r0 < pp.S; r0 += 64)
+            for (int c0 = 0; c0 < std::max(pp.T, 1); c0 += kScoreColChunk)
+                pl.sitems.push_back(ScoreItem{p, r0, c0, std::min(pp.T, c0 + kScoreColChunk)});
     }
     // alignments: whole-CTA ones first, then one-warp ones, each longest first
     const std::vector<int> ord = order_by(bucketC);
@@ -549,6 +551,7 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_DOC, st, [&] { return launch_pairprep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_SCORE_WIDE, st, [&] { return launch_score_wide(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
     if (aligning) {
@@ -1322,7 +1325,7 @@ const char *mine_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
-                                           "k_pairprep"};
+                                           "k_pairprep", "k_score_wide"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
