@@ -736,12 +736,10 @@ __device__ __forceinline__ void emit_kept(const BatchDev &b, const DevDict &d, c
 // One source row of <= 64 tokens: tokens, distinct tokens (warp match, no
 // table), dictionary buckets, translations, then the kept translations.
 __device__ void prep_row_short(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm, int lg,
-                               int64_t s, int32_t a, int32_t L, int lane, uint32_t *seen,
-                               int32_t *cb, int kmax)
+                               int64_t s, int32_t a, int32_t L, int32_t t0, int32_t t1, int lane,
+                               uint32_t *seen, int32_t *cb, int kmax)
 {
-    int32_t t0 = 0, t1 = 0;
-    if (lane < L) t0 = b.tokens[a + lane];
-    if (32 + lane < L) t1 = b.tokens[a + 32 + lane];
+    // t0, t1: tokens a+lane and a+32+lane of the row (0 past its end)
     if (((uint32_t)t0 | (uint32_t)t1) > ELEM_TOKEN) {
         atomicCAS(b.err, 0, ERR_BAD_TOKEN);
         t0 &= (int32_t)ELEM_TOKEN;
@@ -911,16 +909,37 @@ k_pairprep(BatchDev b, DevDict d)
                 if (kk < tb) b.tdoc[kk] = (uint16_t)max(doc_id(sm, lg, tk[q] & (int32_t)ELEM_TOKEN), 0);
             }
         }
-        // 3. source rows, one warp each
-        for (int j = wib; j < pp.S; j += kPPWarps) {
-            const int64_t sj = (int64_t)pp.s0 + j;
+        // 3. source rows, one warp each (rows wib, wib + kPPWarps, ...).  The
+        //    loads of the next row's tokens and of the offsets of the row after
+        //    it are in flight while a row is prepared.
+        auto offsets = [&](int j) {   // lanes 0, 1: start and end of row j
             int32_t v = 0;
-            if (lane < 2) v = b.sent_off[sj + lane];
-            const int32_t a = __shfl_sync(kFull, v, 0), L = __shfl_sync(kFull, v, 1) - a;
+            if (j < pp.S && lane < 2) v = b.sent_off[(int64_t)pp.s0 + j + lane];
+            return v;
+        };
+        auto tokens_of = [&](int32_t a, int32_t L, int32_t &t0, int32_t &t1) {
+            t0 = (L <= 64 && lane < L) ? b.tokens[a + lane] : 0;
+            t1 = (L <= 64 && 32 + lane < L) ? b.tokens[a + 32 + lane] : 0;
+        };
+        int32_t v = offsets(wib);
+        int32_t a = __shfl_sync(kFull, v, 0), L = __shfl_sync(kFull, v, 1) - a;
+        int32_t t0, t1;
+        tokens_of(a, L, t0, t1);
+        v = offsets(wib + kPPWarps);
+        for (int j = wib; j < pp.S; j += kPPWarps) {
+            const int32_t an = __shfl_sync(kFull, v, 0), Ln = __shfl_sync(kFull, v, 1) - an;
+            int32_t n0, n1;
+            tokens_of(an, Ln, n0, n1);               // row j + kPPWarps
+            v = offsets(j + 2 * kPPWarps);          // row j + 2 kPPWarps
+            const int64_t sj = (int64_t)pp.s0 + j;
             if (L > 64)
                 prep_row_long(b, d, sm, lg, sj, a, L, lane, gset, gset_clean, ++stamp, sm.seen[wib]);
             else
-                prep_row_short(b, d, sm, lg, sj, a, L, lane, sm.seen[wib], sm.cbuf[wib], kmax);
+                prep_row_short(b, d, sm, lg, sj, a, L, t0, t1, lane, sm.seen[wib], sm.cbuf[wib], kmax);
+            a = an;
+            L = Ln;
+            t0 = n0;
+            t1 = n1;
         }
     }
 }
