@@ -6,31 +6,37 @@
 // (monotone paths: "cannot go upward or leftward"), the traceback, and the
 // selection of aligned pairs whose score passes the threshold.
 //
-// Kernels:
-//   k_dict_build  one thread per dictionary key -> open-addressed HBM table
+// Kernels, in launch order:
+//   k_dict_build  once per dictionary: bucketed table (8 slots per 64-byte
+//                 bucket) of key -> (offset, count) of its translations
 //   k_validate    sentence offsets are sane (later kernels trust them)
-//   k_score       persistent; one warp per 32 source rows of a pair.
-//                 Row preparation: all tokens of the 32 rows are loaded at
-//                 once, deduplicated per row in a shared-memory hash, looked
-//                 up in the dictionary in parallel, and their translations
-//                 written grouped per token with FIRST (first copy of a
-//                 translation in U_i) and END (last translation of a token)
-//                 flags.  Scoring: for each block of up to 32 target
-//                 sentences (tokens staged by a TMA bulk copy, prefetched one
-//                 block ahead) a shared-memory hash maps token -> 32-bit
-//                 column mask; each lane (one source row) probes its elements
-//                 and accumulates the overlap counts of all 32 columns at once
-//                 in bit-sliced carry-save counters, then scores its 32 cells
-//                 into 32 x 32 tiles of M.
-//   k_align       persistent; large pairs are aligned by a whole CTA (8 warps
-//                 pipelined over stripes of 32 rows, the boundary row passed
-//                 through a shared-memory ring with bounded flag waits), small
-//                 pairs by one warp each.  Inside a stripe: anti-diagonal
-//                 wavefront, lane = row, the cell above passed by
-//                 __shfl_up_sync, score tiles staged by TMA bulk copies three
-//                 tiles deep, 2-bit directions packed 16 per word, then a
-//                 warp-cooperative traceback and the threshold selection of
-//                 every setting that shares the gap.
+//   k_pairprep    one CTA per pair, largest first: the target article's
+//                 distinct tokens get dense ids (ranks of occupied slots of a
+//                 shared table); every target token's id; one warp per source
+//                 row: distinct tokens, dictionary lookups, and the
+//                 translations the target article holds written as (id |
+//                 FIRST | END) -- the only ones that can overlap
+//   k_prep        the same for articles with more than 8192 distinct target
+//                 tokens, keeping every translation (token-keyed path)
+//   k_order       per pair, source rows by list length
+//   k_score       two launches (articles with at most 4096 / more distinct
+//                 target tokens): per item of 64 source rows and one range of
+//                 target columns, block by block of 32 target sentences, a
+//                 column mask per id (direct-indexed shared array, block ids
+//                 TMA-staged), every lane adds the masks of its row's kept
+//                 ids into bit-sliced carry-save counters, 8 x 8 bit
+//                 transposes give the counts, exact reciprocal multiplies the
+//                 ratios; 32 x 32 tiles of M.  Articles beyond 8192 ids use a
+//                 per-block hashed token -> column mask table instead.
+//   k_align       persistent; per size bin (autotuned) a pair is aligned by
+//                 one warp or by a whole CTA (8 warps pipelined over stripes
+//                 of 32 rows, the boundary row through a shared-memory ring
+//                 with bounded flag waits).  Inside a stripe: anti-diagonal
+//                 wavefront, lane = row, the cell above by __shfl_up_sync,
+//                 score tiles by TMA bulk copies three deep, 2-bit directions
+//                 packed 16 per word.
+//   k_trace       one warp per alignment: traceback over the packed codes and
+//                 the threshold selection of every setting that shares the gap
 #include "internal.h"
 
 #include <algorithm>
@@ -221,19 +227,6 @@ __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__
 // Open addressing, linear probing; callers keep the load factor <= 1/2, so
 // every probe sequence meets an empty slot.
 
-__device__ __forceinline__ int tab_slot_from(int2 *tab, uint32_t mask, uint32_t h, int32_t key)
-{
-    for (;;) {
-        int32_t k = tab[h].x;
-        if (k == -1) {
-            k = atomicCAS(&tab[h].x, -1, key);
-            if (k == -1) return (int)h;
-        }
-        if (k == key) return (int)h;
-        h = (h + 1) & mask;
-    }
-}
-
 // Table entries are (key, 32-bit mask) pairs, so one 64-bit shared load
 // answers a probe.  Keys are written once (CAS from -1) and never change.
 __device__ __forceinline__ int tab_slot(int2 *tab, int log2, int32_t key)
@@ -247,47 +240,6 @@ __device__ __forceinline__ int tab_slot(int2 *tab, int log2, int32_t key)
             if (k == -1) return (int)h;
         }
         if (k == key) return (int)h;
-        h = (h + 1) & mask;
-    }
-}
-
-// Slots of up to four keys with their first probes and CASes in flight together.
-__device__ __forceinline__ void tab_slot4(int2 *tab, int log2, const int32_t (&key)[4],
-                                          const bool (&ok)[4], int (&slot)[4])
-{
-    const uint32_t mask = (1u << log2) - 1u;
-    uint32_t h[4];
-    int32_t k[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        h[q] = hmul(key[q]) >> (32 - log2);
-        k[q] = ok[q] ? tab[h[q]].x : key[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (ok[q] && k[q] == -1) {
-            const int32_t o = atomicCAS(&tab[h[q]].x, -1, key[q]);
-            k[q] = (o == -1) ? key[q] : o;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (ok[q] && k[q] != key[q]) {
-            h[q] = (h[q] + 1) & mask;
-            h[q] = (uint32_t)tab_slot_from(tab, mask, h[q], key[q]);
-        }
-        slot[q] = (int)h[q];
-    }
-}
-
-__device__ __forceinline__ uint32_t probe_occ(const int2 *tab, int log2, int32_t key)
-{
-    const uint32_t mask = (1u << log2) - 1u;
-    uint32_t h = hmul(key) >> (32 - log2);
-    for (;;) {
-        const int2 e = tab[h];
-        if (e.x == key) return (uint32_t)e.y;
-        if (e.x == -1) return 0u;
         h = (h + 1) & mask;
     }
 }
