@@ -223,10 +223,32 @@ def cpu_baseline(w, budget_s=20.0):
         done_pairs += len(idx)
         done_cells += int((S[idx] * T[idx]).sum())
         k += chunk
+    # the same oracle on one core, on a shorter sample
+    one_pairs, one_t, k1 = 0, 0.0, 0
+    one_order = rng.permutation(w.batch.n_pairs)
+    while one_t < budget_s / 4 and k1 < len(one_order):
+        idx = one_order[k1:k1 + 8]
+        t0 = time.perf_counter()
+        O.mine_batch(od, w.batch.subset(idx), w.settings, 1)
+        one_t += time.perf_counter() - t0
+        one_pairs += len(idx)
+        k1 += 8
+    cpu_model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    cpu_model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
     return {"value": done_pairs / t_used, "unit": UNIT, "cores": int(used), "kind": "oracle",
             "sample": f"{done_pairs} random pairs of the same workload ({done_cells} cells), "
                       f"{t_used:.1f} s, OpenMP over pairs",
-            "gcups": done_cells * len({g for g, _ in w.settings}) / t_used / 1e9}
+            "gcups": done_cells * len({g for g, _ in w.settings}) / t_used / 1e9,
+            "single_thread": {"value": one_pairs / one_t, "unit": UNIT, "cores": 1,
+                              "sample": f"{one_pairs} random pairs, {one_t:.1f} s"},
+            "cpu": cpu_model, "nproc": os.cpu_count()}
 
 
 # --------------------------------------------------------------------- reference arm
