@@ -293,13 +293,16 @@ int mine_autotune(mine_ctx *ctx);
 
 /* The same tuning on a batch of the caller's workload (host buffers as for
  * mine_run_batch): its score matrices are computed once, then for every size
- * bin present in it (largest pairs excepted, see above) the other strategy
- * is tried on the whole batch's alignment, and kept when that is more than 3%
- * faster.  Synchronous; uses the context's scratch. */
+ * bin present in it each other form its pairs allow (one warp, one CTA,
+ * tiles) is tried on the whole batch's alignment, and the fastest is kept
+ * when more than 3% faster.  Synchronous; uses the context's scratch. */
 int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch);
 
-/* Read (get != 0) or set the strategy table: tab[b] = 1 whole CTA, 0 one warp
- * (where allowed), -1 built-in rule; n entries, n <= MINE_ALIGN_BINS. */
+/* Read (get != 0) or set the strategy table: tab[b] = 2 tiles of 256 x 512
+ * cells over many CTAs (pairs with S > 256 and T > 512; others of the bin
+ * take a whole CTA), 1 whole CTA, 0 one warp (where allowed), -1 built-in
+ * rule (tiles from 2^21 cells, a whole CTA from 2^15); n entries,
+ * n <= MINE_ALIGN_BINS. */
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get);
 
 #ifdef __cplusplus

@@ -83,7 +83,24 @@ struct NwItem {         // one alignment: (pair, gap)
     int32_t gap;        // global gap index
     int64_t code_off;   // uint32 offset of the direction codes (S rows x ceil(T/16) words)
     int64_t match_off;  // uint32 offset of the match list (min(S,T) entries)
+    int64_t tb_off;     // tiled alignments: int32 offset of the tile boundaries and flags
 };
+
+// A tiled alignment is cut into tiles of kAlignTileRows x kAlignTileCols
+// cells computed by different CTAs: tile (R, C) starts once (R-1, C) and
+// (R, C-1) are done.  Between tiles: the last row of every tile row, the
+// last column of every tile column (global memory), a done flag per tile.
+constexpr int kAlignTileRows = 256;        // 8 stripes of 32 rows: one CTA of 8 warps
+constexpr int kAlignTileCols = 512;        // = the shared ring of one stripe
+constexpr int64_t kTiledCells = int64_t(1) << 21;
+struct TileItem {
+    int32_t nw;         // alignment item
+    int16_t R, C;       // tile row and column
+};
+// boundary area of an S x T tiled alignment: rows (NR-1) x (T+1), columns
+// (NC-1) x (S+1), flags NR x NC (int32 each)
+__host__ __device__ inline int64_t tile_rows_of(int32_t S) { return (S + kAlignTileRows - 1) / kAlignTileRows; }
+__host__ __device__ inline int64_t tile_cols_of(int32_t T) { return (T + kAlignTileCols - 1) / kAlignTileCols; }
 
 struct ScoreItem {      // 32 (preparation) or 64 (scoring) source rows of one pair
     int32_t pair;
@@ -110,6 +127,11 @@ struct BatchDev {
     const NwItem *nw_items;
     int32_t n_nw_items;
     int32_t n_nw_big;            // items [0, n_nw_big) are aligned by a whole CTA
+    int32_t n_nw_tiled;          // the last n_nw_tiled items are aligned tile by tile
+    const TileItem *tiles;       // tiles of the tiled items, in order of R + C
+    int32_t n_tiles;
+    int32_t *tbnd;               // tile boundaries and flags (zeroed per batch)
+    int64_t n_tbnd;              // their int32 count
     const int32_t *set_gap;      // [R] global gap index of each setting row
     const int32_t *set_thr;      // [R]
     const int32_t *gap_val;      // [G]
@@ -143,17 +165,22 @@ constexpr int kRing = 512;
 constexpr int64_t kBigCells = 1 << 15;
 constexpr int kAlignBins = MINE_ALIGN_BINS;
 
-// Whole-CTA alignment for an S x T pair: forced when one warp cannot hold the
-// boundary row, else the tuned choice of its size bin (tab may be null; -1
-// entries keep the built-in rule).
-inline bool align_whole_cta(const int8_t *tab, int32_t S, int32_t T)
+// Alignment form of an S x T pair: 0 one warp, 1 one CTA, 2 tiles over many
+// CTAs.  The tuned choice of its size bin (tab may be null; -1 keeps the
+// built-in rule: tiles from kTiledCells, a CTA from kBigCells), except that
+// tiles need more than one tile row and column, and one warp cannot hold a
+// boundary row of kRing or more cells below a first stripe.
+inline int align_kind(const int8_t *tab, int32_t S, int32_t T)
 {
-    if (S > kTile && T >= kRing) return true;
     const int64_t c = (int64_t)S * T;
+    const bool can_tile = S > kAlignTileRows && T > kAlignTileCols;
     int bin = 0;
     while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
-    if (tab && bin < kAlignBins && tab[bin] >= 0) return tab[bin] != 0;
-    return c >= kBigCells;
+    int v = (tab && bin < kAlignBins) ? tab[bin] : -1;
+    if (v < 0) v = (can_tile && c >= kTiledCells) ? 2 : (c >= kBigCells ? 1 : 0);
+    if (v == 2 && !can_tile) v = 1;
+    if (v == 0 && S > kTile && T >= kRing) v = 1;
+    return v;
 }
 
 // launchers (kernels.cu); each returns the number of kernels launched
@@ -167,6 +194,7 @@ int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);        // small articles
 int launch_score_wide(const BatchDev &b, int num_sms, cudaStream_t st);   // all other items
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
+int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 int launch_fill_scores(int32_t *M, int64_t n, uint32_t seed, cudaStream_t st);
@@ -177,6 +205,6 @@ void set_last_error(const char *msg);
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
-                KID_SCORE_WIDE = 9, KID_COUNT = 10 };
+                KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_COUNT = 11 };
 
 }  // namespace mine

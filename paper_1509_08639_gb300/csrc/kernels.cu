@@ -1640,15 +1640,19 @@ struct WarpPipe {
 // column cidx = 32c + u - L; its score comes from tile c-1 (u < L) or tile c
 // (base_prev / base_cur already point at column u = 0 of the lane's row).
 // Direction codes are shifted into `word` (two bits per cell, the oldest in
-// the low bits) and stored when a 16-column word is complete.  GUARD = false
-// for chunks in which every lane is inside the matrix.
-template <bool GUARD>
-__device__ __forceinline__ void stripe_chunk(int c, int lane, int T, bool row_ok, int32_t g,
+// the low bits) and stored when a 16-column word is complete.  Columns
+// [clo, chi) are filled.  GUARD = false for chunks in which every lane is
+// inside them.  TILE: the cell values of the bottom row go to gbot (lane 31
+// of a tile's last stripe; null otherwise) and those of column chi-1 to
+// *gright (null when no tile follows on the right).
+template <bool GUARD, bool TILE = false>
+__device__ __forceinline__ void stripe_chunk(int c, int lane, int clo, int chi, bool row_ok, int32_t g,
                                              int32_t up_val, const int32_t *base_prev,
                                              const int32_t *base_cur, uint32_t flush,
                                              uint32_t *cr, int32_t *ring, int32_t qm,
                                              bool publish, int32_t &h_left, int32_t &up_prev,
-                                             int32_t &h_out, uint32_t &word)
+                                             int32_t &h_out, uint32_t &word,
+                                             int32_t *gbot = nullptr, int32_t *gright = nullptr)
 {
 #pragma unroll 8
     for (int u = 0; u < 32; ++u) {
@@ -1656,7 +1660,7 @@ __device__ __forceinline__ void stripe_chunk(int c, int lane, int T, bool row_ok
         const int32_t from_above = __shfl_sync(kFull, up_val, u);
         up_in = (lane == 0) ? from_above : up_in;
         const int cidx = 32 * c + u - lane;
-        const bool valid = !GUARD || (row_ok && cidx >= 0 && cidx < T);
+        const bool valid = !GUARD || (row_ok && cidx >= clo && cidx < chi);
         if (valid) {
             const int32_t sv = (u < lane ? base_prev : base_cur)[u];
             const int32_t cd = up_prev + sv;
@@ -1668,6 +1672,10 @@ __device__ __forceinline__ void stripe_chunk(int c, int lane, int T, bool row_ok
             word = __funnelshift_r(word, code, 2);
             if ((flush >> u) & 1u) cr[cidx >> 4] = word;
             if (publish) ring[(qm + cidx) & (kRing - 1)] = best;
+            if constexpr (TILE) {
+                if (gbot) gbot[cidx + 1] = best;
+                if (gright && cidx == chi - 1) *gright = best;
+            }
             h_left = best;
             h_out = best;
             up_prev = up_in;
@@ -1760,10 +1768,10 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
             const int32_t *base_cur = sm.tile[wib][b_cur] + lane * kTile - lane;
             const bool publish = has_below && lane == 31;
             if (full_stripe && c >= 1 && 32 * (c + 1) <= T)
-                stripe_chunk<false>(c, lane, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
+                stripe_chunk<false>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
                                     wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word);
             else
-                stripe_chunk<true>(c, lane, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
+                stripe_chunk<true>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
                                    wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word);
             __syncwarp();
             if (publish) {
@@ -1904,7 +1912,7 @@ k_align(BatchDev b)
         int item = 0;
         if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[3], 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= b.n_nw_items) break;
+        if (item >= b.n_nw_items - b.n_nw_tiled) break;
         const NwItem it = b.nw_items[item];
         const PairPlan pp = b.pairs[it.pair];
         if (pp.S == 0 || pp.T == 0) continue;   // nothing to fill; k_trace reports it
@@ -1920,6 +1928,185 @@ k_align(BatchDev b)
         wp.prod_mine = wp.prod_pred = &sm.prod[wib];
         wp.cons_mine = wp.cons_succ = &sm.cons[wib];
         if (!align_stripes(b, sm, wib, wp, item, it, pp, lane, uses)) return;
+    }
+}
+
+// Bounded wait until *flag != 0 (a flag another CTA sets); false when the
+// wait ran out (error word set).
+__device__ __forceinline__ bool flag_wait_set(const int32_t *flag, int32_t *err)
+{
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        if (*(volatile const int32_t *)flag != 0) return true;
+        __nanosleep(64);
+    }
+    atomicCAS(err, 0, ERR_TIMEOUT);
+    return false;
+}
+
+// One tile (R, C) of a tiled alignment by the whole CTA: warp w fills stripe
+// 8R + w over the columns [512C, min(512C + 512, T)), the first stripe takes
+// its row above from the tile row above (global), every stripe its column
+// on the left from the tile on the left (global) and the stripes pass rows
+// to each other through the shared rings as in a whole-CTA alignment.  The
+// tile's last row and column go to global memory for the tiles below and to
+// the right.  Returns false (on every thread) when a bounded wait ran out.
+__device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, const TileItem &ti,
+                           uint32_t (&uses)[kMBuf])
+{
+    const NwItem it = b.nw_items[ti.nw];
+    const PairPlan pp = b.pairs[it.pair];
+    const int S = pp.S, T = pp.T;
+    const int R = ti.R, C = ti.C;
+    const int NR = (int)tile_rows_of(S), NC = (int)tile_cols_of(T);
+    int32_t *hb = b.tbnd + it.tb_off;                              // rows: (NR-1) x (T+1)
+    int32_t *vb = hb + (int64_t)(NR - 1) * (T + 1);                 // columns: (NC-1) x (S+1)
+    int32_t *fl = vb + (int64_t)(NC - 1) * (S + 1);                 // flags: NR x NC
+    // wait for the tiles above and on the left
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        if (R > 0) ok = flag_wait_set(&fl[(R - 1) * NC + C], b.err);
+        if (ok && C > 0) ok = flag_wait_set(&fl[R * NC + C - 1], b.err);
+        __threadfence();
+    }
+    if (threadIdx.x < kAW) {
+        sm.prod[threadIdx.x] = 0;
+        sm.cons[threadIdx.x] = 0;
+    }
+    if (!__syncthreads_and(ok)) return false;
+
+    const int32_t g = b.gap_val[it.gap];
+    const int TT = (T + 31) >> 5;
+    const int TS = (S + 31) >> 5;
+    const int CW = (T + 15) >> 4;
+    const int clo = kAlignTileCols * C, chi = min(T, clo + kAlignTileCols);
+    const int cb = clo >> 5, ce = (chi + 31) >> 5;           // score tiles of the columns
+    const int s = (kAlignTileRows / 32) * R + wib;            // this warp's stripe
+    if (s < TS) {
+        uint32_t *codes = b.codes + it.code_off;
+        const int32_t *Mp = b.M + pp.m_off;
+        const uint32_t f0 = (uint32_t)((lane + 15) & 15);
+        const uint32_t flush = (1u << f0) | (1u << (f0 + 16));
+        const int i0 = 32 * s;
+        const int row = i0 + lane + 1;
+        const bool row_ok = row <= S;
+        const bool full_stripe = i0 + 32 <= S;
+        const bool has_above = wib > 0;                        // in this CTA
+        const bool has_below = wib + 1 < kAW && s + 1 < TS;    // in this CTA
+        const int32_t qbase = -clo;                            // ring positions relative to clo
+        const int pred = wib - 1, succ = wib + 1;
+        uint32_t *cr = codes + (int64_t)(row - 1) * CW;
+        int32_t *gbot = (wib + 1 == kAW && s + 1 < TS && lane == 31) ? hb + (int64_t)R * (T + 1) : nullptr;
+        int32_t *gright = (C + 1 < NC && row_ok) ? vb + (int64_t)C * (S + 1) + row : nullptr;
+        __syncwarp();
+        if (lane == 0) {
+            for (int k = 0; k < kMBuf && cb + k < ce; ++k) {
+                mbar_expect_tx(&sm.bar[wib][k], kTileElems * 4);
+                bulk_g2s(sm.tile[wib][k], Mp + ((int64_t)s * TT + cb + k) * kTileElems, kTileElems * 4,
+                         &sm.bar[wib][k]);
+            }
+        }
+        for (int k = 0; k < kMBuf && cb + k < ce; ++k) uses[k]++;
+        // the column on the left: H[row][clo] and H[row-1][clo]
+        const int32_t *vl = C > 0 ? vb + (int64_t)(C - 1) * (S + 1) : nullptr;
+        int32_t h_left = vl ? (row_ok ? vl[row] : 0) : row * g;
+        int32_t up_prev = vl ? (row - 1 == 0 ? clo * g : (row_ok ? vl[row - 1] : 0)) : (row - 1) * g;
+        int32_t h_out = 0;
+        uint32_t word = 0;
+        const int nchunks = ((chi + 31 + 31) >> 5) - cb;
+        const int32_t *hrow = (R > 0 && wib == 0) ? hb + (int64_t)(R - 1) * (T + 1) : nullptr;
+        int b_cur = 0;
+        for (int cc = 0; cc < nchunks; ++cc) {
+            const int c = cb + cc;
+            if (c < ce) {
+                if (!mbar_wait(&sm.bar[wib][b_cur], (uses[b_cur] - 1) & 1u, b.err)) { ok = false; break; }
+            }
+            const int b_prev = b_cur == 0 ? kMBuf - 1 : b_cur - 1;
+            if (cc >= 2 && c + 1 < ce) {
+                const int bb = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
+                    bulk_g2s(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems, kTileElems * 4,
+                             &sm.bar[wib][bb]);
+                }
+                uses[bb]++;
+            }
+            // the row above for columns 32c+1 .. 32c+32 (lane k holds column 32c+1+k)
+            const int jcol = 32 * c + 1 + lane;
+            int32_t up_val;
+            if (has_above) {
+                const int32_t need = qbase + min(32 * c + 32, chi);
+                if (!flag_wait_ge(&sm.prod[pred], need, b.err)) { ok = false; break; }
+                up_val = (jcol > clo && jcol <= chi) ? sm.ring[pred][(qbase + jcol - 1) & (kRing - 1)] : 0;
+                __syncwarp();
+                if (lane == 0) *(volatile int32_t *)&sm.cons[wib] = need;
+            } else if (hrow) {
+                up_val = (jcol > clo && jcol <= chi) ? hrow[jcol] : 0;
+            } else {
+                up_val = jcol * g;
+            }
+            if (has_below) {
+                const int jmax = min(32 * c + 1, chi);
+                if (jmax > clo && !flag_wait_ge(&sm.cons[succ], qbase + jmax - kRing, b.err)) { ok = false; break; }
+            }
+            const int32_t *base_prev = sm.tile[wib][b_prev] + lane * kTile + 32 - lane;
+            const int32_t *base_cur = sm.tile[wib][b_cur] + lane * kTile - lane;
+            const bool publish = has_below && lane == 31;
+            if (full_stripe && cc >= 1 && 32 * (c + 1) <= chi)
+                stripe_chunk<false, true>(c, lane, clo, chi, row_ok, g, up_val, base_prev, base_cur, flush, cr,
+                                          sm.ring[wib], qbase, publish, h_left, up_prev, h_out, word, gbot,
+                                          gright);
+            else
+                stripe_chunk<true, true>(c, lane, clo, chi, row_ok, g, up_val, base_prev, base_cur, flush, cr,
+                                         sm.ring[wib], qbase, publish, h_left, up_prev, h_out, word, gbot,
+                                         gright);
+            __syncwarp();
+            if (publish) {
+                const int jdone = min(32 * c + 1, chi);
+                if (jdone > clo) {
+                    __threadfence_block();
+                    *(volatile int32_t *)&sm.prod[wib] = qbase + jdone;
+                }
+            }
+            b_cur = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
+        }
+        if (ok) {
+            const int tail = T & 15;
+            if (row_ok && chi == T && tail) cr[(T - 1) >> 4] = word >> (2 * (16 - tail));
+            if (s == TS - 1 && row == S && chi == T) b.hfin[ti.nw] = h_left;
+        }
+        __syncwarp();
+    }
+    // publish: rows and columns written above, then the flag
+    if (!__syncthreads_and(ok)) return false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *(volatile int32_t *)&fl[R * NC + C] = 1;
+    }
+    return true;
+}
+
+// Tiled alignments: persistent CTAs take tiles in order of their
+// anti-diagonal (a tile's predecessors were taken by running CTAs before it).
+__global__ void __launch_bounds__(kAW * 32)
+k_align_tiled(BatchDev b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AlignSmem &sm = *reinterpret_cast<AlignSmem *>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int k = 0; k < kMBuf; ++k) mbar_init(&sm.bar[wib][k], 1);
+        fence_barrier_init();
+    }
+    uint32_t uses[kMBuf] = {0u, 0u, 0u};
+    for (;;) {
+        if (__syncthreads_or(*(volatile int32_t *)b.err != 0)) break;
+        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[7], 1);
+        __syncthreads();
+        const int t = sm.item;
+        if (t >= b.n_tiles) break;
+        if (!align_tile(b, sm, wib, lane, b.tiles[t], uses)) break;
     }
 }
 
@@ -2036,6 +2223,16 @@ int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)
     const int need = std::max(b.n_nw_big, (small + kAW - 1) / kAW);
     const int grid = std::max(1, std::min(num_sms * 2, need));
     k_align<<<grid, kAW * 32, smem, st>>>(b);
+    return 1;
+}
+
+int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    if (b.n_tiles <= 0) return 0;
+    const size_t smem = sizeof(AlignSmem);
+    cudaFuncSetAttribute(k_align_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::max(1, std::min(num_sms * 2, b.n_tiles));
+    k_align_tiled<<<grid, kAW * 32, smem, st>>>(b);
     return 1;
 }
 

@@ -105,6 +105,9 @@ struct Plan {
     std::vector<ScoreItem> sitems;  // 64-row items of the score kernel
     std::vector<int32_t> dorder;    // pairs by sentence count, longest first
     std::vector<NwItem> nitems;
+    std::vector<TileItem> tiles;    // of the tiled alignments (the last n_tiled items)
+    int32_t n_tiled = 0;
+    int64_t tb_words = 0;
     std::vector<int32_t> set_gap, set_thr, gap_val;
     int64_t m_elems = 0, code_words = 0, match_words = 0, sel_cap = 0;
     int32_t R = 0;
@@ -198,13 +201,16 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
             for (int c0 = 0; c0 < std::max(pp.T, 1); c0 += kScoreColChunk)
                 pl.sitems.push_back(ScoreItem{p, r0, c0, std::min(pp.T, c0 + kScoreColChunk)});
     }
-    // alignments: whole-CTA ones first, then one-warp ones, each longest first
+    // alignments: whole-CTA ones first, then one-warp ones, each longest
+    // first, then the tiled ones
     const std::vector<int> ord = order_by(bucketC);
-    for (int pass = 0; pass < 2; ++pass) {
+    const int kind_of_pass[3] = {1, 0, 2};
+    std::vector<TileItem> tl;
+    std::vector<int32_t> tdiag;
+    for (int pass = 0; pass < 3; ++pass) {
         for (int p : ord) {
             const PairPlan &pp = pl.pairs[p];
-            const bool big = align_whole_cta(align_tab, pp.S, pp.T);
-            if (big != (pass == 0)) continue;
+            if (align_kind(align_tab, pp.S, pp.T) != kind_of_pass[pass]) continue;
             const int64_t CW = (pp.T + 15) >> 4;
             for (int g = 0; g < pp.ngap; ++g) {
                 NwItem it;
@@ -214,11 +220,30 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
                 pl.code_words += (int64_t)pp.S * CW;
                 it.match_off = pl.match_words;
                 pl.match_words += std::min(pp.S, pp.T);
+                it.tb_off = -1;
+                if (pass == 2) {
+                    const int64_t NR = tile_rows_of(pp.S), NC = tile_cols_of(pp.T);
+                    it.tb_off = pl.tb_words;
+                    pl.tb_words += align_up((NR - 1) * (pp.T + 1) + (NC - 1) * (pp.S + 1) + NR * NC, 4);
+                    for (int R = 0; R < NR; ++R)
+                        for (int C = 0; C < NC; ++C) {
+                            tl.push_back(TileItem{(int32_t)pl.nitems.size(), (int16_t)R, (int16_t)C});
+                            tdiag.push_back(R + C);
+                        }
+                }
                 pl.nitems.push_back(it);
             }
         }
         if (pass == 0) pl.n_big = (int32_t)pl.nitems.size();
+        if (pass == 1) pl.n_tiled = -(int32_t)pl.nitems.size();
     }
+    pl.n_tiled += (int32_t)pl.nitems.size();
+    // tiles in order of their anti-diagonal: a tile's predecessors come first
+    std::vector<int32_t> idx(tl.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int32_t)k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return tdiag[x] < tdiag[y]; });
+    pl.tiles.resize(tl.size());
+    for (size_t k = 0; k < idx.size(); ++k) pl.tiles[k] = tl[idx[k]];
     return 0;
 }
 
@@ -232,7 +257,7 @@ struct Layout {
     int64_t total = 0;
     // offsets inside the plan blob
     int64_t o_pairs = 0, o_sitems = 0, o_nitems = 0, o_setgap = 0, o_setthr = 0, o_gapval = 0;
-    int64_t o_dorder = 0, o_pitems = 0;
+    int64_t o_dorder = 0, o_pitems = 0, o_tiles = 0, tbnd = 0;
 };
 
 Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel, bool scoring)
@@ -258,6 +283,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     L.o_gapval = sub(4 * pl.gap_val.size());
     L.o_dorder = sub(4 * pl.dorder.size());
     L.o_pitems = sub(sizeof(ScoreItem) * pl.pitems.size());
+    L.o_tiles = sub(sizeof(TileItem) * pl.tiles.size());
     L.plan_bytes = q;
     L.plan = take(q);
     if (copy_inputs) {
@@ -280,6 +306,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     L.codes = take(4 * pl.code_words + 16);
     L.matches = take(4 * pl.match_words + 16);
     L.hfin = take(4 * (int64_t)pl.nitems.size() + 16);
+    L.tbnd = take(4 * pl.tb_words + 16);
     L.counters = take(4 * 16);
     L.nw = take(4 * (int64_t)pl.R);
     L.nsel = take(4 * (int64_t)pl.R);
@@ -298,6 +325,7 @@ void pack_plan(const Plan &pl, const Layout &L, char *dst)
     std::memcpy(dst + L.o_gapval, pl.gap_val.data(), 4 * pl.gap_val.size());
     std::memcpy(dst + L.o_dorder, pl.dorder.data(), 4 * pl.dorder.size());
     std::memcpy(dst + L.o_pitems, pl.pitems.data(), sizeof(ScoreItem) * pl.pitems.size());
+    std::memcpy(dst + L.o_tiles, pl.tiles.data(), sizeof(TileItem) * pl.tiles.size());
 }
 
 BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_t *sent_off,
@@ -319,6 +347,11 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.nw_items = reinterpret_cast<const NwItem *>(plan + L.o_nitems);
     b.n_nw_items = (int32_t)pl.nitems.size();
     b.n_nw_big = pl.n_big;
+    b.n_nw_tiled = pl.n_tiled;
+    b.tiles = reinterpret_cast<const TileItem *>(plan + L.o_tiles);
+    b.n_tiles = (int32_t)pl.tiles.size();
+    b.tbnd = reinterpret_cast<int32_t *>(base + L.tbnd);
+    b.n_tbnd = pl.tb_words;
     b.set_gap = reinterpret_cast<const int32_t *>(plan + L.o_setgap);
     b.set_thr = reinterpret_cast<const int32_t *>(plan + L.o_setthr);
     b.gap_val = reinterpret_cast<const int32_t *>(plan + L.o_gapval);
@@ -555,7 +588,9 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
     }
     if (aligning) {
+        if (b.n_tiles > 0) CK(cudaMemsetAsync(b.tbnd, 0, 4 * b.n_tbnd, st));
         n += timed_launch(ctx, KID_ALIGN, st, [&] { return launch_align(b, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_ALIGN_TILED, st, [&] { return launch_align_tiled(b, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_TRACE, st, [&] { return launch_trace(b, ctx->num_sms, st); });
     }
     CK(cudaGetLastError());
@@ -682,7 +717,13 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
     std::copy(ctx->align_tab, ctx->align_tab + kAlignBins, tab);
     Plan pl;
     if ((rc = plan_with(pl, tab))) return rc;
-    const Layout L = make_layout(pl, dict->d.kmax, true, true, true);
+    // the scratch layout of the plan with every pair that can be tiled tiled:
+    // the largest tile area and tile list of all the plans tried below
+    int8_t all_tiles[kAlignBins];
+    std::fill(all_tiles, all_tiles + kAlignBins, (int8_t)2);
+    Plan pmax;
+    if ((rc = plan_with(pmax, all_tiles))) return rc;
+    const Layout L = make_layout(pmax, dict->d.kmax, true, true, true);
     if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
     if ((rc = ensure_host(ctx->pin, L.plan_bytes + 64))) return rc;
     char *hp = static_cast<char *>(ctx->pin.p);
@@ -716,8 +757,10 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         BatchDev bq = make_batchdev(q, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
         for (int rep = 0; rep < 3; ++rep) {
             CK(cudaMemsetAsync(bq.counters, 0, 4 * 8, st));   // queue heads; keeps the error word
+            if (bq.n_tiles > 0) CK(cudaMemsetAsync(bq.tbnd, 0, 4 * bq.n_tbnd, st));
             if (rep == 1) CK(cudaEventRecord(e0, st));
             ctx->launches += launch_align(bq, ctx->num_sms, st);
+            ctx->launches += launch_align_tiled(bq, ctx->num_sms, st);
         }
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
@@ -729,33 +772,42 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         ms /= 2.0f;
         return 0;
     };
-    // bins present in the batch whose pairs may take either strategy
-    bool present[kAlignBins] = {false};
+    // the forms open to some pair of each bin present in the batch
+    bool can[kAlignBins][3] = {};
     for (const PairPlan &pp : pl.pairs) {
-        if (pp.S > kTile && pp.T >= kRing) continue;
         const int64_t c = (int64_t)pp.S * pp.T;
         int bin = 0;
         while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
-        if (bin < kAlignBins) present[bin] = true;
+        if (bin >= kAlignBins) continue;
+        can[bin][1] = true;
+        if (!(pp.S > kTile && pp.T >= kRing)) can[bin][0] = true;
+        if (pp.S > kAlignTileRows && pp.T > kAlignTileCols) can[bin][2] = true;
     }
     float best = 0.f;
     rc = time_with(tab, best);
     for (int bin = 0; bin < kAlignBins && rc == 0; ++bin) {
-        if (!present[bin]) continue;
-        int8_t trial[kAlignBins];
-        std::copy(tab, tab + kAlignBins, trial);
-        // the strategy the bin has now, then the other one
-        const int64_t c_mid = bin > 0 ? (int64_t(1) << (bin - 1)) : 0;
-        const bool now = tab[bin] >= 0 ? tab[bin] != 0 : c_mid >= kBigCells;
-        trial[bin] = now ? 0 : 1;
-        float t = 0.f;
-        if ((rc = time_with(trial, t))) break;
-        if (t < 0.97f * best) {
-            best = t;
-            tab[bin] = trial[bin];
-        } else {
-            tab[bin] = now ? 1 : 0;
+        if (!can[bin][1]) continue;
+        // the form the bin has now (the built-in rule decides for a pair of
+        // the bin's middle size when the entry is -1), then each other one
+        int now = tab[bin];
+        if (now < 0) {
+            const int64_t c_mid = bin > 0 ? (int64_t(1) << (bin - 1)) : 0;
+            now = (can[bin][2] && c_mid >= kTiledCells) ? 2 : (c_mid >= kBigCells ? 1 : 0);
         }
+        int keep = now;
+        for (int f = 0; f < 3 && rc == 0; ++f) {
+            if (f == now || !can[bin][f]) continue;
+            int8_t trial[kAlignBins];
+            std::copy(tab, tab + kAlignBins, trial);
+            trial[bin] = (int8_t)f;
+            float t = 0.f;
+            if ((rc = time_with(trial, t))) break;
+            if (t < 0.97f * best) {
+                best = t;
+                keep = f;
+            }
+        }
+        tab[bin] = (int8_t)keep;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -772,7 +824,7 @@ int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get)
         std::copy(ctx->align_tab, ctx->align_tab + n, tab);
     } else {
         for (int k = 0; k < n; ++k)
-            if (tab[k] < -1 || tab[k] > 1) return fail(MINE_EINVAL, "strategy entries are -1, 0 or 1");
+            if (tab[k] < -1 || tab[k] > 2) return fail(MINE_EINVAL, "strategy entries are -1, 0, 1 or 2");
         std::copy(tab, tab + n, ctx->align_tab);
         ++ctx->arena_gen;   // cached graphs hold plans of the old table
     }
@@ -1325,7 +1377,7 @@ const char *mine_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
-                                           "k_pairprep", "k_score_wide"};
+                                           "k_pairprep", "k_score_wide", "k_align_tiled"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 

@@ -294,6 +294,38 @@ def test_align_matrix_any_sign(ctx):
             assert got == O.align(M, [(g, th)])[0], (S, T, kind)
 
 
+def test_tiled_alignment_agrees(ctx):
+    """Pairs cut into tiles of 256 x 512 cells over many CTAs (ragged last
+    tiles, a tile row or column of one stripe or one score tile, ties, signed
+    scores) give the oracle's results; so does a mined batch of large pairs."""
+    rng = np.random.default_rng(21)
+    old = ctx.align_strategy()
+    try:
+        ctx.align_strategy([2] * mine.ALIGN_BINS)
+        sizes = [(257, 513), (300, 1000), (600, 600), (1000, 520), (513, 1025), (777, 1300),
+                 (289, 545), (1024, 1024)]
+        for S, T in sizes:
+            for kind in range(3):
+                if kind == 0:
+                    M = synth.random_matrix(rng, S, T, values=[0, 1, 2])
+                    g, th = -1, 0
+                elif kind == 1:
+                    M = synth.random_matrix(rng, S, T, lo=-65536, hi=65536)
+                    g, th = -int(rng.integers(0, 70000)), int(rng.integers(-65536, 65536))
+                else:
+                    M = synth.random_matrix(rng, S, T, lo=0, hi=65536)
+                    g, th = -65536, 32768
+                got = ctx.align_matrix(M, g, th)
+                assert got == O.align(M, [(g, th)])[0], (S, T, kind)
+        w = synth.workload(2, n_pairs=4)
+        sub = _edge_batch(rng, w.dictionary, [(300, 600), (520, 700), (257, 513), (40, 45)], 200000,
+                          lo=5, hi=40)
+        dh = ctx.dict_create(w.dictionary)
+        assert_same(ctx.run_batch(dh, sub, w.settings), oracle_results(w, sub), "tiled batch")
+    finally:
+        ctx.align_strategy(old)
+
+
 def test_align_matrix_textbook_cases(ctx):
     rng = np.random.default_rng(81)
     for _ in range(20):
