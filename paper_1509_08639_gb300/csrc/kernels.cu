@@ -376,7 +376,8 @@ k_prep(BatchDev b, DevDict d)
     __syncwarp();
     uint32_t parity = 0u;
     bool generic = false;
-    if (*(volatile int32_t *)b.err) return;
+    // nothing to do unless k_pairprep left an article with too many distinct tokens
+    if (*(volatile int32_t *)b.err || *(volatile int32_t *)&b.counters[9] == 0) return;
 
     for (;;) {
         int item = 0;
@@ -824,7 +825,10 @@ k_pairprep(BatchDev b, DevDict d)
         }
         __syncthreads();
         const int D = sm.nd;
-        if (tid == 0) b.pdoc[p] = D <= kDirect ? D : -1;
+        if (tid == 0) {
+            b.pdoc[p] = D <= kDirect ? D : -1;
+            if (D > kDirect) atomicExch(&b.counters[9], 1);   // k_prep has work
+        }
         if (D > kDirect) continue;
         const int NW = NS >> 5;
         for (int w = wib; w < NW; w += kPPWarps)
