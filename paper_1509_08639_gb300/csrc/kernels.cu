@@ -537,26 +537,29 @@ k_prep(BatchDev b, DevDict d)
 
 // ---------------------------------------------------------------- k_pairprep
 
-constexpr int kPPThreads = 512;
-constexpr int kPPWarps = kPPThreads / 32;
-constexpr int kDocSlotsMax = 2 * kDirect;          // document table: at most ~53% full
-constexpr int kDocWordsMax = kDocSlotsMax / 32;
+// Two launches: articles of at most kSmallArticleTok target tokens by CTAs of
+// 8 warps with a table of 2 kSmallArticleTok slots (four CTAs per SM, so
+// more pairs are in flight and fewer warps wait at a pair's barriers), the
+// others by CTAs of 16 warps with a table of 2 kDirect slots.
+constexpr int kSmallArticleTok = 4096;
 constexpr int kRowSetBig = 2 * kMaxSentTokens;     // rows of > 64 tokens: per-warp table in global memory
 static_assert(kRowSetBig * 8 <= kScoreScratchPerWarp, "per-warp global table too small");
 
+template <int WARPS, int SLOTS>
 struct alignas(16) PairPrepSmem {
-    int32_t key[kDocSlotsMax];                 // target tokens of the article
-    uint32_t occ[kDocWordsMax];                // occupied slots
-    uint16_t rank[kDocWordsMax];               // occupied slots before each word
-    uint32_t seen[kPPWarps][kDirect / 32];     // ids already kept in the warp's current row
-    int32_t cbuf[kPPWarps][64];                // distinct tokens of the row, compacted
+    int32_t key[SLOTS];                        // target tokens of the article
+    uint32_t occ[SLOTS / 32];                  // occupied slots
+    uint16_t rank[SLOTS / 32];                 // occupied slots before each word
+    uint32_t seen[WARPS][kDirect / 32];        // ids already kept in the warp's current row
+    int32_t cbuf[WARPS][64];                   // distinct tokens of the row, compacted
     int32_t nd;
     int32_t item;
 };
 
 // Document id of target token `tok` (the rank of its slot among the
 // occupied ones), or -1 when the article lacks it.
-__device__ __forceinline__ int doc_id(const PairPrepSmem &sm, int lg, int32_t tok)
+template <class SM>
+__device__ __forceinline__ int doc_id(const SM &sm, int lg, int32_t tok)
 {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h = hmul(tok) >> (32 - lg);
@@ -571,7 +574,8 @@ __device__ __forceinline__ int doc_id(const PairPrepSmem &sm, int lg, int32_t to
     }
 }
 
-__device__ __forceinline__ void doc_insert(PairPrepSmem &sm, int lg, int32_t tok)
+template <class SM>
+__device__ __forceinline__ void doc_insert(SM &sm, int lg, int32_t tok)
 {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h = hmul(tok) >> (32 - lg);
@@ -643,7 +647,8 @@ __device__ __forceinline__ int distinct64(int32_t t0, int32_t t1, int L, int lan
 // Kept translations of one distinct source token per lane (first four given
 // in u, the rest read again): write them from position out + (earlier lanes'
 // kept count) as (id | FIRST | END); advances out by the warp's total.
-__device__ __forceinline__ void emit_kept(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm,
+template <class SM>
+__device__ __forceinline__ void emit_kept(const BatchDev &b, const DevDict &d, const SM &sm,
                                           int lg, const int32_t (&u)[4], int2 oc, uint32_t *seen,
                                           uint32_t *el, int &out, int &nf, int lane)
 {
@@ -688,7 +693,8 @@ __device__ __forceinline__ void emit_kept(const BatchDev &b, const DevDict &d, c
 
 // One source row of <= 64 tokens: tokens, distinct tokens (warp match, no
 // table), dictionary buckets, translations, then the kept translations.
-__device__ void prep_row_short(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm, int lg,
+template <class SM>
+__device__ void prep_row_short(const BatchDev &b, const DevDict &d, const SM &sm, int lg,
                                int64_t s, int32_t a, int32_t L, int32_t t0, int32_t t1, int lane,
                                uint32_t *seen, int32_t *cb, int kmax)
 {
@@ -728,7 +734,8 @@ __device__ void prep_row_short(const BatchDev &b, const DevDict &d, const PairPr
 
 // One source row of any length (distinct tokens through a per-warp table in
 // global memory whose live entries carry the row's stamp).
-__device__ void prep_row_long(const BatchDev &b, const DevDict &d, const PairPrepSmem &sm, int lg,
+template <class SM>
+__device__ void prep_row_long(const BatchDev &b, const DevDict &d, const SM &sm, int lg,
                               int64_t s, int32_t a, int32_t L, int lane, int2 *gset,
                               bool &gset_clean, int32_t stamp, uint32_t *seen)
 {
@@ -775,11 +782,13 @@ __device__ void prep_row_long(const BatchDev &b, const DevDict &d, const PairPre
 //     (n_i, #kept, #kept FIRST) in sinfo.
 // A larger article gets pdoc[p] = -1 and is left to k_prep and the
 // token-keyed score path.
-__global__ void __launch_bounds__(kPPThreads, kPairPrepCtasPerSm)
+template <int WARPS, int SLOTS, int CTAS, bool SMALL>
+__global__ void __launch_bounds__(WARPS * 32, CTAS)
 k_pairprep(BatchDev b, DevDict d)
 {
+    constexpr int kPPWarps = WARPS, kPPThreads = WARPS * 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PairPrepSmem &sm = *reinterpret_cast<PairPrepSmem *>(smem_raw);
+    PairPrepSmem<WARPS, SLOTS> &sm = *reinterpret_cast<PairPrepSmem<WARPS, SLOTS> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     int2 *gset = b.gscratch + (int64_t)(blockIdx.x * kPPWarps + wib) * kGTabSlots;
     bool gset_clean = false;
@@ -789,7 +798,7 @@ k_pairprep(BatchDev b, DevDict d)
     for (;;) {
         if (__syncthreads_or(*(volatile int32_t *)b.err != 0)) break;
         if (tid == 0) {
-            sm.item = atomicAdd(&b.counters[5], 1);
+            sm.item = atomicAdd(&b.counters[SMALL ? 5 : 10], 1);
             sm.nd = 0;
         }
         __syncthreads();
@@ -798,7 +807,8 @@ k_pairprep(BatchDev b, DevDict d)
         const int p = b.dorder[item];
         const PairPlan pp = b.pairs[p];
         const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
-        const int lg = min(max(ceil_log2(2 * max(tb - ta, 1)), 10), 14);
+        if ((tb - ta <= kSmallArticleTok) != SMALL) continue;   // the other launch's pair
+        const int lg = min(max(ceil_log2(2 * max(tb - ta, 1)), 10), SMALL ? 13 : 14);
         const int NS = 1 << lg;
         int4 *kz = reinterpret_cast<int4 *>(sm.key);
         for (int k = tid; k < NS / 4; k += kPPThreads) kz[k] = make_int4(-1, -1, -1, -1);
@@ -2170,14 +2180,23 @@ int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t s
     return 1;
 }
 
+template <int WARPS, int SLOTS, int CTAS, bool SMALL>
+int launch_pairprep_one(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
+{
+    const size_t smem = sizeof(PairPrepSmem<WARPS, SLOTS>);
+    cudaFuncSetAttribute(k_pairprep<WARPS, SLOTS, CTAS, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    const int grid = std::max(1, std::min(num_sms * CTAS, b.n_pairs));
+    k_pairprep<WARPS, SLOTS, CTAS, SMALL><<<grid, WARPS * 32, smem, st>>>(b, d);
+    return 1;
+}
+
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    const size_t smem = sizeof(PairPrepSmem);
-    cudaFuncSetAttribute(k_pairprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = std::max(1, std::min(num_sms * kPairPrepCtasPerSm, b.n_pairs));
-    k_pairprep<<<grid, kPPThreads, smem, st>>>(b, d);
-    return 1;
+    static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 4 <= kGScratchWarpsPerSm, "per-warp global tables");
+    return launch_pairprep_one<16, 2 * kDirect, 2, false>(b, d, num_sms, st) +
+           launch_pairprep_one<8, 2 * kSmallArticleTok, 4, true>(b, d, num_sms, st);
 }
 
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
