@@ -1654,20 +1654,27 @@ struct WarpPipe {
 // column cidx = 32c + u - L; its score comes from tile c-1 (u < L) or tile c
 // (base_prev / base_cur already point at column u = 0 of the lane's row).
 // Direction codes are shifted into `word` (two bits per cell, the oldest in
-// the low bits) and stored when a 16-column word is complete.  Columns
-// [clo, chi) are filled.  GUARD = false for chunks in which every lane is
-// inside them.  TILE: the cell values of the bottom row go to gbot (lane 31
-// of a tile's last stripe; null otherwise) and those of column chi-1 to
-// *gright (null when no tile follows on the right).
+// the low bits; a zero for a step outside the matrix), so after steps 15 and
+// 31 every lane holds 16 codes starting at its own column offset; joined with
+// the previous 16 (`prev`) by a funnel shift of 2 (L & 15) they give the
+// aligned 16-column word 2c - 1 - L/16 (step 15) or 2c - L/16 (step 31) of
+// the lane's row, stored when it lies in [mlo, mhi).  Columns [clo, chi)
+// are filled.  GUARD = false for chunks in which every lane is inside them
+// and every word stored lies in [mlo, mhi).  TILE: the cell values of the
+// bottom row go to gbot (lane 31 of a tile's last stripe; null otherwise)
+// and those of column chi-1 to *gright (null when no tile follows on the
+// right).
 template <bool GUARD, bool TILE = false>
 __device__ __forceinline__ void stripe_chunk(int c, int lane, int clo, int chi, bool row_ok, int32_t g,
                                              int32_t up_val, const int32_t *base_prev,
-                                             const int32_t *base_cur, uint32_t flush,
-                                             uint32_t *cr, int32_t *ring, int32_t qm,
-                                             bool publish, int32_t &h_left, int32_t &up_prev,
-                                             int32_t &h_out, uint32_t &word,
-                                             int32_t *gbot = nullptr, int32_t *gright = nullptr)
+                                             const int32_t *base_cur, uint32_t *cr, int mlo, int mhi,
+                                             int32_t *ring, int32_t qm, bool publish, int32_t &h_left,
+                                             int32_t &up_prev, int32_t &h_out, uint32_t &word,
+                                             uint32_t &prev, int32_t *gbot = nullptr,
+                                             int32_t *gright = nullptr)
 {
+    const uint32_t sh = 2u * (uint32_t)(lane & 15);
+    const int mb = 2 * c - (lane >> 4);
 #pragma unroll 8
     for (int u = 0; u < 32; ++u) {
         int32_t up_in = __shfl_up_sync(kFull, h_out, 1);
@@ -1675,6 +1682,7 @@ __device__ __forceinline__ void stripe_chunk(int c, int lane, int clo, int chi, 
         up_in = (lane == 0) ? from_above : up_in;
         const int cidx = 32 * c + u - lane;
         const bool valid = !GUARD || (row_ok && cidx >= clo && cidx < chi);
+        uint32_t code = 0u;
         if (valid) {
             const int32_t sv = (u < lane ? base_prev : base_cur)[u];
             const int32_t cd = up_prev + sv;
@@ -1682,9 +1690,7 @@ __device__ __forceinline__ void stripe_chunk(int c, int lane, int clo, int chi, 
             const int32_t cl = h_left + g;
             const int32_t cg = max(cu, cl);
             const int32_t best = max(cd, cg);
-            const uint32_t code = cd >= cg ? DIR_DIAG : (cu >= cl ? DIR_UP : DIR_LEFT);
-            word = __funnelshift_r(word, code, 2);
-            if ((flush >> u) & 1u) cr[cidx >> 4] = word;
+            code = cd >= cg ? DIR_DIAG : (cu >= cl ? DIR_UP : DIR_LEFT);
             if (publish) ring[(qm + cidx) & (kRing - 1)] = best;
             if constexpr (TILE) {
                 if (gbot) gbot[cidx + 1] = best;
@@ -1694,7 +1700,22 @@ __device__ __forceinline__ void stripe_chunk(int c, int lane, int clo, int chi, 
             h_out = best;
             up_prev = up_in;
         }
+        word = __funnelshift_r(word, code, 2);
+        if ((u & 15) == 15) {   // the same step for every lane
+            const int m = mb - (u == 15 ? 1 : 0);
+            if (!GUARD || (row_ok && m >= mlo && m < mhi)) cr[m] = __funnelshift_r(prev, word, sh);
+            prev = word;
+        }
     }
+}
+
+// The last aligned word of a lane's row after its final chunk c (the 16
+// codes of `prev` shifted down, zeros above).
+__device__ __forceinline__ void stripe_flush(int c, int lane, bool row_ok, uint32_t *cr, int mlo, int mhi,
+                                             uint32_t prev)
+{
+    const int m = 2 * c + 1 - (lane >> 4);
+    if (row_ok && m >= mlo && m < mhi) cr[m] = __funnelshift_r(prev, 0u, 2u * (uint32_t)(lane & 15));
 }
 
 // Fill H over the stripes w, w+W, ... of one pair and write the direction
@@ -1713,9 +1734,6 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
     const int CW = (T + 15) >> 4;
     uint32_t *codes = b.codes + it.code_off;
     const int32_t *Mp = b.M + pp.m_off;
-    // flush steps of this lane: columns with (cidx & 15) == 15
-    const uint32_t f0 = (uint32_t)((lane + 15) & 15);
-    const uint32_t flush = (1u << f0) | (1u << (f0 + 16));
     for (int s = wp.w; s < TS; s += wp.W) {
         const int gen = s / wp.W;
         const int i0 = 32 * s;
@@ -1740,7 +1758,7 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
         int32_t h_left = row * g;          // H[row][j-1]
         int32_t up_prev = (row - 1) * g;   // H[row-1][j-1]
         int32_t h_out = 0;                 // value handed to the next lane
-        uint32_t word = 0;
+        uint32_t word = 0, prev = 0;
         const int nchunks = (T + 31 + 31) >> 5;
         int b_cur = 0;                     // buffer of tile c (= c % kMBuf)
         for (int c = 0; c < nchunks; ++c) {
@@ -1782,11 +1800,11 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
             const int32_t *base_cur = sm.tile[wib][b_cur] + lane * kTile - lane;
             const bool publish = has_below && lane == 31;
             if (full_stripe && c >= 1 && 32 * (c + 1) <= T)
-                stripe_chunk<false>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
-                                    wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word);
+                stripe_chunk<false>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, cr, 0, CW,
+                                    wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word, prev);
             else
-                stripe_chunk<true>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, flush, cr,
-                                   wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word);
+                stripe_chunk<true>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, cr, 0, CW,
+                                   wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word, prev);
             __syncwarp();
             if (publish) {
                 const int jdone = min(32 * c + 1, T);
@@ -1797,9 +1815,7 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
             }
             b_cur = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
         }
-        // a last word shorter than 16 columns: its codes sit in the high bits
-        const int tail = T & 15;
-        if (row_ok && tail) cr[(T - 1) >> 4] = word >> (2 * (16 - tail));
+        stripe_flush(nchunks - 1, lane, row_ok, cr, 0, CW, prev);
         if (s == TS - 1 && row == S) b.hfin[item] = h_left;
         __syncwarp();
     }
@@ -1998,8 +2014,7 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
     if (s < TS) {
         uint32_t *codes = b.codes + it.code_off;
         const int32_t *Mp = b.M + pp.m_off;
-        const uint32_t f0 = (uint32_t)((lane + 15) & 15);
-        const uint32_t flush = (1u << f0) | (1u << (f0 + 16));
+        const int mlo = clo >> 4, mhi = (chi + 15) >> 4;   // code words of the tile's columns
         const int i0 = 32 * s;
         const int row = i0 + lane + 1;
         const bool row_ok = row <= S;
@@ -2025,7 +2040,7 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
         int32_t h_left = vl ? (row_ok ? vl[row] : 0) : row * g;
         int32_t up_prev = vl ? (row - 1 == 0 ? clo * g : (row_ok ? vl[row - 1] : 0)) : (row - 1) * g;
         int32_t h_out = 0;
-        uint32_t word = 0;
+        uint32_t word = 0, prev = 0;
         const int nchunks = ((chi + 31 + 31) >> 5) - cb;
         const int32_t *hrow = (R > 0 && wib == 0) ? hb + (int64_t)(R - 1) * (T + 1) : nullptr;
         int b_cur = 0;
@@ -2067,13 +2082,13 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
             const int32_t *base_cur = sm.tile[wib][b_cur] + lane * kTile - lane;
             const bool publish = has_below && lane == 31;
             if (full_stripe && cc >= 1 && 32 * (c + 1) <= chi)
-                stripe_chunk<false, true>(c, lane, clo, chi, row_ok, g, up_val, base_prev, base_cur, flush, cr,
-                                          sm.ring[wib], qbase, publish, h_left, up_prev, h_out, word, gbot,
-                                          gright);
+                stripe_chunk<false, true>(c, lane, clo, chi, row_ok, g, up_val, base_prev, base_cur, cr, mlo,
+                                          mhi, sm.ring[wib], qbase, publish, h_left, up_prev, h_out, word,
+                                          prev, gbot, gright);
             else
-                stripe_chunk<true, true>(c, lane, clo, chi, row_ok, g, up_val, base_prev, base_cur, flush, cr,
-                                         sm.ring[wib], qbase, publish, h_left, up_prev, h_out, word, gbot,
-                                         gright);
+                stripe_chunk<true, true>(c, lane, clo, chi, row_ok, g, up_val, base_prev, base_cur, cr, mlo,
+                                         mhi, sm.ring[wib], qbase, publish, h_left, up_prev, h_out, word,
+                                         prev, gbot, gright);
             __syncwarp();
             if (publish) {
                 const int jdone = min(32 * c + 1, chi);
@@ -2085,8 +2100,7 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
             b_cur = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
         }
         if (ok) {
-            const int tail = T & 15;
-            if (row_ok && chi == T && tail) cr[(T - 1) >> 4] = word >> (2 * (16 - tail));
+            stripe_flush(cb + nchunks - 1, lane, row_ok, cr, mlo, mhi, prev);
             if (s == TS - 1 && row == S && chi == T) b.hfin[ti.nw] = h_left;
         }
         __syncwarp();
