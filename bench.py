@@ -472,25 +472,29 @@ def main():
     align_ops = 4 * cells * n_gap                                 # 4 int ops per DP cell
     alu_peak_tops = 152 * 128 * sm_mhz_max * 1e6 / 1e12           # int32 lane-ops/s
     rl = {}
+    # each stage's time covers all of its launches: the two preparation
+    # launches (one region), the score launches for small and wide target
+    # articles, and the alignments of one CTA or warp and of many CTAs
+    stage_extra = {"k_score": "k_score_wide", "k_align": "k_align_tiled"}
     for k in ("k_pairprep", "k_score", "k_align"):
         if k not in per_launch_ms:
             continue
-        t = per_launch_ms[k] / 1e3
+        t = (per_launch_ms[k] + per_launch_ms.get(stage_extra.get(k), 0.0)) / 1e3
         if k == "k_pairprep":
             a = prep_bytes / t / 1e9
             rl[k] = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
                      "frac": a / hbm_peak, "traffic": committed_traffic(k),
-                     "algorithmic_bytes": prep_bytes, "kept_entries": kept, "ms": per_launch_ms[k]}
+                     "algorithmic_bytes": prep_bytes, "kept_entries": kept, "ms": t * 1e3}
         elif k == "k_score":
             a = score_bytes / t / 1e9
             rl[k] = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
                      "frac": a / hbm_peak, "traffic": committed_traffic(k),
-                     "algorithmic_bytes": score_bytes, "ms": per_launch_ms[k]}
+                     "algorithmic_bytes": score_bytes, "ms": t * 1e3}
         else:
             a = align_ops / t / 1e12
             rl[k] = {"bound": "alu", "achieved": a, "peak": alu_peak_tops, "unit": "Tops/s",
                      "frac": a / alu_peak_tops, "traffic": committed_traffic(k),
-                     "algorithmic_ops": align_ops, "ms": per_launch_ms[k],
+                     "algorithmic_ops": align_ops, "ms": t * 1e3,
                      "gcups": cells * n_gap / t / 1e9}
     roof = dict(rl.get(dom, {}))
     roof["kernel"] = dom
