@@ -5,7 +5,9 @@ may import this module.  It loads ``mine_oracle.c`` (compiled by
 :func:`build`) through ctypes and adds two pure-Python pieces that are NOT the
 recurrence: a brute-force enumerator of every monotone alignment (the paper's
 "paths cannot go upward or leftward", Section 4) and the canonical-path rule,
-used to pin the oracle's dynamic programme on tiny inputs.
+used to pin the oracle's dynamic programme on tiny inputs.  Bidirectional
+mining (the union of the two directions' selections) and the tuning
+objective (F1 against known translation pairs) are plain Python as well.
 
 Parity pins for every function here live in ``tests/test_oracle_pins.py``.
 """
@@ -190,6 +192,111 @@ def mine_batch(od: OracleDict, batch, settings, threads: int = 1):
             row.append((int(nws[p * n + k]), [tuple(int(v) for v in r) for r in trip]))
         res.append(row)
     return res, int(used)
+
+
+# ---------------------------------------------------------------------------
+# bidirectional mining (Section 6, Table 2 "BI"; Section 7)
+# ---------------------------------------------------------------------------
+
+class _Packed:
+    """A packed batch (doc_off, sent_off, tokens) built by the oracle itself."""
+
+    def __init__(self, doc_off, sent_off, tokens):
+        self.doc_off, self.sent_off, self.tokens = doc_off, sent_off, tokens
+
+    @property
+    def n_pairs(self) -> int:
+        return (int(self.doc_off.shape[0]) - 1) // 2
+
+    def sizes(self):
+        d = self.doc_off.astype(np.int64)
+        return d[1::2] - d[0:-1:2], d[2::2] - d[1::2]
+
+
+def swap_roles(batch):
+    """The same pairs with the two articles of every pair exchanged: the
+    target article becomes the source (mining in the other direction)."""
+    do = np.asarray(batch.doc_off, np.int64)
+    so = np.asarray(batch.sent_off, np.int64)
+    tk = np.asarray(batch.tokens, np.int32)
+    doc_off, sent_off, toks = [0], [0], []
+    for p in range(batch.n_pairs):
+        for d in (2 * p + 1, 2 * p):
+            for k in range(int(do[d]), int(do[d + 1])):
+                toks.append(tk[int(so[k]):int(so[k + 1])])
+                sent_off.append(sent_off[-1] + int(so[k + 1] - so[k]))
+            doc_off.append(len(sent_off) - 1)
+    tokens = np.concatenate(toks).astype(np.int32) if toks else np.zeros(0, np.int32)
+    return _Packed(np.asarray(doc_off, np.int32), np.asarray(sent_off, np.int32), tokens)
+
+
+def union_selection(fwd, bwd) -> list:
+    """Union of the pairs one setting selects in the two directions.
+
+    fwd holds (i, j, s) with i a source and j a target sentence; bwd holds
+    (j, i, s') from mining with the roles exchanged (its first index is the
+    target sentence).  A pair found in both directions appears once with the
+    larger of its two scores; the result is ordered by (i, j)."""
+    best = {}
+    for i, j, s in fwd:
+        best[(i, j)] = s
+    for j, i, s in bwd:
+        best[(i, j)] = max(best[(i, j)], s) if (i, j) in best else s
+    return [(i, j, best[(i, j)]) for (i, j) in sorted(best)]
+
+
+def mine_batch_bidi(od_fwd: OracleDict, od_bwd: OracleDict, batch, settings, threads: int = 1):
+    """Mining with both dictionaries (source->target and target->source).
+
+    Returns results[p][k] = (nw_score forward, nw_score backward,
+    union of the two selections)."""
+    fwd, _ = mine_batch(od_fwd, batch, settings, threads)
+    bwd, _ = mine_batch(od_bwd, swap_roles(batch), settings, threads)
+    return [[(fwd[p][k][0], bwd[p][k][0], union_selection(fwd[p][k][1], bwd[p][k][1]))
+             for k in range(len(settings))] for p in range(batch.n_pairs)]
+
+
+# ---------------------------------------------------------------------------
+# tuning objective for Threshold and Penalty (Section 4; Section 6, Table 2
+# "NWT"): F1 of the selected pairs against known translation pairs
+# ---------------------------------------------------------------------------
+
+def f1_counts(results, batch, truth):
+    """Per setting k: (true positives, selected pairs) summed over the batch,
+    and the number of known pairs.
+
+    results[p][k] = (..., selection) with selection = [(i, j, s)] (the last
+    entry of the tuple); truth[doc_off[2p] + i] = the target sentence that
+    source sentence i of pair p translates, or -1.  A selected (i, j) is a
+    true positive when truth says j for i."""
+    do = np.asarray(batch.doc_off, np.int64)
+    n = len(results[0]) if results else 0
+    tp = [0] * n
+    nsel = [0] * n
+    for p, row in enumerate(results):
+        s0 = int(do[2 * p])
+        for k in range(n):
+            sel = row[k][-1]
+            nsel[k] += len(sel)
+            tp[k] += sum(1 for (i, j, _) in sel if int(truth[s0 + i]) == j)
+    n_truth = 0
+    for p in range(len(results)):
+        n_truth += sum(1 for i in range(int(do[2 * p]), int(do[2 * p + 1])) if int(truth[i]) >= 0)
+    return tp, nsel, n_truth
+
+
+def best_setting(tp, nsel, n_truth) -> int:
+    """Index of the setting of highest F1 = 2 tp / (selected + known), exact
+    rational comparison, the lowest index among equals; F1 = 0 when both
+    counts are 0."""
+    from fractions import Fraction
+    f1 = [Fraction(2 * t, s + n_truth) if s + n_truth > 0 else Fraction(0)
+          for t, s in zip(tp, nsel)]
+    best = 0
+    for k in range(1, len(f1)):
+        if f1[k] > f1[best]:
+            best = k
+    return best
 
 
 # ---------------------------------------------------------------------------

@@ -189,8 +189,13 @@ def make_dictionary(rng, vocab: int, kmax: int) -> Dictionary:
 
 
 def make_pairs(rng, cdf, d: Dictionary, S, T, frac, len_lo, len_hi,
-               p_drop=0.05, p_ins=0.05) -> Batch:
-    """P article pairs with S[p] x T[p] sentences; frac[p] of T translated."""
+               p_drop=0.05, p_ins=0.05, planted: list | None = None) -> Batch:
+    """P article pairs with S[p] x T[p] sentences; frac[p] of T translated.
+
+    When ``planted`` is a list, an int64 array of (pair, source sentence,
+    target sentence) rows, indices local to the pair's articles, is appended
+    to it: which target sentence is the translation of which source sentence
+    (the random draws are the same either way)."""
     S = np.asarray(S, np.int64)
     T = np.asarray(T, np.int64)
     P = S.shape[0]
@@ -215,6 +220,10 @@ def make_pairs(rng, cdf, d: Dictionary, S, T, frac, len_lo, len_hi,
             tr_src[o:o + n] = src_base[p] + np.sort(rng.choice(int(S[p]), n, replace=False))
             tr_slot[o:o + n] = tgt_base[p] + np.sort(rng.choice(int(T[p]), n, replace=False))
             o += n
+    if planted is not None:
+        pair_of_tr = np.repeat(np.arange(P, dtype=np.int64), n_tr)
+        planted.append(np.stack([pair_of_tr, tr_src - src_base[pair_of_tr],
+                                 tr_slot - tgt_base[pair_of_tr]], axis=1))
 
     # translated sentences (pool B): dictionary translation, then drop/insert noise
     base = _seg_gather(src_tok, src_start[tr_src], src_len[tr_src]).astype(np.int64)
@@ -287,7 +296,7 @@ class Workload:
     gaps: list          # Q16, <= 0
     thresholds: list    # Q16, in [0, 65536]
     settings: list      # [(gap, threshold)] evaluated for every pair
-    planted: np.ndarray = None   # unused by the miner; (pair, src, tgt) of translated sentences
+    planted: np.ndarray = None   # (pair, src, tgt) rows: translated sentences, local indices
 
 
 WORKLOAD_NAMES = {
@@ -360,9 +369,10 @@ def workload(cfg: int, n_pairs: int | None = None, seed: int | None = None) -> W
     else:
         raise ValueError(f"unknown workload {cfg}")
     cdf = _zipf_cdf(V)
-    b = make_pairs(rng, cdf, d, S, T, frac, lo, hi)
+    planted = []
+    b = make_pairs(rng, cdf, d, S, T, frac, lo, hi, planted=planted)
     settings = [(g, t) for g in gaps for t in thrs]
-    return Workload(WORKLOAD_NAMES[cfg], b, d, gaps, thrs, settings)
+    return Workload(WORKLOAD_NAMES[cfg], b, d, gaps, thrs, settings, planted[0])
 
 
 def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int = 1513) -> np.ndarray:
@@ -378,3 +388,42 @@ def random_matrix(rng, S, T, lo=-65536, hi=65536, values=None) -> np.ndarray:
     if values is not None:
         return np.asarray(rng.choice(np.asarray(values, np.int64), size=(S, T)), np.int32)
     return rng.integers(lo, hi + 1, size=(S, T)).astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# inputs of bidirectional mining and of the tuning objective
+# --------------------------------------------------------------------------
+
+def invert_dictionary(d: Dictionary) -> Dictionary:
+    """The reverse dictionary (target language -> source language): key t
+    lists, in increasing order, every source ID that has t among its
+    translations; keys are the target IDs that occur.  Raises if a key would
+    get more than 32 translations (the miner's limit per key)."""
+    cnt = (d.trans_off[1:] - d.trans_off[:-1]).astype(np.int64)
+    src = np.repeat(d.keys.astype(np.int64), cnt)
+    tgt = d.trans.astype(np.int64)
+    order = np.lexsort((src, tgt))
+    tgt, src = tgt[order], src[order]
+    if tgt.shape[0]:
+        keep = np.ones(tgt.shape[0], bool)
+        keep[1:] = (tgt[1:] != tgt[:-1]) | (src[1:] != src[:-1])
+        tgt, src = tgt[keep], src[keep]
+    keys, first, per = np.unique(tgt, return_index=True, return_counts=True)
+    if per.shape[0] and int(per.max()) > 32:
+        raise ValueError("a target ID has more than 32 source translations")
+    off = np.zeros(keys.shape[0] + 1, np.int64)
+    np.cumsum(per, out=off[1:])
+    return Dictionary(keys.astype(np.int32), off.astype(np.int32), src.astype(np.int32))
+
+
+def truth_of(batch: Batch, planted) -> np.ndarray:
+    """int32[n_sent]: for source sentence k of pair p (global index
+    doc_off[2p] + k) the planted target sentence (index in pair p's target
+    article), -1 elsewhere (untranslated source sentences and every target
+    sentence)."""
+    n_sent = int(batch.doc_off[-1])
+    truth = np.full(n_sent, -1, np.int32)
+    pl = np.asarray(planted, np.int64).reshape(-1, 3)
+    if pl.shape[0]:
+        truth[batch.doc_off[2 * pl[:, 0]].astype(np.int64) + pl[:, 1]] = pl[:, 2].astype(np.int32)
+    return truth

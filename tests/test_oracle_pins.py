@@ -406,3 +406,200 @@ def test_planted_mistake_is_caught(name, tmp_path):
 
 def test_unmutated_oracle_passes_all_pins():
     assert _run_all_pins(O.lib()) == []
+
+
+# ------------------------------------------- bidirectional mining and tuning pins
+#
+# Section 6 (Table 2, "BI") mines with classifiers trained in both directions
+# and keeps what either finds; Section 4 tunes Threshold and Penalty (Table 2,
+# "NWT").  The oracle's union of the two directions and its F1 objective are
+# pinned by hand-worked examples, special cases and set identities; planted
+# mistakes in a copy of the Python oracle must be caught.
+
+def _dicts(c):
+    f = synth.dictionary_from_map({int(k): v for k, v in c["fwd_dictionary"].items()})
+    b = synth.dictionary_from_map({int(k): v for k, v in c["bwd_dictionary"].items()})
+    return f, b
+
+
+def check_bidi_hand_examples(m=O):
+    g = _gold("bidi_hand_examples.json")
+    st = [(g["gap"], g["theta"])]
+    for c in g["cases"]:
+        df, db = _dicts(c)
+        of, ob = m.OracleDict(df), m.OracleDict(db)
+        b = synth.docs_from_lists(c["src"], c["tgt"])
+        sb = m.swap_roles(b)
+        assert m.score_matrix(of, *b.pair(0)).tolist() == c["M_fwd"], c["name"]
+        so = np.asarray(sb.sent_off)
+        do = np.asarray(sb.doc_off)
+        src = (so[do[0]:do[1] + 1] - so[do[0]], sb.tokens[so[do[0]]:so[do[1]]])
+        tgt = (so[do[1]:do[2] + 1] - so[do[1]], sb.tokens[so[do[1]]:so[do[2]]])
+        assert m.score_matrix(ob, src, tgt).tolist() == c["M_bwd"], c["name"]
+        fw, _ = m.mine_batch(of, b, st)
+        bw, _ = m.mine_batch(ob, sb, st)
+        assert fw[0][0] == (c["nw_fwd"], [tuple(t) for t in c["sel_fwd"]]), c["name"]
+        assert bw[0][0] == (c["nw_bwd"], [tuple(t) for t in c["sel_bwd"]]), c["name"]
+        r = m.mine_batch_bidi(of, ob, b, st)
+        assert r[0][0] == (c["nw_fwd"], c["nw_bwd"], [tuple(t) for t in c["union"]]), c["name"]
+
+
+def test_bidi_hand_examples():
+    check_bidi_hand_examples()
+
+
+def _small_bidi_workload(n_pairs=10):
+    w = synth.workload(2, n_pairs=n_pairs)
+    return w, synth.invert_dictionary(w.dictionary)
+
+
+def check_bidi_identities(m=O):
+    w, inv = _small_bidi_workload()
+    st = [(-65536, 32768), (-16384, 16384), (-131072, 49152)]
+    of, ob = m.OracleDict(w.dictionary), m.OracleDict(inv)
+    b = w.batch
+    sb = m.swap_roles(b)
+    # exchanging the roles twice gives the batch back
+    bb = m.swap_roles(sb)
+    for f in ("doc_off", "sent_off", "tokens"):
+        assert np.array_equal(np.asarray(getattr(bb, f)), np.asarray(getattr(b, f)))
+    S, T = b.sizes()
+    S2, T2 = sb.sizes()
+    assert np.array_equal(S, T2) and np.array_equal(T, S2)
+    fw, _ = m.mine_batch(of, b, st)
+    bw, _ = m.mine_batch(ob, sb, st)
+    un = m.mine_batch_bidi(of, ob, b, st)
+    for p in range(b.n_pairs):
+        for k in range(len(st)):
+            F = {(i, j): s for i, j, s in fw[p][k][1]}
+            B = {(i, j): s for j, i, s in bw[p][k][1]}
+            nf, nb, U = un[p][k]
+            assert (nf, nb) == (fw[p][k][0], bw[p][k][0])
+            keys = [(i, j) for i, j, _ in U]
+            assert keys == sorted(set(keys)) and len(keys) == len(set(F) | set(B))
+            assert set(keys) == set(F) | set(B)
+            for i, j, s in U:
+                assert s == max(F.get((i, j), -1), B.get((i, j), -1))
+                assert s > st[k][1]
+            # each direction's selection is a monotone chain: i and j increase together
+            for sel in (sorted(F), sorted(B)):
+                assert all(a[1] < c[1] for a, c in zip(sel, sel[1:]))
+
+
+def test_bidi_identities():
+    check_bidi_identities()
+
+
+def check_bidi_special_cases(m=O):
+    w, _ = _small_bidi_workload(6)
+    st = [(-65536, 32768), (-32768, 20000)]
+    of = m.OracleDict(w.dictionary)
+    fw, _ = m.mine_batch(of, w.batch, st)
+    # a reverse dictionary that translates nothing scores every backward cell
+    # 0.25 q_l <= 16384: nothing above these thresholds, so the union is the
+    # forward selection
+    empty = synth.dictionary_from_map({})
+    un = m.mine_batch_bidi(of, m.OracleDict(empty), w.batch, st)
+    for p in range(w.batch.n_pairs):
+        for k in range(len(st)):
+            assert un[p][k][2] == fw[p][k][1]
+    # one-sentence articles in both roles: the union holds (0, 0) exactly
+    # when one direction scores it above the threshold
+    b = synth.docs_from_lists([[1, 2]], [[11]])
+    d1 = synth.dictionary_from_map({1: [11]})
+    d2 = synth.dictionary_from_map({11: [1]})
+    r = m.mine_batch_bidi(m.OracleDict(d1), m.OracleDict(d2), b, [(-65536, 0), (-65536, 65536)])
+    assert r[0][0][2] and r[0][0][2][0][:2] == (0, 0) and r[0][1][2] == []
+
+
+def test_bidi_special_cases():
+    check_bidi_special_cases()
+
+
+def check_f1_hand_example(m=O):
+    g = _gold("f1_hand_example.json")
+    b = synth.Batch(np.asarray(g["doc_off"], np.int32), np.zeros(11, np.int32), np.zeros(0, np.int32))
+    res = [[(0, [tuple(t) for t in sel]) for sel in row] for row in g["selections"]]
+    tp, nsel, nt = m.f1_counts(res, b, np.asarray(g["truth"], np.int32))
+    assert (tp, nsel, nt) == (g["tp"], g["selected"], g["n_truth"])
+    assert [[2 * t, s + nt] for t, s in zip(tp, nsel)] == g["f1_num_den"]
+    assert m.best_setting(tp, nsel, nt) == g["best"]
+
+
+def test_f1_hand_example():
+    check_f1_hand_example()
+
+
+def check_f1_closed_forms(m=O):
+    w = synth.workload(2, n_pairs=8)
+    st = [(-65536, 32768), (-16384, 16384), (-131072, 49152)]
+    res, _ = m.mine_batch(m.OracleDict(w.dictionary), w.batch, st)
+    do = w.batch.doc_off
+    for k in range(len(st)):
+        # known pairs = exactly what setting k selects: F1 = 1 there
+        truth = np.full(int(do[-1]), -1, np.int32)
+        for p in range(w.batch.n_pairs):
+            for i, j, _ in res[p][k][1]:
+                truth[int(do[2 * p]) + i] = j
+        tp, nsel, nt = m.f1_counts(res, w.batch, truth)
+        assert tp[k] == nsel[k] == nt
+        best = m.best_setting(tp, nsel, nt)
+        assert 2 * tp[best] == nsel[best] + nt and best <= k
+    # nothing known: every F1 is 0 and the first setting is best
+    none = np.full(int(do[-1]), -1, np.int32)
+    tp, nsel, nt = m.f1_counts(res, w.batch, none)
+    assert tp == [0, 0, 0] and nt == 0 and m.best_setting(tp, nsel, nt) == 0
+    # nothing selected and nothing known: F1 counts as 0
+    assert m.best_setting([0, 0], [0, 0], 0) == 0
+    # the generator's planted pairs: each known pair is one source sentence
+    tr = synth.truth_of(w.batch, w.planted)
+    _, _, nt = m.f1_counts(res, w.batch, tr)
+    assert nt == w.planted.shape[0]
+
+
+def test_f1_closed_forms():
+    check_f1_closed_forms()
+
+
+_PY_MUTANTS = {
+    "union without the role exchange": ("    for j, i, s in bwd:\n", "    for i, j, s in bwd:\n"),
+    "union keeps the forward score": ("best[(i, j)] = max(best[(i, j)], s) if (i, j) in best else s",
+                                      "best[(i, j)] = best[(i, j)] if (i, j) in best else s"),
+    "roles not exchanged": ("for d in (2 * p + 1, 2 * p):", "for d in (2 * p, 2 * p + 1):"),
+    "true positive with swapped indices": ("if int(truth[s0 + i]) == j)", "if int(truth[s0 + j]) == i)"),
+    "known pairs counted over target sentences": ("range(int(do[2 * p]), int(do[2 * p + 1])) if int(truth[i]) >= 0",
+                                                  "range(int(do[2 * p]), int(do[2 * p + 2])) if int(truth[i]) >= 0"),
+    "ties go to the last setting": ("if f1[k] > f1[best]:", "if f1[k] >= f1[best]:"),
+    "precision instead of F1": ("Fraction(2 * t, s + n_truth) if s + n_truth > 0",
+                                "Fraction(t, s) if s > 0"),
+}
+
+
+def _run_py_pins(m):
+    failed = []
+    for c in (check_bidi_hand_examples, check_bidi_identities, check_bidi_special_cases,
+              check_f1_hand_example, check_f1_closed_forms):
+        try:
+            c(m)
+        except (AssertionError, ZeroDivisionError, IndexError, KeyError):
+            failed.append(c)
+    return failed
+
+
+@pytest.mark.parametrize("name", sorted(_PY_MUTANTS))
+def test_planted_mistake_in_union_or_objective_is_caught(name, tmp_path):
+    import importlib.util
+    old, new = _PY_MUTANTS[name]
+    src = open(O.__file__).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not unique in the oracle"
+    path = tmp_path / "oracle_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("oracle_mutant", str(path))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    m._lib = O.lib()   # the unmutated C part
+    assert _run_py_pins(m), f"no pin caught the planted mistake {name!r}"
+
+
+def test_unmutated_union_and_objective_pass_all_pins():
+    assert _run_py_pins(O) == []
