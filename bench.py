@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident path (for profiler captures)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the bidirectional-mining and tuning-objective measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in alignment strategy (no tuning launches before the run)")
     return ap.parse_args()
@@ -289,6 +291,70 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- GB300 arm
 
+def extras_run(ctx, w, dh, reps=3):
+    """Bidirectional mining (both dictionaries, union of the selections) and
+    the tuning objective (F1 of a 64-setting sweep against the generator's
+    planted pairs) on the benchmark batch, each through its host-buffer call:
+    wall time per call (inputs copied in, results copied out) and the device
+    time of every kernel from one profiled call."""
+    from paper_1509_08639_gb300 import mine, synth
+    b = w.batch
+    P = b.n_pairs
+    S, T = b.sizes()
+    inv = synth.reverse_dictionary(w.dictionary)
+    hb = ctx.dict_create(inv)
+    do, so, tk = (np.ascontiguousarray(x, np.int32) for x in (b.doc_off, b.sent_off, b.tokens))
+    n = len(w.settings)
+    g = np.asarray([s_[0] for s_ in w.settings], np.int32)
+    th = np.asarray([s_[1] for s_ in w.settings], np.int32)
+    bc = mine.BatchC(P, so.shape[0] - 1, tk.shape[0], mine._ptr(do), mine._ptr(so), mine._ptr(tk))
+    sc = mine.SettingsC(n, mine._ptr(g), mine._ptr(th))
+    cap = 2 * int(n * np.minimum(S, T).sum())
+    outs = (np.zeros(P * n, np.int32), np.zeros(P * n, np.int32), np.zeros(P * n, np.int32),
+            np.zeros(P * n + 1, np.int64), np.zeros((cap, 3), np.int32), cap)
+
+    def timed(fn):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        wall = (time.perf_counter() - t0) / reps
+        ctx.profile(True)
+        ctx.profile_read()
+        fn()
+        prof = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
+        ctx.profile(False)
+        return wall, prof
+
+    wall, prof = timed(lambda: ctx.run_batch_bidi_raw(dh, hb, bc, sc, outs))
+    n_union = int(outs[2].sum())
+    bidi = {"value": P / wall, "unit": UNIT, "ms_per_call": wall * 1e3,
+            "device_ms": sum(prof.values()), "kernel_ms": prof,
+            "selected_union": n_union,
+            "how": "mine_run_batch_bidi, host buffers, %d calls after 1 warm-up; second dictionary = "
+                   "the inverse of the first with 20%% of its entries dropped and one random entry "
+                   "added to 30%% of its keys (%d keys)" % (reps, inv.n_keys)}
+    sweep = [(gg, tt) for gg in synth.SWEEP_GAPS for tt in synth.SWEEP_THRESHOLDS]
+    truth = synth.truth_of(b, w.planted)
+    res = {}
+
+    def tune():
+        res["r"] = ctx.tune_f1(dh, b, sweep, truth)
+
+    wall_t, prof_t = timed(tune)
+    tp, nsel, nt, best = res["r"]
+    f1 = 2 * tp[best] / max(nsel[best] + nt, 1)
+    tuning = {"value": P / wall_t, "unit": UNIT, "ms_per_call": wall_t * 1e3,
+              "device_ms": sum(prof_t.values()), "kernel_ms": prof_t,
+              "settings": len(sweep), "distinct_gaps": len(synth.SWEEP_GAPS),
+              "best": {"gap": sweep[best][0], "threshold": sweep[best][1], "f1": f1,
+                       "tp": tp[best], "selected": nsel[best], "known": nt},
+              "how": "mine_tune_f1 over 8 gaps x 8 thresholds against the planted pairs, host "
+                     "buffers, %d calls after 1 warm-up" % reps}
+    ctx.dict_destroy(hb)
+    return bidi, tuning
+
+
 def serving_run(ctx, dh, rate, seconds):
     """Poisson arrivals of 40x45 pairs with a 1% tail of 2000x2000 pairs."""
     from paper_1509_08639_gb300 import synth
@@ -455,6 +521,9 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         serving = serving_run(ctx, dh, args.serve_rate, args.serve_seconds)
+    bidi = tuning = None
+    if not args.no_extras and rank == 0:
+        bidi, tuning = extras_run(ctx, w, dh)
 
     # ---- roofline of the dominant kernel
     hbm_peak, sm_mhz_max, peak_kind = peaks()
@@ -519,6 +588,8 @@ def main():
         "plain": plain,
         "batched_vs_plain": (value / ws) / plain["value"] if plain else None,
         "serving": serving,
+        "bidirectional": bidi,
+        "tuning": tuning,
         "roofline": roof,
         "roofline_kernels": rl,
         "kernel_ms_per_step": {k: v[0] for k, v in timed.items()},

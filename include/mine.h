@@ -252,6 +252,40 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
 int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,
                    int64_t out_len);
 
+/* Bidirectional mining (Section 6: classifiers trained from the foreign to
+ * the native language and the other way round each find bi-sentences the
+ * other misses, Table 2 "BI"; Section 7).  Every pair of the host batch is
+ * mined twice with the same settings: with `fwd` (source -> target
+ * dictionary) as mine_run_batch does, and with the two articles exchanged and
+ * `bwd` (target -> source dictionary).  Per pair p and setting k at
+ * r = p*n + k: nw_fwd[r] and nw_bwd[r] (the two alignments' scores), n_sel[r]
+ * and sel[sel_off[r] .. sel_off[r+1]) the union of the two selections in
+ * (source sentence, target sentence) indices, ordered by source then target
+ * sentence; a pair both directions select appears once with the larger of its
+ * two scores.  sel_cap: capacity of sel (2 * mine_batch_capacity() is always
+ * enough; MINE_EINVAL if the union does not fit).  Host memory throughout,
+ * synchronous; errors as mine_run_batch. */
+int mine_run_batch_bidi(mine_ctx *ctx, const mine_dict *fwd, const mine_dict *bwd,
+                        const mine_batch *batch, const mine_settings *settings, mine_q16 *nw_fwd,
+                        mine_q16 *nw_bwd, int32_t *n_sel, int64_t *sel_off, mine_pair *sel,
+                        int64_t sel_cap);
+
+/* Tuning objective for Threshold and Penalty (Section 4: a tuning algorithm
+ * adjusts the two parameters; Table 2 "NWT").  Mines the host batch with
+ * every setting, then scores each setting k by F1 against known translation
+ * pairs: truth[s] (host, n_sent entries) is, for source sentence s of pair p
+ * (global sentence index), the index within p's target article of the
+ * sentence it translates, or -1; entries of target sentences are ignored;
+ * MINE_EINVAL for an entry outside [-1, T_p).  Outputs (host): tp[k] =
+ * selected pairs (i, j) with truth == j, n_selected[k] = selected pairs,
+ * *n_truth = source sentences with truth >= 0, *best = the k of highest
+ * F1 = 2 tp / (n_selected + n_truth) (exact comparison; the lowest k among
+ * equals; F1 = 0 when both counts are 0).  tp and n_selected hold n entries.
+ * Synchronous; errors as mine_run_batch. */
+int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                 const mine_settings *settings, const int32_t *truth, int64_t *tp,
+                 int64_t *n_selected, int64_t *n_truth, int32_t *best);
+
 /* Wait for all work of the context's device and report a device-side
  * validation failure of the last mine_run_batch_device call (malformed
  * sentence offsets, token IDs out of range) as MINE_EINVAL. */

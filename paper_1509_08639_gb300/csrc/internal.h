@@ -183,7 +183,28 @@ inline int align_kind(const int8_t *tab, int32_t S, int32_t T)
     return v;
 }
 
-// launchers (kernels.cu); each returns the number of kernels launched
+// Union of the selections of a batch mined in both directions (the second
+// plan has every pair's articles exchanged; same pairs, same settings).
+struct UnionDev {
+    const PairPlan *fwd, *bwd;
+    int32_t n_pairs, nset;
+    const int32_t *sel_f, *sel_b;    // selected triples of each direction
+    const int32_t *nsel_f, *nsel_b;  // their counts, row set0 + k of each plan
+    int32_t *out;                    // row (p, k) at 2 (sel_base + k min(S,T)) triples
+    int32_t *n_out;                  // [rows of the forward plan]
+};
+
+// Tuning objective: true positives and sizes of the selections per setting.
+struct F1Dev {
+    const PairPlan *pairs;
+    int32_t n_pairs, nset;
+    const int32_t *sel, *n_sel;
+    const int32_t *truth;            // [n_sent] known target sentence of a source sentence, or -1
+    unsigned long long *acc;         // [2 nset + 1]: tp per setting, selected per setting, known
+    int32_t *best;                   // [1]
+};
+
+// launchers (kernels.cu, bidi_tune.cu); each returns the number of kernels launched
 int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_keys, DevDict d,
                       int32_t *err, cudaStream_t st);
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
@@ -198,6 +219,8 @@ int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 int launch_fill_scores(int32_t *M, int64_t n, uint32_t seed, cudaStream_t st);
+int launch_union(const UnionDev &u, int num_sms, cudaStream_t st);
+int launch_f1(const F1Dev &f, int num_sms, cudaStream_t st);
 
 // Record the text returned by mine_last_error() for this thread (runtime.cu).
 void set_last_error(const char *msg);
@@ -205,6 +228,7 @@ void set_last_error(const char *msg);
 // kernel identities for per-kernel timing
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
-                KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_COUNT = 11 };
+                KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_UNION = 11, KID_F1 = 12,
+                KID_COUNT = 13 };
 
 }  // namespace mine

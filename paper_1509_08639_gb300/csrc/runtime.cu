@@ -144,10 +144,11 @@ int add_settings(Plan &pl, const Setting *set, int n, int32_t S, int32_t T, int6
     return 0;
 }
 
-// settings_of(p) -> (pointer, count) of pair p's settings
+// settings_of(p) -> (pointer, count) of pair p's settings; swap: every
+// pair's two articles exchange roles (the target article is the source)
 template <class F>
 int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F settings_of,
-               int64_t max_abs_s, bool mined, const int8_t *align_tab = nullptr)
+               int64_t max_abs_s, bool mined, const int8_t *align_tab = nullptr, bool swap = false)
 {
     pl = Plan();
     pl.P = P;
@@ -169,6 +170,10 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         pp.S = doc_off[2 * p + 1] - pp.s0;
         pp.t0 = doc_off[2 * p + 1];
         pp.T = doc_off[2 * p + 2] - pp.t0;
+        if (swap) {   // mining in the other direction: the target article is the source
+            std::swap(pp.s0, pp.t0);
+            std::swap(pp.S, pp.T);
+        }
         const Setting *set;
         int n;
         settings_of(p, set, n);
@@ -1158,6 +1163,194 @@ int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     return MINE_OK;
 }
 
+int mine_run_batch_bidi(mine_ctx *ctx, const mine_dict *fwd, const mine_dict *bwd,
+                        const mine_batch *batch, const mine_settings *settings, mine_q16 *nw_fwd,
+                        mine_q16 *nw_bwd, int32_t *n_sel, int64_t *sel_off, mine_pair *sel,
+                        int64_t sel_cap)
+{
+    if (!ctx || !fwd || !bwd) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if ((rc = check_settings(settings))) return rc;
+    const int32_t P = batch->n_pairs;
+    const int n = settings->n;
+    if (P > 0 && (!nw_fwd || !nw_bwd || !n_sel || !sel_off)) return fail(MINE_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    ++ctx->arena_gen;
+    std::vector<Setting> set(n);
+    for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
+    auto all = [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; };
+    Plan pf, pb;
+    if ((rc = build_plan(pf, P, batch->doc_off, batch->n_sent, all, 65536, true, ctx->align_tab))) return rc;
+    if ((rc = build_plan(pb, P, batch->doc_off, batch->n_sent, all, 65536, true, ctx->align_tab, true)))
+        return rc;
+    pf.n_tok = pb.n_tok = batch->n_tok;
+    sel_off[0] = 0;
+    if (P == 0) return MINE_OK;
+    // one arena: the forward batch (with the inputs), the backward batch
+    // (reading the same inputs), then the union and its counts
+    const Layout Lf = make_layout(pf, fwd->d.kmax, true, true, true);
+    const Layout Lb = make_layout(pb, bwd->d.kmax, false, true, true);
+    const int64_t ob = align_up(Lf.total, 256);
+    const int64_t ou = ob + align_up(Lb.total, 256);
+    const int64_t on = ou + align_up(12 * 2 * pf.sel_cap + 16, 256);
+    if ((rc = ensure_dev(ctx->arena, on + 4 * (int64_t)pf.R + 16))) return rc;
+    const int64_t pb_at = align_up(Lf.plan_bytes, 64);
+    const int64_t ho_at = pb_at + align_up(Lb.plan_bytes, 64);
+    const int64_t out_bytes = 12 * (int64_t)pf.R + 16 + 24 * pf.sel_cap + 64;
+    if ((rc = ensure_host(ctx->pin, ho_at + out_bytes))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pf, Lf, hp);
+    pack_plan(pb, Lb, hp + pb_at);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + Lf.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + Lf.tokens);
+    CK(cudaMemcpyAsync(base + Lf.plan, hp, Lf.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(base + ob + Lb.plan, hp + pb_at, Lb.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    BatchDev bf = make_batchdev(pf, Lf, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    BatchDev bb = make_batchdev(pb, Lb, base + ob, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    if ((rc = enqueue_kernels(ctx, bf, fwd, batch->n_sent, batch->n_tok, true, st))) return rc;
+    if ((rc = enqueue_kernels(ctx, bb, bwd, batch->n_sent, batch->n_tok, true, st))) return rc;
+    UnionDev u;
+    u.fwd = bf.pairs;
+    u.bwd = bb.pairs;
+    u.n_pairs = P;
+    u.nset = n;
+    u.sel_f = bf.sel;
+    u.sel_b = bb.sel;
+    u.nsel_f = bf.n_sel;
+    u.nsel_b = bb.n_sel;
+    u.out = reinterpret_cast<int32_t *>(base + ou);
+    u.n_out = reinterpret_cast<int32_t *>(base + on);
+    ctx->launches += timed_launch(ctx, KID_UNION, st, [&] { return launch_union(u, ctx->num_sms, st); });
+    CK(cudaGetLastError());
+    char *ho = hp + ho_at;
+    int32_t *h_nwf = reinterpret_cast<int32_t *>(ho);
+    int32_t *h_nwb = h_nwf + pf.R;
+    int32_t *h_ns = h_nwb + pf.R;
+    int32_t *h_err = h_ns + pf.R;
+    int32_t *h_sel = h_err + 4;
+    CK(cudaMemcpyAsync(h_nwf, bf.nw_score, 4 * pf.R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_nwb, bb.nw_score, 4 * pf.R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_ns, u.n_out, 4 * pf.R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_err, bf.err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_err + 1, bb.err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_sel, u.out, 24 * pf.sel_cap, cudaMemcpyDeviceToHost, st));
+    ctx->h2d_bytes += Lf.plan_bytes + Lb.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
+    ctx->d2h_bytes += 12 * (int64_t)pf.R + 8 + 24 * pf.sel_cap;
+    CK(cudaStreamSynchronize(st));
+    if (h_err[0]) return fail(MINE_EINVAL, device_err_text(h_err[0]));
+    if (h_err[1]) return fail(MINE_EINVAL, device_err_text(h_err[1]));
+    int64_t tot = 0;
+    for (int32_t r = 0; r < pf.R; ++r) tot += h_ns[r];
+    if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
+    int64_t o = 0;
+    for (int32_t p = 0; p < P; ++p) {
+        const PairPlan &pp = pf.pairs[p];
+        const int64_t cap = std::min(pp.S, pp.T);
+        for (int k = 0; k < n; ++k) {
+            const int64_t r = (int64_t)p * n + k;
+            nw_fwd[r] = h_nwf[r];
+            nw_bwd[r] = h_nwb[r];
+            n_sel[r] = h_ns[r];
+            sel_off[r] = o;
+            std::memcpy(sel + o, h_sel + 3 * 2 * (pp.sel_base + k * cap), 12 * (size_t)h_ns[r]);
+            o += h_ns[r];
+        }
+    }
+    sel_off[(int64_t)P * n] = o;
+    return MINE_OK;
+}
+
+int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                 const mine_settings *settings, const int32_t *truth, int64_t *tp,
+                 int64_t *n_selected, int64_t *n_truth, int32_t *best)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if ((rc = check_settings(settings))) return rc;
+    const int32_t P = batch->n_pairs;
+    const int n = settings->n;
+    if (!tp || !n_selected || !n_truth || !best || (batch->n_sent > 0 && !truth))
+        return fail(MINE_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    ++ctx->arena_gen;
+    std::vector<Setting> set(n);
+    for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
+    Plan pl;
+    rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true,
+                    ctx->align_tab);
+    if (rc) return rc;
+    pl.n_tok = batch->n_tok;
+    // a known pair names a target sentence of its own pair (or -1)
+    for (const PairPlan &pp : pl.pairs)
+        for (int32_t i = 0; i < pp.S; ++i) {
+            const int32_t v = truth[pp.s0 + i];
+            if (v < -1 || v >= pp.T) return fail(MINE_EINVAL, "truth entry outside [-1, T) of its pair");
+        }
+    for (int k = 0; k < n; ++k) tp[k] = n_selected[k] = 0;
+    *n_truth = 0;
+    *best = 0;
+    if (P == 0) return MINE_OK;
+    const Layout L = make_layout(pl, dict->d.kmax, true, true, true);
+    const int64_t o_truth = align_up(L.total, 256);
+    const int64_t o_acc = o_truth + align_up(4 * batch->n_sent + 16, 256);
+    const int64_t acc_bytes = 8 * (2 * (int64_t)n + 1) + 16;
+    if ((rc = ensure_dev(ctx->arena, o_acc + acc_bytes))) return rc;
+    const int64_t ho_at = align_up(L.plan_bytes, 64);
+    if ((rc = ensure_host(ctx->pin, ho_at + acc_bytes + 64))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    int32_t *d_truth = reinterpret_cast<int32_t *>(base + o_truth);
+    unsigned long long *d_acc = reinterpret_cast<unsigned long long *>(base + o_acc);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_truth, truth, 4 * batch->n_sent, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d_acc, 0, acc_bytes, st));
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return rc;
+    F1Dev f;
+    f.pairs = b.pairs;
+    f.n_pairs = P;
+    f.nset = n;
+    f.sel = b.sel;
+    f.n_sel = b.n_sel;
+    f.truth = d_truth;
+    f.acc = d_acc;
+    f.best = reinterpret_cast<int32_t *>(d_acc + 2 * n + 1);
+    ctx->launches += timed_launch(ctx, KID_F1, st, [&] { return launch_f1(f, ctx->num_sms, st); });
+    CK(cudaGetLastError());
+    unsigned long long *h_acc = reinterpret_cast<unsigned long long *>(hp + ho_at);
+    int32_t *h_err = reinterpret_cast<int32_t *>(h_acc + 2 * n + 2);
+    CK(cudaMemcpyAsync(h_acc, d_acc, 8 * (2 * (int64_t)n + 2), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
+    ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok + 4 * batch->n_sent;
+    ctx->d2h_bytes += 8 * (2 * (int64_t)n + 2) + 4;
+    CK(cudaStreamSynchronize(st));
+    if (*h_err) return fail(MINE_EINVAL, device_err_text(*h_err));
+    for (int k = 0; k < n; ++k) {
+        tp[k] = (int64_t)h_acc[k];
+        n_selected[k] = (int64_t)h_acc[n + k];
+    }
+    *n_truth = (int64_t)h_acc[2 * n];
+    *best = *reinterpret_cast<const int32_t *>(h_acc + 2 * n + 1);
+    return MINE_OK;
+}
+
 int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
                           const int32_t *doc_off_host, const mine_settings *settings,
                           mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
@@ -1377,7 +1570,8 @@ const char *mine_kernel_name(int32_t id)
 {
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
-                                           "k_pairprep", "k_score_wide", "k_align_tiled"};
+                                           "k_pairprep", "k_score_wide", "k_align_tiled",
+                                           "k_union", "k_f1"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 

@@ -94,6 +94,10 @@ SIGNATURES = {
     "mine_autotune_batch": (_I, [_P, _P, ctypes.POINTER(BatchC)]),
     "mine_score_f32": (_I, [_P, _P, ctypes.POINTER(BatchC), _P, _L]),
     "mine_align_strategy": (_I, [_P, _P, _I, _I]),
+    "mine_run_batch_bidi": (_I, [_P, _P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P,
+                                 _P, _P, _P, _P, _L]),
+    "mine_tune_f1": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P, _P, _P,
+                          ctypes.POINTER(_L), ctypes.POINTER(_I)]),
 }
 
 ALIGN_BINS = 40
@@ -204,6 +208,59 @@ class Context:
         _check(self.L.mine_run_batch(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc),
                                      _ptr(nw), _ptr(ns), _ptr(off), _ptr(sel), cap), self.L)
         return unpack_results(P, n, nw, ns, off, sel)
+
+    def run_batch_bidi(self, fwd_h, bwd_h, batch, settings):
+        """Both directions; results[p][k] = (nw forward, nw backward, union [(i, j, s)])."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        P = (do.shape[0] - 1) // 2
+        n = len(settings)
+        g = _c32([s[0] for s in settings])
+        th = _c32([s[1] for s in settings])
+        bc = BatchC(P, so.shape[0] - 1, tk.shape[0], _ptr(do), _ptr(so), _ptr(tk))
+        sc = SettingsC(n, _ptr(g), _ptr(th))
+        cap = max(2 * int(self.L.mine_batch_capacity(_ptr(do), P, n)), 1)
+        nwf = np.zeros(P * n, np.int32)
+        nwb = np.zeros(P * n, np.int32)
+        ns = np.zeros(P * n, np.int32)
+        off = np.zeros(P * n + 1, np.int64)
+        sel = np.zeros((cap, 3), np.int32)
+        _check(self.L.mine_run_batch_bidi(self.h, fwd_h, bwd_h, ctypes.byref(bc), ctypes.byref(sc),
+                                          _ptr(nwf), _ptr(nwb), _ptr(ns), _ptr(off), _ptr(sel), cap),
+               self.L)
+        res = []
+        for p in range(P):
+            row = []
+            for k in range(n):
+                r = p * n + k
+                trip = sel[off[r]:off[r] + ns[r]]
+                row.append((int(nwf[r]), int(nwb[r]), [tuple(int(v) for v in t) for t in trip]))
+            res.append(row)
+        return res
+
+    def run_batch_bidi_raw(self, fwd_h, bwd_h, bc, sc, outs):
+        """Bidirectional host-buffer call with pre-built ctypes structs (benchmark path)."""
+        nwf, nwb, ns, off, sel, cap = outs
+        return _check(self.L.mine_run_batch_bidi(self.h, fwd_h, bwd_h, ctypes.byref(bc),
+                                                 ctypes.byref(sc), _ptr(nwf), _ptr(nwb), _ptr(ns),
+                                                 _ptr(off), _ptr(sel), cap), self.L)
+
+    def tune_f1(self, dict_h, batch, settings, truth):
+        """Tuning objective over the settings: (tp, n_selected, n_truth, best)."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        P = (do.shape[0] - 1) // 2
+        n = len(settings)
+        g = _c32([s[0] for s in settings])
+        th = _c32([s[1] for s in settings])
+        tr = _c32(truth)
+        bc = BatchC(P, so.shape[0] - 1, tk.shape[0], _ptr(do), _ptr(so), _ptr(tk))
+        sc = SettingsC(n, _ptr(g), _ptr(th))
+        tp = np.zeros(n, np.int64)
+        nsel = np.zeros(n, np.int64)
+        nt = ctypes.c_int64()
+        best = ctypes.c_int32()
+        _check(self.L.mine_tune_f1(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc), _ptr(tr),
+                                   _ptr(tp), _ptr(nsel), ctypes.byref(nt), ctypes.byref(best)), self.L)
+        return [int(v) for v in tp], [int(v) for v in nsel], int(nt.value), int(best.value)
 
     def run_batch_raw(self, dict_h, bc, sc, outs):
         """Host-buffer call with pre-built ctypes structs (benchmark path)."""

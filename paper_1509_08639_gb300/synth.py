@@ -416,6 +416,40 @@ def invert_dictionary(d: Dictionary) -> Dictionary:
     return Dictionary(keys.astype(np.int32), off.astype(np.int32), src.astype(np.int32))
 
 
+def reverse_dictionary(d: Dictionary, seed: int = 1519, p_drop: float = 0.2,
+                       p_add: float = 0.3) -> Dictionary:
+    """A target -> source dictionary of its own, standing in for a model
+    trained in the other direction: the inverse of ``d`` with each entry
+    dropped with probability p_drop and, per key with probability p_add, one
+    uniformly drawn source ID added (distinct per key, at most 32).  With the
+    exact inverse the score of a pair is the same in both directions (the two
+    coverage terms exchange roles), so mining the other way would find
+    nothing new."""
+    inv = invert_dictionary(d)
+    rng = np.random.default_rng(seed)
+    cnt = (inv.trans_off[1:] - inv.trans_off[:-1]).astype(np.int64)
+    key_of = np.repeat(np.arange(inv.n_keys, dtype=np.int64), cnt)
+    keep = rng.random(inv.trans.shape[0]) >= p_drop
+    src_vocab = int(d.keys.max()) + 1 if d.n_keys else 1
+    add = rng.random(inv.n_keys) < p_add
+    add_key = np.nonzero(add)[0].astype(np.int64)
+    add_val = rng.integers(0, src_vocab, size=add_key.shape[0])
+    k_all = np.concatenate([key_of[keep], add_key])
+    v_all = np.concatenate([inv.trans[keep].astype(np.int64), add_val])
+    order = np.lexsort((v_all, k_all))
+    k_all, v_all = k_all[order], v_all[order]
+    if k_all.shape[0]:
+        uniq = np.ones(k_all.shape[0], bool)
+        uniq[1:] = (k_all[1:] != k_all[:-1]) | (v_all[1:] != v_all[:-1])
+        k_all, v_all = k_all[uniq], v_all[uniq]
+    per = np.bincount(k_all, minlength=inv.n_keys)
+    if per.shape[0] and int(per.max()) > 32:
+        raise ValueError("a key would get more than 32 translations")
+    off = np.zeros(inv.n_keys + 1, np.int64)
+    np.cumsum(per, out=off[1:])
+    return Dictionary(inv.keys.copy(), off.astype(np.int32), v_all.astype(np.int32))
+
+
 def truth_of(batch: Batch, planted) -> np.ndarray:
     """int32[n_sent]: for source sentence k of pair p (global index
     doc_off[2p] + k) the planted target sentence (index in pair p's target

@@ -450,7 +450,32 @@ def test_bidi_hand_examples():
 
 def _small_bidi_workload(n_pairs=10):
     w = synth.workload(2, n_pairs=n_pairs)
-    return w, synth.invert_dictionary(w.dictionary)
+    return w, synth.reverse_dictionary(w.dictionary)
+
+
+def check_bidi_exact_inverse_transposes(m=O):
+    # with the exact inverse dictionary, a' = |U'_j ∩ X_i| counts the source
+    # tokens that hit V_j (= b) and b' counts the target tokens some source
+    # token translates to (= a), while m' = n_i and n' = m_j: the two coverage
+    # terms exchange roles and the backward matrix is the transpose
+    w = synth.workload(2, n_pairs=6)
+    inv = synth.invert_dictionary(w.dictionary)
+    of, ob = m.OracleDict(w.dictionary), m.OracleDict(inv)
+    sb = m.swap_roles(w.batch)
+    so, do = np.asarray(sb.sent_off), np.asarray(sb.doc_off)
+    for p in range(w.batch.n_pairs):
+        Mf = m.score_matrix(of, *w.batch.pair(p))
+        src = (so[do[2 * p]:do[2 * p + 1] + 1] - so[do[2 * p]], sb.tokens[so[do[2 * p]]:so[do[2 * p + 1]]])
+        tgt = (so[do[2 * p + 1]:do[2 * p + 2] + 1] - so[do[2 * p + 1]],
+               sb.tokens[so[do[2 * p + 1]]:so[do[2 * p + 2]]])
+        Mb = m.score_matrix(ob, src, tgt)
+        assert np.array_equal(Mb, Mf.T), p
+    r = m.mine_batch_bidi(of, ob, w.batch, [(-65536, 32768)])
+    assert all(row[0][0] == row[0][1] for row in r)
+
+
+def test_bidi_exact_inverse_transposes():
+    check_bidi_exact_inverse_transposes()
 
 
 def check_bidi_identities(m=O):
@@ -578,7 +603,7 @@ _PY_MUTANTS = {
 def _run_py_pins(m):
     failed = []
     for c in (check_bidi_hand_examples, check_bidi_identities, check_bidi_special_cases,
-              check_f1_hand_example, check_f1_closed_forms):
+              check_bidi_exact_inverse_transposes, check_f1_hand_example, check_f1_closed_forms):
         try:
             c(m)
         except (AssertionError, ZeroDivisionError, IndexError, KeyError):
