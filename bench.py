@@ -542,13 +542,14 @@ def main():
     alu_peak_tops = 152 * 128 * sm_mhz_max * 1e6 / 1e12           # int32 lane-ops/s
     rl = {}
     # each stage's time covers all of its launches: the two preparation
-    # launches (one region), the score launches for small and wide target
+    # launches (small and wide target articles), the score launches for small and wide target
     # articles, and the alignments of one CTA or warp and of many CTAs
-    stage_extra = {"k_score": "k_score_wide", "k_align": "k_align_tiled"}
+    stage_extra = {"k_pairprep": ("k_pairprep_wide",), "k_score": ("k_score_wide",),
+                   "k_align": ("k_align_tiled",)}
     for k in ("k_pairprep", "k_score", "k_align"):
         if k not in per_launch_ms:
             continue
-        t = (per_launch_ms[k] + per_launch_ms.get(stage_extra.get(k), 0.0)) / 1e3
+        t = (per_launch_ms[k] + sum(per_launch_ms.get(x, 0.0) for x in stage_extra[k])) / 1e3
         if k == "k_pairprep":
             a = prep_bytes / t / 1e9
             rl[k] = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
@@ -565,8 +566,12 @@ def main():
                      "frac": a / alu_peak_tops, "traffic": committed_traffic(k),
                      "algorithmic_ops": align_ops, "ms": t * 1e3,
                      "gcups": cells * n_gap / t / 1e9}
+    if rl:   # the stage of the longest device time
+        dom = max(rl, key=lambda k: rl[k]["ms"])
     roof = dict(rl.get(dom, {}))
     roof["kernel"] = dom
+    if dom in stage_extra:
+        roof["launches"] = [x for x in stage_extra[dom] if x in per_launch_ms] + [dom]
     roof["peak_kind"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if roof.get("bound") == "hbm" \
         else "derived: 152 SMs x 128 int32 lanes x max SM clock"
 

@@ -61,7 +61,14 @@ struct DevDict {
     int32_t log2;
     int32_t kmax;       // largest translation count of any key
     int64_t n_trans;
+    // The same keys with their first kInlineTrans translations inline:
+    // 64-byte buckets of two 32-byte entries (key, off << 6 | cnt, t0..t5),
+    // bucket = key * 0x9E3779B1 >> (32 - inl_log2), overflow into the next
+    // bucket; empty key = -1.  One bucket read gives a key's translations.
+    int4 *inl;          // [4 << inl_log2]
+    int32_t inl_log2;
 };
+constexpr int kInlineTrans = 6;
 
 struct PairPlan {       // 48 bytes
     int32_t s0, S;      // source sentences [s0, s0+S) (global sentence index)
@@ -210,6 +217,7 @@ int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_k
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
                     cudaStream_t st);
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);        // small articles
@@ -229,6 +237,6 @@ void set_last_error(const char *msg);
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
                 KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_UNION = 11, KID_F1 = 12,
-                KID_COUNT = 13 };
+                KID_DOC_WIDE = 13, KID_COUNT = 14 };
 
 }  // namespace mine

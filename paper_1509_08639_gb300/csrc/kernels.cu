@@ -192,6 +192,54 @@ __device__ __forceinline__ int2 dict_find(const DevDict &d, int32_t key)
     }
 }
 
+// Inline table: the bucket of `key` and, from its 64 loaded bytes, the
+// entry holding it (0 or 1), -1 when the key is absent, or -2 when the bucket
+// is full without it (the search goes on in the next bucket).
+__device__ __forceinline__ uint32_t inl_bucket(const DevDict &d, int32_t key)
+{
+    return hmul(key) >> (32 - d.inl_log2);
+}
+
+__device__ __forceinline__ void inl_load(const DevDict &d, uint32_t bk, int4 (&q)[4])
+{
+    const int4 *p = d.inl + 4 * (size_t)bk;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = __ldg(p + i);
+}
+
+__device__ __forceinline__ int inl_match(const int4 (&q)[4], int32_t key)
+{
+    if (q[0].x == key) return 0;
+    if (q[2].x == key) return 1;
+    return q[2].x == -1 ? -1 : -2;
+}
+
+// (off, cnt) and the first four translations of `key` (0 past cnt) from its
+// bucket chain in the inline table; cnt = 0 when the key is absent.
+__device__ __forceinline__ int2 inl_find(const DevDict &d, int32_t key, int32_t (&u)[4])
+{
+    const uint32_t nbm = (1u << d.inl_log2) - 1u;
+    uint32_t bk = inl_bucket(d, key);
+    for (;;) {   // ends: the table is at most half full
+        int4 q[4];
+        inl_load(d, bk, q);
+        const int e = inl_match(q, key);
+        if (e != -2) {
+            if (e < 0) {
+                u[0] = u[1] = u[2] = u[3] = 0;
+                return make_int2(0, 0);
+            }
+            const int4 h = q[2 * e], t = q[2 * e + 1];
+            u[0] = h.z;
+            u[1] = h.w;
+            u[2] = t.x;
+            u[3] = t.y;
+            return make_int2((int32_t)((uint32_t)h.y >> 6), h.y & 63);
+        }
+        bk = (bk + 1) & nbm;
+    }
+}
+
 __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__restrict__ trans_off,
                              int32_t n_keys, DevDict d, int32_t *err)
 {
@@ -219,6 +267,24 @@ __global__ void k_dict_build(const int32_t *__restrict__ keys, const int32_t *__
                 }
             }
             bk = (bk + 1) & nbm;
+        }
+        // the inline table (a repeated key was reported above)
+        const uint32_t ibm = (1u << d.inl_log2) - 1u;
+        uint32_t ib = inl_bucket(d, key);
+        done = false;
+        for (uint32_t probe = 0; probe <= ibm && !done; ++probe) {
+            for (int e = 0; e < 2 && !done; ++e) {
+                int32_t *ent = reinterpret_cast<int32_t *>(d.inl + 4 * (size_t)ib + 2 * e);
+                const int32_t old = atomicCAS(ent, -1, key);
+                if (old == -1) {
+                    ent[1] = (int32_t)(((uint32_t)off << 6) | (uint32_t)cnt);
+                    for (int t = 0; t < kInlineTrans; ++t) ent[2 + t] = t < cnt ? d.trans[off + t] : 0;
+                    done = true;
+                } else if (old == key) {
+                    done = true;
+                }
+            }
+            ib = (ib + 1) & ibm;
         }
     }
 }
@@ -574,22 +640,21 @@ __device__ __forceinline__ int doc_id(const SM &sm, int lg, int32_t tok)
     }
 }
 
+// Insert target token `tok`; true when this call added it (the caller
+// counts the additions, one atomic per warp).
 template <class SM>
-__device__ __forceinline__ void doc_insert(SM &sm, int lg, int32_t tok)
+__device__ __forceinline__ bool doc_insert(SM &sm, int lg, int32_t tok)
 {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h = hmul(tok) >> (32 - lg);
     volatile int32_t *key = sm.key;
     for (;;) {
         const int32_t k = key[h];
-        if (k == tok) return;
+        if (k == tok) return false;
         if (k == -1) {
             const int32_t old = atomicCAS(&sm.key[h], -1, tok);
-            if (old == -1) {
-                atomicAdd(&sm.nd, 1);
-                return;
-            }
-            if (old == tok) return;
+            if (old == -1) return true;
+            if (old == tok) return false;
         }
         h = (h + 1) & mask;
     }
@@ -712,16 +777,8 @@ __device__ void prep_row_short(const BatchDev &b, const DevDict &d, const SM &sm
         const bool v = k < n;
         const int32_t key = v ? cb[k] : 0;
         int2 oc = make_int2(0, 0);
-        if (v) {
-            int4 q[4];
-            dict_load(d, dict_bucket(d, key), q);
-            bool more;
-            oc = dict_match(q, key, more);
-            if (more) oc = dict_find(d, key);
-        }
-        int32_t u[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) u[q] = q < oc.y ? __ldg(&d.trans[oc.x + q]) : 0;
+        int32_t u[4] = {0, 0, 0, 0};
+        if (v) oc = inl_find(d, key, u);
         emit_kept(b, d, sm, lg, u, oc, seen, el, out, nf, lane);
     }
     nf = (int)__reduce_add_sync(kFull, (unsigned)nf);
@@ -756,10 +813,9 @@ __device__ void prep_row_long(const BatchDev &b, const DevDict &d, const SM &sm,
         }
         const bool isnew = valid && rset_insert(gset, 11, tok, stamp);
         n_i += __popc(__ballot_sync(kFull, isnew));
-        const int2 oc = isnew ? dict_find(d, tok) : make_int2(0, 0);
-        int32_t u[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) u[q] = q < oc.y ? __ldg(&d.trans[oc.x + q]) : 0;
+        int2 oc = make_int2(0, 0);
+        int32_t u[4] = {0, 0, 0, 0};
+        if (isnew) oc = inl_find(d, tok, u);
         emit_kept(b, d, sm, lg, u, oc, seen, el, out, nf, lane);
     }
     nf = (int)__reduce_add_sync(kFull, (unsigned)nf);
@@ -813,25 +869,32 @@ k_pairprep(BatchDev b, DevDict d)
         int4 *kz = reinterpret_cast<int4 *>(sm.key);
         for (int k = tid; k < NS / 4; k += kPPThreads) kz[k] = make_int4(-1, -1, -1, -1);
         __syncthreads();
-        // 1. distinct target tokens; four loads in flight per thread; stops
-        //    once they cannot all get ids
-        for (int32_t k = ta + tid; k < tb; k += 4 * kPPThreads) {
-            if (*(volatile int32_t *)&sm.nd > kDirect) break;
+        // 1. distinct target tokens; four loads in flight per thread; the
+        //    warp adds its new tokens to the count at once; a wide article
+        //    stops once its tokens cannot all get ids (before its table fills:
+        //    at most 4 kPPThreads more insertions than kDirect < SLOTS)
+        static_assert(SMALL || kDirect + 4 * kPPThreads < SLOTS, "table of a wide article");
+        for (int32_t kw = ta + (tid & ~31); kw < tb; kw += 4 * kPPThreads) {   // warp-uniform
+            if (!SMALL && __shfl_sync(kFull, *(volatile int32_t *)&sm.nd, 0) > kDirect) break;
+            const int32_t k = kw + lane;
             int32_t tk[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int32_t kk = k + q * kPPThreads;
                 tk[q] = kk < tb ? b.tokens[kk] : -1;
             }
+            unsigned added = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (k + q * kPPThreads >= tb) break;
-                if ((uint32_t)tk[q] > ELEM_TOKEN) {
-                    atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    continue;
+                if (k + q * kPPThreads < tb) {
+                    if ((uint32_t)tk[q] > ELEM_TOKEN)
+                        atomicCAS(b.err, 0, ERR_BAD_TOKEN);
+                    else
+                        added += doc_insert(sm, lg, tk[q]) ? 1u : 0u;
                 }
-                doc_insert(sm, lg, tk[q]);
             }
+            added = __reduce_add_sync(kFull, added);
+            if (lane == 0 && added) atomicAdd(&sm.nd, (int)added);
         }
         __syncthreads();
         const int D = sm.nd;
@@ -2205,12 +2268,18 @@ int launch_pairprep_one(const BatchDev &b, const DevDict &d, int num_sms, cudaSt
     return 1;
 }
 
+static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 4 <= kGScratchWarpsPerSm, "per-warp global tables");
+
+int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
+{
+    if (b.n_pairs <= 0) return 0;
+    return launch_pairprep_one<16, 2 * kDirect, 2, false>(b, d, num_sms, st);
+}
+
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 4 <= kGScratchWarpsPerSm, "per-warp global tables");
-    return launch_pairprep_one<16, 2 * kDirect, 2, false>(b, d, num_sms, st) +
-           launch_pairprep_one<8, 2 * kSmallArticleTok, 4, true>(b, d, num_sms, st);
+    return launch_pairprep_one<8, 2 * kSmallArticleTok, 4, true>(b, d, num_sms, st);
 }
 
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)

@@ -586,6 +586,7 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
         BatchDev bd = b;
         bd.kmax = dict->d.kmax;
+        n += timed_launch(ctx, KID_DOC_WIDE, st, [&] { return launch_pairprep_wide(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_DOC, st, [&] { return launch_pairprep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
@@ -952,12 +953,16 @@ int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_of
     d->d.kmax = kmax;
     d->d.n_trans = n_trans;
     const size_t slots_bytes = sizeof(int2) << d->d.log2;
-    CK(cudaMalloc(&d->slots_mem, slots_bytes));
+    // inline table: two entries per 64-byte bucket, at most half of them used
+    d->d.inl_log2 = std::max(4, ceil_log2_host((int64_t)n_keys));
+    const size_t inl_bytes = (size_t)64 << d->d.inl_log2;
+    CK(cudaMalloc(&d->slots_mem, slots_bytes + inl_bytes));
     CK(cudaMalloc(&d->trans_mem, 4 * (size_t)std::max<int64_t>(n_trans, 1)));
     d->d.slots = static_cast<int2 *>(d->slots_mem);
+    d->d.inl = reinterpret_cast<int4 *>(static_cast<char *>(d->slots_mem) + slots_bytes);
     d->d.trans = static_cast<int32_t *>(d->trans_mem);
     cudaStream_t st = ctx->stream;
-    CK(cudaMemsetAsync(d->slots_mem, 0xff, slots_bytes, st));
+    CK(cudaMemsetAsync(d->slots_mem, 0xff, slots_bytes + inl_bytes, st));
     if (n_trans > 0) CK(cudaMemcpyAsync(d->trans_mem, trans, 4 * n_trans, cudaMemcpyHostToDevice, st));
     if (n_keys > 0) {
         void *tmp = nullptr;
@@ -1571,7 +1576,7 @@ const char *mine_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
                                            "k_pairprep", "k_score_wide", "k_align_tiled",
-                                           "k_union", "k_f1"};
+                                           "k_union", "k_f1", "k_pairprep_wide"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
