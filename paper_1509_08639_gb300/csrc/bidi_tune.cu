@@ -54,6 +54,8 @@ __device__ __forceinline__ int keys_below(const int32_t *L, int n, uint32_t x)
 // larger of the two scores.
 __global__ void __launch_bounds__(256) k_union(UnionDev u)
 {
+    // the selections of a batch whose alignment stopped are not written
+    if (*(volatile const int32_t *)u.err_f || *(volatile const int32_t *)u.err_b) return;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const int64_t rows = (int64_t)u.n_pairs * u.nset;
@@ -129,6 +131,7 @@ constexpr int kMaxSettings = 256;
 __global__ void __launch_bounds__(256) k_f1(F1Dev f)
 {
     __shared__ unsigned long long acc[2 * kMaxSettings + 1];
+    if (*(volatile const int32_t *)f.err) return;   // selections not written
     const int lane = threadIdx.x & 31;
     const int nacc = 2 * f.nset + 1;
     for (int q = threadIdx.x; q < nacc; q += blockDim.x) acc[q] = 0ull;
@@ -177,6 +180,7 @@ __device__ __forceinline__ bool f1_better(const F1Frac &a, const F1Frac &b)
 // One warp: the setting of highest F1, the lowest index among equals.
 __global__ void __launch_bounds__(32) k_f1_best(F1Dev f)
 {
+    if (*(volatile const int32_t *)f.err) return;
     const int lane = threadIdx.x;
     const unsigned long long known = f.acc[2 * f.nset];
     F1Frac best{0ull, 1ull, 1 << 30};

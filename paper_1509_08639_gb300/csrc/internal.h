@@ -181,8 +181,7 @@ inline int align_kind(const int8_t *tab, int32_t S, int32_t T)
 {
     const int64_t c = (int64_t)S * T;
     const bool can_tile = S > kAlignTileRows && T > kAlignTileCols;
-    int bin = 0;
-    while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
+    const int bin = c > 0 ? 64 - __builtin_clzll((unsigned long long)c) : 0;   // 2^bin > c
     int v = (tab && bin < kAlignBins) ? tab[bin] : -1;
     if (v < 0) v = (can_tile && c >= kTiledCells) ? 2 : (c >= kBigCells ? 1 : 0);
     if (v == 2 && !can_tile) v = 1;
@@ -199,6 +198,7 @@ struct UnionDev {
     const int32_t *nsel_f, *nsel_b;  // their counts, row set0 + k of each plan
     int32_t *out;                    // row (p, k) at 2 (sel_base + k min(S,T)) triples
     int32_t *n_out;                  // [rows of the forward plan]
+    const int32_t *err_f, *err_b;    // error words of the two batches (nothing is done if set)
 };
 
 // Tuning objective: true positives and sizes of the selections per setting.
@@ -209,6 +209,7 @@ struct F1Dev {
     const int32_t *truth;            // [n_sent] known target sentence of a source sentence, or -1
     unsigned long long *acc;         // [2 nset + 1]: tp per setting, selected per setting, known
     int32_t *best;                   // [1]
+    const int32_t *err;              // error word of the batch (nothing is done if set)
 };
 
 // launchers (kernels.cu, bidi_tune.cu); each returns the number of kernels launched
@@ -228,6 +229,9 @@ int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_tile(const int32_t *src, int32_t S, int32_t T, int32_t *dst, cudaStream_t st);
 int launch_fill_scores(int32_t *M, int64_t n, uint32_t seed, cudaStream_t st);
 int launch_union(const UnionDev &u, int num_sms, cudaStream_t st);
+// packed outputs of the host call: rows r = p n + k, offsets off[0..R], triples in out
+int launch_pack(const BatchDev &b, int32_t n, int32_t R, int32_t *bsum, int64_t *off, int32_t *out,
+                cudaStream_t st);
 int launch_f1(const F1Dev &f, int num_sms, cudaStream_t st);
 
 // Record the text returned by mine_last_error() for this thread (runtime.cu).
@@ -237,6 +241,6 @@ void set_last_error(const char *msg);
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
                 KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_UNION = 11, KID_F1 = 12,
-                KID_DOC_WIDE = 13, KID_COUNT = 14 };
+                KID_DOC_WIDE = 13, KID_PACK = 14, KID_COUNT = 15 };
 
 }  // namespace mine

@@ -2351,6 +2351,106 @@ int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st)
     return 1;
 }
 
+// Outputs of a batch in the host call's packed form: row r = p n + k (n
+// settings per pair) has its n_sel[r] selected triples at off[r] of `out`,
+// off[R] = their total.  Two passes over blocks of 1024 rows: the sums per
+// block, then each block's offsets (after the blocks before it) and the copy
+// of its rows' triples, one warp per row.  Nothing is done after a device
+// error: the counts of a batch whose alignment stopped are not written.
+constexpr int kPackBlock = 1024;
+
+__global__ void __launch_bounds__(kPackBlock) k_pack_sums(const int32_t *__restrict__ n_sel, int32_t R,
+                                                          int32_t *__restrict__ bsum, const int32_t *err)
+{
+    __shared__ int part[kPackBlock / 32];
+    if (*(volatile const int32_t *)err) return;
+    const int r = blockIdx.x * kPackBlock + threadIdx.x;
+    const int v = r < R ? n_sel[r] : 0;
+    const int w = (int)__reduce_add_sync(kFull, (unsigned)v);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int t = (int)__reduce_add_sync(kFull, (unsigned)part[threadIdx.x]);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kPackBlock) k_pack_place(BatchDev b, int32_t n, int32_t R,
+                                                           const int32_t *__restrict__ bsum,
+                                                           int64_t *__restrict__ off, int32_t *__restrict__ out)
+{
+    __shared__ int wsum[32];
+    __shared__ int64_t base;
+    __shared__ int64_t roff[kPackBlock];
+    if (*(volatile const int32_t *)b.err) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (w == 0) {
+        int64_t before = 0, all = 0;
+        const int nblk = (R + kPackBlock - 1) / kPackBlock;
+        for (int c = lane; c < nblk; c += 32) {
+            const int64_t v = bsum[c];
+            all += v;
+            if (c < (int)blockIdx.x) before += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(kFull, before, o);
+            all += __shfl_xor_sync(kFull, all, o);
+        }
+        if (lane == 0) {
+            base = before;
+            if (blockIdx.x == gridDim.x - 1) off[R] = all;
+        }
+    }
+    const int r = blockIdx.x * kPackBlock + tid;
+    const int v = r < R ? b.n_sel[r] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int x = wsum[lane];
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, xi, o);
+            if (lane >= o) xi += y;
+        }
+        wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    const int64_t o = base + wsum[w] + incl - v;
+    roff[tid] = o;
+    if (r < R) off[r] = o;
+    __syncthreads();
+    // copy the triples of the block's rows, one warp per row
+    const int rows = min(kPackBlock, R - (int)blockIdx.x * kPackBlock);
+    for (int q = w; q < rows; q += kPackBlock / 32) {
+        const int rr = blockIdx.x * kPackBlock + q;
+        const int p = rr / n, k = rr - p * n;
+        const PairPlan pp = b.pairs[p];
+        const int64_t cap = min(pp.S, pp.T);
+        const int cnt = b.n_sel[rr];
+        const int32_t *src = b.sel + 3 * (pp.sel_base + k * cap);
+        int32_t *dst = out + 3 * roff[q];
+        for (int e = lane; e < 3 * cnt; e += 32) dst[e] = src[e];
+    }
+}
+
+int launch_pack(const BatchDev &b, int32_t n, int32_t R, int32_t *bsum, int64_t *off, int32_t *out,
+                cudaStream_t st)
+{
+    if (R <= 0) return 0;
+    const int nblk = (R + kPackBlock - 1) / kPackBlock;
+    k_pack_sums<<<nblk, kPackBlock, 0, st>>>(b.n_sel, R, bsum, b.err);
+    k_pack_place<<<nblk, kPackBlock, 0, st>>>(b, n, R, bsum, off, out);
+    return 2;
+}
+
 // Random scores in [0, 65536) for timing (a multiplicative hash of the index).
 __global__ void k_fill_scores(int32_t *__restrict__ M, int64_t n, uint32_t seed)
 {

@@ -43,9 +43,7 @@ int fail(int code, const std::string &msg)
 
 int ceil_log2_host(int64_t x)
 {
-    int l = 0;
-    while ((int64_t(1) << l) < x) ++l;
-    return l;
+    return x <= 1 ? 0 : 64 - __builtin_clzll((unsigned long long)(x - 1));
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -164,6 +162,8 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         return fail(MINE_EINVAL, "doc_off[2P] must equal n_sent");
     pl.pairs.resize(P);
     std::vector<int> bucketS(P), bucketC(P), bucketD(P);
+    std::vector<int8_t> kind(P);
+    int64_t n_pitems = 0, n_sitems = 0;
     for (int32_t p = 0; p < P; ++p) {
         PairPlan &pp = pl.pairs[p];
         pp.s0 = doc_off[2 * p];
@@ -189,7 +189,12 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         bucketS[p] = ceil_log2_host((int64_t)pp.T + 1);
         bucketC[p] = ceil_log2_host((int64_t)pp.S * pp.T + 1);
         bucketD[p] = ceil_log2_host((int64_t)pp.S + pp.T + 1);
+        kind[p] = (int8_t)align_kind(align_tab, pp.S, pp.T);
+        n_pitems += (pp.S + 31) / 32;
+        n_sitems += (int64_t)((pp.S + 63) / 64) * ((std::max(pp.T, 1) + kScoreColChunk - 1) / kScoreColChunk);
     }
+    pl.pitems.reserve(n_pitems);
+    pl.sitems.reserve(n_sitems);
     // longest-first orders (counting sort on the bit length of the work)
     auto order_by = [&](const std::vector<int> &key) {
         std::vector<int> cnt(66, 0), ord(P);
@@ -212,10 +217,13 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
     const int kind_of_pass[3] = {1, 0, 2};
     std::vector<TileItem> tl;
     std::vector<int32_t> tdiag;
+    int64_t n_items = 0;
+    for (int p = 0; p < P; ++p) n_items += pl.pairs[p].ngap;
+    pl.nitems.reserve(n_items);
     for (int pass = 0; pass < 3; ++pass) {
         for (int p : ord) {
             const PairPlan &pp = pl.pairs[p];
-            if (align_kind(align_tab, pp.S, pp.T) != kind_of_pass[pass]) continue;
+            if (kind[p] != kind_of_pass[pass]) continue;
             const int64_t CW = (pp.T + 15) >> 4;
             for (int g = 0; g < pp.ngap; ++g) {
                 NwItem it;
@@ -478,6 +486,7 @@ struct mine_ctx {
     cudaStream_t stream = nullptr;
     std::mutex api_mu;                 // synchronous calls
     DevBuf arena;                      // scratch of the synchronous calls
+    DevBuf inbuf;                      // inputs of the host-buffer batch call
     HostBuf pin;                       // staging of the synchronous calls
     std::atomic<int64_t> launches{0};
     std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // synchronous host-buffer calls
@@ -1055,62 +1064,66 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     if ((rc = set_device(ctx))) return rc;
     ++ctx->arena_gen;
+    cudaStream_t st = ctx->stream;
+    sel_off[0] = 0;
+    if (P == 0) return MINE_OK;
+    // the inputs go first, into their own buffer: their copy overlaps the
+    // planning below
+    const int64_t in_tok_at = align_up(4 * (batch->n_sent + 1), 256);
+    if ((rc = ensure_dev(ctx->inbuf, in_tok_at + 4 * batch->n_tok + 16))) return rc;
+    int32_t *d_sent = static_cast<int32_t *>(ctx->inbuf.p);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(static_cast<char *>(ctx->inbuf.p) + in_tok_at);
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    // from here on a failure waits for those copies (the caller may free the
+    // inputs once the call returns)
+    auto bail = [&](int code) {
+        cudaStreamSynchronize(st);
+        return code;
+    };
     std::vector<Setting> set(n);
     for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
     Plan pl;
     rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
                     [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true,
                     ctx->align_tab);
-    if (rc) return rc;
+    if (rc) return bail(rc);
     pl.n_tok = batch->n_tok;
-    sel_off[0] = 0;
-    if (P == 0) return MINE_OK;
-    const Layout L = make_layout(pl, dict->d.kmax, true, true, true);
-    if ((rc = ensure_dev(ctx->arena, L.total))) return rc;
-    const int64_t out_bytes = 8 * (int64_t)pl.R + 12 * pl.sel_cap + 64;
-    if ((rc = ensure_host(ctx->pin, L.plan_bytes + out_bytes))) return rc;
+    const int32_t R = pl.R;
+    Layout L = make_layout(pl, dict->d.kmax, false, true, true);
+    // packed outputs: offsets, triples, block sums
+    const int64_t o_off = align_up(L.total, 256);
+    const int64_t o_pk = o_off + align_up(8 * ((int64_t)R + 1), 256);
+    const int64_t o_bs = o_pk + align_up(12 * pl.sel_cap + 16, 256);
+    const int64_t total = o_bs + 4 * ((int64_t)R / 1024 + 1) + 16;
+    if ((rc = ensure_dev(ctx->arena, total))) return bail(rc);
+    if ((rc = ensure_host(ctx->pin, L.plan_bytes + 64))) return bail(rc);
     char *hp = static_cast<char *>(ctx->pin.p);
     pack_plan(pl, L, hp);
     char *base = static_cast<char *>(ctx->arena.p);
-    cudaStream_t st = ctx->stream;
-    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
-    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
     CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
-    if (batch->n_tok > 0)
-        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return rc;
-    char *ho = hp + align_up(L.plan_bytes, 64);
-    int32_t *h_nw = reinterpret_cast<int32_t *>(ho);
-    int32_t *h_ns = h_nw + pl.R;
-    int32_t *h_err = h_ns + pl.R;
-    int32_t *h_sel = h_err + 4;
-    CK(cudaMemcpyAsync(h_nw, b.nw_score, 4 * pl.R, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_ns, b.n_sel, 4 * pl.R, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_sel, b.sel, 12 * pl.sel_cap, cudaMemcpyDeviceToHost, st));
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return bail(rc);
+    int64_t *d_off = reinterpret_cast<int64_t *>(base + o_off);
+    int32_t *d_pk = reinterpret_cast<int32_t *>(base + o_pk);
+    int32_t *d_bs = reinterpret_cast<int32_t *>(base + o_bs);
+    ctx->launches += timed_launch(ctx, KID_PACK, st, [&] { return launch_pack(b, n, R, d_bs, d_off, d_pk, st); });
+    CK(cudaGetLastError());
+    // results straight into the caller's arrays
+    int32_t h_err = 0;
+    const int64_t cp = std::min(sel_cap, pl.sel_cap);
+    CK(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, st));
+    if (cp > 0 && sel) CK(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
     ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
-    ctx->d2h_bytes += 8 * (int64_t)pl.R + 4 + 12 * pl.sel_cap;
+    ctx->d2h_bytes += 8 * (int64_t)R + 8 * ((int64_t)R + 1) + 4 + (sel ? 12 * cp : 0);
     CK(cudaStreamSynchronize(st));
-    if (*h_err) return fail(MINE_EINVAL, device_err_text(*h_err));
-    int64_t tot = 0;
-    for (int32_t r = 0; r < pl.R; ++r) tot += h_ns[r];
+    if (h_err) return fail(MINE_EINVAL, device_err_text(h_err));
+    const int64_t tot = sel_off[R];
     if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
-    int64_t o = 0;
-    for (int32_t p = 0; p < P; ++p) {
-        const PairPlan &pp = pl.pairs[p];
-        const int64_t cap = std::min(pp.S, pp.T);
-        for (int k = 0; k < n; ++k) {
-            const int64_t r = (int64_t)p * n + k;
-            nw_score[r] = h_nw[r];
-            n_sel[r] = h_ns[r];
-            sel_off[r] = o;
-            std::memcpy(sel + o, h_sel + 3 * (pp.sel_base + k * cap), 12 * (size_t)h_ns[r]);
-            o += h_ns[r];
-        }
-    }
-    sel_off[(int64_t)P * n] = o;
     return MINE_OK;
 }
 
@@ -1232,6 +1245,8 @@ int mine_run_batch_bidi(mine_ctx *ctx, const mine_dict *fwd, const mine_dict *bw
     u.nsel_b = bb.n_sel;
     u.out = reinterpret_cast<int32_t *>(base + ou);
     u.n_out = reinterpret_cast<int32_t *>(base + on);
+    u.err_f = bf.err;
+    u.err_b = bb.err;
     ctx->launches += timed_launch(ctx, KID_UNION, st, [&] { return launch_union(u, ctx->num_sms, st); });
     CK(cudaGetLastError());
     char *ho = hp + ho_at;
@@ -1337,6 +1352,7 @@ int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
     f.truth = d_truth;
     f.acc = d_acc;
     f.best = reinterpret_cast<int32_t *>(d_acc + 2 * n + 1);
+    f.err = b.err;
     ctx->launches += timed_launch(ctx, KID_F1, st, [&] { return launch_f1(f, ctx->num_sms, st); });
     CK(cudaGetLastError());
     unsigned long long *h_acc = reinterpret_cast<unsigned long long *>(hp + ho_at);
@@ -1576,7 +1592,7 @@ const char *mine_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
                                            "k_pairprep", "k_score_wide", "k_align_tiled",
-                                           "k_union", "k_f1", "k_pairprep_wide"};
+                                           "k_union", "k_f1", "k_pairprep_wide", "k_pack"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 
