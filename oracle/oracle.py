@@ -6,8 +6,9 @@ may import this module.  It loads ``mine_oracle.c`` (compiled by
 recurrence: a brute-force enumerator of every monotone alignment (the paper's
 "paths cannot go upward or leftward", Section 4) and the canonical-path rule,
 used to pin the oracle's dynamic programme on tiny inputs.  Bidirectional
-mining (the union of the two directions' selections) and the tuning
-objective (F1 against known translation pairs) are plain Python as well.
+mining (the union of the two directions' selections), the tuning objective
+(F1 against known translation pairs) and the contrast without the path
+constraint (each source sentence's best target) are plain Python as well.
 
 Parity pins for every function here live in ``tests/test_oracle_pins.py``.
 """
@@ -297,6 +298,53 @@ def best_setting(tp, nsel, n_truth) -> int:
         if f1[k] > f1[best]:
             best = k
     return best
+
+
+# ---------------------------------------------------------------------------
+# contrast without the path constraint (Section 4: Yalign's A* search is not
+# kept from going upward or leftward, so sentences can be matched again)
+# ---------------------------------------------------------------------------
+
+def best_match(M, theta):
+    """Alignment without the constraint that paths cannot go upward or
+    leftward, in its limit: a path may come back to any target sentence, so
+    every source sentence i takes its best-scoring target j (the lowest j
+    among equal scores), kept when s(i, j) > theta.
+
+    Returns ([(i, j, s)] by increasing i, the number of target sentences
+    taken by more than one source sentence)."""
+    M = np.asarray(M)
+    S = M.shape[0]
+    sel = []
+    for i in range(S):
+        if M.shape[1] == 0:
+            break
+        row = [int(v) for v in M[i]]
+        j = 0
+        for c in range(1, len(row)):
+            if row[c] > row[j]:
+                j = c
+        if row[j] > theta:
+            sel.append((i, j, row[j]))
+    taken = {}
+    for _, j, _ in sel:
+        taken[j] = taken.get(j, 0) + 1
+    return sel, sum(1 for c in taken.values() if c > 1)
+
+
+def best_match_batch(od: OracleDict, batch, theta):
+    """best_match of every pair's score matrix: [(selection, repeated)]."""
+    out = []
+    for p in range(batch.n_pairs):
+        do = np.asarray(batch.doc_off, np.int64)
+        so = np.asarray(batch.sent_off, np.int64)
+        tk = np.asarray(batch.tokens, np.int32)
+        docs = []
+        for d in (2 * p, 2 * p + 1):
+            o = so[do[d]:do[d + 1] + 1]
+            docs.append(((o - o[0]).astype(np.int32), tk[int(o[0]):int(o[-1])]))
+        out.append(best_match(score_matrix(od, docs[0], docs[1]), theta))
+    return out
 
 
 # ---------------------------------------------------------------------------

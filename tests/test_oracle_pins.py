@@ -628,3 +628,80 @@ def test_planted_mistake_in_union_or_objective_is_caught(name, tmp_path):
 
 def test_unmutated_union_and_objective_pass_all_pins():
     assert _run_py_pins(O) == []
+
+
+# ------------------------------- contrast without the path constraint (Section 4)
+
+def check_best_match_hand_example(m=O):
+    g = _gold("best_match_hand_example.json")
+    sel, rep = m.best_match(np.asarray(g["M"], np.int32), g["theta"])
+    assert [list(t) for t in sel] == g["selected"] and rep == g["repeated"]
+
+
+def test_best_match_hand_example():
+    check_best_match_hand_example()
+
+
+def check_best_match_closed_forms(m=O):
+    # a permutation matrix of high scores: every row takes its own column, no repeats
+    perm = np.random.default_rng(3).permutation(9)
+    M = np.full((9, 9), 1000, np.int32)
+    M[np.arange(9), perm] = 60000
+    sel, rep = m.best_match(M, 32768)
+    assert sel == [(i, int(perm[i]), 60000) for i in range(9)] and rep == 0
+    # one dominant column: every row takes it, one repeated target
+    M = np.full((5, 4), 1000, np.int32)
+    M[:, 2] = 50000
+    sel, rep = m.best_match(M, 32768)
+    assert [j for _, j, _ in sel] == [2] * 5 and rep == 1
+    # a constant matrix takes column 0 (lowest index among equals); the
+    # threshold is strict
+    M = np.full((3, 6), 40000, np.int32)
+    assert m.best_match(M, 39999)[0] == [(i, 0, 40000) for i in range(3)]
+    assert m.best_match(M, 40000) == ([], 0)
+    # no target sentences, no source sentences
+    assert m.best_match(np.zeros((4, 0), np.int32), 0) == ([], 0)
+    assert m.best_match(np.zeros((0, 4), np.int32), 0) == ([], 0)
+    # every source sentence the monotone alignment keeps has a cell above the
+    # threshold, so the best match keeps it too (with its row maximum)
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        M = synth.random_matrix(rng, int(rng.integers(1, 12)), int(rng.integers(1, 12)), lo=0, hi=65536)
+        nw = O.align(M, [(-65536, 32768)])[0][1]
+        bm, _ = m.best_match(M, 32768)
+        assert {i for i, _, _ in nw} <= {i for i, _, _ in bm}
+        for i, j, s in bm:
+            assert s == M[i].max() and M[i, :j].max(initial=-1) < s
+
+
+def test_best_match_closed_forms():
+    check_best_match_closed_forms()
+
+
+_BM_MUTANTS = {
+    "ties to the last column": ("            if row[c] > row[j]:\n                j = c", "            if row[c] >= row[j]:\n                j = c"),
+    "threshold not strict": ("        if row[j] > theta:\n            sel.append", "        if row[j] >= theta:\n            sel.append"),
+    "repeats counted per occurrence": ("return sel, sum(1 for c in taken.values() if c > 1)",
+                                       "return sel, sum(c for c in taken.values() if c > 1)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(_BM_MUTANTS))
+def test_planted_mistake_in_best_match_is_caught(name, tmp_path):
+    import importlib.util
+    old, new = _BM_MUTANTS[name]
+    src = open(O.__file__).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not unique in the oracle"
+    path = tmp_path / "oracle_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("oracle_mutant", str(path))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    m._lib = O.lib()
+    failed = []
+    for c in (check_best_match_hand_example, check_best_match_closed_forms):
+        try:
+            c(m)
+        except AssertionError:
+            failed.append(c)
+    assert failed, f"no pin caught the planted mistake {name!r}"
