@@ -13,6 +13,7 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -351,8 +352,25 @@ def extras_run(ctx, w, dh, reps=3):
                        "tp": tp[best], "selected": nsel[best], "known": nt},
               "how": "mine_tune_f1 over 8 gaps x 8 thresholds against the planted pairs, host "
                      "buffers, %d calls after 1 warm-up" % reps}
+    # the contrast without the path constraint: each source sentence's best target
+    thr = w.settings[0][1]
+    ns = np.zeros(P, np.int32)
+    rep = np.zeros(P, np.int32)
+    off = np.zeros(P + 1, np.int64)
+    bsel = np.zeros((int(so.shape[0] - 1), 3), np.int32)
+
+    def run_best():
+        mine._check(ctx.L.mine_best_match(ctx.h, dh, ctypes.byref(bc), int(thr), mine._ptr(ns), mine._ptr(rep),
+                                          mine._ptr(off), mine._ptr(bsel), int(bsel.shape[0])), ctx.L)
+
+    wall_b, prof_b = timed(run_best)
+    best_match = {"value": P / wall_b, "unit": UNIT, "ms_per_call": wall_b * 1e3,
+                  "device_ms": sum(prof_b.values()), "kernel_ms": prof_b, "threshold": thr,
+                  "selected": int(ns.sum()), "repeated_targets": int(rep.sum()),
+                  "how": "mine_best_match (each source sentence takes its best target; no path "
+                         "constraint), host buffers, %d calls after 1 warm-up" % reps}
     ctx.dict_destroy(hb)
-    return bidi, tuning
+    return bidi, tuning, best_match
 
 
 def serving_run(ctx, dh, rate, seconds):
@@ -521,9 +539,9 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         serving = serving_run(ctx, dh, args.serve_rate, args.serve_seconds)
-    bidi = tuning = None
+    bidi = tuning = best_match = None
     if not args.no_extras and rank == 0:
-        bidi, tuning = extras_run(ctx, w, dh)
+        bidi, tuning, best_match = extras_run(ctx, w, dh)
 
     # ---- roofline of the dominant kernel
     hbm_peak, sm_mhz_max, peak_kind = peaks()
@@ -595,6 +613,7 @@ def main():
         "serving": serving,
         "bidirectional": bidi,
         "tuning": tuning,
+        "best_match": best_match,
         "roofline": roof,
         "roofline_kernels": rl,
         "kernel_ms_per_step": {k: v[0] for k, v in timed.items()},

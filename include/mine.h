@@ -286,6 +286,21 @@ int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
                  const mine_settings *settings, const int32_t *truth, int64_t *tp,
                  int64_t *n_selected, int64_t *n_truth, int32_t *best);
 
+/* Contrast without the path constraint (Section 4: Yalign's A* search may go
+ * upward or leftward in the score matrix and so come back to sentences it has
+ * already matched, repeating the same phrase; the monotone global alignment
+ * cannot).  In its limit every source sentence takes its best-scoring target
+ * sentence (the lowest index among equal scores), kept when that score is
+ * above `threshold` (Q16 in [0, 65536]).  Per pair p of the host batch:
+ * n_sel[p], sel[sel_off[p] .. sel_off[p+1]) the kept (source, target, score)
+ * by increasing source sentence (sel_off has P + 1 entries), and repeated[p]
+ * the number of target sentences taken by more than one source sentence.
+ * sel_cap: capacity of sel (the batch's source sentence count is always
+ * enough; MINE_EINVAL if the selection does not fit).  Host memory,
+ * synchronous; errors as mine_run_batch. */
+int mine_best_match(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, mine_q16 threshold,
+                    int32_t *n_sel, int32_t *repeated, int64_t *sel_off, mine_pair *sel, int64_t sel_cap);
+
 /* Wait for all work of the context's device and report a device-side
  * validation failure of the last mine_run_batch_device call (malformed
  * sentence offsets, token IDs out of range) as MINE_EINVAL. */

@@ -212,7 +212,22 @@ struct F1Dev {
     const int32_t *err;              // error word of the batch (nothing is done if set)
 };
 
-// launchers (kernels.cu, bidi_tune.cu); each returns the number of kernels launched
+// Contrast without the path constraint: each source sentence's best target.
+struct BestDev {
+    const PairPlan *pairs;
+    int32_t n_pairs;
+    const ScoreItem *items;          // 32-row groups of source sentences (the preparation items)
+    int32_t n_items;
+    const int32_t *M;                // tiled scores
+    int32_t thr;
+    int2 *best;                      // [n_sent] (target, score) of a source sentence, or (-1, 0)
+    int32_t *out;                    // [3 n_sent] selected (i, j, s) of pair p from 3 s0 on
+    int32_t *n_sel, *rep;            // [n_pairs] selected pairs, target sentences taken twice or more
+    uint32_t *seen1, *seen2;         // [n_sent / 32 + 1] each, zeroed: targets taken once, twice
+    const int32_t *err;              // error word of the scoring (nothing is done if set)
+};
+
+// launchers (kernels.cu, bidi_tune.cu, best_match.cu); each returns the number of kernels launched
 int launch_dict_build(const int32_t *keys, const int32_t *trans_off, int32_t n_keys, DevDict d,
                       int32_t *err, cudaStream_t st);
 int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int32_t *err,
@@ -233,6 +248,7 @@ int launch_union(const UnionDev &u, int num_sms, cudaStream_t st);
 int launch_pack(const BatchDev &b, int32_t n, int32_t R, int32_t *bsum, int64_t *off, int32_t *out,
                 cudaStream_t st);
 int launch_f1(const F1Dev &f, int num_sms, cudaStream_t st);
+int launch_best(const BestDev &d, int num_sms, cudaStream_t st);
 
 // Record the text returned by mine_last_error() for this thread (runtime.cu).
 void set_last_error(const char *msg);
@@ -241,6 +257,6 @@ void set_last_error(const char *msg);
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
                 KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_UNION = 11, KID_F1 = 12,
-                KID_DOC_WIDE = 13, KID_PACK = 14, KID_COUNT = 15 };
+                KID_DOC_WIDE = 13, KID_PACK = 14, KID_BEST = 15, KID_COUNT = 16 };
 
 }  // namespace mine

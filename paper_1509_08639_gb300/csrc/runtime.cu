@@ -1372,6 +1372,90 @@ int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
     return MINE_OK;
 }
 
+int mine_best_match(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, mine_q16 threshold,
+                    int32_t *n_sel, int32_t *repeated, int64_t *sel_off, mine_pair *sel, int64_t sel_cap)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    const int32_t P = batch->n_pairs;
+    if (P > 0 && (!n_sel || !repeated || !sel_off)) return fail(MINE_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    ++ctx->arena_gen;
+    const Setting set(-65536, threshold);   // validates the threshold; no alignment runs
+    Plan pl;
+    rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
+                    [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, 65536, true,
+                    ctx->align_tab);
+    if (rc) return rc;
+    pl.n_tok = batch->n_tok;
+    if (sel_off) sel_off[0] = 0;
+    if (P == 0) return MINE_OK;
+    const Layout L = make_layout(pl, dict->d.kmax, true, false, true);
+    const int64_t ns = batch->n_sent;
+    const int64_t words = ns / 32 + 1;
+    const int64_t o_best = align_up(L.total, 256);
+    const int64_t o_out = o_best + align_up(8 * ns + 16, 256);
+    const int64_t o_cnt = o_out + align_up(12 * ns + 16, 256);
+    const int64_t o_bits = o_cnt + align_up(8 * (int64_t)P + 16, 256);
+    if ((rc = ensure_dev(ctx->arena, o_bits + 8 * words + 16))) return rc;
+    const int64_t ho = align_up(L.plan_bytes, 64);
+    if ((rc = ensure_host(ctx->pin, ho + 8 * (int64_t)P + 12 * ns + 64))) return rc;
+    char *hp = static_cast<char *>(ctx->pin.p);
+    pack_plan(pl, L, hp);
+    char *base = static_cast<char *>(ctx->arena.p);
+    cudaStream_t st = ctx->stream;
+    int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if (batch->n_tok > 0)
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(base + o_bits, 0, 8 * words, st));
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
+    BestDev d;
+    d.pairs = b.pairs;
+    d.n_pairs = P;
+    d.items = b.prep_items;
+    d.n_items = b.n_prep_items;
+    d.M = b.M;
+    d.thr = threshold;
+    d.best = reinterpret_cast<int2 *>(base + o_best);
+    d.out = reinterpret_cast<int32_t *>(base + o_out);
+    d.n_sel = reinterpret_cast<int32_t *>(base + o_cnt);
+    d.rep = d.n_sel + P;
+    d.seen1 = reinterpret_cast<uint32_t *>(base + o_bits);
+    d.seen2 = d.seen1 + words;
+    d.err = b.err;
+    ctx->launches += timed_launch(ctx, KID_BEST, st, [&] { return launch_best(d, ctx->num_sms, st); });
+    CK(cudaGetLastError());
+    int32_t *h_cnt = reinterpret_cast<int32_t *>(hp + ho);
+    int32_t *h_out = h_cnt + 2 * P;
+    int32_t h_err = 0;
+    CK(cudaMemcpyAsync(h_cnt, d.n_sel, 8 * (size_t)P, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_out, d.out, 12 * (size_t)ns, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
+    ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
+    ctx->d2h_bytes += 8 * (int64_t)P + 12 * ns + 4;
+    CK(cudaStreamSynchronize(st));
+    if (h_err) return fail(MINE_EINVAL, device_err_text(h_err));
+    int64_t tot = 0;
+    for (int32_t p = 0; p < P; ++p) tot += h_cnt[p];
+    if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
+    int64_t o = 0;
+    for (int32_t p = 0; p < P; ++p) {
+        n_sel[p] = h_cnt[p];
+        repeated[p] = h_cnt[P + p];
+        sel_off[p] = o;
+        std::memcpy(sel + o, h_out + 3 * (int64_t)pl.pairs[p].s0, 12 * (size_t)h_cnt[p]);
+        o += h_cnt[p];
+    }
+    sel_off[P] = o;
+    return MINE_OK;
+}
+
 int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
                           const int32_t *doc_off_host, const mine_settings *settings,
                           mine_q16 *nw_score, int32_t *n_sel, mine_pair *sel, int64_t sel_cap,
@@ -1592,7 +1676,7 @@ const char *mine_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
                                            "k_pairprep", "k_score_wide", "k_align_tiled",
-                                           "k_union", "k_f1", "k_pairprep_wide", "k_pack"};
+                                           "k_union", "k_f1", "k_pairprep_wide", "k_pack", "k_best"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 

@@ -98,6 +98,7 @@ SIGNATURES = {
                                  _P, _P, _P, _P, _L]),
     "mine_tune_f1": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P, _P, _P,
                           ctypes.POINTER(_L), ctypes.POINTER(_I)]),
+    "mine_best_match": (_I, [_P, _P, ctypes.POINTER(BatchC), _I, _P, _P, _P, _P, _L]),
 }
 
 ALIGN_BINS = 40
@@ -261,6 +262,21 @@ class Context:
         _check(self.L.mine_tune_f1(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc), _ptr(tr),
                                    _ptr(tp), _ptr(nsel), ctypes.byref(nt), ctypes.byref(best)), self.L)
         return [int(v) for v in tp], [int(v) for v in nsel], int(nt.value), int(best.value)
+
+    def best_match(self, dict_h, batch, threshold):
+        """Contrast without the path constraint: [(selection [(i, j, s)], repeated)] per pair."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        P = (do.shape[0] - 1) // 2
+        bc = BatchC(P, so.shape[0] - 1, tk.shape[0], _ptr(do), _ptr(so), _ptr(tk))
+        cap = max(int(so.shape[0] - 1), 1)
+        ns = np.zeros(P, np.int32)
+        rep = np.zeros(P, np.int32)
+        off = np.zeros(P + 1, np.int64)
+        sel = np.zeros((cap, 3), np.int32)
+        _check(self.L.mine_best_match(self.h, dict_h, ctypes.byref(bc), int(threshold), _ptr(ns), _ptr(rep),
+                                      _ptr(off), _ptr(sel), cap), self.L)
+        return [([tuple(int(v) for v in t) for t in sel[off[p]:off[p] + ns[p]]], int(rep[p]))
+                for p in range(P)]
 
     def run_batch_raw(self, dict_h, bc, sc, outs):
         """Host-buffer call with pre-built ctypes structs (benchmark path)."""
