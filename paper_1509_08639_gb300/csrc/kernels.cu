@@ -640,21 +640,25 @@ __device__ __forceinline__ int doc_id(const SM &sm, int lg, int32_t tok)
     }
 }
 
-// Insert target token `tok`; true when this call added it (the caller
-// counts the additions, one atomic per warp).
+// Insert target token `tok`; returns its slot, and `added` is set when this
+// call added it (the caller counts the additions, one atomic per warp).
 template <class SM>
-__device__ __forceinline__ bool doc_insert(SM &sm, int lg, int32_t tok)
+__device__ __forceinline__ uint32_t doc_insert(SM &sm, int lg, int32_t tok, bool &added)
 {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h = hmul(tok) >> (32 - lg);
     volatile int32_t *key = sm.key;
+    added = false;
     for (;;) {
         const int32_t k = key[h];
-        if (k == tok) return false;
+        if (k == tok) return h;
         if (k == -1) {
             const int32_t old = atomicCAS(&sm.key[h], -1, tok);
-            if (old == -1) return true;
-            if (old == tok) return false;
+            if (old == -1) {
+                added = true;
+                return h;
+            }
+            if (old == tok) return h;
         }
         h = (h + 1) & mask;
     }
@@ -864,7 +868,9 @@ k_pairprep(BatchDev b, DevDict d)
         const PairPlan pp = b.pairs[p];
         const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
         if ((tb - ta <= kSmallArticleTok) != SMALL) continue;   // the other launch's pair
-        const int lg = min(max(ceil_log2(2 * max(tb - ta, 1)), 10), SMALL ? 13 : 14);
+        // at most a quarter of the slots used where the table allows (the
+        // probes of absent translations, the common case, end sooner)
+        const int lg = min(max(ceil_log2(4 * max(tb - ta, 1)), 10), SMALL ? 13 : 14);
         const int NS = 1 << lg;
         int4 *kz = reinterpret_cast<int4 *>(sm.key);
         for (int k = tid; k < NS / 4; k += kPPThreads) kz[k] = make_int4(-1, -1, -1, -1);
@@ -886,11 +892,17 @@ k_pairprep(BatchDev b, DevDict d)
             unsigned added = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (k + q * kPPThreads < tb) {
-                    if ((uint32_t)tk[q] > ELEM_TOKEN)
+                const int32_t kk = k + q * kPPThreads;
+                if (kk < tb) {
+                    uint32_t h = 0;
+                    if ((uint32_t)tk[q] > ELEM_TOKEN) {
                         atomicCAS(b.err, 0, ERR_BAD_TOKEN);
-                    else
-                        added += doc_insert(sm, lg, tk[q]) ? 1u : 0u;
+                    } else {
+                        bool a;
+                        h = doc_insert(sm, lg, tk[q], a);
+                        added += a ? 1u : 0u;
+                    }
+                    b.tdoc[kk] = (uint16_t)h;   // the slot; its rank replaces it below
                 }
             }
             added = __reduce_add_sync(kFull, added);
@@ -924,18 +936,21 @@ k_pairprep(BatchDev b, DevDict d)
             }
         }
         __syncthreads();
-        // 2. id of every target token
+        // 2. id of every target token: the rank of the slot phase 1 found for
+        //    it (each thread rewrites the entries it wrote there)
         for (int32_t k = ta + tid; k < tb; k += 4 * kPPThreads) {
-            int32_t tk[4];
+            uint32_t hs[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int32_t kk = k + q * kPPThreads;
-                tk[q] = kk < tb ? b.tokens[kk] : 0;
+                hs[q] = kk < tb ? b.tdoc[kk] : 0u;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int32_t kk = k + q * kPPThreads;
-                if (kk < tb) b.tdoc[kk] = (uint16_t)max(doc_id(sm, lg, tk[q] & (int32_t)ELEM_TOKEN), 0);
+                const uint32_t h = hs[q] & ((1u << lg) - 1u);
+                const uint32_t w = h >> 5;
+                if (kk < tb) b.tdoc[kk] = (uint16_t)((int)sm.rank[w] + __popc(sm.occ[w] & ((1u << (h & 31)) - 1u)));
             }
         }
         // 3. source rows, one warp each (rows wib, wib + kPPWarps, ...).  The
