@@ -1753,13 +1753,16 @@ __device__ __forceinline__ void stripe_chunk(int c, int lane, int clo, int chi, 
 {
     const uint32_t sh = 2u * (uint32_t)(lane & 15);
     const int mb = 2 * c - (lane >> 4);
+    // step u is inside [clo, chi) when u + voff, taken unsigned, is below vspan
+    const int voff = 32 * c - lane - clo;
+    const uint32_t vspan = (row_ok && chi > clo) ? (uint32_t)(chi - clo) : 0u;
 #pragma unroll 8
     for (int u = 0; u < 32; ++u) {
         int32_t up_in = __shfl_up_sync(kFull, h_out, 1);
         const int32_t from_above = __shfl_sync(kFull, up_val, u);
         up_in = (lane == 0) ? from_above : up_in;
         const int cidx = 32 * c + u - lane;
-        const bool valid = !GUARD || (row_ok && cidx >= clo && cidx < chi);
+        const bool valid = !GUARD || (uint32_t)(u + voff) < vspan;
         uint32_t code = 0u;
         if (valid) {
             const int32_t sv = (u < lane ? base_prev : base_cur)[u];
