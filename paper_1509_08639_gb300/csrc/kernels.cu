@@ -107,6 +107,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// L2 policy for data read once: its lines are the first to be evicted, so a
+// stream of them does not push out what is read again soon (the direction
+// codes the traceback reads next).
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void bulk_g2s_once(void *dst, const void *src, uint32_t bytes,
+                                              unsigned long long *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            s2u(dst)),
+        "l"(src), "r"(bytes), "r"(s2u(bar)), "l"(policy)
+        : "memory");
+}
+
 // Test the phase; a thread whose phase is incomplete may be suspended for up
 // to kWaitHintNs before the test returns false (no busy spinning).
 __device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity)
@@ -1808,6 +1828,7 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
                               int item, const NwItem &it, const PairPlan &pp, int lane,
                               uint32_t (&uses)[kMBuf])
 {
+    const uint64_t pol = l2_evict_first();   // score tiles are read once
     const int S = pp.S, T = pp.T;
     const int32_t g = b.gap_val[it.gap];
     const int TT = (T + 31) >> 5;
@@ -1831,8 +1852,8 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
         if (lane == 0) {
             for (int k = 0; k < kMBuf && k < TT; ++k) {
                 mbar_expect_tx(&sm.bar[wib][k], kTileElems * 4);
-                bulk_g2s(sm.tile[wib][k], Mp + ((int64_t)s * TT + k) * kTileElems, kTileElems * 4,
-                         &sm.bar[wib][k]);
+                bulk_g2s_once(sm.tile[wib][k], Mp + ((int64_t)s * TT + k) * kTileElems, kTileElems * 4,
+                         &sm.bar[wib][k], pol);
             }
         }
         for (int k = 0; k < kMBuf && k < TT; ++k) uses[k]++;
@@ -1853,8 +1874,8 @@ __device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const W
                 __syncwarp();
                 if (lane == 0) {
                     mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
-                    bulk_g2s(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems,
-                             kTileElems * 4, &sm.bar[wib][bb]);
+                    bulk_g2s_once(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems,
+                             kTileElems * 4, &sm.bar[wib][bb], pol);
                 }
                 uses[bb]++;
             }
@@ -2064,6 +2085,7 @@ __device__ __forceinline__ bool flag_wait_set(const int32_t *flag, int32_t *err)
 __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, const TileItem &ti,
                            uint32_t (&uses)[kMBuf])
 {
+    const uint64_t pol = l2_evict_first();   // score tiles are read once
     const NwItem it = b.nw_items[ti.nw];
     const PairPlan pp = b.pairs[it.pair];
     const int S = pp.S, T = pp.T;
@@ -2111,8 +2133,8 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
         if (lane == 0) {
             for (int k = 0; k < kMBuf && cb + k < ce; ++k) {
                 mbar_expect_tx(&sm.bar[wib][k], kTileElems * 4);
-                bulk_g2s(sm.tile[wib][k], Mp + ((int64_t)s * TT + cb + k) * kTileElems, kTileElems * 4,
-                         &sm.bar[wib][k]);
+                bulk_g2s_once(sm.tile[wib][k], Mp + ((int64_t)s * TT + cb + k) * kTileElems, kTileElems * 4,
+                         &sm.bar[wib][k], pol);
             }
         }
         for (int k = 0; k < kMBuf && cb + k < ce; ++k) uses[k]++;
@@ -2136,8 +2158,8 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
                 __syncwarp();
                 if (lane == 0) {
                     mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
-                    bulk_g2s(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems, kTileElems * 4,
-                             &sm.bar[wib][bb]);
+                    bulk_g2s_once(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems, kTileElems * 4,
+                             &sm.bar[wib][bb], pol);
                 }
                 uses[bb]++;
             }
