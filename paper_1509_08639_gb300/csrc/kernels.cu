@@ -1733,6 +1733,7 @@ __global__ void k_tile(const int32_t *__restrict__ src, int32_t S, int32_t T, in
 constexpr int kAW = 8;      // warps per CTA (pipeline depth of a large alignment)
 constexpr int kMBuf = 3;    // score tiles in flight per warp
 
+constexpr int kOwnMax = 64;   // whole-CTA alignments a CTA traces back itself
 struct AlignSmem {
     int32_t tile[kAW][kMBuf][kTileElems];
     int32_t ring[kAW][kRing];
@@ -1740,6 +1741,8 @@ struct AlignSmem {
     int32_t prod[kAW];      // stream values published by warp w (its last rows)
     int32_t cons[kAW];      // stream values warp w consumed from its predecessor
     int32_t item;
+    int32_t n_own;          // whole-CTA alignments filled here, not yet traced back
+    int32_t own[kOwnMax];
 };
 
 struct WarpPipe {
@@ -2010,10 +2013,13 @@ k_align(BatchDev b)
         fence_barrier_init();
     }
     uint32_t uses[kMBuf] = {0u, 0u, 0u};
+    if (threadIdx.x == 0) sm.n_own = 0;
     __syncthreads();
     if (*(volatile int32_t *)b.err) return;
 
-    // large alignments: the whole CTA on one pair
+    // large alignments: the whole CTA on one pair.  Their tracebacks are long
+    // and serial; warp 0 does them once the queue is empty, while the other
+    // warps go on to the small alignments (k_trace takes the rest).
     for (;;) {
         if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[2], 1);
         if (threadIdx.x < kAW) {
@@ -2038,7 +2044,19 @@ k_align(BatchDev b)
         align_stripes(b, sm, wib, wp, item, it, pp, lane, uses);
         __syncthreads();
         if (*(volatile int32_t *)b.err) return;
+        if (sm.n_own < kOwnMax) {   // (uniform: read after the barrier, written below)
+            __syncthreads();
+            if (threadIdx.x == 0) sm.own[sm.n_own++] = item;
+        } else if (wib == 0) {
+            trace_and_select(b, it, pp, b.hfin[item], lane);   // more than kOwnMax: at once
+        }
     }
+    if (wib == 0)
+        for (int k = 0; k < sm.n_own; ++k) {
+            const int item = sm.own[k];
+            const NwItem it = b.nw_items[item];
+            trace_and_select(b, it, b.pairs[it.pair], b.hfin[item], lane);
+        }
     // small alignments: one warp each
     for (;;) {
         int item = 0;
@@ -2247,9 +2265,9 @@ k_trace(BatchDev b)
 {
     const int lane = threadIdx.x & 31;
     if (*(volatile int32_t *)b.err) return;
-    for (;;) {
+    for (;;) {   // the whole-CTA alignments [0, n_nw_big) are traced back by k_align
         int item = 0;
-        if (lane == 0) item = atomicAdd(&b.counters[4], 1);
+        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[4], 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_nw_items) break;
         const NwItem it = b.nw_items[item];
@@ -2384,8 +2402,9 @@ int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st)
 
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st)
 {
-    if (b.n_nw_items <= 0) return 0;
-    const int need = (b.n_nw_items + 3) / 4;
+    const int n = b.n_nw_items - b.n_nw_big;   // the whole-CTA ones are traced back by k_align
+    if (n <= 0) return 0;
+    const int need = (n + 3) / 4;
     const int grid = std::max(1, std::min(num_sms * 8, need));
     k_trace<<<grid, 128, 0, st>>>(b);
     return 1;

@@ -663,6 +663,7 @@ int time_align(mine_ctx *ctx, int bin, int side, int32_t P, int cta, cudaEvent_t
         CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
         if (rep == 1) CK(cudaEventRecord(e0, st));
         ctx->launches += launch_align(b, ctx->num_sms, st);
+        ctx->launches += launch_trace(b, ctx->num_sms, st);   // part of each form's cost
     }
     CK(cudaEventRecord(e1, st));
     CK(cudaEventSynchronize(e1));
@@ -776,6 +777,7 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
             if (rep == 1) CK(cudaEventRecord(e0, st));
             ctx->launches += launch_align(bq, ctx->num_sms, st);
             ctx->launches += launch_align_tiled(bq, ctx->num_sms, st);
+            ctx->launches += launch_trace(bq, ctx->num_sms, st);   // one-warp forms trace inside k_align
         }
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
