@@ -87,6 +87,44 @@ def test_full_size_lognormal_batch_sampled(ctx):
     assert (nw <= 65536 * np.minimum(S, T) - 65536 * np.abs(S - T)).all()
 
 
+def test_pinned_host_inputs(ctx):
+    """The host-buffer call with pinned inputs and outputs (as the benchmark
+    makes it), twice in a row: results as the oracle's, on lognormal pairs and
+    on a pair whose target article has more than 8,192 distinct tokens (the
+    token-keyed path)."""
+    torch = pytest.importorskip("torch")
+    w = synth.workload(2, n_pairs=200)
+    rng = np.random.default_rng(83)
+    docs = [w.batch.doc(d) for d in range(2 * w.batch.n_pairs)]
+    def rand_doc(n_sent, lo, hi):
+        lens = rng.integers(lo, hi + 1, n_sent)
+        off = np.zeros(n_sent + 1, np.int32)
+        np.cumsum(lens, out=off[1:])
+        return off, rng.integers(0, 200000, int(off[-1])).astype(np.int32)
+    docs += [rand_doc(120, 5, 40), rand_doc(700, 15, 25)]     # about 14,000 distinct target tokens
+    b = synth.pack_docs(docs)
+    wb = synth.Workload("pinned", b, w.dictionary, [], [], w.settings + [(-16384, 16384)])
+    want = oracle_results(wb)
+    dh = ctx.dict_create(w.dictionary)
+    P, n = b.n_pairs, len(wb.settings)
+    pin_sent = torch.from_numpy(b.sent_off.copy()).pin_memory()
+    pin_tok = torch.from_numpy(b.tokens.copy()).pin_memory()
+    do = np.ascontiguousarray(b.doc_off)
+    g = np.asarray([s[0] for s in wb.settings], np.int32)
+    th = np.asarray([s[1] for s in wb.settings], np.int32)
+    bc = mine.BatchC(P, b.sent_off.shape[0] - 1, b.tokens.shape[0], mine._ptr(do), pin_sent.data_ptr(),
+                     pin_tok.data_ptr())
+    sc = mine.SettingsC(n, mine._ptr(g), mine._ptr(th))
+    S, T = b.sizes()
+    cap = int(n * np.minimum(S, T).sum())
+    outs = (np.zeros(P * n, np.int32), np.zeros(P * n, np.int32), np.zeros(P * n + 1, np.int64),
+            np.zeros((cap, 3), np.int32), cap)
+    for _ in range(2):
+        ctx.run_batch_raw(dh, bc, sc, outs)
+        got = mine.unpack_results(P, n, *outs[:4])
+        assert_same(got, want, "pinned inputs")
+
+
 def test_device_batch_graph_replay(ctx):
     """Repeating a device-buffer batch replays its captured graph: every
     kernel runs again on the current contents of the input buffers, so new
