@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--plain-pairs", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=5000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-sweep", default="1000,20000",
+                    help="further offered rates (pairs/s), 1.5 s each; empty for none")
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident path (for profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
@@ -376,7 +378,8 @@ def extras_run(ctx, w, dh, reps=3):
 def serving_run(ctx, dh, rate, seconds):
     """Poisson arrivals of 40x45 pairs with a 1% tail of 2000x2000 pairs."""
     from paper_1509_08639_gb300 import synth
-    w5 = synth.workload(5, n_pairs=max(int(rate * seconds * 1.1) + 16, 64))
+    # a pool of pairs drawn like config 5's (cycled when the run needs more)
+    w5 = synth.workload(5, n_pairs=min(max(int(rate * seconds * 1.1) + 16, 64), 4000))
     # the request pool uses its own dictionary: register it
     dh5 = ctx.dict_create(w5.dictionary)
     arrivals = synth.poisson_arrivals(rate, seconds)
@@ -539,6 +542,8 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         serving = serving_run(ctx, dh, args.serve_rate, args.serve_seconds)
+        rates = [float(r) for r in args.serve_sweep.split(",") if r.strip()]
+        serving["sweep"] = [serving_run(ctx, dh, r, 1.5) for r in rates]
     bidi = tuning = best_match = None
     if not args.no_extras and rank == 0:
         bidi, tuning, best_match = extras_run(ctx, w, dh)
