@@ -39,7 +39,7 @@ constexpr int kScoreCtasPerSmScore = 6;     // its resident CTAs per SM
 constexpr int kBlkTokCap = 1536;            // tokens of one staged 32-column block at most
 constexpr int kPairPrepCtasPerSm = 2;       // CTAs (16 warps each) per SM of the pair preparation
 // per-warp global tables: enough for the largest grid of the three kernels using them
-constexpr int kGScratchWarpsPerSm = 32;
+constexpr int kGScratchWarpsPerSm = 40;
 static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kGScratchWarpsPerSm &&
                   kScoreWarps * kScoreCtasPerSm <= kGScratchWarpsPerSm &&
                   16 * kPairPrepCtasPerSm <= kGScratchWarpsPerSm,

@@ -624,9 +624,10 @@ k_prep(BatchDev b, DevDict d)
 // ---------------------------------------------------------------- k_pairprep
 
 // Two launches: articles of at most kSmallArticleTok target tokens by CTAs of
-// 8 warps with a table of 2 kSmallArticleTok slots (four CTAs per SM, so
-// more pairs are in flight and fewer warps wait at a pair's barriers), the
-// others by CTAs of 16 warps with a table of 2 kDirect slots.
+// 8 warps with a table of 2 kSmallArticleTok slots (five CTAs per SM, the
+// most their shared memory allows, with registers capped to fit: more pairs
+// in flight and fewer warps waiting at a pair's barriers), the others by
+// CTAs of 16 warps with a table of 2 kDirect slots.
 constexpr int kSmallArticleTok = 4096;
 constexpr int kRowSetBig = 2 * kMaxSentTokens;     // rows of > 64 tokens: per-warp table in global memory
 static_assert(kRowSetBig * 8 <= kScoreScratchPerWarp, "per-warp global table too small");
@@ -2326,7 +2327,7 @@ int launch_pairprep_one(const BatchDev &b, const DevDict &d, int num_sms, cudaSt
     return 1;
 }
 
-static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 4 <= kGScratchWarpsPerSm, "per-warp global tables");
+static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 5 <= kGScratchWarpsPerSm, "per-warp global tables");
 
 int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
@@ -2337,7 +2338,7 @@ int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaS
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    return launch_pairprep_one<8, 2 * kSmallArticleTok, 4, true>(b, d, num_sms, st);
+    return launch_pairprep_one<8, 2 * kSmallArticleTok, 5, true>(b, d, num_sms, st);
 }
 
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
