@@ -36,7 +36,7 @@ constexpr int kScoreWarps = 4;              // warps per CTA of the score kernel
 constexpr int kScoreCtasPerSm = 4;          // CTAs per SM of the preparation kernel (grid = SMs x this)
 constexpr int kScoreWarpsScore = 2;         // warps per CTA of the score kernel (64 rows per item)
 constexpr int kScoreCtasPerSmScore = 6;     // its resident CTAs per SM
-constexpr int kBlkTokCap = 1536;            // tokens of one staged 32-column block at most
+constexpr int kBlkTokCap = 1024;            // tokens of one staged 32-column block at most
 constexpr int kPairPrepCtasPerSm = 2;       // CTAs (16 warps each) per SM of the pair preparation
 // per-warp global tables: enough for the largest grid of the three kernels using them
 constexpr int kGScratchWarpsPerSm = 40;

@@ -1633,7 +1633,7 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, KeyedWarp &sm, unsi
 // target tokens (queue counters[1]); DIRECT = kDirect with KEYED: all other
 // items, document-id or token-keyed (queue counters[6]).
 template <int DIRECT, bool KEYED>
-__global__ void __launch_bounds__(kSWS * 32)
+__global__ void __launch_bounds__(kSWS * 32, KEYED ? 1 : 11)   // small launch: 11 CTAs per SM fit
 k_score(BatchDev b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
