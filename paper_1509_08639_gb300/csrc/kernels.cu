@@ -708,8 +708,11 @@ __device__ __forceinline__ bool rset_insert(int2 *set, int lg, int32_t tok, int3
 }
 
 // Distinct tokens of a row of L <= 64 tokens (t0: tokens 0..31, t1: 32..63,
-// one per lane), compacted into cb[0..n); returns n.
-__device__ __forceinline__ int distinct64(int32_t t0, int32_t t1, int L, int lane, int32_t *cb)
+// one per lane), compacted into cb[0..n); returns n.  ht: 256 zero words of
+// shared memory (zero again on return), a small table for rows of more than
+// 32 tokens.
+__device__ __forceinline__ int distinct64(int32_t t0, int32_t t1, int L, int lane, int32_t *cb,
+                                          uint32_t *ht)
 {
     const bool v0 = lane < L, v1 = 32 + lane < L;
     const int32_t k0 = v0 ? t0 : -1 - lane;   // tokens are >= 0: sentinels never match one
@@ -721,9 +724,33 @@ __device__ __forceinline__ int distinct64(int32_t t0, int32_t t1, int L, int lan
         const int32_t k1 = v1 ? t1 : -1 - lane;
         const uint32_t m1 = __match_any_sync(kFull, k1);
         lead1 = v1 && (__ffs(m1) - 1 == lane);
+        // a second-half token already in the first half: the first half's
+        // distinct tokens (keys token + 1) go into the table, the second
+        // half's look them up, and the table is cleared again
+        int slot0 = -1;
+        if (lead0) {
+            uint32_t h = hmul(t0) >> 24;
+            while (atomicCAS(&ht[h], 0u, (uint32_t)t0 + 1u) != 0u) h = (h + 1) & 255u;   // keys differ
+            slot0 = (int)h;
+        }
+        __syncwarp();
         bool dup = false;
-        for (int q = 0; q < 32; ++q) dup |= __shfl_sync(kFull, k0, q) == k1;
+        if (lead1) {
+            uint32_t h = hmul(t1) >> 24;
+            for (;;) {   // ends: at most 32 of the 256 slots are used
+                const uint32_t v = ht[h];
+                if (v == (uint32_t)t1 + 1u) {
+                    dup = true;
+                    break;
+                }
+                if (v == 0u) break;
+                h = (h + 1) & 255u;
+            }
+        }
         lead1 = lead1 && !dup;
+        __syncwarp();
+        if (slot0 >= 0) ht[slot0] = 0u;
+        __syncwarp();
     }
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t b0 = __ballot_sync(kFull, lead0), b1 = __ballot_sync(kFull, lead1);
@@ -794,7 +821,7 @@ __device__ void prep_row_short(const BatchDev &b, const DevDict &d, const SM &sm
         t0 &= (int32_t)ELEM_TOKEN;
         t1 &= (int32_t)ELEM_TOKEN;
     }
-    const int n = distinct64(t0, t1, L, lane, cb);
+    const int n = distinct64(t0, t1, L, lane, cb, seen);   // (the row's id bitmap is zero here)
     uint32_t *el = b.elems + elem_base(a, s, kmax);
     int out = 0, nf = 0;
     for (int g = 0; 32 * g < n; ++g) {
