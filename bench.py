@@ -567,7 +567,8 @@ def main():
     # each stage's time covers all of its launches: the two preparation
     # launches (small and wide target articles), the score launches for small and wide target
     # articles, and the alignments of one CTA or warp and of many CTAs
-    stage_extra = {"k_pairprep": ("k_pairprep_wide",), "k_score": ("k_score_wide",),
+    stage_extra = {"k_pairprep": ("k_pairprep_wide", "k_pairprep_xwide"),
+                   "k_score": ("k_score_wide", "k_score_xwide"),
                    "k_align": ("k_align_tiled",)}
     for k in ("k_pairprep", "k_score", "k_align"):
         if k not in per_launch_ms:

@@ -49,6 +49,9 @@ static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kGScratchWarpsPerSm &&
 // that mask array is never set.
 constexpr int kDirect = 8192;
 constexpr uint32_t kZeroEnt = kDirect;
+// Articles with more distinct tokens, up to kDirectX, are prepared again by a
+// third launch with a larger table and scored through a larger mask array.
+constexpr int kDirectX = 16384;
 // per-warp global table of the score kernel: 2 * kMaxSentTokens (key, mask) entries
 constexpr int64_t kScoreScratchPerWarp = 2 * (int64_t)kMaxSentTokens * 8;
 
@@ -235,9 +238,11 @@ int launch_validate(const int32_t *sent_off, int64_t n_sent, int64_t n_tok, int3
 int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
+int launch_pairprep_xwide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st);
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st);        // small articles
 int launch_score_wide(const BatchDev &b, int num_sms, cudaStream_t st);   // all other items
+int launch_score_xwide(const BatchDev &b, int num_sms, cudaStream_t st);  // kDirect < ids <= kDirectX
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st);
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st);
@@ -257,6 +262,7 @@ void set_last_error(const char *msg);
 enum KernelId { KID_DICT = 0, KID_VALIDATE = 1, KID_PREP = 2, KID_SCORE = 3, KID_ALIGN = 4,
                 KID_TILE = 5, KID_TRACE = 6, KID_ORDER = 7, KID_DOC = 8,
                 KID_SCORE_WIDE = 9, KID_ALIGN_TILED = 10, KID_UNION = 11, KID_F1 = 12,
-                KID_DOC_WIDE = 13, KID_PACK = 14, KID_BEST = 15, KID_COUNT = 16 };
+                KID_DOC_WIDE = 13, KID_PACK = 14, KID_BEST = 15, KID_DOC_XWIDE = 16,
+                KID_SCORE_XWIDE = 17, KID_COUNT = 18 };
 
 }  // namespace mine

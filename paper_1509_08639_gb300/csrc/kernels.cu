@@ -463,7 +463,7 @@ k_prep(BatchDev b, DevDict d)
     uint32_t parity = 0u;
     bool generic = false;
     // nothing to do unless k_pairprep left an article with too many distinct tokens
-    if (*(volatile int32_t *)b.err || *(volatile int32_t *)&b.counters[9] == 0) return;
+    if (*(volatile int32_t *)b.err || *(volatile int32_t *)&b.counters[14] == 0) return;
 
     for (;;) {
         int item = 0;
@@ -632,12 +632,13 @@ constexpr int kSmallArticleTok = 4096;
 constexpr int kRowSetBig = 2 * kMaxSentTokens;     // rows of > 64 tokens: per-warp table in global memory
 static_assert(kRowSetBig * 8 <= kScoreScratchPerWarp, "per-warp global table too small");
 
-template <int WARPS, int SLOTS>
+template <int WARPS, int SLOTS, int IDS>
 struct alignas(16) PairPrepSmem {
+    static constexpr int kIds = IDS;           // document ids below this
     int32_t key[SLOTS];                        // target tokens of the article
     uint32_t occ[SLOTS / 32];                  // occupied slots
     uint16_t rank[SLOTS / 32];                 // occupied slots before each word
-    uint32_t seen[WARPS][kDirect / 32];        // ids already kept in the warp's current row
+    uint32_t seen[WARPS][IDS / 32];            // ids already kept in the warp's current row
     int32_t cbuf[WARPS][64];                   // distinct tokens of the row, compacted
     int32_t nd;
     int32_t item;
@@ -837,7 +838,7 @@ __device__ void prep_row_short(const BatchDev &b, const DevDict &d, const SM &sm
     if (lane == 0) b.sinfo[s] = make_int4(n, out, nf, 0);
     __syncwarp();
     uint4 *sz = reinterpret_cast<uint4 *>(seen);
-    for (int q = lane; q < kDirect / 128; q += 32) sz[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = lane; q < SM::kIds / 128; q += 32) sz[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
 }
 
@@ -874,12 +875,18 @@ __device__ void prep_row_long(const BatchDev &b, const DevDict &d, const SM &sm,
     if (lane == 0) b.sinfo[s] = make_int4(n_i, out, nf, 0);
     __syncwarp();
     uint4 *sz = reinterpret_cast<uint4 *>(seen);
-    for (int q = lane; q < kDirect / 128; q += 32) sz[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = lane; q < SM::kIds / 128; q += 32) sz[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
 }
 
+// Modes of the preparation launches: articles of more than kSmallArticleTok
+// target tokens (wide), the others (small), and the articles the wide launch
+// found to hold more than kDirect distinct tokens (extra wide: up to kDirectX
+// ids, a table of 2 kDirectX slots, one CTA per SM).
+constexpr int kModeWide = 0, kModeSmall = 1, kModeXWide = 2;
+
 // One CTA per pair (largest first), for every pair whose target article has
-// at most kDirect distinct tokens:
+// at most kDirect (kDirectX in the extra-wide mode) distinct tokens:
 //  1. the article's distinct tokens go into a shared table; their dense ids
 //     are the ranks of the occupied slots (pdoc[p] = D, the count);
 //  2. every target token's id goes to tdoc;
@@ -890,35 +897,40 @@ __device__ void prep_row_long(const BatchDev &b, const DevDict &d, const SM &sm,
 //     (n_i, #kept, #kept FIRST) in sinfo.
 // A larger article gets pdoc[p] = -1 and is left to k_prep and the
 // token-keyed score path.
-template <int WARPS, int SLOTS, int CTAS, bool SMALL>
+template <int WARPS, int SLOTS, int CTAS, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, CTAS)
 k_pairprep(BatchDev b, DevDict d)
 {
+    constexpr bool SMALL = MODE == kModeSmall, XW = MODE == kModeXWide;
+    constexpr int IDS = XW ? kDirectX : kDirect;
     constexpr int kPPWarps = WARPS, kPPThreads = WARPS * 32;
+    // nothing to do unless the wide launch left an article with too many ids
+    if (XW && *(volatile int32_t *)&b.counters[9] == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PairPrepSmem<WARPS, SLOTS> &sm = *reinterpret_cast<PairPrepSmem<WARPS, SLOTS> *>(smem_raw);
+    PairPrepSmem<WARPS, SLOTS, IDS> &sm = *reinterpret_cast<PairPrepSmem<WARPS, SLOTS, IDS> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     int2 *gset = b.gscratch + (int64_t)(blockIdx.x * kPPWarps + wib) * kGTabSlots;
     bool gset_clean = false;
     int32_t stamp = 0;
-    for (int k = tid; k < kPPWarps * (kDirect / 32); k += kPPThreads) (&sm.seen[0][0])[k] = 0u;
+    for (int k = tid; k < kPPWarps * (IDS / 32); k += kPPThreads) (&sm.seen[0][0])[k] = 0u;
     const int kmax = b.kmax;
     for (;;) {
         if (__syncthreads_or(*(volatile int32_t *)b.err != 0)) break;
         if (tid == 0) {
-            sm.item = atomicAdd(&b.counters[SMALL ? 5 : 10], 1);
+            sm.item = atomicAdd(&b.counters[SMALL ? 5 : (XW ? 11 : 10)], 1);
             sm.nd = 0;
         }
         __syncthreads();
         const int item = sm.item;
         if (item >= b.n_pairs) break;
         const int p = b.dorder[item];
+        if (XW && b.pdoc[p] != -1) continue;    // prepared by one of the other launches
         const PairPlan pp = b.pairs[p];
         const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
-        if ((tb - ta <= kSmallArticleTok) != SMALL) continue;   // the other launch's pair
+        if (!XW && (tb - ta <= kSmallArticleTok) != SMALL) continue;   // the other launch's pair
         // at most a quarter of the slots used where the table allows (the
         // probes of absent translations, the common case, end sooner)
-        const int lg = min(max(ceil_log2(4 * max(tb - ta, 1)), 10), SMALL ? 13 : 14);
+        const int lg = min(max(ceil_log2(4 * max(tb - ta, 1)), 10), SMALL ? 13 : (XW ? 15 : 14));
         const int NS = 1 << lg;
         int4 *kz = reinterpret_cast<int4 *>(sm.key);
         for (int k = tid; k < NS / 4; k += kPPThreads) kz[k] = make_int4(-1, -1, -1, -1);
@@ -926,10 +938,10 @@ k_pairprep(BatchDev b, DevDict d)
         // 1. distinct target tokens; four loads in flight per thread; the
         //    warp adds its new tokens to the count at once; a wide article
         //    stops once its tokens cannot all get ids (before its table fills:
-        //    at most 4 kPPThreads more insertions than kDirect < SLOTS)
-        static_assert(SMALL || kDirect + 4 * kPPThreads < SLOTS, "table of a wide article");
+        //    at most 4 kPPThreads more insertions than IDS < SLOTS)
+        static_assert(SMALL || IDS + 4 * kPPThreads < SLOTS, "table of a wide article");
         for (int32_t kw = ta + (tid & ~31); kw < tb; kw += 4 * kPPThreads) {   // warp-uniform
-            if (!SMALL && __shfl_sync(kFull, *(volatile int32_t *)&sm.nd, 0) > kDirect) break;
+            if (!SMALL && __shfl_sync(kFull, *(volatile int32_t *)&sm.nd, 0) > IDS) break;
             const int32_t k = kw + lane;
             int32_t tk[4];
 #pragma unroll
@@ -959,10 +971,17 @@ k_pairprep(BatchDev b, DevDict d)
         __syncthreads();
         const int D = sm.nd;
         if (tid == 0) {
-            b.pdoc[p] = D <= kDirect ? D : -1;
-            if (D > kDirect) atomicExch(&b.counters[9], 1);   // k_prep has work
+            if (!XW) {
+                b.pdoc[p] = D <= IDS ? D : -1;
+                if (D > IDS) atomicExch(&b.counters[9], 1);   // the extra-wide launch has work
+            } else if (D <= IDS) {
+                b.pdoc[p] = D;
+                atomicExch(&b.counters[13], 1);   // so has the extra-wide score launch
+            } else {
+                atomicExch(&b.counters[14], 1);   // k_prep has work (pdoc stays -1)
+            }
         }
-        if (D > kDirect) continue;
+        if (D > IDS) continue;
         const int NW = NS >> 5;
         for (int w = wib; w < NW; w += kPPWarps)
             sm.occ[w] = __ballot_sync(kFull, sm.key[32 * w + lane] != -1);
@@ -1657,12 +1676,15 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, KeyedWarp &sm, unsi
 }
 
 // DIRECT = kDirectSmall: items of articles with at most that many distinct
-// target tokens (queue counters[1]); DIRECT = kDirect with KEYED: all other
-// items, document-id or token-keyed (queue counters[6]).
+// target tokens (queue counters[1]); DIRECT = kDirectX: articles with more
+// than kDirect and at most kDirectX (queue counters[12]); DIRECT = kDirect
+// with KEYED: all other items, document-id or token-keyed (queue counters[6]).
 template <int DIRECT, bool KEYED>
 __global__ void __launch_bounds__(kSWS * 32, KEYED ? 1 : 11)   // small launch: 11 CTAs per SM fit
 k_score(BatchDev b)
 {
+    constexpr bool XW = !KEYED && DIRECT == kDirectX;
+    if (XW && *(volatile int32_t *)&b.counters[13] == 0) return;   // no such article
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScoreSmem<DIRECT, KEYED> &S = *reinterpret_cast<ScoreSmem<DIRECT, KEYED> *>(smem_raw);
     const int tid = threadIdx.x;
@@ -1688,13 +1710,15 @@ k_score(BatchDev b)
         // every thread leaves together: on an error (here or in another CTA)
         // or when the queue is empty
         if (__syncthreads_or(!ok || *(volatile int32_t *)b.err != 0)) break;
-        if (tid == 0) S.item = atomicAdd(&b.counters[KEYED ? 6 : 1], 1);
+        if (tid == 0) S.item = atomicAdd(&b.counters[KEYED ? 6 : (XW ? 12 : 1)], 1);
         __syncthreads();
         const int item = S.item;
         if (item >= b.n_score_items) break;
         const ScoreItem si = b.score_items[item];
         const int D = b.pdoc[si.pair];
-        if (KEYED ? (D >= 0 && D <= kDirectSmall) : (D < 0 || D > kDirectSmall)) continue;   // the other launch's
+        if (KEYED ? (D >= 0 && (D <= kDirectSmall || D > kDirect))
+                  : (XW ? (D <= kDirect || D > kDirectX) : (D < 0 || D > kDirectSmall)))
+            continue;   // another launch's item
         const PairPlan pp = b.pairs[si.pair];
         const int TT = (pp.T + 31) >> 5;
         // this warp's 32 rows, in the pair's order of element counts (the
@@ -2343,14 +2367,14 @@ int launch_prep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t s
     return 1;
 }
 
-template <int WARPS, int SLOTS, int CTAS, bool SMALL>
+template <int WARPS, int SLOTS, int CTAS, int MODE>
 int launch_pairprep_one(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
-    const size_t smem = sizeof(PairPrepSmem<WARPS, SLOTS>);
-    cudaFuncSetAttribute(k_pairprep<WARPS, SLOTS, CTAS, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = sizeof(PairPrepSmem<WARPS, SLOTS, MODE == kModeXWide ? kDirectX : kDirect>);
+    cudaFuncSetAttribute(k_pairprep<WARPS, SLOTS, CTAS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     const int grid = std::max(1, std::min(num_sms * CTAS, b.n_pairs));
-    k_pairprep<WARPS, SLOTS, CTAS, SMALL><<<grid, WARPS * 32, smem, st>>>(b, d);
+    k_pairprep<WARPS, SLOTS, CTAS, MODE><<<grid, WARPS * 32, smem, st>>>(b, d);
     return 1;
 }
 
@@ -2359,13 +2383,19 @@ static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 5 <= kGScratchWarpsPerSm, "pe
 int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    return launch_pairprep_one<16, 2 * kDirect, 2, false>(b, d, num_sms, st);
+    return launch_pairprep_one<16, 2 * kDirect, 2, kModeWide>(b, d, num_sms, st);
 }
 
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    return launch_pairprep_one<8, 2 * kSmallArticleTok, 5, true>(b, d, num_sms, st);
+    return launch_pairprep_one<8, 2 * kSmallArticleTok, 5, kModeSmall>(b, d, num_sms, st);
+}
+
+int launch_pairprep_xwide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
+{
+    if (b.n_pairs <= 0) return 0;
+    return launch_pairprep_one<16, 2 * kDirectX, 1, kModeXWide>(b, d, num_sms, st);
 }
 
 int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
@@ -2404,6 +2434,12 @@ int launch_score_wide(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
     return launch_score_one<kDirect, true>(b, num_sms, st);
+}
+
+int launch_score_xwide(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    if (b.n_score_items <= 0) return 0;
+    return launch_score_one<kDirectX, false>(b, num_sms, st);
 }
 
 int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)

@@ -597,10 +597,12 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         bd.kmax = dict->d.kmax;
         n += timed_launch(ctx, KID_DOC_WIDE, st, [&] { return launch_pairprep_wide(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_DOC, st, [&] { return launch_pairprep(bd, dict->d, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_DOC_XWIDE, st, [&] { return launch_pairprep_xwide(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE_WIDE, st, [&] { return launch_score_wide(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
+        n += timed_launch(ctx, KID_SCORE_XWIDE, st, [&] { return launch_score_xwide(bd, ctx->num_sms, st); });
     }
     if (aligning) {
         if (b.n_tiles > 0) CK(cudaMemsetAsync(b.tbnd, 0, 4 * b.n_tbnd, st));
@@ -1678,7 +1680,8 @@ const char *mine_kernel_name(int32_t id)
     static const char *names[KID_COUNT] = {"k_dict_build", "k_validate", "k_prep", "k_score",
                                            "k_align", "k_tile", "k_trace", "k_order",
                                            "k_pairprep", "k_score_wide", "k_align_tiled",
-                                           "k_union", "k_f1", "k_pairprep_wide", "k_pack", "k_best"};
+                                           "k_union", "k_f1", "k_pairprep_wide", "k_pack", "k_best",
+                                           "k_pairprep_xwide", "k_score_xwide"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 

@@ -356,9 +356,9 @@ class Context:
 
     def profile_read(self):
         """{kernel name: (total device ms, timed launches)} since the last read."""
-        ms = np.zeros(16, np.float64)
-        n = np.zeros(16, np.int64)
-        k = _check(self.L.mine_profile_read(self.h, _ptr(ms), _ptr(n), 16), self.L)
+        ms = np.zeros(32, np.float64)
+        n = np.zeros(32, np.int64)
+        k = _check(self.L.mine_profile_read(self.h, _ptr(ms), _ptr(n), 32), self.L)
         return {self.L.mine_kernel_name(i).decode(): (float(ms[i]), int(n[i])) for i in range(k)}
 
     # --------------------------------------------------------------- alignment only

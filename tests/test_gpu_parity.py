@@ -89,9 +89,9 @@ def test_full_size_lognormal_batch_sampled(ctx):
 
 def test_pinned_host_inputs(ctx):
     """The host-buffer call with pinned inputs and outputs (as the benchmark
-    makes it), twice in a row: results as the oracle's, on lognormal pairs and
-    on a pair whose target article has more than 8,192 distinct tokens (the
-    token-keyed path)."""
+    makes it), twice in a row: results as the oracle's, on lognormal pairs, on
+    a pair whose target article has between 8,192 and 16,384 distinct tokens
+    (the extra-wide launches) and on one with more (the token-keyed path)."""
     torch = pytest.importorskip("torch")
     w = synth.workload(2, n_pairs=200)
     rng = np.random.default_rng(83)
@@ -102,6 +102,7 @@ def test_pinned_host_inputs(ctx):
         np.cumsum(lens, out=off[1:])
         return off, rng.integers(0, 200000, int(off[-1])).astype(np.int32)
     docs += [rand_doc(120, 5, 40), rand_doc(700, 15, 25)]     # about 14,000 distinct target tokens
+    docs += [rand_doc(60, 5, 40), rand_doc(1000, 25, 35)]     # about 28,000: the token-keyed path
     b = synth.pack_docs(docs)
     wb = synth.Workload("pinned", b, w.dictionary, [], [], w.settings + [(-16384, 16384)])
     want = oracle_results(wb)
