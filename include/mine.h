@@ -220,6 +220,35 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
                    const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
                    int64_t *sel_off, mine_pair *sel, int64_t sel_cap);
 
+/* Host-buffer batch calls in flight together, at most. */
+#define MINE_ASYNC_DEPTH 2
+
+/* mine_run_batch without waiting: checks the arguments, enqueues the copy of
+ * the inputs, the kernels and the copies of the results into the caller's
+ * arrays, and returns a ticket (> 0) for mine_batch_wait.  Same arguments,
+ * outputs and errors as mine_run_batch; an error of the device work (bad
+ * tokens or offsets, sel_cap too small) is returned by mine_batch_wait.
+ * Every array (inputs and outputs) belongs to the library until
+ * mine_batch_wait has returned for the ticket: the caller neither frees nor
+ * writes them, nor reads the outputs, before then.  Each call in flight has
+ * its own input buffer, scratch and staging, so with PINNED host arrays
+ * (cudaMallocHost or cudaHostRegister) the input copies of one call run on a
+ * copy stream while the kernels of the call before it run; the kernels of
+ * successive calls run one after another.  With pageable arrays the call
+ * waits for its copies.  MINE_EAGAIN when MINE_ASYNC_DEPTH calls are in
+ * flight (wait for one first).  The dictionary cannot be destroyed
+ * (MINE_EBUSY) while a call using it is in flight; mine_close waits for
+ * every call in flight. */
+int mine_run_batch_async(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                         const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
+                         int64_t *sel_off, mine_pair *sel, int64_t sel_cap, uint64_t *ticket);
+
+/* Wait for the call of mine_run_batch_async that returned `ticket`; its
+ * outputs are then complete.  Returns that call's status (as
+ * mine_run_batch would have); MINE_EINVAL for a ticket that is not in
+ * flight (never issued, or already waited for). */
+int mine_batch_wait(mine_ctx *ctx, uint64_t ticket);
+
 /* The same with the batch already in DEVICE memory and outputs in DEVICE
  * memory, enqueued on `stream` (a cudaStream_t; NULL = the context's own
  * stream) without a host round trip for the data.  batch->sent_off and

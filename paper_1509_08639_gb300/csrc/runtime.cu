@@ -478,6 +478,31 @@ struct Slot {
     void *gscratch = nullptr;          // score-kernel tables for long sentences
 };
 
+// Result bookkeeping of one enqueued host-buffer batch call.
+struct HostCallOut {
+    int64_t R = 0;                     // result rows (pairs x settings)
+    int32_t *h_err = nullptr;          // pinned copy of the device error word
+    int64_t h2d = 0, d2h = 0;          // bytes copied each way
+};
+
+// One host-buffer batch call in flight (mine_run_batch_async): its own
+// input buffer, scratch, staging and long-sentence tables, so that its
+// input copies can run while the kernels of the call before it run.
+struct AsyncCall {
+    bool busy = false, waiting = false;
+    uint64_t ticket = 0;
+    DevBuf inbuf, arena;
+    HostBuf pin;
+    void *gscratch = nullptr;
+    cudaEvent_t in_ready = nullptr;    // inputs and plan on the device (copy stream)
+    cudaEvent_t done = nullptr;        // last result copy (context stream)
+    const mine_dict *dict = nullptr;
+    const int64_t *sel_off = nullptr;
+    const mine_pair *sel = nullptr;
+    int64_t sel_cap = 0;
+    HostCallOut out;
+};
+
 }  // namespace
 
 struct mine_ctx {
@@ -533,6 +558,11 @@ struct mine_ctx {
     uint64_t next_ticket = 1;
     std::thread worker;
     std::vector<mine_dict *> dicts;
+
+    // host-buffer batch calls in flight (mine_run_batch_async)
+    cudaStream_t cstream = nullptr;    // their input copies
+    AsyncCall acall[MINE_ASYNC_DEPTH];
+    uint64_t next_async = 1;
 };
 
 namespace {
@@ -910,6 +940,19 @@ int mine_close(mine_ctx *ctx)
     ctx->q_cv.notify_all();
     if (ctx->worker.joinable()) ctx->worker.join();
     cudaSetDevice(ctx->device);
+    // host-buffer batch calls still in flight: wait for them (the caller
+    // keeps their arrays until this returns)
+    for (AsyncCall &a : ctx->acall) {
+        if (a.busy) {
+            cudaEventSynchronize(a.done);
+            const_cast<mine_dict *>(a.dict)->inflight--;
+            a.busy = false;
+        }
+        if (a.in_ready) cudaEventDestroy(a.in_ready);
+        if (a.done) cudaEventDestroy(a.done);
+        if (a.gscratch) cudaFree(a.gscratch);
+    }
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
     for (mine_result &r : ctx->ready) std::free(r.pairs);
     ctx->ready.clear();
     for (mine_dict *d : ctx->dicts) {
@@ -1054,36 +1097,43 @@ static int check_batch(const mine_batch *b)
     return 0;
 }
 
-int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
-                   const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
-                   int64_t *sel_off, mine_pair *sel, int64_t sel_cap)
+// Buffers and streams of one host-buffer batch call.
+struct HostCallRes {
+    DevBuf *inbuf, *arena;
+    HostBuf *pin;
+    void *gscratch;
+    cudaStream_t st;         // kernels and result copies
+    cudaStream_t cst;        // input and plan copies (st itself for a synchronous call)
+    cudaEvent_t in_ready;    // recorded on cst after them when cst != st
+};
+
+// Enqueue one host-buffer batch call of P > 0 pairs: the inputs go first,
+// into their own buffer (their copy overlaps the planning), then the plan;
+// the kernels, the packing of the selections and the copies of every result
+// into the caller's arrays follow on res.st.  Nothing waits for the device
+// unless a step fails: then both streams are synchronised, so the caller may
+// free its inputs on return.
+static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                              const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
+                              int64_t *sel_off, mine_pair *sel, int64_t sel_cap,
+                              const HostCallRes &res, HostCallOut &out)
 {
-    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
-    int rc = check_batch(batch);
-    if (rc) return rc;
-    if ((rc = check_settings(settings))) return rc;
     const int32_t P = batch->n_pairs;
     const int n = settings->n;
-    if (P > 0 && (!nw_score || !n_sel || !sel_off)) return fail(MINE_EINVAL, "null output");
-    std::lock_guard<std::mutex> lk(ctx->api_mu);
-    if ((rc = set_device(ctx))) return rc;
-    ++ctx->arena_gen;
-    cudaStream_t st = ctx->stream;
-    sel_off[0] = 0;
-    if (P == 0) return MINE_OK;
-    // the inputs go first, into their own buffer: their copy overlaps the
-    // planning below
+    const cudaStream_t st = res.st, cst = res.cst;
+    int rc = 0;
     const int64_t in_tok_at = align_up(4 * (batch->n_sent + 1), 256);
-    if ((rc = ensure_dev(ctx->inbuf, in_tok_at + 4 * batch->n_tok + 16))) return rc;
-    int32_t *d_sent = static_cast<int32_t *>(ctx->inbuf.p);
-    int32_t *d_tok = reinterpret_cast<int32_t *>(static_cast<char *>(ctx->inbuf.p) + in_tok_at);
-    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, st));
+    if ((rc = ensure_dev(*res.inbuf, in_tok_at + 4 * batch->n_tok + 16))) return rc;
+    int32_t *d_sent = static_cast<int32_t *>(res.inbuf->p);
+    int32_t *d_tok = reinterpret_cast<int32_t *>(static_cast<char *>(res.inbuf->p) + in_tok_at);
+    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, cst));
     if (batch->n_tok > 0)
-        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, cst));
     // from here on a failure waits for those copies (the caller may free the
     // inputs once the call returns)
     auto bail = [&](int code) {
-        cudaStreamSynchronize(st);
+        cudaStreamSynchronize(cst);
+        if (st != cst) cudaStreamSynchronize(st);
         return code;
     };
     std::vector<Setting> set(n);
@@ -1101,13 +1151,20 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     const int64_t o_pk = o_off + align_up(8 * ((int64_t)R + 1), 256);
     const int64_t o_bs = o_pk + align_up(12 * pl.sel_cap + 16, 256);
     const int64_t total = o_bs + 4 * ((int64_t)R / 1024 + 1) + 16;
-    if ((rc = ensure_dev(ctx->arena, total))) return bail(rc);
-    if ((rc = ensure_host(ctx->pin, L.plan_bytes + 64))) return bail(rc);
-    char *hp = static_cast<char *>(ctx->pin.p);
+    const int64_t err_at = align_up(L.plan_bytes, 64);   // the error word after the plan
+    if ((rc = ensure_dev(*res.arena, total))) return bail(rc);
+    if ((rc = ensure_host(*res.pin, err_at + 64))) return bail(rc);
+    char *hp = static_cast<char *>(res.pin->p);
     pack_plan(pl, L, hp);
-    char *base = static_cast<char *>(ctx->arena.p);
-    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
-    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
+    int32_t *h_err = reinterpret_cast<int32_t *>(hp + err_at);
+    *h_err = 0;
+    char *base = static_cast<char *>(res.arena->p);
+    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, cst));
+    if (cst != st) {
+        CK(cudaEventRecord(res.in_ready, cst));
+        CK(cudaStreamWaitEvent(st, res.in_ready, 0));
+    }
+    BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, res.gscratch);
     if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return bail(rc);
     int64_t *d_off = reinterpret_cast<int64_t *>(base + o_off);
     int32_t *d_pk = reinterpret_cast<int32_t *>(base + o_pk);
@@ -1115,20 +1172,126 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     ctx->launches += timed_launch(ctx, KID_PACK, st, [&] { return launch_pack(b, n, R, d_bs, d_off, d_pk, st); });
     CK(cudaGetLastError());
     // results straight into the caller's arrays
-    int32_t h_err = 0;
     const int64_t cp = std::min(sel_cap, pl.sel_cap);
     CK(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, st));
     if (cp > 0 && sel) CK(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
-    ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
-    ctx->d2h_bytes += 8 * (int64_t)R + 8 * ((int64_t)R + 1) + 4 + (sel ? 12 * cp : 0);
-    CK(cudaStreamSynchronize(st));
-    if (h_err) return fail(MINE_EINVAL, device_err_text(h_err));
-    const int64_t tot = sel_off[R];
+    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
+    out.R = R;
+    out.h_err = h_err;
+    out.h2d = L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
+    out.d2h = 8 * (int64_t)R + 8 * ((int64_t)R + 1) + 4 + (sel ? 12 * cp : 0);
+    return MINE_OK;
+}
+
+// Status of a completed host-buffer batch call.
+static int finish_host_batch(const HostCallOut &o, const int64_t *sel_off, const mine_pair *sel,
+                             int64_t sel_cap)
+{
+    if (!o.h_err) return MINE_OK;   // no pairs
+    if (*o.h_err) return fail(MINE_EINVAL, device_err_text(*o.h_err));
+    const int64_t tot = sel_off[o.R];
     if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
     return MINE_OK;
+}
+
+int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                   const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
+                   int64_t *sel_off, mine_pair *sel, int64_t sel_cap)
+{
+    if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if ((rc = check_settings(settings))) return rc;
+    const int32_t P = batch->n_pairs;
+    if (P > 0 && (!nw_score || !n_sel || !sel_off)) return fail(MINE_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    ++ctx->arena_gen;
+    sel_off[0] = 0;
+    if (P == 0) return MINE_OK;
+    const HostCallRes res{&ctx->inbuf, &ctx->arena, &ctx->pin, ctx->gscratch, ctx->stream, ctx->stream,
+                          nullptr};
+    HostCallOut o;
+    if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap, res, o)))
+        return rc;
+    ctx->h2d_bytes += o.h2d;
+    ctx->d2h_bytes += o.d2h;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return finish_host_batch(o, sel_off, sel, sel_cap);
+}
+
+int mine_run_batch_async(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                         const mine_settings *settings, mine_q16 *nw_score, int32_t *n_sel,
+                         int64_t *sel_off, mine_pair *sel, int64_t sel_cap, uint64_t *ticket)
+{
+    if (!ctx || !dict || !ticket) return fail(MINE_EINVAL, "null context, dictionary or ticket");
+    *ticket = 0;
+    int rc = check_batch(batch);
+    if (rc) return rc;
+    if ((rc = check_settings(settings))) return rc;
+    const int32_t P = batch->n_pairs;
+    if (P > 0 && (!nw_score || !n_sel || !sel_off)) return fail(MINE_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if ((rc = set_device(ctx))) return rc;
+    AsyncCall *c = nullptr;
+    for (AsyncCall &a : ctx->acall)
+        if (!a.busy) {
+            c = &a;
+            break;
+        }
+    if (!c) return fail(MINE_EAGAIN, "MINE_ASYNC_DEPTH batch calls in flight: wait for one first");
+    if (!ctx->cstream) CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+    if (!c->in_ready) CK(cudaEventCreateWithFlags(&c->in_ready, cudaEventDisableTiming));
+    if (!c->done) CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+    if (!c->gscratch) CK(cudaMalloc(&c->gscratch, ctx->gscratch_bytes));
+    sel_off[0] = 0;
+    c->out = HostCallOut{};
+    if (P > 0) {
+        const HostCallRes res{&c->inbuf, &c->arena, &c->pin, c->gscratch, ctx->stream, ctx->cstream,
+                              c->in_ready};
+        if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap,
+                                     res, c->out)))
+            return rc;
+        ctx->h2d_bytes += c->out.h2d;
+        ctx->d2h_bytes += c->out.d2h;
+    }
+    CK(cudaEventRecord(c->done, ctx->stream));
+    c->busy = true;
+    c->waiting = false;
+    c->ticket = ctx->next_async++;
+    c->dict = dict;
+    const_cast<mine_dict *>(dict)->inflight++;
+    c->sel_off = sel_off;
+    c->sel = sel;
+    c->sel_cap = sel_cap;
+    *ticket = c->ticket;
+    return MINE_OK;
+}
+
+int mine_batch_wait(mine_ctx *ctx, uint64_t ticket)
+{
+    if (!ctx) return fail(MINE_EINVAL, "null context");
+    AsyncCall *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        for (AsyncCall &a : ctx->acall)
+            if (a.busy && !a.waiting && a.ticket == ticket) {
+                c = &a;
+                break;
+            }
+        if (!c) return fail(MINE_EINVAL, "no batch call in flight with this ticket");
+        c->waiting = true;   // the slot stays taken while this thread waits without the lock
+    }
+    const cudaError_t e = cudaEventSynchronize(c->done);
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    const int rc = e == cudaSuccess ? finish_host_batch(c->out, c->sel_off, c->sel, c->sel_cap)
+                                    : fail(MINE_ECUDA, std::string("cudaEventSynchronize: ") +
+                                                           cudaGetErrorString(e));
+    const_cast<mine_dict *>(c->dict)->inflight--;
+    c->busy = c->waiting = false;
+    return rc;
 }
 
 int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,

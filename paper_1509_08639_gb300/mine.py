@@ -80,6 +80,9 @@ SIGNATURES = {
     "mine_batch_capacity": (_L, [_P, _I, _I]),
     "mine_run_batch": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P, _P,
                             _P, _P, _L]),
+    "mine_run_batch_async": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P,
+                                  _P, _P, _P, _L, ctypes.POINTER(ctypes.c_uint64)]),
+    "mine_batch_wait": (_I, [_P, ctypes.c_uint64]),
     "mine_run_batch_device": (_I, [_P, _P, ctypes.POINTER(BatchC), _P,
                                    ctypes.POINTER(SettingsC), _P, _P, _P, _L, _P]),
     "mine_check": (_I, [_P]),
@@ -149,6 +152,14 @@ def make_doc(sent_off, tokens):
     return Doc(_ptr(so), _ptr(tk), so.shape[0] - 1), (so, tk)
 
 
+class AsyncBatch:
+    """A call of ``Context.run_batch_async`` in flight: its ticket, and every
+    array the library reads or writes until ``Context.batch_wait``."""
+
+    def __init__(self, ticket, P, n, inputs, outs):
+        self.ticket, self.P, self.n, self.inputs, self.outs = ticket, P, n, inputs, outs
+
+
 class Context:
     """One miner context on one CUDA device."""
 
@@ -209,6 +220,40 @@ class Context:
         _check(self.L.mine_run_batch(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc),
                                      _ptr(nw), _ptr(ns), _ptr(off), _ptr(sel), cap), self.L)
         return unpack_results(P, n, nw, ns, off, sel)
+
+    def run_batch_async(self, dict_h, batch, settings):
+        """Enqueue a host-buffer call and return at once; ``batch_wait`` on the
+        returned handle gives what ``run_batch`` would have returned.  The
+        handle keeps every array of the call alive until then."""
+        do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
+        P = (do.shape[0] - 1) // 2
+        n = len(settings)
+        g = _c32([s[0] for s in settings])
+        th = _c32([s[1] for s in settings])
+        bc = BatchC(P, so.shape[0] - 1, tk.shape[0], _ptr(do), _ptr(so), _ptr(tk))
+        sc = SettingsC(n, _ptr(g), _ptr(th))
+        cap = max(int(self.L.mine_batch_capacity(_ptr(do), P, n)), 1)
+        outs = (np.zeros(P * n, np.int32), np.zeros(P * n, np.int32), np.zeros(P * n + 1, np.int64),
+                np.zeros((cap, 3), np.int32), cap)
+        t = self.run_batch_async_raw(dict_h, bc, sc, outs)
+        return AsyncBatch(t, P, n, (do, so, tk, g, th, bc, sc), outs)
+
+    def batch_wait(self, handle):
+        """Wait for a call of ``run_batch_async``; results[p][k] = (nw_score, [(i, j, s)])."""
+        self.batch_wait_raw(handle.ticket)
+        nw, ns, off, sel, _ = handle.outs
+        return unpack_results(handle.P, handle.n, nw, ns, off, sel)
+
+    def run_batch_async_raw(self, dict_h, bc, sc, outs):
+        """Asynchronous host-buffer call with pre-built ctypes structs; returns its ticket."""
+        nw, ns, off, sel, cap = outs
+        t = ctypes.c_uint64()
+        _check(self.L.mine_run_batch_async(self.h, dict_h, ctypes.byref(bc), ctypes.byref(sc), _ptr(nw),
+                                           _ptr(ns), _ptr(off), _ptr(sel), cap, ctypes.byref(t)), self.L)
+        return int(t.value)
+
+    def batch_wait_raw(self, ticket):
+        return _check(self.L.mine_batch_wait(self.h, ctypes.c_uint64(ticket)), self.L)
 
     def run_batch_bidi(self, fwd_h, bwd_h, batch, settings):
         """Both directions; results[p][k] = (nw forward, nw backward, union [(i, j, s)])."""

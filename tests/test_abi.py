@@ -72,4 +72,6 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.mine_dict_create(None, None, None, None, 0, None) == -1
     assert lib.mine_align_matrix(None, None, 0, 0, 0, 0, None, None, None) == -1
     assert lib.mine_run_batch(None, None, None, None, None, None, None, None, 0) == -1
+    assert lib.mine_run_batch_async(None, None, None, None, None, None, None, None, 0, None) == -1
+    assert lib.mine_batch_wait(None, 1) == -1
     assert lib.mine_check(None) == -1
