@@ -494,8 +494,9 @@ struct AsyncCall {
     DevBuf inbuf, arena;
     HostBuf pin;
     void *gscratch = nullptr;
-    cudaEvent_t in_ready = nullptr;    // inputs and plan on the device (copy stream)
-    cudaEvent_t done = nullptr;        // last result copy (context stream)
+    cudaEvent_t in_ready = nullptr;    // inputs and plan on the device (input stream)
+    cudaEvent_t packed = nullptr;      // results packed (context stream)
+    cudaEvent_t done = nullptr;        // last result copy (output stream)
     const mine_dict *dict = nullptr;
     const int64_t *sel_off = nullptr;
     const mine_pair *sel = nullptr;
@@ -561,6 +562,7 @@ struct mine_ctx {
 
     // host-buffer batch calls in flight (mine_run_batch_async)
     cudaStream_t cstream = nullptr;    // their input copies
+    cudaStream_t ostream = nullptr;    // their result copies
     AsyncCall acall[MINE_ASYNC_DEPTH];
     uint64_t next_async = 1;
 };
@@ -949,10 +951,12 @@ int mine_close(mine_ctx *ctx)
             a.busy = false;
         }
         if (a.in_ready) cudaEventDestroy(a.in_ready);
+        if (a.packed) cudaEventDestroy(a.packed);
         if (a.done) cudaEventDestroy(a.done);
         if (a.gscratch) cudaFree(a.gscratch);
     }
     if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+    if (ctx->ostream) cudaStreamDestroy(ctx->ostream);
     for (mine_result &r : ctx->ready) std::free(r.pairs);
     ctx->ready.clear();
     for (mine_dict *d : ctx->dicts) {
@@ -1102,15 +1106,17 @@ struct HostCallRes {
     DevBuf *inbuf, *arena;
     HostBuf *pin;
     void *gscratch;
-    cudaStream_t st;         // kernels and result copies
+    cudaStream_t st;         // kernels
     cudaStream_t cst;        // input and plan copies (st itself for a synchronous call)
     cudaEvent_t in_ready;    // recorded on cst after them when cst != st
+    cudaStream_t ost;        // result copies (st itself for a synchronous call)
+    cudaEvent_t packed;      // recorded on st after the packing when ost != st
 };
 
 // Enqueue one host-buffer batch call of P > 0 pairs: the inputs go first,
 // into their own buffer (their copy overlaps the planning), then the plan;
-// the kernels, the packing of the selections and the copies of every result
-// into the caller's arrays follow on res.st.  Nothing waits for the device
+// the kernels and the packing of the selections follow on res.st, the copies
+// of every result into the caller's arrays on res.ost.  Nothing waits for the device
 // unless a step fails: then both streams are synchronised, so the caller may
 // free its inputs on return.
 static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
@@ -1134,6 +1140,7 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     auto bail = [&](int code) {
         cudaStreamSynchronize(cst);
         if (st != cst) cudaStreamSynchronize(st);
+        if (res.ost != st) cudaStreamSynchronize(res.ost);
         return code;
     };
     std::vector<Setting> set(n);
@@ -1172,12 +1179,17 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     ctx->launches += timed_launch(ctx, KID_PACK, st, [&] { return launch_pack(b, n, R, d_bs, d_off, d_pk, st); });
     CK(cudaGetLastError());
     // results straight into the caller's arrays
+    const cudaStream_t ost = res.ost;
+    if (ost != st) {
+        CK(cudaEventRecord(res.packed, st));
+        CK(cudaStreamWaitEvent(ost, res.packed, 0));
+    }
     const int64_t cp = std::min(sel_cap, pl.sel_cap);
-    CK(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, st));
-    if (cp > 0 && sel) CK(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
+    CK(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
+    CK(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, ost));
+    if (cp > 0 && sel) CK(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, ost));
+    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, ost));
     out.R = R;
     out.h_err = h_err;
     out.h2d = L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
@@ -1212,7 +1224,7 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     sel_off[0] = 0;
     if (P == 0) return MINE_OK;
     const HostCallRes res{&ctx->inbuf, &ctx->arena, &ctx->pin, ctx->gscratch, ctx->stream, ctx->stream,
-                          nullptr};
+                          nullptr, ctx->stream, nullptr};
     HostCallOut o;
     if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap, res, o)))
         return rc;
@@ -1243,21 +1255,25 @@ int mine_run_batch_async(mine_ctx *ctx, const mine_dict *dict, const mine_batch 
         }
     if (!c) return fail(MINE_EAGAIN, "MINE_ASYNC_DEPTH batch calls in flight: wait for one first");
     if (!ctx->cstream) CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+    if (!ctx->ostream) CK(cudaStreamCreateWithFlags(&ctx->ostream, cudaStreamNonBlocking));
     if (!c->in_ready) CK(cudaEventCreateWithFlags(&c->in_ready, cudaEventDisableTiming));
+    if (!c->packed) CK(cudaEventCreateWithFlags(&c->packed, cudaEventDisableTiming));
     if (!c->done) CK(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
     if (!c->gscratch) CK(cudaMalloc(&c->gscratch, ctx->gscratch_bytes));
     sel_off[0] = 0;
     c->out = HostCallOut{};
     if (P > 0) {
         const HostCallRes res{&c->inbuf, &c->arena, &c->pin, c->gscratch, ctx->stream, ctx->cstream,
-                              c->in_ready};
+                              c->in_ready, ctx->ostream, c->packed};
         if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap,
                                      res, c->out)))
             return rc;
         ctx->h2d_bytes += c->out.h2d;
         ctx->d2h_bytes += c->out.d2h;
     }
-    CK(cudaEventRecord(c->done, ctx->stream));
+    // P == 0: nothing was enqueued; the event still orders the wait after
+    // earlier work of the context
+    CK(cudaEventRecord(c->done, P > 0 ? ctx->ostream : ctx->stream));
     c->busy = true;
     c->waiting = false;
     c->ticket = ctx->next_async++;
