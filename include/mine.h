@@ -128,7 +128,8 @@ int mine_close(mine_ctx *ctx);
 int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_off,
                      const int32_t *trans, int32_t n_keys, mine_dict **out);
 
-/* MINE_EBUSY while submitted requests that use it have not finished. */
+/* MINE_EBUSY while submitted requests that use it have not finished, or
+ * while a mine_run_batch_async call that uses it has not been waited for. */
 int mine_dict_destroy(mine_ctx *ctx, mine_dict *dict);
 
 /* Queue one article pair for mining with one (gap, threshold) setting.
@@ -371,9 +372,10 @@ int mine_autotune(mine_ctx *ctx);
 
 /* The same tuning on a batch of the caller's workload (host buffers as for
  * mine_run_batch): its score matrices are computed once, then for every size
- * bin present in it each other form its pairs allow (one warp, one CTA,
- * tiles) is tried on the whole batch's alignment, and the fastest is kept
- * when more than 3% faster.  Synchronous; uses the context's scratch. */
+ * bin present in it each other form its pairs allow (one warp; one CTA, for
+ * a bin holding a pair of more than 32 source sentences; tiles) is tried on
+ * the whole batch's alignment (mean of four timed runs), and the fastest is
+ * kept when more than 3% faster.  Synchronous; uses the context's scratch. */
 int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch);
 
 /* Read (get != 0) or set the strategy table: tab[b] = 2 tiles of 256 x 512

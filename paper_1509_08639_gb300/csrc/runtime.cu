@@ -805,7 +805,7 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         pack_plan(q, L, hp);
         CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
         BatchDev bq = make_batchdev(q, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 5; ++rep) {   // one untimed, four timed
             CK(cudaMemsetAsync(bq.counters, 0, 4 * 8, st));   // queue heads; keeps the error word
             if (bq.n_tiles > 0) CK(cudaMemsetAsync(bq.tbnd, 0, 4 * bq.n_tbnd, st));
             if (rep == 1) CK(cudaEventRecord(e0, st));
@@ -820,24 +820,29 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         CK(cudaMemcpy(&derr, bq.err, 4, cudaMemcpyDeviceToHost));
         if (derr) return fail(derr == ERR_TIMEOUT ? MINE_ETIMEDOUT : MINE_EINVAL, device_err_text(derr));
         CK(cudaEventElapsedTime(&ms, e0, e1));
-        ms /= 2.0f;
+        ms /= 4.0f;
         return 0;
     };
-    // the forms open to some pair of each bin present in the batch
+    // the forms open to some pair of each bin present in the batch.  A whole
+    // CTA pipelines its warps over 32-row stripes: for a pair of one stripe
+    // seven of its eight warps would idle, so that form is tried only for
+    // bins holding a pair of more rows.
+    bool present[kAlignBins] = {};
     bool can[kAlignBins][3] = {};
     for (const PairPlan &pp : pl.pairs) {
         const int64_t c = (int64_t)pp.S * pp.T;
         int bin = 0;
         while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
         if (bin >= kAlignBins) continue;
-        can[bin][1] = true;
+        present[bin] = true;
+        if (pp.S > kTile) can[bin][1] = true;
         if (!(pp.S > kTile && pp.T >= kRing)) can[bin][0] = true;
         if (pp.S > kAlignTileRows && pp.T > kAlignTileCols) can[bin][2] = true;
     }
     float best = 0.f;
     rc = time_with(tab, best);
     for (int bin = 0; bin < kAlignBins && rc == 0; ++bin) {
-        if (!can[bin][1]) continue;
+        if (!present[bin]) continue;
         // the form the bin has now (the built-in rule decides for a pair of
         // the bin's middle size when the entry is -1), then each other one
         int now = tab[bin];
