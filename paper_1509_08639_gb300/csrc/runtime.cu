@@ -1278,7 +1278,13 @@ int mine_run_batch_async(mine_ctx *ctx, const mine_dict *dict, const mine_batch 
     }
     // P == 0: nothing was enqueued; the event still orders the wait after
     // earlier work of the context
-    CK(cudaEventRecord(c->done, P > 0 ? ctx->ostream : ctx->stream));
+    const cudaError_t er = cudaEventRecord(c->done, P > 0 ? ctx->ostream : ctx->stream);
+    if (er != cudaSuccess) {   // nothing to wait on: finish the enqueued work here
+        cudaStreamSynchronize(ctx->cstream);
+        cudaStreamSynchronize(ctx->stream);
+        cudaStreamSynchronize(ctx->ostream);
+        return fail(MINE_ECUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(er));
+    }
     c->busy = true;
     c->waiting = false;
     c->ticket = ctx->next_async++;
