@@ -340,8 +340,8 @@ int mine_check(mine_ctx *ctx);
  * (for launch accounting by callers). */
 int64_t mine_launch_count(mine_ctx *ctx);
 
-/* Bytes copied host->device and device->host so far by mine_run_batch calls
- * on this context (inputs, launch plan, results). */
+/* Bytes copied host->device and device->host so far by mine_run_batch and
+ * mine_run_batch_async calls on this context (inputs, launch plan, results). */
 int mine_io_bytes(mine_ctx *ctx, int64_t *h2d, int64_t *d2h);
 
 /* Per-kernel device timing: when enabled, every kernel the context launches

@@ -1,10 +1,11 @@
 // runtime.cu -- host side of the miner: the C ABI of include/mine.h.
 //
 // Contexts own a stream, a growable scratch arena for the synchronous batch
-// calls, and a serving engine: a host thread that forms batches from
-// submitted article pairs (continuous batching), admits them against a fixed
-// device-memory pool (the budget), runs up to max_inflight batches at once on
-// their own streams, and hands results to mine_poll.
+// calls, two sets of buffers (and a copy stream each way) for host-buffer
+// batch calls in flight, and a serving engine: a host thread that forms
+// batches from submitted article pairs (continuous batching), admits them
+// against a fixed device-memory pool (the budget), runs up to max_inflight
+// batches at once on their own streams, and hands results to mine_poll.
 #include "internal.h"
 
 #include <algorithm>
@@ -515,7 +516,7 @@ struct mine_ctx {
     DevBuf inbuf;                      // inputs of the host-buffer batch call
     HostBuf pin;                       // staging of the synchronous calls
     std::atomic<int64_t> launches{0};
-    std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // synchronous host-buffer calls
+    std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // host-buffer batch calls
     // per-kernel timing (CUDA events on the launching stream)
     std::mutex prof_mu;
     bool prof_on = false;
