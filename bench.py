@@ -442,7 +442,7 @@ def main():
     dh = ctx.dict_create(w.dictionary)
     # alignment strategy per size bin, timed on this GPU
     t_tune = time.perf_counter()
-    align_table = ctx.align_strategy() if args.no_autotune else ctx.autotune_batch(dh, w.batch)
+    align_table = ctx.align_strategy() if args.no_autotune else ctx.autotune_batch(dh, w.batch, w.settings)
     t_tune = time.perf_counter() - t_tune
 
     # ---- device-resident inputs
@@ -660,7 +660,7 @@ def main():
                      "whole_cta_bins": [k for k, v in enumerate(align_table) if v == 1],
                      "one_warp_bins": [k for k, v in enumerate(align_table) if v == 0],
                      "bin": "ceil(log2(S*T+1)); other bins keep the built-in rule",
-                     "how": "mine_autotune_batch on the benchmark batch (strategies timed on its alignment)"},
+                     "how": "mine_autotune_batch on the benchmark batch and settings (strategies timed on its alignments)"},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

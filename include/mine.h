@@ -371,12 +371,16 @@ const char *mine_kernel_name(int32_t id);
 int mine_autotune(mine_ctx *ctx);
 
 /* The same tuning on a batch of the caller's workload (host buffers as for
- * mine_run_batch): its score matrices are computed once, then for every size
- * bin present in it each other form its pairs allow (one warp; one CTA, for
- * a bin holding a pair of more than 32 source sentences; tiles) is tried on
- * the whole batch's alignment (mean of four timed runs), and the fastest is
- * kept when more than 3% faster.  Synchronous; uses the context's scratch. */
-int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch);
+ * mine_run_batch) with the settings it will be mined with (settings NULL:
+ * one setting, gap -65536 and threshold 32768; the distinct gaps set the
+ * alignments per pair): its score matrices are computed once, then for
+ * every size bin present in it each other form its pairs allow (one warp;
+ * one CTA, for a bin holding a pair of more than 32 source sentences; tiles)
+ * is tried on the whole batch's alignments (mean of four timed runs), and
+ * the fastest is kept when more than 3% faster.  Synchronous; uses the
+ * context's scratch. */
+int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                        const mine_settings *settings);
 
 /* Read (get != 0) or set the strategy table: tab[b] = 2 tiles of 256 x 512
  * cells over many CTAs (pairs with S > 256 and T > 512; others of the bin

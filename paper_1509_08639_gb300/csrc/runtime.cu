@@ -112,34 +112,79 @@ struct Plan {
     int32_t R = 0;
     int32_t n_big = 0;              // alignments [0, n_big) use a whole CTA
     int64_t n_sent = 0, n_tok = 0;
+
+    // empty again, keeping the vectors' storage (a plan reused call after
+    // call allocates nothing once it has grown)
+    void reset()
+    {
+        P = 0;
+        pairs.clear();
+        pitems.clear();
+        sitems.clear();
+        dorder.clear();
+        nitems.clear();
+        tiles.clear();
+        n_tiled = 0;
+        tb_words = 0;
+        set_gap.clear();
+        set_thr.clear();
+        gap_val.clear();
+        m_elems = code_words = match_words = sel_cap = 0;
+        R = 0;
+        n_big = 0;
+        n_sent = n_tok = 0;
+    }
+};
+
+// A pair's settings list, checked once for every pair that has the same
+// list: each setting's gap as an index into the list's distinct gaps (in
+// order of first appearance) and the largest |gap|.
+struct SettingsSeen {
+    std::vector<Setting> list;
+    std::vector<int32_t> local, thr, gaps;
+    int64_t max_g = 0;
+    bool valid = false;
 };
 
 // Validate a pair's settings and add them to the plan; returns the number of
-// distinct gaps (their indices start at gap0).
-int add_settings(Plan &pl, const Setting *set, int n, int32_t S, int32_t T, int64_t max_abs_s,
-                 bool mined, int32_t &gap0, int32_t &ngap)
+// distinct gaps (their indices start at gap0).  `seen` keeps the last list
+// checked: a pair with the same list only has its size bound checked.
+int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_t S, int32_t T,
+                 int64_t max_abs_s, bool mined, int32_t &gap0, int32_t &ngap)
 {
     if (n < 1 || n > 256) return fail(MINE_EINVAL, "settings count must be in [1, 256]");
-    gap0 = (int32_t)pl.gap_val.size();
-    for (int k = 0; k < n; ++k) {
-        const int32_t g = set[k].first, th = set[k].second;
-        if (g > 0) return fail(MINE_EINVAL, "gap must be <= 0");
-        if (mined && (th < 0 || th > 65536))
-            return fail(MINE_EINVAL, "threshold must be in [0, 65536]");
-        const int64_t bound = (int64_t)(S + T) * (-(int64_t)g) + (int64_t)std::min(S, T) * max_abs_s;
-        if (bound >= (int64_t(1) << 31))
-            return fail(MINE_EOVERFLOW, "(S+T)*|gap| + min(S,T)*max|s| reaches 2^31");
-        int gi = -1;
-        for (int q = gap0; q < (int)pl.gap_val.size(); ++q)
-            if (pl.gap_val[q] == g) gi = q;
-        if (gi < 0) {
-            gi = (int)pl.gap_val.size();
-            pl.gap_val.push_back(g);
+    if (!seen.valid || (int)seen.list.size() != n || !std::equal(set, set + n, seen.list.begin())) {
+        seen.valid = false;
+        seen.list.assign(set, set + n);
+        seen.local.resize(n);
+        seen.thr.resize(n);
+        seen.gaps.clear();
+        seen.max_g = 0;
+        for (int k = 0; k < n; ++k) {
+            const int32_t g = set[k].first, th = set[k].second;
+            if (g > 0) return fail(MINE_EINVAL, "gap must be <= 0");
+            if (mined && (th < 0 || th > 65536))
+                return fail(MINE_EINVAL, "threshold must be in [0, 65536]");
+            const auto it = std::find(seen.gaps.begin(), seen.gaps.end(), g);
+            seen.local[k] = (int32_t)(it - seen.gaps.begin());
+            seen.thr[k] = th;
+            if (it == seen.gaps.end()) seen.gaps.push_back(g);
+            seen.max_g = std::max(seen.max_g, -(int64_t)g);
         }
-        pl.set_gap.push_back(gi);
-        pl.set_thr.push_back(th);
+        seen.valid = true;
     }
-    ngap = (int32_t)pl.gap_val.size() - gap0;
+    // the bound grows with |gap|: the largest decides for every setting
+    const int64_t bound = (int64_t)(S + T) * seen.max_g + (int64_t)std::min(S, T) * max_abs_s;
+    if (bound >= (int64_t(1) << 31))
+        return fail(MINE_EOVERFLOW, "(S+T)*|gap| + min(S,T)*max|s| reaches 2^31");
+    gap0 = (int32_t)pl.gap_val.size();
+    pl.gap_val.insert(pl.gap_val.end(), seen.gaps.begin(), seen.gaps.end());
+    const size_t at = pl.set_gap.size();
+    pl.set_gap.resize(at + n);
+    pl.set_thr.insert(pl.set_thr.end(), seen.thr.begin(), seen.thr.end());
+    int32_t *sg = pl.set_gap.data() + at;
+    for (int k = 0; k < n; ++k) sg[k] = gap0 + seen.local[k];
+    ngap = (int32_t)seen.gaps.size();
     return 0;
 }
 
@@ -149,7 +194,7 @@ template <class F>
 int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F settings_of,
                int64_t max_abs_s, bool mined, const int8_t *align_tab = nullptr, bool swap = false)
 {
-    pl = Plan();
+    pl.reset();
     pl.P = P;
     pl.n_sent = n_sent;
     if (P < 0) return fail(MINE_EINVAL, "negative pair count");
@@ -162,6 +207,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
     if ((int64_t)doc_off[2 * (int64_t)P] != n_sent)
         return fail(MINE_EINVAL, "doc_off[2P] must equal n_sent");
     pl.pairs.resize(P);
+    SettingsSeen seen;
     std::vector<int> bucketS(P), bucketC(P), bucketD(P);
     std::vector<int8_t> kind(P);
     int64_t n_pitems = 0, n_sitems = 0;
@@ -180,7 +226,11 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         settings_of(p, set, n);
         pp.set0 = pl.R;
         pp.nset = n;
-        int rc = add_settings(pl, set, n, pp.S, pp.T, max_abs_s, mined, pp.gap0, pp.ngap);
+        if (p == 0) {   // the first pair's count as a guess for every pair
+            pl.set_gap.reserve((size_t)P * n);
+            pl.set_thr.reserve((size_t)P * n);
+        }
+        int rc = add_settings(pl, seen, set, n, pp.S, pp.T, max_abs_s, mined, pp.gap0, pp.ngap);
         if (rc) return rc;
         pl.R += n;
         pp.m_off = pl.m_elems;
@@ -494,6 +544,7 @@ struct AsyncCall {
     uint64_t ticket = 0;
     DevBuf inbuf, arena;
     HostBuf pin;
+    Plan plan;                         // reused call after call (its storage stays)
     void *gscratch = nullptr;
     cudaEvent_t in_ready = nullptr;    // inputs and plan on the device (input stream)
     cudaEvent_t packed = nullptr;      // results packed (context stream)
@@ -515,6 +566,7 @@ struct mine_ctx {
     DevBuf arena;                      // scratch of the synchronous calls
     DevBuf inbuf;                      // inputs of the host-buffer batch call
     HostBuf pin;                       // staging of the synchronous calls
+    Plan plan;                         // of the synchronous host-buffer batch call
     std::atomic<int64_t> launches{0};
     std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // host-buffer batch calls
     // per-kernel timing (CUDA events on the launching stream)
@@ -746,21 +798,33 @@ int mine_autotune(mine_ctx *ctx)
 }
 
 static int check_batch(const mine_batch *b);
+static int check_settings(const mine_settings *s);
 
-int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch)
+int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
+                        const mine_settings *settings)
 {
     if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
     int rc = check_batch(batch);
     if (rc) return rc;
+    if (settings && (rc = check_settings(settings))) return rc;
     const int32_t P = batch->n_pairs;
     if (P == 0) return MINE_OK;
     std::lock_guard<std::mutex> lk(ctx->api_mu);
     if ((rc = set_device(ctx))) return rc;
     ++ctx->arena_gen;
-    const Setting set(-65536, 32768);
+    // the settings the batch will be mined with: their distinct gaps are
+    // the alignments each pair gets
+    std::vector<Setting> set;
+    if (settings) {
+        for (int k = 0; k < settings->n; ++k) set.push_back(Setting(settings->gaps[k], settings->thresholds[k]));
+    } else {
+        set.push_back(Setting(-65536, 32768));
+    }
+    const int nset = (int)set.size();
     auto plan_with = [&](Plan &pl, const int8_t *tab) {
         int r = build_plan(pl, P, batch->doc_off, batch->n_sent,
-                           [&](int32_t, const Setting *&s, int &cnt) { s = &set; cnt = 1; }, 65536, true, tab);
+                           [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = nset; }, 65536,
+                           true, tab);
         pl.n_tok = batch->n_tok;
         return r;
     };
@@ -1111,6 +1175,7 @@ static int check_batch(const mine_batch *b)
 struct HostCallRes {
     DevBuf *inbuf, *arena;
     HostBuf *pin;
+    Plan *plan;
     void *gscratch;
     cudaStream_t st;         // kernels
     cudaStream_t cst;        // input and plan copies (st itself for a synchronous call)
@@ -1151,7 +1216,7 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     };
     std::vector<Setting> set(n);
     for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
-    Plan pl;
+    Plan &pl = *res.plan;
     rc = build_plan(pl, P, batch->doc_off, batch->n_sent,
                     [&](int32_t, const Setting *&s, int &cnt) { s = set.data(); cnt = n; }, 65536, true,
                     ctx->align_tab);
@@ -1229,8 +1294,8 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     ++ctx->arena_gen;
     sel_off[0] = 0;
     if (P == 0) return MINE_OK;
-    const HostCallRes res{&ctx->inbuf, &ctx->arena, &ctx->pin, ctx->gscratch, ctx->stream, ctx->stream,
-                          nullptr, ctx->stream, nullptr};
+    const HostCallRes res{&ctx->inbuf, &ctx->arena, &ctx->pin, &ctx->plan, ctx->gscratch, ctx->stream,
+                          ctx->stream, nullptr, ctx->stream, nullptr};
     HostCallOut o;
     if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap, res, o)))
         return rc;
@@ -1269,8 +1334,8 @@ int mine_run_batch_async(mine_ctx *ctx, const mine_dict *dict, const mine_batch 
     sel_off[0] = 0;
     c->out = HostCallOut{};
     if (P > 0) {
-        const HostCallRes res{&c->inbuf, &c->arena, &c->pin, c->gscratch, ctx->stream, ctx->cstream,
-                              c->in_ready, ctx->ostream, c->packed};
+        const HostCallRes res{&c->inbuf, &c->arena, &c->pin, &c->plan, c->gscratch, ctx->stream,
+                              ctx->cstream, c->in_ready, ctx->ostream, c->packed};
         if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap,
                                      res, c->out)))
             return rc;

@@ -94,7 +94,7 @@ SIGNATURES = {
     "mine_profile_read": (_I, [_P, _P, _P, _I]),
     "mine_kernel_name": (ctypes.c_char_p, [_I]),
     "mine_autotune": (_I, [_P]),
-    "mine_autotune_batch": (_I, [_P, _P, ctypes.POINTER(BatchC)]),
+    "mine_autotune_batch": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC)]),
     "mine_score_f32": (_I, [_P, _P, ctypes.POINTER(BatchC), _P, _L]),
     "mine_align_strategy": (_I, [_P, _P, _I, _I]),
     "mine_run_batch_bidi": (_I, [_P, _P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P,
@@ -383,12 +383,19 @@ class Context:
         _check(self.L.mine_autotune(self.h), self.L)
         return self.align_strategy()
 
-    def autotune_batch(self, dict_h, batch):
-        """Tune the per-bin alignment strategy on a batch of the workload;
+    def autotune_batch(self, dict_h, batch, settings=None):
+        """Tune the per-bin alignment strategy on a batch of the workload and
+        the settings it will be mined with (None: one default setting);
         returns the strategy table."""
         do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
         bc = BatchC(batch.n_pairs, int(so.shape[0] - 1), int(tk.shape[0]), _ptr(do), _ptr(so), _ptr(tk))
-        _check(self.L.mine_autotune_batch(self.h, dict_h, ctypes.byref(bc)), self.L)
+        sc = None
+        if settings is not None:
+            g = _c32([s[0] for s in settings])
+            th = _c32([s[1] for s in settings])
+            sc = SettingsC(len(settings), _ptr(g), _ptr(th))
+        _check(self.L.mine_autotune_batch(self.h, dict_h, ctypes.byref(bc),
+                                          ctypes.byref(sc) if sc is not None else None), self.L)
         return self.align_strategy()
 
     def align_strategy(self, table=None):

@@ -235,6 +235,13 @@ def test_alignment_strategies_agree(ctx):
         tuned = ctx.autotune_batch(dh, w.batch)
         assert all(v in (-1, 0, 1) for v in tuned)
         assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned on the batch")
+        # tuned with a sweep of settings (three distinct gaps per pair)
+        sweep = w.settings + [(-16384, 16384), (0, 65536), (-16384, 40000)]
+        tuned = ctx.autotune_batch(dh, w.batch, sweep)
+        assert all(v in (-1, 0, 1, 2) for v in tuned)
+        assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned on the batch and a sweep")
+        with pytest.raises(mine.MineError):
+            ctx.autotune_batch(dh, w.batch, [(1, 0)])            # gap > 0
     finally:
         ctx.align_strategy(old)
 
