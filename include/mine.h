@@ -234,8 +234,9 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
  * writes them, nor reads the outputs, before then.  Each call in flight has
  * its own input buffer, scratch and staging, so with PINNED host arrays
  * (cudaMallocHost or cudaHostRegister) the input copies of one call run on a
- * copy stream while the kernels of the call before it run; the kernels of
- * successive calls run one after another.  With pageable arrays the call
+ * copy stream while the kernels of the call before it run, and its result
+ * copies on another while the kernels of the call after it run; the kernels
+ * of successive calls run one after another.  With pageable arrays the call
  * waits for its copies.  MINE_EAGAIN when MINE_ASYNC_DEPTH calls are in
  * flight (wait for one first).  The dictionary cannot be destroyed
  * (MINE_EBUSY) while a call using it is in flight; mine_close waits for
