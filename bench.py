@@ -195,6 +195,8 @@ def kept_entries(w):
     st = _sorted_unique((tok_sent[~tgt] << 32) | tokens[~tgt])
     s_sent, s_tok = st >> 32, st & 0xFFFFFFFF
     keys = d.keys.astype(np.int64)
+    if keys.shape[0] == 0:
+        return 0
     toff = d.trans_off.astype(np.int64)
     order = np.argsort(keys)
     ks = keys[order]
