@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import datetime
 import hashlib
 import json
 import os
@@ -37,7 +38,7 @@ UNIT = "article pairs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", type=int, default=2, help="1..5 (parity cases); 2 is the bench")
@@ -89,15 +90,21 @@ def whole_job_rate(units_per_rank: int, ws: int, seconds: float) -> float:
 # --------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle sampling around the timed region.  Each
+    sample carries nvidia-smi's own timestamp; the summary keeps those taken
+    between mark_start() and mark_end() (all samples when none was, or when
+    the timestamps cannot be read)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
+    TS_FORMAT = "%Y/%m/%d %H:%M:%S.%f"
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -105,12 +112,18 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -121,26 +134,40 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @classmethod
+    def parse(cls, line):
+        """(time or None, sm MHz, max sm MHz, hw, hw thermal, sw thermal, power cap)."""
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            return None
+        try:
+            row = (float(f[2]), float(f[3]), f[6], f[7], f[8], f[9])
+        except ValueError:
+            return None
+        try:
+            t = datetime.datetime.strptime(f[0], cls.TS_FORMAT).timestamp()
+        except ValueError:
+            t = None
+        return (t,) + row
+
     def summary(self):
         if self.proc is None or not self.path or not os.path.exists(self.path):
             return None
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
-            except ValueError:
-                continue
+        rows = [r for r in (self.parse(line) for line in open(self.path)) if r is not None]
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [r[0] for r in rows]
+        window = "whole sampler run"
+        if self.t0 is not None and self.t1 is not None and all(r[0] is not None for r in rows):
+            inside = [r for r in rows if self.t0 <= r[0] <= self.t1]
+            if inside:
+                rows, window = inside, "timed region"
+        sm = [r[1] for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": reasons, "samples": len(rows), "window": window,
+                "interval_ms": self.INTERVAL_MS}
 
 
 # --------------------------------------------------------------------- helpers
@@ -475,11 +502,13 @@ def main():
     barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        clk.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark_end()
     barrier()
     launches = ctx.launch_count() - launches0
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, ws)

@@ -1,9 +1,11 @@
-"""Host-side arithmetic of the benchmark's roofline, on the CPU: the count
-of kept translations (the entries the preparation kernel writes, part of
-its algorithmic bytes), computed with numpy in bench.py, against a direct
-loop over pairs, sentences, distinct tokens and dictionary entries."""
+"""Host-side logic of the benchmark, on the CPU: the count of kept
+translations (the entries the preparation kernel writes, part of its
+algorithmic bytes), computed with numpy in bench.py, against a direct loop
+over pairs, sentences, distinct tokens and dictionary entries; and the clock
+sampler's choice of the samples taken during the timed region."""
 import os
 import sys
+import time
 
 import numpy as np
 
@@ -47,3 +49,59 @@ def test_kept_entries_of_edge_batches():
     w0 = synth.Workload("empty dictionary", b, synth.dictionary_from_map({}), [], [],
                         [(-65536, 32768)], np.zeros((0, 3), np.int64))
     assert bench.kept_entries(w0) == 0
+
+
+def _fake_smi(tmp_path, flag, stamp=True):
+    fake = tmp_path / "nvidia-smi"
+    ts = ("datetime.datetime.now().strftime('%Y/%m/%d %H:%M:%S.%f')[:-3]" if stamp else "'n/a'")
+    fake.write_text(
+        "#!" + sys.executable + "\n"
+        "import datetime, os, sys, time\n"
+        "while True:\n"
+        f"    on = os.path.exists({str(flag)!r})\n"
+        "    mhz = 2070 if on else 1000\n"
+        "    cap = 'Active' if on else 'Not Active'\n"
+        f"    ts = {ts}\n"
+        "    print(f'{ts}, 0, {mhz}, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, {cap}', flush=True)\n"
+        "    time.sleep(0.02)\n")
+    fake.chmod(0o755)
+
+
+def test_clock_sampler_keeps_the_timed_region(tmp_path, monkeypatch):
+    """A stand-in for nvidia-smi prints a timestamped sample every 20 ms:
+    1000 MHz outside the timed region, 2070 MHz with the power cap active
+    while a file exists; the summary keeps the samples of the region."""
+    flag = tmp_path / "loaded"
+    _fake_smi(tmp_path, flag)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    with bench.ClockSampler(0) as clk:
+        time.sleep(0.1)
+        flag.write_text("1")
+        time.sleep(0.05)          # the stand-in sees the new state
+        clk.mark_start()
+        time.sleep(0.3)
+        clk.mark_end()
+        time.sleep(0.05)
+        flag.unlink()
+    s = clk.summary()
+    assert s["window"] == "timed region"
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] >= 5
+    # no region marked: every sample counts
+    with bench.ClockSampler(0) as clk2:
+        time.sleep(0.1)
+    s2 = clk2.summary()
+    assert s2["window"] == "whole sampler run" and s2["sm_mhz"] == 1000.0 and s2["reasons"] == []
+
+
+def test_clock_sampler_without_readable_timestamps(tmp_path, monkeypatch):
+    flag = tmp_path / "loaded"
+    _fake_smi(tmp_path, flag, stamp=False)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    with bench.ClockSampler(0) as clk:
+        clk.mark_start()
+        time.sleep(0.1)
+        clk.mark_end()
+    s = clk.summary()
+    assert s["window"] == "whole sampler run" and s["samples"] >= 3 and s["sm_mhz"] == 1000.0
