@@ -6,7 +6,7 @@
  * comparable articles and the alignment model of a language pair, find the
  * sentence pairs that are close translation matches.  The comparison is a
  * Needleman-Wunsch global alignment over the sentence-pair score matrix M
- * ("paths cannot go upward or leftward in the M matrix"), with two parameters:
+ * (a path never moves upward or leftward in M), with two parameters:
  * Threshold (confidence needed to accept an aligned pair) and Penalty (how
  * much skipping ahead is allowed).  The paper's confidence is an SVM
  * probability; this library replaces it by a deterministic fixed-point score
@@ -132,7 +132,13 @@ int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_of
  * while a mine_run_batch_async call that uses it has not been waited for. */
 int mine_dict_destroy(mine_ctx *ctx, mine_dict *dict);
 
-/* Queue one article pair for mining with one (gap, threshold) setting.
+/* Queue one article pair for mining with one (gap, threshold) setting: the
+ * unit of work of Section 4 (one pair of comparable articles, the alignment
+ * model of the language pair, Penalty and Threshold in, the sentence pairs
+ * that are close translation matches out; the paper's faster Yalign takes
+ * article after article from a database in one session without reloading its
+ * model, which the context plays here: the dictionary stays resident and
+ * requests are batched as they arrive).
  * The documents are copied before the call returns.  The result arrives
  * through mine_poll with the returned ticket.  Returns MINE_ENOMEM when the
  * request alone exceeds the device budget, MINE_EOVERFLOW per Limits. */
@@ -147,16 +153,32 @@ int mine_submit_sweep(mine_ctx *ctx, const mine_doc *src, const mine_doc *tgt,
                       const mine_dict *dict, int32_t n, const mine_q16 *gaps,
                       const mine_q16 *thresholds, uint64_t *ticket);
 
-/* Collect up to max_out finished results into out[] (host array), waiting up
+/* Collect finished requests: for each, the aligned sentence pairs whose
+ * confidence passes the threshold (Section 4: the Threshold parameter sets the
+ * confidence an aligned pair needs to be accepted) and the alignment score.
+ * Collect up to max_out finished results into out[] (host array), waiting up
  * to timeout_us microseconds (0: do not wait; <0: wait until at least one
  * result is ready or nothing is in flight).  Returns the number written
  * (>= 0) or a negative error. */
 int mine_poll(mine_ctx *ctx, mine_result *out, int32_t max_out, int32_t timeout_us);
 
+/* Serving statistics since the context opened: *batches = batches the
+ * serving loop has run, *max_overlap = the largest number of them that were
+ * on the device at the same moment, from device timestamps taken on each
+ * batch's stream before its first copy and after its last (the last 65,536
+ * batches are kept).  A value above 1 shows that requests arriving while
+ * others run were admitted and overlapped on the device.  Either pointer may
+ * be NULL.  No counterpart in the paper. */
+int mine_serving_stats(mine_ctx *ctx, int64_t *batches, int32_t *max_overlap);
+
 /* Release result->pairs; safe on a zeroed result. */
 void mine_result_free(mine_ctx *ctx, mine_result *result);
 
-/* Alignment only, synchronously, on a caller-supplied score matrix: M is a
+/* The Needleman-Wunsch step of Section 4 alone (the global alignment of the
+ * score matrix M with the Penalty as gap cost, paths that never go upward or
+ * leftward, then the Threshold on the aligned pairs), for a matrix the
+ * caller supplies instead of the dictionary score.
+ * Alignment only, synchronously, on a caller-supplied score matrix: M is a
  * host S x T row-major int32 matrix of any sign.  Writes the selected pairs
  * (s > threshold, increasing i) to out[] (host, capacity min(S,T)), their
  * count to *n_out and H[S][T] to *nw_score.  Any int32 threshold is
@@ -175,8 +197,9 @@ int mine_align_matrix(mine_ctx *ctx, const mine_q16 *M, int32_t S, int32_t T, mi
  * Scratch lives in one static device array of about 8.3 MB that every GPU
  * loading this library holds until the process exits, so S and T are limited
  * to 1024 (MINE_EINVAL beyond).  The first call on a device looks up the
- * array's device address for that device; make that first call before any
- * stream capture.  Every call shares the array (a call clears what must start
+ * array's device address for that device and keeps it for the life of the
+ * process (a device reset after that first call is not supported); make that
+ * first call before any stream capture.  Every call shares the array (a call clears what must start
  * at zero), so calls that overlap on the GPU, from several threads or
  * streams, race: serialize them.  Calls no cudaMalloc or cudaFree. */
 int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T, mine_q16 gap,
@@ -281,6 +304,15 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
  * floats, host memory owned by the caller).  Within 1e-5 of the same score in
  * exact arithmetic.  No alignment runs.  Errors as mine_run_batch. */
 int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,
+                   int64_t out_len);
+
+/* The fixed-point score matrices themselves: for every pair p of the host
+ * batch, its S_p x T_p matrix of s(i,j) (Q16, the definition at the top of
+ * this file; Section 4: the confidence of a sentence pair that the alignment
+ * runs over), written row-major to out, pair after pair (out_len >= sum S*T
+ * values, host memory owned by the caller).  These are the exact values the
+ * mining calls align.  No alignment runs.  Errors as mine_run_batch. */
+int mine_score_q16(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, mine_q16 *out,
                    int64_t out_len);
 
 /* Bidirectional mining (Section 6: classifiers trained from the foreign to
@@ -389,6 +421,25 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
  * rule (tiles from 2^21 cells, a whole CTA from 2^15); n entries,
  * n <= MINE_ALIGN_BINS. */
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get);
+
+/* The roofline of the alignment: the measured rate of int32 add and max
+ * operations of a device (device < 0: the current one).  Every thread of a
+ * full grid runs independent chains of max(x + g, y) in three forms (plain C,
+ * the fused add-then-max intrinsic, max then add); the operations written
+ * are counted (an add and a max are two, fused or not) and the fastest form's
+ * rate is written to *ops_per_s, each form's to per_form[0..n_form) (host, may
+ * be NULL).  Takes about a second.  No counterpart in the paper. */
+int mine_int_peak(int32_t device, double *ops_per_s, double *per_form, int32_t n_form);
+
+/* Fault injection for tests; the paper has no counterpart.  With kind
+ * MINE_INJECT_CUDA_CALL, the count-th CUDA call that the next host-buffer
+ * batch calls (mine_run_batch, mine_run_batch_async) check after their first
+ * input copy is not made and fails as if CUDA had returned an error: the call
+ * then waits for the copies and kernels it had already enqueued and returns
+ * MINE_ECUDA, so the caller may free its arrays at once.  count 0 turns the
+ * injection off.  MINE_EINVAL for an unknown kind or a negative count. */
+#define MINE_INJECT_CUDA_CALL 1
+int mine_test_inject(mine_ctx *ctx, int32_t kind, int32_t count);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmine.so")
-SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "bidi_tune.cu", "best_match.cu"]
+SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "bidi_tune.cu", "best_match.cu", "int_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "-I" + CSRC]

@@ -88,7 +88,9 @@ int fail_na(int code, const char *msg)
 }
 
 // Device address of the static array on the current device (looked up once
-// per device: in host code the array's name is only a stand-in).
+// per device: in host code the array's name is only a stand-in).  The
+// address is kept for the life of the process, so a device reset
+// (cudaDeviceReset) after the first call on that device is not supported.
 int scratch_of_current_device(DeviceScratch &out)
 {
     int dev = 0;
@@ -133,14 +135,19 @@ extern "C" int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T
     DeviceScratch ds;
     int rc = scratch_of_current_device(ds);
     if (rc) return rc;
+    // a launch error left behind by some earlier, unrelated call must not be
+    // taken for one of ours: clear it, then check each launch of this call
+    (void)cudaGetLastError();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int32_t *sc = ds.ptr;
     char *plan = reinterpret_cast<char *>(sc + kOffPlan);
     k_noalloc_setup<<<1, 32, 0, st>>>(sc, S, T, gap, threshold);
+    if (cudaGetLastError() != cudaSuccess) return fail_na(MINE_ECUDA, "set-up kernel launch failed");
     if (S > 0 && T > 0) {
         if (cudaMemcpyAsync(sc + kOffMrow, M, 4 * (size_t)S * T, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return fail_na(MINE_ECUDA, "copy of the matrix failed");
         launch_tile(sc + kOffMrow, S, T, sc + kOffM, st);
+        if (cudaGetLastError() != cudaSuccess) return fail_na(MINE_ECUDA, "tiling kernel launch failed");
     }
     BatchDev b{};
     b.n_pairs = 1;
@@ -163,8 +170,9 @@ extern "C" int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T
     b.sel = sc + kOffSel;
     b.hfin = sc + kOffOut + 2;
     launch_align(b, ds.num_sms, st);
+    if (cudaGetLastError() != cudaSuccess) return fail_na(MINE_ECUDA, "alignment kernel launch failed");
     launch_trace(b, ds.num_sms, st);
-    if (cudaGetLastError() != cudaSuccess) return fail_na(MINE_ECUDA, "kernel launch failed");
+    if (cudaGetLastError() != cudaSuccess) return fail_na(MINE_ECUDA, "traceback kernel launch failed");
     int32_t head[2] = {0, 0}, derr = 0;
     if (cudaMemcpyAsync(head, sc + kOffOut, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(&derr, sc + kOffCounters + 8, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -448,6 +448,13 @@ const char *device_err_text(int32_t e)
     }
 }
 
+// The ABI code of a device error word: MINE_ETIMEDOUT for a bounded wait that
+// ran out, MINE_EINVAL for malformed inputs found on the device.
+int device_fail(int32_t e)
+{
+    return fail(e == ERR_TIMEOUT ? MINE_ETIMEDOUT : MINE_EINVAL, device_err_text(e));
+}
+
 // ------------------------------------------------------------------ pool
 
 // First-fit allocator over one device region: the serving budget.
@@ -519,6 +526,7 @@ struct Request {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;   // timed: before the first copy, after the last
     bool busy = false;
     std::vector<Request> reqs;
     int64_t pool_off = -1, pool_bytes = 0;
@@ -568,6 +576,9 @@ struct mine_ctx {
     HostBuf pin;                       // staging of the synchronous calls
     Plan plan;                         // of the synchronous host-buffer batch call
     std::atomic<int64_t> launches{0};
+    // test fault injection (mine_test_inject): the checked CUDA call of a
+    // host-buffer batch call at which a failure is faked, counting down
+    std::atomic<int32_t> inject_cuda_at{0};
     std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // host-buffer batch calls
     // per-kernel timing (CUDA events on the launching stream)
     std::mutex prof_mu;
@@ -612,6 +623,11 @@ struct mine_ctx {
     uint64_t next_ticket = 1;
     std::thread worker;
     std::vector<mine_dict *> dicts;
+    // device time span of every served batch (ms after `origin`), for the
+    // overlap statistic of mine_serving_stats (guarded by q_mu)
+    cudaEvent_t origin = nullptr;
+    std::vector<std::pair<float, float>> spans;
+    int64_t n_batches = 0;
 
     // host-buffer batch calls in flight (mine_run_batch_async)
     cudaStream_t cstream = nullptr;    // their input copies
@@ -626,6 +642,14 @@ int set_device(mine_ctx *ctx)
 {
     CK(cudaSetDevice(ctx->device));
     return 0;
+}
+
+// True for the checked CUDA call at which mine_test_inject asked for a
+// failure (the call is then not made).
+bool inject_cuda_error(mine_ctx *ctx)
+{
+    if (ctx->inject_cuda_at.load(std::memory_order_relaxed) <= 0) return false;
+    return ctx->inject_cuda_at.fetch_sub(1) == 1;
 }
 
 cudaEvent_t prof_event(mine_ctx *ctx)
@@ -883,7 +907,7 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         CK(cudaGetLastError());
         int32_t derr = 0;
         CK(cudaMemcpy(&derr, bq.err, 4, cudaMemcpyDeviceToHost));
-        if (derr) return fail(derr == ERR_TIMEOUT ? MINE_ETIMEDOUT : MINE_EINVAL, device_err_text(derr));
+        if (derr) return device_fail(derr);
         CK(cudaEventElapsedTime(&ms, e0, e1));
         ms /= 4.0f;
         return 0;
@@ -989,10 +1013,14 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     // one set of per-warp long-sentence tables per batch that can run at once
     ctx->gscratch_bytes = (size_t)ctx->num_sms * kGScratchWarpsPerSm * kScoreScratchPerWarp;
     CK(cudaMalloc(&ctx->gscratch, ctx->gscratch_bytes));
+    CK(cudaEventCreate(&ctx->origin));
+    CK(cudaEventRecord(ctx->origin, ctx->stream));
     for (int k = 0; k < c.max_inflight; ++k) {
         std::unique_ptr<Slot> s(new Slot());
         CK(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+        CK(cudaEventCreate(&s->t0));
+        CK(cudaEventCreate(&s->t1));
         CK(cudaMalloc(&s->gscratch, ctx->gscratch_bytes));
         ctx->slots.push_back(std::move(s));
     }
@@ -1037,8 +1065,11 @@ int mine_close(mine_ctx *ctx)
     for (auto &s : ctx->slots) {
         cudaStreamDestroy(s->st);
         cudaEventDestroy(s->ev);
+        if (s->t0) cudaEventDestroy(s->t0);
+        if (s->t1) cudaEventDestroy(s->t1);
         cudaFree(s->gscratch);
     }
+    if (ctx->origin) cudaEventDestroy(ctx->origin);
     cudaFree(ctx->gscratch);
     if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
     ctx->slots.clear();
@@ -1112,7 +1143,7 @@ int mine_dict_create(mine_ctx *ctx, const int32_t *keys, const int32_t *trans_of
         if (herr) {
             cudaFree(d->slots_mem);
             cudaFree(d->trans_mem);
-            return fail(MINE_EINVAL, device_err_text(herr));
+            return device_fail(herr);
         }
     }
     CK(cudaStreamSynchronize(st));
@@ -1203,17 +1234,24 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     if ((rc = ensure_dev(*res.inbuf, in_tok_at + 4 * batch->n_tok + 16))) return rc;
     int32_t *d_sent = static_cast<int32_t *>(res.inbuf->p);
     int32_t *d_tok = reinterpret_cast<int32_t *>(static_cast<char *>(res.inbuf->p) + in_tok_at);
-    CK(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, cst));
-    if (batch->n_tok > 0)
-        CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, cst));
-    // from here on a failure waits for those copies (the caller may free the
-    // inputs once the call returns)
+    // from the first copy on, every failure waits for the copies and kernels
+    // already enqueued on the call's streams before it returns: the caller may
+    // free or reuse its arrays as soon as the call has returned
     auto bail = [&](int code) {
         cudaStreamSynchronize(cst);
         if (st != cst) cudaStreamSynchronize(st);
         if (res.ost != st) cudaStreamSynchronize(res.ost);
         return code;
     };
+#define CKB(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = inject_cuda_error(ctx) ? cudaErrorInvalidValue : (call);                  \
+        if (e_ != cudaSuccess)                                                                     \
+            return bail(fail(MINE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)));     \
+    } while (0)
+    CKB(cudaMemcpyAsync(d_sent, batch->sent_off, 4 * (batch->n_sent + 1), cudaMemcpyHostToDevice, cst));
+    if (batch->n_tok > 0)
+        CKB(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, cst));
     std::vector<Setting> set(n);
     for (int k = 0; k < n; ++k) set[k] = Setting(settings->gaps[k], settings->thresholds[k]);
     Plan &pl = *res.plan;
@@ -1237,10 +1275,10 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     int32_t *h_err = reinterpret_cast<int32_t *>(hp + err_at);
     *h_err = 0;
     char *base = static_cast<char *>(res.arena->p);
-    CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, cst));
+    CKB(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, cst));
     if (cst != st) {
-        CK(cudaEventRecord(res.in_ready, cst));
-        CK(cudaStreamWaitEvent(st, res.in_ready, 0));
+        CKB(cudaEventRecord(res.in_ready, cst));
+        CKB(cudaStreamWaitEvent(st, res.in_ready, 0));
     }
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, res.gscratch);
     if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return bail(rc);
@@ -1248,23 +1286,24 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     int32_t *d_pk = reinterpret_cast<int32_t *>(base + o_pk);
     int32_t *d_bs = reinterpret_cast<int32_t *>(base + o_bs);
     ctx->launches += timed_launch(ctx, KID_PACK, st, [&] { return launch_pack(b, n, R, d_bs, d_off, d_pk, st); });
-    CK(cudaGetLastError());
+    CKB(cudaGetLastError());
     // results straight into the caller's arrays
     const cudaStream_t ost = res.ost;
     if (ost != st) {
-        CK(cudaEventRecord(res.packed, st));
-        CK(cudaStreamWaitEvent(ost, res.packed, 0));
+        CKB(cudaEventRecord(res.packed, st));
+        CKB(cudaStreamWaitEvent(ost, res.packed, 0));
     }
     const int64_t cp = std::min(sel_cap, pl.sel_cap);
-    CK(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
-    CK(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
-    CK(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, ost));
-    if (cp > 0 && sel) CK(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, ost));
-    CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, ost));
+    CKB(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
+    CKB(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
+    CKB(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, ost));
+    if (cp > 0 && sel) CKB(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, ost));
+    CKB(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, ost));
     out.R = R;
     out.h_err = h_err;
     out.h2d = L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
     out.d2h = 8 * (int64_t)R + 8 * ((int64_t)R + 1) + 4 + (sel ? 12 * cp : 0);
+#undef CKB
     return MINE_OK;
 }
 
@@ -1273,7 +1312,7 @@ static int finish_host_batch(const HostCallOut &o, const int64_t *sel_off, const
                              int64_t sel_cap)
 {
     if (!o.h_err) return MINE_OK;   // no pairs
-    if (*o.h_err) return fail(MINE_EINVAL, device_err_text(*o.h_err));
+    if (*o.h_err) return device_fail(*o.h_err);
     const int64_t tot = sel_off[o.R];
     if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
     return MINE_OK;
@@ -1387,8 +1426,11 @@ int mine_batch_wait(mine_ctx *ctx, uint64_t ticket)
     return rc;
 }
 
-int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,
-                   int64_t out_len)
+// The score matrices of a host batch, row-major pair after pair, as Q16
+// integers (f32 = 0) or single-precision floats (f32 = 1); out holds 4-byte
+// cells.
+static int score_matrices(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, void *out,
+                          int64_t out_len, int f32)
 {
     if (!ctx || !dict) return fail(MINE_EINVAL, "null context or dictionary");
     int rc = check_batch(batch);
@@ -1423,21 +1465,42 @@ int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     if (batch->n_tok > 0)
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-    b.f32 = 1;
+    b.f32 = f32;
     if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
     int32_t *h_err = reinterpret_cast<int32_t *>(hp + align_up(L.plan_bytes, 64));
-    float *h_m = reinterpret_cast<float *>(h_err + 16);
+    const int32_t *h_m = h_err + 16;
     CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_m, b.M, m_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(const_cast<int32_t *>(h_m), b.M, m_bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (*h_err) return fail(MINE_EINVAL, device_err_text(*h_err));
-    // tiles -> row-major, pair after pair
+    if (*h_err) return device_fail(*h_err);
+    // tiles -> row-major, pair after pair (4-byte cells copied as they are)
+    int32_t *o32 = static_cast<int32_t *>(out);
     int64_t o = 0;
     for (const PairPlan &pp : pl.pairs) {
         const int TT = (pp.T + kTile - 1) / kTile;
         for (int i = 0; i < pp.S; ++i)
-            for (int j = 0; j < pp.T; ++j) out[o++] = h_m[m_cell(pp.m_off, TT, i, j)];
+            for (int j = 0; j < pp.T; ++j) o32[o++] = h_m[m_cell(pp.m_off, TT, i, j)];
     }
+    return MINE_OK;
+}
+
+int mine_score_f32(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, float *out,
+                   int64_t out_len)
+{
+    return score_matrices(ctx, dict, batch, out, out_len, 1);
+}
+
+int mine_score_q16(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch, mine_q16 *out,
+                   int64_t out_len)
+{
+    return score_matrices(ctx, dict, batch, out, out_len, 0);
+}
+
+int mine_test_inject(mine_ctx *ctx, int32_t kind, int32_t count)
+{
+    if (!ctx || count < 0) return fail(MINE_EINVAL, "null context or negative count");
+    if (kind != MINE_INJECT_CUDA_CALL) return fail(MINE_EINVAL, "unknown injection kind");
+    ctx->inject_cuda_at.store(count);
     return MINE_OK;
 }
 
@@ -1524,8 +1587,8 @@ int mine_run_batch_bidi(mine_ctx *ctx, const mine_dict *fwd, const mine_dict *bw
     ctx->h2d_bytes += Lf.plan_bytes + Lb.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
     ctx->d2h_bytes += 12 * (int64_t)pf.R + 8 + 24 * pf.sel_cap;
     CK(cudaStreamSynchronize(st));
-    if (h_err[0]) return fail(MINE_EINVAL, device_err_text(h_err[0]));
-    if (h_err[1]) return fail(MINE_EINVAL, device_err_text(h_err[1]));
+    if (h_err[0]) return device_fail(h_err[0]);
+    if (h_err[1]) return device_fail(h_err[1]);
     int64_t tot = 0;
     for (int32_t r = 0; r < pf.R; ++r) tot += h_ns[r];
     if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
@@ -1622,7 +1685,7 @@ int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
     ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok + 4 * batch->n_sent;
     ctx->d2h_bytes += 8 * (2 * (int64_t)n + 2) + 4;
     CK(cudaStreamSynchronize(st));
-    if (*h_err) return fail(MINE_EINVAL, device_err_text(*h_err));
+    if (*h_err) return device_fail(*h_err);
     for (int k = 0; k < n; ++k) {
         tp[k] = (int64_t)h_acc[k];
         n_selected[k] = (int64_t)h_acc[n + k];
@@ -1700,7 +1763,7 @@ int mine_best_match(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batc
     ctx->h2d_bytes += L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
     ctx->d2h_bytes += 8 * (int64_t)P + 12 * ns + 4;
     CK(cudaStreamSynchronize(st));
-    if (h_err) return fail(MINE_EINVAL, device_err_text(h_err));
+    if (h_err) return device_fail(h_err);
     int64_t tot = 0;
     for (int32_t p = 0; p < P; ++p) tot += h_cnt[p];
     if (tot > sel_cap || (tot > 0 && !sel)) return fail(MINE_EINVAL, "sel_cap too small");
@@ -1879,7 +1942,7 @@ int mine_check(mine_ctx *ctx)
     if (ctx->err_off >= 0 && ctx->arena.p) {
         int32_t e = 0;
         CK(cudaMemcpy(&e, static_cast<char *>(ctx->arena.p) + ctx->err_off, 4, cudaMemcpyDeviceToHost));
-        if (e) return fail(MINE_EINVAL, device_err_text(e));
+        if (e) return device_fail(e);
     }
     return MINE_OK;
 }
@@ -2028,6 +2091,33 @@ int mine_poll(mine_ctx *ctx, mine_result *out, int32_t max_out, int32_t timeout_
     return got;
 }
 
+int mine_serving_stats(mine_ctx *ctx, int64_t *batches, int32_t *max_overlap)
+{
+    if (!ctx) return fail(MINE_EINVAL, "null context");
+    std::vector<std::pair<float, int>> ev;
+    int64_t nb = 0;
+    {
+        std::lock_guard<std::mutex> lk(ctx->q_mu);
+        nb = ctx->n_batches;
+        ev.reserve(2 * ctx->spans.size());
+        for (const auto &sp : ctx->spans) {
+            ev.emplace_back(sp.first, +1);
+            ev.emplace_back(sp.second, -1);
+        }
+    }
+    // sweep over the span ends in time order (an end before a start at the
+    // same instant: touching spans do not overlap)
+    std::sort(ev.begin(), ev.end());
+    int cur = 0, best = 0;
+    for (const auto &e : ev) {
+        cur += e.second;
+        best = std::max(best, cur);
+    }
+    if (batches) *batches = nb;
+    if (max_overlap) *max_overlap = best;
+    return MINE_OK;
+}
+
 void mine_result_free(mine_ctx *, mine_result *result)
 {
     if (!result) return;
@@ -2045,6 +2135,8 @@ void mine_result_free(mine_ctx *, mine_result *result)
 // wait at most batch_window_us before they form the next batch, which runs
 // concurrently on another slot.
 namespace {
+
+constexpr size_t kMaxSpans = 1 << 16;   // served batches whose device span is kept
 
 void finish_slot(mine_ctx *ctx, Slot &s)
 {
@@ -2068,7 +2160,7 @@ void finish_slot(mine_ctx *ctx, Slot &s)
             if (ce != cudaSuccess) {
                 r.status = MINE_ECUDA;
             } else if (dev_err) {
-                r.status = MINE_EINVAL;
+                r.status = dev_err == ERR_TIMEOUT ? MINE_ETIMEDOUT : MINE_EINVAL;
             } else {
                 const int64_t row = pp.set0 + k;
                 r.nw_score = h_nw[row];
@@ -2081,8 +2173,16 @@ void finish_slot(mine_ctx *ctx, Slot &s)
             res.push_back(r);
         }
     }
+    float a = 0.f, z = 0.f;
+    const bool timed = ce == cudaSuccess && cudaEventElapsedTime(&a, ctx->origin, s.t0) == cudaSuccess &&
+                       cudaEventElapsedTime(&z, ctx->origin, s.t1) == cudaSuccess;
     {
         std::lock_guard<std::mutex> lk(ctx->q_mu);
+        ctx->n_batches++;
+        if (timed) {
+            if (ctx->spans.size() >= kMaxSpans) ctx->spans.erase(ctx->spans.begin(), ctx->spans.begin() + kMaxSpans / 2);
+            ctx->spans.emplace_back(a, z);
+        }
         for (auto &r : res) ctx->ready.push_back(r);
         for (auto &rq : s.reqs) {
             const_cast<mine_dict *>(rq.dict)->inflight--;
@@ -2148,6 +2248,7 @@ int launch_slot(mine_ctx *ctx, Slot &s)
     char *base = ctx->pool.base + s.pool_off;
     int32_t *d_sent = reinterpret_cast<int32_t *>(base + L.sent_off);
     int32_t *d_tok = reinterpret_cast<int32_t *>(base + L.tokens);
+    CK(cudaEventRecord(s.t0, s.st));
     CK(cudaMemcpyAsync(base + L.plan, hi, L.plan_bytes, cudaMemcpyHostToDevice, s.st));
     CK(cudaMemcpyAsync(d_sent, h_sent, 4 * (n_sent + 1), cudaMemcpyHostToDevice, s.st));
     if (n_tok > 0) CK(cudaMemcpyAsync(d_tok, h_tok, 4 * n_tok, cudaMemcpyHostToDevice, s.st));
@@ -2159,6 +2260,7 @@ int launch_slot(mine_ctx *ctx, Slot &s)
     CK(cudaMemcpyAsync(ho + s.out_err, b.err, 4, cudaMemcpyDeviceToHost, s.st));
     if (s.plan.sel_cap > 0)
         CK(cudaMemcpyAsync(ho + s.out_sel, b.sel, 12 * s.plan.sel_cap, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaEventRecord(s.t1, s.st));
     CK(cudaEventRecord(s.ev, s.st));
     s.busy = true;
     return 0;

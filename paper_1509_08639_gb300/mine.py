@@ -96,6 +96,10 @@ SIGNATURES = {
     "mine_autotune": (_I, [_P]),
     "mine_autotune_batch": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC)]),
     "mine_score_f32": (_I, [_P, _P, ctypes.POINTER(BatchC), _P, _L]),
+    "mine_score_q16": (_I, [_P, _P, ctypes.POINTER(BatchC), _P, _L]),
+    "mine_test_inject": (_I, [_P, _I, _I]),
+    "mine_serving_stats": (_I, [_P, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
+    "mine_int_peak": (_I, [_I, ctypes.POINTER(ctypes.c_double), _P, _I]),
     "mine_align_strategy": (_I, [_P, _P, _I, _I]),
     "mine_run_batch_bidi": (_I, [_P, _P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P,
                                  _P, _P, _P, _P, _L]),
@@ -105,6 +109,7 @@ SIGNATURES = {
 }
 
 ALIGN_BINS = 40
+INJECT_CUDA_CALL = 1   # mine_test_inject kinds (include/mine.h)
 
 _lib = None
 
@@ -359,17 +364,28 @@ class Context:
         _check(self.L.mine_io_bytes(self.h, ctypes.byref(a), ctypes.byref(b)), self.L)
         return a.value, b.value
 
+    def test_inject(self, kind: int, count: int):
+        """Fault injection for tests (mine_test_inject)."""
+        _check(self.L.mine_test_inject(self.h, int(kind), int(count)), self.L)
+
     def profile(self, enable: bool = True):
         _check(self.L.mine_profile(self.h, 1 if enable else 0), self.L)
 
     def score_f32(self, dict_h, batch):
         """Single-precision score matrices of every pair (list of S x T float32 arrays)."""
+        return self._scores(dict_h, batch, np.float32, self.L.mine_score_f32)
+
+    def score_q16(self, dict_h, batch):
+        """Fixed-point (Q16) score matrices of every pair (list of S x T int32 arrays)."""
+        return self._scores(dict_h, batch, np.int32, self.L.mine_score_q16)
+
+    def _scores(self, dict_h, batch, dtype, fn):
         do, so, tk = _c32(batch.doc_off), _c32(batch.sent_off), _c32(batch.tokens)
         S, T = batch.sizes()
         cells = int((S * T).sum())
-        out = np.zeros(max(cells, 1), np.float32)
+        out = np.zeros(max(cells, 1), dtype)
         bc = BatchC(batch.n_pairs, int(so.shape[0] - 1), int(tk.shape[0]), _ptr(do), _ptr(so), _ptr(tk))
-        _check(self.L.mine_score_f32(self.h, dict_h, ctypes.byref(bc), _ptr(out), cells), self.L)
+        _check(fn(self.h, dict_h, ctypes.byref(bc), _ptr(out), cells), self.L)
         res, o = [], 0
         for p in range(batch.n_pairs):
             n = int(S[p] * T[p])
@@ -436,6 +452,12 @@ class Context:
                self.L)
         return t.value
 
+    def serving_stats(self):
+        """(batches served, largest number of them on the device at once)."""
+        nb, mo = ctypes.c_int64(), ctypes.c_int32()
+        _check(self.L.mine_serving_stats(self.h, ctypes.byref(nb), ctypes.byref(mo)), self.L)
+        return int(nb.value), int(mo.value)
+
     def poll(self, max_out=1024, timeout_us=0):
         """[(ticket, setting, status, nw_score, [(i, j, s)], latency_ns)]"""
         buf = (Result * max_out)()
@@ -466,6 +488,15 @@ def align_matrix_noalloc(M, gap, threshold, stream=None):
                                        ctypes.cast(out, ctypes.c_void_p), ctypes.byref(n),
                                        ctypes.byref(nw), st), L)
     return nw.value, [(out[k].src_sent, out[k].tgt_sent, out[k].score) for k in range(n.value)]
+
+
+def int_peak(device: int = -1):
+    """Measured int32 add/max rate of the device: (ops/s, [ops/s per form])."""
+    L = load()
+    best = ctypes.c_double()
+    forms = np.zeros(3, np.float64)
+    _check(L.mine_int_peak(int(device), ctypes.byref(best), _ptr(forms), 3), L)
+    return float(best.value), [float(v) for v in forms]
 
 
 def unpack_results(P, n, nw, ns, off, sel):

@@ -171,3 +171,47 @@ def test_close_waits_for_calls_in_flight():
     for h in handles:
         nw, ns, off, sel, _ = h.outs
         assert mine.unpack_results(h.P, h.n, nw, ns, off, sel) == want
+
+
+def test_injected_cuda_failure_waits_and_the_context_recovers(ctx):
+    """A CUDA call that fails after the first input copy (faked on the host
+    by mine_test_inject, the call not made) returns MINE_ECUDA from the
+    synchronous and the asynchronous call, with nothing of the call left in
+    flight; the next call on the context mines as the oracle does."""
+    torch = pytest.importorskip("torch")
+    w = synth.workload(2, n_pairs=120)
+    want = oracle_results(w.dictionary, w.batch, w.settings)
+    dh = ctx.dict_create(w.dictionary)
+    b = w.batch
+    P, n = b.n_pairs, len(w.settings)
+    S, T = b.sizes()
+    cap = int(n * np.minimum(S, T).sum())
+    for sync, positions in ((True, (1, 2, 3, 4, 5, 9)), (False, (1, 3, 4, 5, 6, 8, 13))):
+        for at in positions:
+            # pinned inputs and outputs: the copies really are asynchronous
+            sent = torch.from_numpy(b.sent_off.copy()).pin_memory()
+            tok = torch.from_numpy(b.tokens.copy()).pin_memory()
+            do = np.ascontiguousarray(b.doc_off)
+            g = np.asarray([s[0] for s in w.settings], np.int32)
+            th = np.asarray([s[1] for s in w.settings], np.int32)
+            bc = mine.BatchC(P, b.sent_off.shape[0] - 1, b.tokens.shape[0], mine._ptr(do),
+                             sent.data_ptr(), tok.data_ptr())
+            sc = mine.SettingsC(n, mine._ptr(g), mine._ptr(th))
+            pins = [torch.zeros(P * n, dtype=torch.int32).pin_memory(),
+                    torch.zeros(P * n, dtype=torch.int32).pin_memory(),
+                    torch.zeros(P * n + 1, dtype=torch.int64).pin_memory(),
+                    torch.zeros(3 * cap, dtype=torch.int32).pin_memory()]
+            outs = tuple(x.numpy() for x in pins) + (cap,)
+            ctx.test_inject(mine.INJECT_CUDA_CALL, at)
+            with pytest.raises(mine.MineError) as e:
+                if sync:
+                    ctx.run_batch_raw(dh, bc, sc, outs)
+                else:
+                    ctx.run_batch_async_raw(dh, bc, sc, outs)
+            assert e.value.code == -7, (sync, at)
+            ctx.test_inject(mine.INJECT_CUDA_CALL, 0)
+            # the failed call's buffers may go at once
+            del sent, tok, outs, pins
+            assert_same(ctx.run_batch(dh, b, w.settings), want, f"after a failure at {at}")
+    got = ctx.batch_wait(ctx.run_batch_async(dh, b, w.settings))
+    assert_same(got, want, "asynchronous call after the failures")
