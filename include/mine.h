@@ -436,9 +436,16 @@ int mine_int_peak(int32_t device, double *ops_per_s, double *per_form, int32_t n
  * batch calls (mine_run_batch, mine_run_batch_async) check after their first
  * input copy is not made and fails as if CUDA had returned an error: the call
  * then waits for the copies and kernels it had already enqueued and returns
- * MINE_ECUDA, so the caller may free its arrays at once.  count 0 turns the
- * injection off.  MINE_EINVAL for an unknown kind or a negative count. */
+ * MINE_ECUDA, so the caller may free its arrays at once.  With kind
+ * MINE_INJECT_WITHHOLD_ROWS, the next count host-buffer batch calls run with
+ * the first warp of every warp pipeline of the alignment keeping its rows to
+ * itself and every flag wait giving up after a few milliseconds: a batch with
+ * a pair aligned by a pipeline of warps ends with MINE_ETIMEDOUT (the kernels
+ * return on their own; nothing hangs) and the context stays usable.  count 0
+ * turns an injection off.  MINE_EINVAL for an unknown kind or a negative
+ * count. */
 #define MINE_INJECT_CUDA_CALL 1
+#define MINE_INJECT_WITHHOLD_ROWS 2
 int mine_test_inject(mine_ctx *ctx, int32_t kind, int32_t count);
 
 #ifdef __cplusplus

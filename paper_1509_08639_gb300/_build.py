@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmine.so")
-SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "bidi_tune.cu", "best_match.cu", "int_peak.cu"]
+SOURCES = ["kernels.cu", "align.cu", "runtime.cu", "noalloc.cu", "bidi_tune.cu", "best_match.cu", "int_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "-I" + CSRC]
@@ -27,7 +27,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "internal.h"), os.path.join(INCLUDE, "mine.h")]
+    files += [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "async_copy.cuh"),
+              os.path.join(INCLUDE, "mine.h")]
     return files
 
 

@@ -1,0 +1,346 @@
+// align.cu -- the Needleman-Wunsch fill of the miner (Section 4 of Wolk &
+// Marasek: global alignment of the sentence-pair score matrix M with the
+// Penalty as gap cost; a path never moves upward or leftward).
+//
+//   H[0][0] = 0, H[i][0] = i g, H[0][j] = j g,
+//   H[i][j] = max(H[i-1][j-1] + s(i,j), H[i-1][j] + g, H[i][j-1] + g),
+//   direction DIAG if the diagonal attains the maximum, else UP if the cell
+//   above does, else LEFT; 2-bit codes, 16 per word, row-major per alignment.
+//
+// Wavefront.  One lane per row, 32 rows (a stripe) per warp; lane L is L
+// steps behind lane 0, so at every step each lane holds the cell above its
+// next one in lane L-1 (one shuffle).  A warp runs on from one of its stripes
+// into the next without draining: lane L's virtual column v = t - L walks
+// stripe after stripe (each T' = T rounded up to 32 columns wide), and lane 0
+// takes the row above a stripe from lane 31 of the stripe before it through
+// a ring in shared memory that lane 31 both writes (its own row) and reads
+// (the value lane 0 needs at the next step), handing it over in the same
+// rotation shuffle: the lane-0 boundary costs one store, one load and one
+// select per step, and no warp-level synchronisation (one thread owns the
+// ring).  A pipeline of G warps shares a pair: warp w takes stripes w, w+G,
+// ... and reads the ring of warp w-1 (bounded flag waits once per 32 steps).
+//
+// Scores.  Each lane keeps its own row of the score tiles in a ring of three
+// 32-column slots plus a copy of slot 0 after slot 2, so the 32 scores a
+// lane reads in 32 steps are always contiguous: one shared load per step at
+// a fixed offset.  Every lane fetches its 128-byte tile row (the tiles of M
+// are 32 x 32, row-major) with eight 16-byte asynchronous copies, one tile
+// ahead; it alone reads that row, so no barrier is needed.
+//
+// Per step a lane issues the shuffle, the score load, three integer
+// operations for the cell (add; max of up and left with the up-wins flag;
+// fused add-then-max), the code select and shift, and the lane-31 ring
+// store, load and select.
+#include "async_copy.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <climits>
+
+namespace mine {
+namespace {
+
+constexpr uint32_t kFullMaskA = 0xffffffffu;
+constexpr int kNwWarps = kNwPipe;    // warps per CTA (one CTA per SM)
+constexpr int kNwSlots = 3;          // score tiles resident per lane row
+// words per lane row: the slots, the copy of slot 0, and 4 words of padding
+// (16-byte copies of 8 consecutive lanes then fall into distinct banks)
+constexpr int kNwRowW = 32 * (kNwSlots + 1) + 4;
+constexpr int kNwRing = 512;         // boundary ring entries per warp
+
+template <int K>
+struct NwSmem {
+    int32_t rows[K][32][kNwRowW];
+    int32_t ring[K][kNwRing];
+    int32_t prod[K];                 // keys published by warp w's lane 31 (INT_MAX: done)
+    int32_t cons[K];                 // keys warp w has read from its predecessor (INT_MAX: done)
+    int32_t item;
+};
+
+// 16-byte asynchronous copy global -> shared, cached in L2 only.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Where lane 0's up value comes from in a chunk of 32 steps: the ring (the
+// chunk's 32 values read at its start, one per lane, and shuffled to lane 0
+// step by step), H[0][j] of the pair's first stripe, or -- stripes one tile
+// wide -- lane 31's value of the step before, which is exactly the row above.
+enum XSrc { X_RING = 0, X_ARITH = 1, X_ROT = 2 };
+
+// 32 wavefront steps.  srow: this lane's scores, srow[u] at step u.  rw:
+// lane 31 writes its value of step u to rw[u] (the ring read by the next
+// stripe's lane 0).  rv: lane k holds lane 0's up value of step k (X_RING).
+// xa: H[0][j] of lane 0's cell at u = 0 (X_ARITH; + u g at step u).  RESET:
+// lanes start a stripe at step u = lane (h = row g, the diagonal (row - 1) g).
+// a1 / a2: where the aligned code words completed at steps 15 and 31 go
+// (null: not stored).
+template <bool RESET, int XS>
+__device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ srow, int32_t *rw, int32_t rv,
+                                         int lane, int src, int32_t g, int32_t rh, int32_t xa,
+                                         uint32_t sh, uint32_t *a1, uint32_t *a2, int32_t &h,
+                                         int32_t &up_prev, uint32_t &word, uint32_t &prev)
+{
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+        const int32_t rot = __shfl_sync(kFullMaskA, h, src);   // the cell above, from lane - 1
+        int32_t up_in;
+        if (XS == X_ROT) {
+            up_in = rot;
+        } else {
+            const int32_t l0 = XS == X_ARITH ? xa + u * g : __shfl_sync(kFullMaskA, rv, u);
+            up_in = lane == 0 ? l0 : rot;
+        }
+        if (RESET && u == lane) {
+            h = rh;
+            up_prev = rh - g;
+        }
+        const int32_t sv = srow[u];
+        const int32_t cd = up_prev + sv;
+        bool pu;
+        const int32_t m = __vibmax_s32(up_in, h, &pu);       // max(up, left), pu = up >= left
+        const int32_t best = __viaddmax_s32(m, g, cd);       // max(max(up, left) + g, diag + s)
+        const uint32_t code = best == cd ? DIR_DIAG : (pu ? DIR_UP : DIR_LEFT);
+        word = __funnelshift_r(word, code, 2);
+        h = best;
+        up_prev = up_in;
+        if (XS != X_ROT && lane == 31) rw[u] = best;
+        if (u == 15) {
+            if (a1) *a1 = __funnelshift_r(prev, word, sh);
+            prev = word;
+        } else if (u == 31) {
+            if (a2) *a2 = __funnelshift_r(prev, word, sh);
+            prev = word;
+        }
+    }
+}
+
+// Wait until every copy this thread has in flight has landed, so that the
+// CTA may end after an error.
+__device__ __forceinline__ void nw_drain() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Fill H for one alignment by warp wg of a pipeline of G warps (w = its
+// warp in the CTA; the pipeline is warps w - wg .. w - wg + G - 1).  Returns
+// false when a bounded wait ran out (error word set).
+template <int K>
+__device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, int lane, const NwItem &it,
+                       const PairPlan &pp)
+{
+    const int S = pp.S, T = pp.T;
+    const int TT = (T + 31) >> 5;           // column tiles; stripes are Tp = 32 TT wide
+    const int Tp = TT << 5;
+    const int NS = (S + 31) >> 5;           // stripes of the pair
+    const bool self = G == 1;
+    int32_t *prod_mine = &sm.prod[w];
+    int32_t *cons_mine = &sm.cons[w];
+    if (wg >= NS) {   // nothing for this warp: its partners must not wait on it
+        if (lane == 0) {
+            *(volatile int32_t *)prod_mine = INT_MAX;
+            *(volatile int32_t *)cons_mine = INT_MAX;
+        }
+        __syncwarp();
+        return true;
+    }
+    const int nq = (NS - wg + G - 1) / G;   // stripes of this warp: wg, wg + G, ...
+    const int32_t g = b.gap_val[it.gap];
+    const int CW = (T + 15) >> 4;
+    uint32_t *codes = b.codes + it.code_off;
+    const int32_t *Mp = b.M + pp.m_off;
+    const int base_w = w - wg;
+    const int pw = self ? w : base_w + (wg == 0 ? G - 1 : wg - 1);
+    const int sw = self ? w : base_w + (wg == G - 1 ? 0 : wg + 1);
+    int32_t *ring_out = sm.ring[w];
+    const int32_t *ring_in = sm.ring[pw];
+    const int32_t *prod_pred = &sm.prod[pw];
+    const int32_t *cons_succ = &sm.cons[sw];
+    // the consumer's key of a value lane 31 writes at virtual column v is
+    // v + off_out (the next stripe of the same warp, or warp 0's next one)
+    const int32_t off_out = (self || wg == G - 1) ? Tp : 0;
+    // keys the successor reads from this warp's ring: all of its stripes'
+    // keys, except that warp 0 takes its first stripe's from row 0
+    const int nq_succ = wg == G - 1 ? (NS + G - 1) / G : (NS - wg - 1 + G - 1) / G;
+    const int32_t succ_first = wg == G - 1 ? Tp : 0;
+    const int32_t succ_last = nq_succ * Tp - 1;
+    const int src = (lane + 31) & 31;
+    // testing the bounded waits: the first warp of a pipeline keeps its rows
+    // to itself, so the next warp's wait runs out
+    const bool publish = !(b.test_withhold && !self && wg == 0);
+    const uint32_t sh = 2u * (uint32_t)(lane & 15);
+    int32_t *myrow = sm.rows[w][lane];
+    const int ntile = nq * TT;              // virtual tiles of this warp
+    const int nchunks = ntile + 1;
+
+    // the lane's row of virtual tile k of this warp into its slot (and into
+    // the copy of slot 0): eight 16-byte asynchronous copies per lane, one
+    // commit group per tile
+    auto issue = [&](int k) {
+        const int q = k / TT;
+        const int C = k - q * TT;
+        const int s = wg + q * G;
+        const int32_t *src_row = Mp + ((int64_t)s * TT + C) * kTileElems + lane * kTile;
+        const int slot = k % kNwSlots;
+        const uint32_t d0 = s2u(myrow + 32 * slot);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) cp_async16(d0 + 16 * e, src_row + 4 * e);
+        if (slot == 0) {
+            const uint32_t d1 = s2u(myrow + 32 * kNwSlots);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) cp_async16(d1 + 16 * e, src_row + 4 * e);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    int32_t h = 0, up_prev = 0;
+    uint32_t word = 0, prev = 0;
+    issue(0);
+    for (int c = 0; c < nchunks; ++c) {
+        // tile c has landed once at most the group of tile c + 1 is pending
+        if (c + 1 < ntile) {
+            issue(c + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        const int q = c / TT;                      // stripe (of this warp) lane 0 is in
+        const int r = c - q * TT;
+        const bool reset = r == 0 && q < nq;
+        // lane 0's up values of this chunk: keys 32c .. 32c + 31
+        int xs = X_RING;
+        if (wg == 0 && c < TT) xs = X_ARITH;       // the pair's first stripe: H[0][j]
+        else if (Tp == 32) xs = X_ROT;            // (one warp) lane 31's previous value
+        if (c == ntile) xs = X_ARITH;              // lane 0 is past its last stripe
+        if (!self) {
+            if (xs == X_RING && !flag_wait_ge(prod_pred, 32 * c + 31, b.err, b.wait_spins)) return false;
+            // lane 31 overwrites keys need - 31 .. need in this chunk: wait
+            // until the successor has read those of them it reads at all
+            const int32_t need = 32 * c + off_out - kNwRing;
+            if (succ_first <= succ_last && need >= succ_first && need - 31 <= succ_last &&
+                !flag_wait_ge(cons_succ, min(need, succ_last), b.err, b.wait_spins))
+                return false;
+            __threadfence_block();
+        } else {
+            __syncwarp();   // lane 31's ring stores of earlier chunks, read by every lane below
+        }
+        // lane k: key 32c + k, stored at slot key - 1
+        const int32_t rv = xs == X_RING ? ring_in[(32 * c + lane - 1) & (kNwRing - 1)] : 0;
+        const int base_c = (((32 * c - lane) % (32 * kNwSlots)) + 32 * kNwSlots) % (32 * kNwSlots);
+        const int32_t *srow = myrow + base_c;
+        int32_t *rw = ring_out + ((32 * c - 32 + off_out) & (kNwRing - 1));
+        const int32_t xa = (32 * c + 1) * g;
+        // the new stripe of a reset chunk, for the row of each lane
+        const int32_t rh = (int32_t)(32 * (wg + q * G) + lane + 1) * g;
+        // aligned code words completed at steps 15 and 31
+        uint32_t *a1 = nullptr, *a2 = nullptr;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int m = 2 * c - 1 + e - (lane >> 4);
+            uint32_t *ad = nullptr;
+            const int qm = m < 2 * TT * q ? q - 1 : q;
+            const int wi = m - 2 * TT * qm;
+            const int row = 32 * (wg + qm * G) + lane + 1;
+            if (m >= 0 && qm < nq && wi < CW && row <= S) ad = codes + (int64_t)(row - 1) * CW + wi;
+            if (e == 0) a1 = ad;
+            else a2 = ad;
+        }
+        if (reset) {
+            if (xs == X_RING)
+                nw_chunk<true, X_RING>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+            else if (xs == X_ARITH)
+                nw_chunk<true, X_ARITH>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+            else
+                nw_chunk<true, X_ROT>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+        } else {
+            if (xs == X_RING)
+                nw_chunk<false, X_RING>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+            else if (xs == X_ARITH)
+                nw_chunk<false, X_ARITH>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+            else
+                nw_chunk<false, X_ROT>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+        }
+        if (!self) {
+            __syncwarp();
+            if (lane == 31) {
+                __threadfence_block();
+                if (publish) *(volatile int32_t *)prod_mine = 32 * c + off_out;
+                *(volatile int32_t *)cons_mine = 32 * c + 31;
+            }
+        }
+    }
+    if (!self) {
+        __syncwarp();
+        if (lane == 31) {
+            __threadfence_block();
+            if (publish) *(volatile int32_t *)prod_mine = INT_MAX;
+            *(volatile int32_t *)cons_mine = INT_MAX;
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// Persistent alignment kernel: first the pairs aligned by the whole CTA (a
+// pipeline of K warps), then one warp per pair.  Tracebacks follow in k_trace.
+template <int K>
+__global__ void __launch_bounds__(K * 32, 1) k_nw(BatchDev b)
+{
+    extern __shared__ __align__(128) unsigned char nw_smem_raw[];
+    NwSmem<K> &sm = *reinterpret_cast<NwSmem<K> *>(nw_smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if (*(volatile int32_t *)b.err) return;
+
+    for (;;) {
+        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[2], 1);
+        if (threadIdx.x < K) {
+            sm.prod[threadIdx.x] = -1;   // keys <= -1 published / consumed: none
+            sm.cons[threadIdx.x] = -1;
+        }
+        __syncthreads();
+        const int item = sm.item;
+        if (item >= b.n_nw_big) break;
+        const NwItem it = b.nw_items[item];
+        const PairPlan pp = b.pairs[it.pair];
+        // warp 0 of a pipeline of G warps needs the row above its second
+        // stripe from warp G - 1 before it has filled G of its own chunks:
+        // G < T'/32 keeps that dependency acyclic
+        const int G = min(min(K, (pp.S + 31) >> 5), max(1, ((pp.T + 31) >> 5) - 1));
+        bool ok = true;
+        if (w < G) ok = nw_run<K>(b, sm, w, w, G, lane, it, pp);
+        if (!__syncthreads_and(ok)) {
+            nw_drain();
+            return;
+        }
+    }
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[3], 1);
+        item = __shfl_sync(kFullMaskA, item, 0);
+        if (item >= b.n_nw_items - b.n_nw_tiled) break;
+        const NwItem it = b.nw_items[item];
+        const PairPlan pp = b.pairs[it.pair];
+        if (pp.S == 0 || pp.T == 0) continue;   // nothing to fill; k_trace reports it
+        if (!nw_run<K>(b, sm, w, 0, 1, lane, it, pp)) {
+            nw_drain();
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)
+{
+    const int items = b.n_nw_items - b.n_nw_tiled;
+    if (items <= 0) return 0;
+    const size_t smem = sizeof(NwSmem<kNwWarps>);
+    cudaFuncSetAttribute(k_nw<kNwWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int small = items - b.n_nw_big;
+    const int need = std::max(b.n_nw_big, (small + kNwWarps - 1) / kNwWarps);
+    const int grid = std::max(1, std::min(num_sms, need));
+    k_nw<kNwWarps><<<grid, kNwWarps * 32, smem, st>>>(b);
+    return 1;
+}
+
+}  // namespace mine

@@ -32,6 +32,7 @@ constexpr int kMaxSentTokens = MINE_MAX_SENT_TOKENS;
 constexpr uint32_t kWaitLimit = 1u << 22;   // bounded spins on shared-memory flags
 constexpr uint32_t kWaitHintNs = 100000;     // mbarrier try_wait suspend-time hint (100 us)
 constexpr uint32_t kMbarTries = 20000;       // try_wait attempts before giving up (<= ~2 s)
+constexpr uint32_t kTestWaitSpins = 20000;   // flag-wait tries of a test with withheld rows (a few ms)
 constexpr int kScoreWarps = 4;              // warps per CTA of the score kernel
 constexpr int kScoreCtasPerSm = 4;          // CTAs per SM of the preparation kernel (grid = SMs x this)
 constexpr int kScoreWarpsScore = 2;         // warps per CTA of the score kernel (64 rows per item)
@@ -162,17 +163,22 @@ struct BatchDev {
     int32_t f32;                 // score kernel writes single-precision scores (float bits) into M
     int32_t *counters;           // [8] work-queue heads
     int32_t *err;                // error word (0 = fine)
+    uint32_t wait_spins;         // tries of a bounded flag wait (0: kWaitLimit)
+    int32_t test_withhold;       // testing only: warp 0 of every warp pipeline publishes no rows
     // outputs
     int32_t *nw_score;           // [R]
     int32_t *n_sel;              // [R]
     int32_t *sel;                // mine_pair triples
 };
 
-// A one-warp alignment keeps the whole previous stripe row in a ring of kRing
-// entries, so a pair with more than 32 source sentences and T >= kRing target
-// sentences is aligned by a whole CTA, as is every pair of kBigCells or more.
+// A one-warp alignment keeps the previous stripe's last row in a ring of
+// kRing entries, so a pair with more than 32 source sentences and T >= kRing
+// target sentences is aligned by a whole CTA (a pipeline of kNwPipe warps),
+// as is every pair of kBigCells or more.  A pipeline needs more than kNwPipe
+// 32-column tiles per row (T > 32 kNwPipe); narrower pairs take one warp.
 constexpr int kRing = 512;
 constexpr int64_t kBigCells = 1 << 15;
+constexpr int kNwPipe = 8;
 constexpr int kAlignBins = MINE_ALIGN_BINS;
 
 // Alignment form of an S x T pair: 0 one warp, 1 one CTA, 2 tiles over many
@@ -188,6 +194,7 @@ inline int align_kind(const int8_t *tab, int32_t S, int32_t T)
     int v = (tab && bin < kAlignBins) ? tab[bin] : -1;
     if (v < 0) v = (can_tile && c >= kTiledCells) ? 2 : (c >= kBigCells ? 1 : 0);
     if (v == 2 && !can_tile) v = 1;
+    if (v == 1 && T <= kTile * kNwPipe) v = 0;
     if (v == 0 && S > kTile && T >= kRing) v = 1;
     return v;
 }

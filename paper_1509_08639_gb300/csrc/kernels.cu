@@ -38,6 +38,7 @@
 //   k_trace       one warp per alignment: traceback over the packed codes and
 //                 the threshold selection of every setting that shares the gap
 #include "internal.h"
+#include "async_copy.cuh"
 
 #include <algorithm>
 #include <cstdint>
@@ -64,103 +65,6 @@ __device__ __forceinline__ int ceil_log2(int x)
 __device__ __forceinline__ uint32_t mul_q16(uint32_t x, uint64_t K)
 {
     return (uint32_t)(((uint64_t)x * K) >> 32);
-}
-
-// ---------------------------------------------------------------- TMA / mbarrier
-
-__device__ __forceinline__ uint32_t s2u(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s2u(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also announces `bytes` of transaction on the barrier.
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s2u(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// TMA bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            s2u(dst)),
-        "l"(src), "r"(bytes), "r"(s2u(bar))
-        : "memory");
-}
-
-// L2 policy for data read once: its lines are the first to be evicted, so a
-// stream of them does not push out what is read again soon (the direction
-// codes the traceback reads next).
-__device__ __forceinline__ uint64_t l2_evict_first()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ void bulk_g2s_once(void *dst, const void *src, uint32_t bytes,
-                                              unsigned long long *bar, uint64_t policy)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            s2u(dst)),
-        "l"(src), "r"(bytes), "r"(s2u(bar)), "l"(policy)
-        : "memory");
-}
-
-// Test the phase; a thread whose phase is incomplete may be suspended for up
-// to kWaitHintNs before the test returns false (no busy spinning).
-__device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(s2u(bar)), "r"(parity), "r"(kWaitHintNs)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase with the given parity; gives up after kMbarTries tests
-// (at most about kMbarTries * kWaitHintNs), records ERR_TIMEOUT and returns
-// false.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err)
-{
-    for (uint32_t it = 0; it < kMbarTries; ++it)
-        if (mbar_test(bar, parity)) return true;
-    atomicCAS(err, 0, ERR_TIMEOUT);
-    return false;
-}
-
-// Spin until *flag >= v (shared memory, written by another warp of the CTA).
-__device__ __forceinline__ bool flag_wait_ge(const int32_t *flag, int32_t v, int32_t *err)
-{
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
-        if (*(volatile const int32_t *)flag >= v) return true;
-        __nanosleep(32);
-    }
-    atomicCAS(err, 0, ERR_TIMEOUT);
-    return false;
 }
 
 // ---------------------------------------------------------------- dictionary
@@ -1785,7 +1689,6 @@ __global__ void k_tile(const int32_t *__restrict__ src, int32_t S, int32_t T, in
 constexpr int kAW = 8;      // warps per CTA (pipeline depth of a large alignment)
 constexpr int kMBuf = 3;    // score tiles in flight per warp
 
-constexpr int kOwnMax = 64;   // whole-CTA alignments a CTA traces back itself
 struct AlignSmem {
     int32_t tile[kAW][kMBuf][kTileElems];
     int32_t ring[kAW][kRing];
@@ -1793,15 +1696,8 @@ struct AlignSmem {
     int32_t prod[kAW];      // stream values published by warp w (its last rows)
     int32_t cons[kAW];      // stream values warp w consumed from its predecessor
     int32_t item;
-    int32_t n_own;          // whole-CTA alignments filled here, not yet traced back
-    int32_t own[kOwnMax];
 };
 
-struct WarpPipe {
-    int w, W;               // position in the pipeline and its width
-    int32_t *ring_mine, *ring_pred;
-    int32_t *prod_mine, *prod_pred, *cons_mine, *cons_succ;
-};
 
 // One chunk of 32 wavefront steps of a stripe.  At step u lane L is at
 // column cidx = 32c + u - L; its score comes from tile c-1 (u < L) or tile c
@@ -1874,117 +1770,23 @@ __device__ __forceinline__ void stripe_flush(int c, int lane, bool row_ok, uint3
     if (row_ok && m >= mlo && m < mhi) cr[m] = __funnelshift_r(prev, 0u, 2u * (uint32_t)(lane & 15));
 }
 
-// Fill H over the stripes w, w+W, ... of one pair and write the direction
-// codes.  Stripe s publishes its last row (lane 31) as the stream values
-// gen*T + j - 1 (gen = s / W) of its warp's ring; stripe s+1 consumes them.
-// The lane holding (S, T) writes H[S][T] to hfin.  Returns false if a
-// bounded wait ran out.
-__device__ bool align_stripes(const BatchDev &b, AlignSmem &sm, int wib, const WarpPipe &wp,
-                              int item, const NwItem &it, const PairPlan &pp, int lane,
-                              uint32_t (&uses)[kMBuf])
-{
-    const uint64_t pol = l2_evict_first();   // score tiles are read once
-    const int S = pp.S, T = pp.T;
-    const int32_t g = b.gap_val[it.gap];
-    const int TT = (T + 31) >> 5;
-    const int TS = (S + 31) >> 5;
-    const int CW = (T + 15) >> 4;
-    uint32_t *codes = b.codes + it.code_off;
-    const int32_t *Mp = b.M + pp.m_off;
-    for (int s = wp.w; s < TS; s += wp.W) {
-        const int gen = s / wp.W;
-        const int i0 = 32 * s;
-        const int row = i0 + lane + 1;
-        const bool row_ok = row <= S;
-        const bool full_stripe = i0 + 32 <= S;
-        const bool has_above = s > 0;
-        const bool has_below = s + 1 < TS;
-        const int32_t qp_base = has_above ? ((s - 1) / wp.W) * T : 0;
-        const int32_t qm_base = gen * T;
-        uint32_t *cr = codes + (int64_t)(row - 1) * CW;
-        // first tiles of this stripe (buffers only ever read by generic loads)
-        __syncwarp();
-        if (lane == 0) {
-            for (int k = 0; k < kMBuf && k < TT; ++k) {
-                mbar_expect_tx(&sm.bar[wib][k], kTileElems * 4);
-                bulk_g2s_once(sm.tile[wib][k], Mp + ((int64_t)s * TT + k) * kTileElems, kTileElems * 4,
-                         &sm.bar[wib][k], pol);
-            }
-        }
-        for (int k = 0; k < kMBuf && k < TT; ++k) uses[k]++;
-        int32_t h_left = row * g;          // H[row][j-1]
-        int32_t up_prev = (row - 1) * g;   // H[row-1][j-1]
-        int32_t h_out = 0;                 // value handed to the next lane
-        uint32_t word = 0, prev = 0;
-        const int nchunks = (T + 31 + 31) >> 5;
-        int b_cur = 0;                     // buffer of tile c (= c % kMBuf)
-        for (int c = 0; c < nchunks; ++c) {
-            if (c < TT) {
-                if (!mbar_wait(&sm.bar[wib][b_cur], (uses[b_cur] - 1) & 1u, b.err)) return false;
-            }
-            const int b_prev = b_cur == 0 ? kMBuf - 1 : b_cur - 1;
-            if (c >= 2 && c + 1 < TT) {
-                // tile c-2 is no longer read: refill its buffer with tile c+1
-                const int bb = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_expect_tx(&sm.bar[wib][bb], kTileElems * 4);
-                    bulk_g2s_once(sm.tile[wib][bb], Mp + ((int64_t)s * TT + c + 1) * kTileElems,
-                             kTileElems * 4, &sm.bar[wib][bb], pol);
-                }
-                uses[bb]++;
-            }
-            // the row above for columns 32c+1 .. 32c+32 (lane k holds column 32c+1+k)
-            const int jcol = 32 * c + 1 + lane;
-            int32_t up_val;
-            if (has_above) {
-                const int32_t need = qp_base + min(32 * c + 32, T);
-                if (!flag_wait_ge(wp.prod_pred, need, b.err)) return false;
-                up_val = jcol <= T ? wp.ring_pred[(qp_base + jcol - 1) & (kRing - 1)] : 0;
-                __syncwarp();
-                if (lane == 0) *(volatile int32_t *)wp.cons_mine = need;
-            } else {
-                up_val = jcol * g;
-            }
-            if (has_below) {
-                // lane 31 writes columns up to 32c+1 in this chunk: their ring
-                // slots must have been read by the successor
-                const int jmax = min(32 * c + 1, T);
-                if (jmax >= 1 && !flag_wait_ge(wp.cons_succ, qm_base + jmax - kRing, b.err))
-                    return false;
-            }
-            const int32_t *base_prev = sm.tile[wib][b_prev] + lane * kTile + 32 - lane;
-            const int32_t *base_cur = sm.tile[wib][b_cur] + lane * kTile - lane;
-            const bool publish = has_below && lane == 31;
-            if (full_stripe && c >= 1 && 32 * (c + 1) <= T)
-                stripe_chunk<false>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, cr, 0, CW,
-                                    wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word, prev);
-            else
-                stripe_chunk<true>(c, lane, 0, T, row_ok, g, up_val, base_prev, base_cur, cr, 0, CW,
-                                   wp.ring_mine, qm_base, publish, h_left, up_prev, h_out, word, prev);
-            __syncwarp();
-            if (publish) {
-                const int jdone = min(32 * c + 1, T);
-                if (jdone >= 1) {
-                    __threadfence_block();
-                    *(volatile int32_t *)wp.prod_mine = qm_base + jdone;
-                }
-            }
-            b_cur = b_cur == kMBuf - 1 ? 0 : b_cur + 1;
-        }
-        stripe_flush(nchunks - 1, lane, row_ok, cr, 0, CW, prev);
-        if (s == TS - 1 && row == S) b.hfin[item] = h_left;
-        __syncwarp();
-    }
-    return true;
-}
-
+// H[S][T] of the alignment is the score of its optimal path: the scores of
+// the path's diagonal steps (the matches) plus g for each of its
+// S + T - 2 nm gap steps.  The selection keeps, per setting sharing the gap,
+// the matches whose score passes the threshold.
 __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPlan &pp,
-                                                int gap_idx, int32_t H, const uint32_t *matches,
+                                                int gap_idx, const uint32_t *matches,
                                                 int nm, int lane)
 {
     const int cap = min(pp.S, pp.T);
     const int TT = (pp.T + 31) >> 5;
+    int32_t sum = 0;
+    for (int q = lane; q < nm; q += 32) {
+        const uint32_t ij = matches[q];
+        sum += b.M[m_cell(pp.m_off, TT, (int)(ij >> 16) - 1, (int)(ij & 0xffffu) - 1)];
+    }
+    sum = (int32_t)__reduce_add_sync(kFull, (uint32_t)sum);
+    const int32_t H = sum + b.gap_val[gap_idx] * (pp.S + pp.T - 2 * nm);
     for (int k = 0; k < pp.nset; ++k) {
         const int row = pp.set0 + k;
         if (b.set_gap[row] != gap_idx) continue;
@@ -2021,8 +1823,7 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
 
 // Traceback from (S,T): blocks of 32 rows x 16 columns of codes held in
 // registers, one lane per row; then the selection.
-__device__ void trace_and_select(const BatchDev &b, const NwItem &it, const PairPlan &pp,
-                                 int32_t H, int lane)
+__device__ void trace_and_select(const BatchDev &b, const NwItem &it, const PairPlan &pp, int lane)
 {
     const int S = pp.S, T = pp.T;
     uint32_t *matches = b.matches + it.match_off;
@@ -2050,87 +1851,7 @@ __device__ void trace_and_select(const BatchDev &b, const NwItem &it, const Pair
         } while (i >= rb && i > 0 && j > 0 && ((j - 1) >> 4) == w);
     }
     __syncwarp();
-    select_and_emit(b, pp, it.gap, H, matches, nm, lane);
-}
-
-__global__ void __launch_bounds__(kAW * 32)
-k_align(BatchDev b)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AlignSmem &sm = *reinterpret_cast<AlignSmem *>(smem_raw);
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    if (lane == 0) {
-        for (int k = 0; k < kMBuf; ++k) mbar_init(&sm.bar[wib][k], 1);
-        fence_barrier_init();
-    }
-    uint32_t uses[kMBuf] = {0u, 0u, 0u};
-    if (threadIdx.x == 0) sm.n_own = 0;
-    __syncthreads();
-    if (*(volatile int32_t *)b.err) return;
-
-    // large alignments: the whole CTA on one pair.  Their tracebacks are long
-    // and serial; warp 0 does them once the queue is empty, while the other
-    // warps go on to the small alignments (k_trace takes the rest).
-    for (;;) {
-        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[2], 1);
-        if (threadIdx.x < kAW) {
-            sm.prod[threadIdx.x] = 0;
-            sm.cons[threadIdx.x] = 0;
-        }
-        __syncthreads();
-        const int item = sm.item;
-        if (item >= b.n_nw_big) break;
-        const NwItem it = b.nw_items[item];
-        const PairPlan pp = b.pairs[it.pair];
-        WarpPipe wp;
-        wp.w = wib;
-        wp.W = kAW;
-        const int pred = (wib + kAW - 1) % kAW, succ = (wib + 1) % kAW;
-        wp.ring_mine = sm.ring[wib];
-        wp.ring_pred = sm.ring[pred];
-        wp.prod_mine = &sm.prod[wib];
-        wp.prod_pred = &sm.prod[pred];
-        wp.cons_mine = &sm.cons[wib];
-        wp.cons_succ = &sm.cons[succ];
-        align_stripes(b, sm, wib, wp, item, it, pp, lane, uses);
-        __syncthreads();
-        if (*(volatile int32_t *)b.err) return;
-        if (sm.n_own < kOwnMax) {   // (uniform: read after the barrier, written below)
-            __syncthreads();
-            if (threadIdx.x == 0) sm.own[sm.n_own++] = item;
-        } else if (wib == 0) {
-            trace_and_select(b, it, pp, b.hfin[item], lane);   // more than kOwnMax: at once
-        }
-    }
-    if (wib == 0)
-        for (int k = 0; k < sm.n_own; ++k) {
-            const int item = sm.own[k];
-            const NwItem it = b.nw_items[item];
-            trace_and_select(b, it, b.pairs[it.pair], b.hfin[item], lane);
-        }
-    // small alignments: one warp each
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[3], 1);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= b.n_nw_items - b.n_nw_tiled) break;
-        const NwItem it = b.nw_items[item];
-        const PairPlan pp = b.pairs[it.pair];
-        if (pp.S == 0 || pp.T == 0) continue;   // nothing to fill; k_trace reports it
-        if (lane == 0) {
-            sm.prod[wib] = 0;
-            sm.cons[wib] = 0;
-        }
-        __syncwarp();
-        WarpPipe wp;
-        wp.w = 0;
-        wp.W = 1;
-        wp.ring_mine = wp.ring_pred = sm.ring[wib];
-        wp.prod_mine = wp.prod_pred = &sm.prod[wib];
-        wp.cons_mine = wp.cons_succ = &sm.cons[wib];
-        if (!align_stripes(b, sm, wib, wp, item, it, pp, lane, uses)) return;
-    }
+    select_and_emit(b, pp, it.gap, matches, nm, lane);
 }
 
 // Bounded wait until *flag != 0 (a flag another CTA sets); false when the
@@ -2317,18 +2038,18 @@ k_trace(BatchDev b)
 {
     const int lane = threadIdx.x & 31;
     if (*(volatile int32_t *)b.err) return;
-    for (;;) {   // the whole-CTA alignments [0, n_nw_big) are traced back by k_align
+    for (;;) {
         int item = 0;
-        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[4], 1);
+        if (lane == 0) item = atomicAdd(&b.counters[4], 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= b.n_nw_items) break;
         const NwItem it = b.nw_items[item];
         const PairPlan pp = b.pairs[it.pair];
         if (pp.S == 0 || pp.T == 0) {
-            select_and_emit(b, pp, it.gap, (pp.S + pp.T) * b.gap_val[it.gap], nullptr, 0, lane);
+            select_and_emit(b, pp, it.gap, nullptr, 0, lane);
             continue;
         }
-        trace_and_select(b, it, pp, b.hfin[item], lane);
+        trace_and_select(b, it, pp, lane);
     }
 }
 
@@ -2442,18 +2163,6 @@ int launch_score_xwide(const BatchDev &b, int num_sms, cudaStream_t st)
     return launch_score_one<kDirectX, false>(b, num_sms, st);
 }
 
-int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)
-{
-    if (b.n_nw_items <= 0) return 0;
-    const size_t smem = sizeof(AlignSmem);
-    cudaFuncSetAttribute(k_align, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int small = b.n_nw_items - b.n_nw_big;
-    const int need = std::max(b.n_nw_big, (small + kAW - 1) / kAW);
-    const int grid = std::max(1, std::min(num_sms * 2, need));
-    k_align<<<grid, kAW * 32, smem, st>>>(b);
-    return 1;
-}
-
 int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_tiles <= 0) return 0;
@@ -2466,7 +2175,7 @@ int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st)
 
 int launch_trace(const BatchDev &b, int num_sms, cudaStream_t st)
 {
-    const int n = b.n_nw_items - b.n_nw_big;   // the whole-CTA ones are traced back by k_align
+    const int n = b.n_nw_items;
     if (n <= 0) return 0;
     const int need = (n + 3) / 4;
     const int grid = std::max(1, std::min(num_sms * 8, need));

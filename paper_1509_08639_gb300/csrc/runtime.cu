@@ -579,6 +579,9 @@ struct mine_ctx {
     // test fault injection (mine_test_inject): the checked CUDA call of a
     // host-buffer batch call at which a failure is faked, counting down
     std::atomic<int32_t> inject_cuda_at{0};
+    // host-buffer batch calls still to run with withheld pipeline rows and
+    // short device waits (mine_test_inject, MINE_INJECT_WITHHOLD_ROWS)
+    std::atomic<int32_t> inject_withhold{0};
     std::atomic<int64_t> h2d_bytes{0}, d2h_bytes{0};   // host-buffer batch calls
     // per-kernel timing (CUDA events on the launching stream)
     std::mutex prof_mu;
@@ -1281,6 +1284,10 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
         CKB(cudaStreamWaitEvent(st, res.in_ready, 0));
     }
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, res.gscratch);
+    if (ctx->inject_withhold.load() > 0 && ctx->inject_withhold.fetch_sub(1) > 0) {
+        b.test_withhold = 1;
+        b.wait_spins = kTestWaitSpins;
+    }
     if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return bail(rc);
     int64_t *d_off = reinterpret_cast<int64_t *>(base + o_off);
     int32_t *d_pk = reinterpret_cast<int32_t *>(base + o_pk);
@@ -1499,8 +1506,13 @@ int mine_score_q16(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
 int mine_test_inject(mine_ctx *ctx, int32_t kind, int32_t count)
 {
     if (!ctx || count < 0) return fail(MINE_EINVAL, "null context or negative count");
-    if (kind != MINE_INJECT_CUDA_CALL) return fail(MINE_EINVAL, "unknown injection kind");
-    ctx->inject_cuda_at.store(count);
+    if (kind == MINE_INJECT_CUDA_CALL) {
+        ctx->inject_cuda_at.store(count);
+    } else if (kind == MINE_INJECT_WITHHOLD_ROWS) {
+        ctx->inject_withhold.store(count);
+    } else {
+        return fail(MINE_EINVAL, "unknown injection kind");
+    }
     return MINE_OK;
 }
 

@@ -110,6 +110,7 @@ SIGNATURES = {
 
 ALIGN_BINS = 40
 INJECT_CUDA_CALL = 1   # mine_test_inject kinds (include/mine.h)
+INJECT_WITHHOLD_ROWS = 2
 
 _lib = None
 

@@ -477,6 +477,37 @@ def test_serving_alone_and_in_the_mix():
     assert overlap >= 2, f"{batches} batches, never two on the device at once"
 
 
+def test_bounded_wait_runs_out_and_the_context_recovers(ctx):
+    """Failure detection without a fault: the first warp of every warp
+    pipeline withholds its rows (mine_test_inject, short waits), so the next
+    warp's bounded wait runs out; the kernels return on their own, the call
+    reports MINE_ETIMEDOUT, and the next call on the context mines exactly as
+    the oracle does."""
+    rng = np.random.default_rng(12)
+    d = synth.make_dictionary(rng, 5000, 3)
+    b = _edge_batch(rng, d, [(400, 400), (40, 45), (300, 600), (70, 33)], 5000)
+    w = synth.Workload("pipeline", b, d, [], [], [(-65536, 32768)])
+    dh = ctx.dict_create(d)
+    want = oracle_results(w)
+    old = ctx.align_strategy()
+    try:
+        ctx.align_strategy([1] * mine.ALIGN_BINS)   # a warp pipeline wherever the shape allows
+        assert_same(ctx.run_batch(dh, b, w.settings), want, "warp pipelines")
+        ctx.test_inject(mine.INJECT_WITHHOLD_ROWS, 1)
+        with pytest.raises(mine.MineError) as e:
+            ctx.run_batch(dh, b, w.settings)
+        assert e.value.code == -5                     # MINE_ETIMEDOUT
+        assert_same(ctx.run_batch(dh, b, w.settings), want, "after the timeout")
+        ctx.test_inject(mine.INJECT_WITHHOLD_ROWS, 1)
+        with pytest.raises(mine.MineError) as e:
+            ctx.batch_wait(ctx.run_batch_async(dh, b, w.settings))
+        assert e.value.code == -5
+        assert_same(ctx.batch_wait(ctx.run_batch_async(dh, b, w.settings)), want, "asynchronous, after")
+    finally:
+        ctx.test_inject(mine.INJECT_WITHHOLD_ROWS, 0)
+        ctx.align_strategy(old)
+
+
 def test_errors_are_reported(ctx):
     w = synth.workload(1)
     dh = ctx.dict_create(w.dictionary)
