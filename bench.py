@@ -691,9 +691,8 @@ def main():
         "int_peak": {"value": int_peak_tops, "unit": "Tops/s", "forms": [v / 1e12 for v in int_peak_forms],
                      "how": "mine_int_peak: full grid of independent max(x + g, y) chains, ops written counted"},
         "autotune": {"seconds": t_tune,
-                     "whole_cta_bins": [k for k, v in enumerate(align_table) if v == 1],
-                     "one_warp_bins": [k for k, v in enumerate(align_table) if v == 0],
-                     "tiled_bins": [k for k, v in enumerate(align_table) if v == 2],
+                     "table": {str(k): {0: "1 warp", 3: "2 warps", 4: "4 warps", 1: "8 warps",
+                                        2: "tiles"}[v] for k, v in enumerate(align_table) if v >= 0},
                      "bin": "ceil(log2(S*T+1)); other bins keep the built-in rule",
                      "how": "mine_autotune_batch on the benchmark batch and settings (strategies timed on its alignments)"},
     }

@@ -390,16 +390,18 @@ int mine_profile_read(mine_ctx *ctx, double *ms, int64_t *launches, int32_t n);
 const char *mine_kernel_name(int32_t id);
 
 /* Autotuner of the alignment strategy per size bin.  Bin b holds the pairs
- * with ceil(log2(S*T + 1)) == b, b < MINE_ALIGN_BINS.  For every bin of up to
+ * with ceil(log2(S*T + 1)) == b, b < MINE_ALIGN_BINS.  The strategies
+ * (values of the table, see mine_align_strategy) differ in how many warps
+ * share one alignment: one warp runs from one 32-row stripe of the pair into
+ * the next; a pipeline of 2, 4 or 8 warps gives warp w the stripes w, w+G,
+ * ...; tiles spread a large pair over many CTAs.  For every bin of up to
  * 2^17 cells this times, on the context's GPU, the alignment kernel over a
- * batch of random square score matrices of that size aligned (a) one warp per
- * alignment and (b) by a whole CTA of 8 pipelined warps, and records the
- * faster; larger bins keep the built-in rule (whole CTA from 2^15 cells).
- * A pair with S > 32 and T >= 512 is always aligned by a whole CTA (the
- * one-warp form keeps one boundary row of at most 512 cells).  Runs
- * synchronously on the context's stream and uses its scratch (about 70 MB).
- * The strategy does not change any result, only the time.  No counterpart in
- * the paper, whose single GPU NW (Section 5, Table 3) has no size classes. */
+ * batch of random square score matrices of that size under each pipeline
+ * width the side allows, and records the fastest; larger bins keep the
+ * built-in rule.  Runs synchronously on the context's stream and uses its
+ * scratch (about 70 MB).  The strategy does not change any result, only the
+ * time.  No counterpart in the paper, whose single GPU NW (Section 5,
+ * Table 3) has no size classes. */
 #define MINE_ALIGN_BINS 40
 int mine_autotune(mine_ctx *ctx);
 
@@ -407,19 +409,23 @@ int mine_autotune(mine_ctx *ctx);
  * mine_run_batch) with the settings it will be mined with (settings NULL:
  * one setting, gap -65536 and threshold 32768; the distinct gaps set the
  * alignments per pair): its score matrices are computed once, then for
- * every size bin present in it each other form its pairs allow (one warp;
- * one CTA, for a bin holding a pair of more than 32 source sentences; tiles)
+ * every size bin present in it each strategy some pair of the bin can take
  * is tried on the whole batch's alignments (mean of four timed runs), and
- * the fastest is kept when more than 3% faster.  Synchronous; uses the
- * context's scratch. */
+ * the fastest is kept when more than 3% faster than the bin's entry before.
+ * Synchronous; uses the context's scratch. */
 int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
                         const mine_settings *settings);
 
-/* Read (get != 0) or set the strategy table: tab[b] = 2 tiles of 256 x 512
- * cells over many CTAs (pairs with S > 256 and T > 512; others of the bin
- * take a whole CTA), 1 whole CTA, 0 one warp (where allowed), -1 built-in
- * rule (tiles from 2^21 cells, a whole CTA from 2^15); n entries,
- * n <= MINE_ALIGN_BINS. */
+/* Read (get != 0) or set the strategy table, n entries (n <= MINE_ALIGN_BINS):
+ * tab[b] = 0 one warp per alignment, 3 a pipeline of 2 warps, 4 of 4 warps,
+ * 1 of 8 warps (a whole CTA), 2 tiles of 256 x 512 cells over many CTAs, -1
+ * the built-in rule (tiles from 2^21 cells where the pair has more than 256
+ * rows and 512 columns, else 8 warps from 2^17 cells, 4 from 2^16, 2 from
+ * 2^15, one below).  A pair that cannot take its bin's strategy takes the
+ * nearest it can: a pipeline narrowed to at most its number of 32-row
+ * stripes and of 32-column tiles minus one (by halving), two warps where
+ * one cannot hold the boundary ring (more than 32 rows and T >= 512), 8
+ * warps in place of tiles for a pair of one tile row or column. */
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get);
 
 /* The roofline of the alignment: the measured rate of int32 add and max

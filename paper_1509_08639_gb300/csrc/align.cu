@@ -20,12 +20,10 @@
 // ring).  A pipeline of G warps shares a pair: warp w takes stripes w, w+G,
 // ... and reads the ring of warp w-1 (bounded flag waits once per 32 steps).
 //
-// Scores.  Each lane keeps its own row of the score tiles in a ring of three
-// 32-column slots plus a copy of slot 0 after slot 2, so the 32 scores a
-// lane reads in 32 steps are always contiguous: one shared load per step at
-// a fixed offset.  Every lane fetches its 128-byte tile row (the tiles of M
-// are 32 x 32, row-major) with eight 16-byte asynchronous copies, one tile
-// ahead; it alone reads that row, so no barrier is needed.
+// Scores.  The 32 x 32 tiles of M come in by one 4 KB bulk copy each, one
+// tile ahead, three slots per warp; in a chunk of 32 steps lane L reads the
+// tile before for its first L steps and the current one after (the skew puts
+// the 32 lanes' reads in distinct banks).
 //
 // Per step a lane issues the shuffle, the score load, three integer
 // operations for the cell (add; max of up and left with the up-wins flag;
@@ -41,27 +39,19 @@ namespace mine {
 namespace {
 
 constexpr uint32_t kFullMaskA = 0xffffffffu;
-constexpr int kNwWarps = kNwPipe;    // warps per CTA (one CTA per SM)
-constexpr int kNwSlots = 3;          // score tiles resident per lane row
-// words per lane row: the slots, the copy of slot 0, and 4 words of padding
-// (16-byte copies of 8 consecutive lanes then fall into distinct banks)
-constexpr int kNwRowW = 32 * (kNwSlots + 1) + 4;
+constexpr int kNwWarps = kNwPipe;    // warps per CTA (two CTAs per SM)
+constexpr int kNwSlots = 3;          // score tiles resident per warp (two read, one in flight)
 constexpr int kNwRing = 512;         // boundary ring entries per warp
 
 template <int K>
 struct NwSmem {
-    int32_t rows[K][32][kNwRowW];
+    int32_t tile[K][kNwSlots][kTileElems];   // 32 x 32 score tiles, row-major
     int32_t ring[K][kNwRing];
+    unsigned long long bar[K][kNwSlots];
     int32_t prod[K];                 // keys published by warp w's lane 31 (INT_MAX: done)
     int32_t cons[K];                 // keys warp w has read from its predecessor (INT_MAX: done)
-    int32_t item;
+    int32_t gitem[kNwGroups][K];     // the item a group (at its first warp) took, per run
 };
-
-// 16-byte asynchronous copy global -> shared, cached in L2 only.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
 
 // Where lane 0's up value comes from in a chunk of 32 steps: the ring (the
 // chunk's 32 values read at its start, one per lane, and shuffled to lane 0
@@ -69,7 +59,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 // wide -- lane 31's value of the step before, which is exactly the row above.
 enum XSrc { X_RING = 0, X_ARITH = 1, X_ROT = 2 };
 
-// 32 wavefront steps.  srow: this lane's scores, srow[u] at step u.  rw:
+// 32 wavefront steps.  Lane L's score at step u is bp[u] (u < L: the tile
+// before, at column 32 - L + u of its row) or bc[u] (u >= L: column u - L of
+// the current tile); the skew keeps the 32 lanes' reads in distinct banks.  rw:
 // lane 31 writes its value of step u to rw[u] (the ring read by the next
 // stripe's lane 0).  rv: lane k holds lane 0's up value of step k (X_RING).
 // xa: H[0][j] of lane 0's cell at u = 0 (X_ARITH; + u g at step u).  RESET:
@@ -77,9 +69,10 @@ enum XSrc { X_RING = 0, X_ARITH = 1, X_ROT = 2 };
 // a1 / a2: where the aligned code words completed at steps 15 and 31 go
 // (null: not stored).
 template <bool RESET, int XS>
-__device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ srow, int32_t *rw, int32_t rv,
+__device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ bp, const int32_t *__restrict__ bc,
+                                         int32_t *__restrict__ rw, int32_t rv,
                                          int lane, int src, int32_t g, int32_t rh, int32_t xa,
-                                         uint32_t sh, uint32_t *a1, uint32_t *a2, int32_t &h,
+                                         uint32_t sh, uint32_t *__restrict__ a1, uint32_t *__restrict__ a2, int32_t &h,
                                          int32_t &up_prev, uint32_t &word, uint32_t &prev)
 {
 #pragma unroll
@@ -96,7 +89,7 @@ __device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ srow, int32
             h = rh;
             up_prev = rh - g;
         }
-        const int32_t sv = srow[u];
+        const int32_t sv = (u < lane ? bp : bc)[u];
         const int32_t cd = up_prev + sv;
         bool pu;
         const int32_t m = __vibmax_s32(up_in, h, &pu);       // max(up, left), pu = up >= left
@@ -116,16 +109,21 @@ __device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ srow, int32
     }
 }
 
-// Wait until every copy this thread has in flight has landed, so that the
-// CTA may end after an error.
-__device__ __forceinline__ void nw_drain() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Wait (bounded) until every tile copy this warp has in flight has landed,
+// so that the CTA may end after an error.
+template <int K>
+__device__ void nw_drain(NwSmem<K> &sm, int w, const uint32_t (&uses)[kNwSlots], int32_t *err)
+{
+    for (int k = 0; k < kNwSlots; ++k)
+        if (uses[k] > 0) mbar_wait(&sm.bar[w][k], (uses[k] - 1) & 1u, err);
+}
 
 // Fill H for one alignment by warp wg of a pipeline of G warps (w = its
 // warp in the CTA; the pipeline is warps w - wg .. w - wg + G - 1).  Returns
 // false when a bounded wait ran out (error word set).
 template <int K>
 __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, int lane, const NwItem &it,
-                       const PairPlan &pp)
+                       const PairPlan &pp, uint32_t (&uses)[kNwSlots], uint64_t pol)
 {
     const int S = pp.S, T = pp.T;
     const int TT = (T + 31) >> 5;           // column tiles; stripes are Tp = 32 TT wide
@@ -167,40 +165,32 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
     // to itself, so the next warp's wait runs out
     const bool publish = !(b.test_withhold && !self && wg == 0);
     const uint32_t sh = 2u * (uint32_t)(lane & 15);
-    int32_t *myrow = sm.rows[w][lane];
     const int ntile = nq * TT;              // virtual tiles of this warp
     const int nchunks = ntile + 1;
 
-    // the lane's row of virtual tile k of this warp into its slot (and into
-    // the copy of slot 0): eight 16-byte asynchronous copies per lane, one
-    // commit group per tile
+    // virtual tile k of this warp into slot k % 3: one 4 KB bulk copy
     auto issue = [&](int k) {
         const int q = k / TT;
         const int C = k - q * TT;
         const int s = wg + q * G;
-        const int32_t *src_row = Mp + ((int64_t)s * TT + C) * kTileElems + lane * kTile;
         const int slot = k % kNwSlots;
-        const uint32_t d0 = s2u(myrow + 32 * slot);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) cp_async16(d0 + 16 * e, src_row + 4 * e);
-        if (slot == 0) {
-            const uint32_t d1 = s2u(myrow + 32 * kNwSlots);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) cp_async16(d1 + 16 * e, src_row + 4 * e);
+        __syncwarp();
+        if (lane == 0) {
+            mbar_expect_tx(&sm.bar[w][slot], kTileElems * 4);
+            bulk_g2s_once(sm.tile[w][slot], Mp + ((int64_t)s * TT + C) * kTileElems, kTileElems * 4,
+                          &sm.bar[w][slot], pol);
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        uses[slot]++;
     };
 
     int32_t h = 0, up_prev = 0;
     uint32_t word = 0, prev = 0;
     issue(0);
     for (int c = 0; c < nchunks; ++c) {
-        // tile c has landed once at most the group of tile c + 1 is pending
-        if (c + 1 < ntile) {
-            issue(c + 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (c + 1 < ntile) issue(c + 1);
+        if (c < ntile) {
+            const int slot = c % kNwSlots;
+            if (!mbar_wait(&sm.bar[w][slot], (uses[slot] - 1) & 1u, b.err)) return false;
         }
         const int q = c / TT;                      // stripe (of this warp) lane 0 is in
         const int r = c - q * TT;
@@ -224,8 +214,8 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
         }
         // lane k: key 32c + k, stored at slot key - 1
         const int32_t rv = xs == X_RING ? ring_in[(32 * c + lane - 1) & (kNwRing - 1)] : 0;
-        const int base_c = (((32 * c - lane) % (32 * kNwSlots)) + 32 * kNwSlots) % (32 * kNwSlots);
-        const int32_t *srow = myrow + base_c;
+        const int32_t *bp = sm.tile[w][(c + kNwSlots - 1) % kNwSlots] + lane * kTile + 32 - lane;
+        const int32_t *bc = sm.tile[w][c % kNwSlots] + lane * kTile - lane;
         int32_t *rw = ring_out + ((32 * c - 32 + off_out) & (kNwRing - 1));
         const int32_t xa = (32 * c + 1) * g;
         // the new stripe of a reset chunk, for the row of each lane
@@ -245,18 +235,18 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
         }
         if (reset) {
             if (xs == X_RING)
-                nw_chunk<true, X_RING>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+                nw_chunk<true, X_RING>(bp, bc, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
             else if (xs == X_ARITH)
-                nw_chunk<true, X_ARITH>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+                nw_chunk<true, X_ARITH>(bp, bc, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
             else
-                nw_chunk<true, X_ROT>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+                nw_chunk<true, X_ROT>(bp, bc, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
         } else {
             if (xs == X_RING)
-                nw_chunk<false, X_RING>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+                nw_chunk<false, X_RING>(bp, bc, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
             else if (xs == X_ARITH)
-                nw_chunk<false, X_ARITH>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+                nw_chunk<false, X_ARITH>(bp, bc, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
             else
-                nw_chunk<false, X_ROT>(srow, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
+                nw_chunk<false, X_ROT>(bp, bc, rw, rv, lane, src, g, rh, xa, sh, a1, a2, h, up_prev, word, prev);
         }
         if (!self) {
             __syncwarp();
@@ -279,52 +269,71 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
     return true;
 }
 
-// Persistent alignment kernel: first the pairs aligned by the whole CTA (a
-// pipeline of K warps), then one warp per pair.  Tracebacks follow in k_trace.
-template <int K>
-__global__ void __launch_bounds__(K * 32, 1) k_nw(BatchDev b)
+// Named barrier of a pipeline group: id 1 for the whole CTA (8 warps), 2-3
+// for groups of 4, 4-7 for groups of 2.
+__device__ __forceinline__ void group_sync(int G, int base_w)
 {
+    if (G == 1) {
+        __syncwarp();
+    } else {
+        const int id = (kNwPipe / G) + base_w / G;
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(G * 32) : "memory");
+    }
+}
+
+// Persistent alignment kernel.  The items come in four runs: pairs aligned
+// by pipelines of 8, 4 and 2 warps, then one warp per pair.  The CTA first
+// works as one group of 8 warps on the first run; a group whose run is empty
+// splits in two and each half takes the next run, without waiting for the
+// other groups.  Tracebacks follow in k_trace.
+template <int K>
+__global__ void __launch_bounds__(K * 32, 2) k_nw(BatchDev b)
+{
+    static_assert(K == kNwPipe, "groups of 8, 4, 2, 1 warps");
     extern __shared__ __align__(128) unsigned char nw_smem_raw[];
     NwSmem<K> &sm = *reinterpret_cast<NwSmem<K> *>(nw_smem_raw);
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        for (int k = 0; k < kNwSlots; ++k) mbar_init(&sm.bar[w][k], 1);
+        fence_barrier_init();
+    }
+    uint32_t uses[kNwSlots] = {0u, 0u, 0u};
+    const uint64_t pol = l2_evict_first();   // score tiles are read once per gap
     __syncthreads();
     if (*(volatile int32_t *)b.err) return;
 
-    for (;;) {
-        if (threadIdx.x == 0) sm.item = atomicAdd(&b.counters[2], 1);
-        if (threadIdx.x < K) {
-            sm.prod[threadIdx.x] = -1;   // keys <= -1 published / consumed: none
-            sm.cons[threadIdx.x] = -1;
+    int beg = 0;
+    for (int gi = 0; gi < kNwGroups; ++gi) {
+        const int G = K >> gi;
+        const int end = beg + b.n_nw_grp[gi];
+        const int base_w = w - w % G, wg = w - base_w;
+        while (beg < end) {
+            // the group's first warp takes the next item of the run
+            if (wg == 0 && lane == 0) sm.gitem[gi][base_w] = atomicAdd(&b.counters[ctr_nw(gi)], 1);
+            if (lane == 0) {
+                sm.prod[w] = -1;   // keys <= -1 published / consumed: none
+                sm.cons[w] = -1;
+            }
+            group_sync(G, base_w);
+            const int item = beg + *(volatile int32_t *)&sm.gitem[gi][base_w];
+            if (item >= end) break;
+            const NwItem it = b.nw_items[item];
+            const PairPlan pp = b.pairs[it.pair];
+            // warp 0 of a pipeline of Ge warps needs the row above its second
+            // stripe from warp Ge - 1 before it has filled Ge of its own
+            // chunks: Ge < T'/32 keeps that dependency acyclic
+            const int Ge = min(min(G, (pp.S + 31) >> 5), max(1, ((pp.T + 31) >> 5) - 1));
+            bool ok = true;
+            if (pp.S > 0 && pp.T > 0 && wg < Ge) ok = nw_run<K>(b, sm, w, wg, Ge, lane, it, pp, uses, pol);
+            if (!ok) atomicCAS(b.err, 0, ERR_TIMEOUT);
+            group_sync(G, base_w);
+            if (*(volatile int32_t *)b.err) {
+                nw_drain<K>(sm, w, uses, b.err);
+                return;
+            }
         }
-        __syncthreads();
-        const int item = sm.item;
-        if (item >= b.n_nw_big) break;
-        const NwItem it = b.nw_items[item];
-        const PairPlan pp = b.pairs[it.pair];
-        // warp 0 of a pipeline of G warps needs the row above its second
-        // stripe from warp G - 1 before it has filled G of its own chunks:
-        // G < T'/32 keeps that dependency acyclic
-        const int G = min(min(K, (pp.S + 31) >> 5), max(1, ((pp.T + 31) >> 5) - 1));
-        bool ok = true;
-        if (w < G) ok = nw_run<K>(b, sm, w, w, G, lane, it, pp);
-        if (!__syncthreads_and(ok)) {
-            nw_drain();
-            return;
-        }
-    }
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = b.n_nw_big + atomicAdd(&b.counters[3], 1);
-        item = __shfl_sync(kFullMaskA, item, 0);
-        if (item >= b.n_nw_items - b.n_nw_tiled) break;
-        const NwItem it = b.nw_items[item];
-        const PairPlan pp = b.pairs[it.pair];
-        if (pp.S == 0 || pp.T == 0) continue;   // nothing to fill; k_trace reports it
-        if (!nw_run<K>(b, sm, w, 0, 1, lane, it, pp)) {
-            nw_drain();
-            return;
-        }
+        beg = end;
     }
 }
 
@@ -336,9 +345,13 @@ int launch_align(const BatchDev &b, int num_sms, cudaStream_t st)
     if (items <= 0) return 0;
     const size_t smem = sizeof(NwSmem<kNwWarps>);
     cudaFuncSetAttribute(k_nw<kNwWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int small = items - b.n_nw_big;
-    const int need = std::max(b.n_nw_big, (small + kNwWarps - 1) / kNwWarps);
-    const int grid = std::max(1, std::min(num_sms, need));
+    // CTAs that have work in the first run they can take part in
+    int need = 0;
+    for (int gi = 0; gi < kNwGroups; ++gi) {
+        const int per_cta = 1 << gi;   // groups of 8 >> gi warps per CTA
+        need = std::max(need, (b.n_nw_grp[gi] + per_cta - 1) / per_cta);
+    }
+    const int grid = std::max(1, std::min(2 * num_sms, need));
     k_nw<kNwWarps><<<grid, kNwWarps * 32, smem, st>>>(b);
     return 1;
 }

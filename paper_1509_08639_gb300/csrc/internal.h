@@ -24,6 +24,7 @@ constexpr int32_t ERR_BAD_TOKEN = 3;
 constexpr int32_t ERR_TIMEOUT = 4;          // a bounded device wait ran out
 
 constexpr int kWarp = 32;
+constexpr int kNwGroups = 4;                // alignment pipelines of 8, 4, 2 and 1 warps
 constexpr int kTile = 32;                   // score matrices are stored as 32 x 32 tiles
 constexpr int kTileElems = kTile * kTile;
 constexpr int kColHashSlots = 1024;         // per-warp target-token table of a column block
@@ -137,7 +138,7 @@ struct BatchDev {
     int32_t n_score_items;
     const NwItem *nw_items;
     int32_t n_nw_items;
-    int32_t n_nw_big;            // items [0, n_nw_big) are aligned by a whole CTA
+    int32_t n_nw_grp[kNwGroups]; // items aligned by pipelines of 8, 4, 2 warps and by one warp, in that order from 0
     int32_t n_nw_tiled;          // the last n_nw_tiled items are aligned tile by tile
     const TileItem *tiles;       // tiles of the tiled items, in order of R + C
     int32_t n_tiles;
@@ -171,32 +172,49 @@ struct BatchDev {
     int32_t *sel;                // mine_pair triples
 };
 
-// A one-warp alignment keeps the previous stripe's last row in a ring of
-// kRing entries, so a pair with more than 32 source sentences and T >= kRing
-// target sentences is aligned by a whole CTA (a pipeline of kNwPipe warps),
-// as is every pair of kBigCells or more.  A pipeline needs more than kNwPipe
-// 32-column tiles per row (T > 32 kNwPipe); narrower pairs take one warp.
+// Alignment forms (the values of the strategy table, mine_align_strategy):
+// a pipeline of 1, 2, 4 or 8 warps (warp w of a pipeline of G takes stripes
+// w, w + G, ... of 32 rows), or tiles over many CTAs.  A one-warp alignment
+// keeps the previous stripe's last row in a ring of kRing entries, so a pair
+// with more than 32 source sentences and T >= kRing target sentences needs a
+// pipeline of two or more warps; a pipeline of G warps needs G stripes and
+// more than G tiles of 32 columns per row.
+enum : int { AF_WARP1 = 0, AF_WARP8 = 1, AF_TILED = 2, AF_WARP2 = 3, AF_WARP4 = 4, AF_FORMS = 5 };
 constexpr int kRing = 512;
-constexpr int64_t kBigCells = 1 << 15;
-constexpr int kNwPipe = 8;
+constexpr int kNwPipe = 8;                  // warps of the widest pipeline (a CTA)
+__host__ __device__ inline int form_warps(int f)
+{
+    return f == AF_WARP8 ? 8 : f == AF_WARP4 ? 4 : f == AF_WARP2 ? 2 : f == AF_WARP1 ? 1 : 0;
+}
+// queue heads of the alignment groups (pipelines of 8, 4, 2, 1 warps) in the
+// batch's counters
+__host__ __device__ constexpr int ctr_nw(int gi) { return gi == 0 ? 2 : gi == 1 ? 16 : gi == 2 ? 17 : 3; }
+constexpr int kCounters = 32;               // queue heads and flags of a batch (index 8: error word)
 constexpr int kAlignBins = MINE_ALIGN_BINS;
 
-// Alignment form of an S x T pair: 0 one warp, 1 one CTA, 2 tiles over many
-// CTAs.  The tuned choice of its size bin (tab may be null; -1 keeps the
-// built-in rule: tiles from kTiledCells, a CTA from kBigCells), except that
-// tiles need more than one tile row and column, and one warp cannot hold a
-// boundary row of kRing or more cells below a first stripe.
+// Alignment form of an S x T pair: the tuned choice of its size bin (tab
+// may be null; -1 keeps the built-in rule: tiles from kTiledCells, else
+// about 2^14 cells or more per warp of a pipeline), made feasible: tiles
+// need more than one tile row and column; a pipeline is narrowed (by powers
+// of two) to at most the stripes and the column tiles - 1 of the pair, and
+// widened to two warps where one warp cannot hold the ring.
 inline int align_kind(const int8_t *tab, int32_t S, int32_t T)
 {
     const int64_t c = (int64_t)S * T;
     const bool can_tile = S > kAlignTileRows && T > kAlignTileCols;
     const int bin = c > 0 ? 64 - __builtin_clzll((unsigned long long)c) : 0;   // 2^bin > c
     int v = (tab && bin < kAlignBins) ? tab[bin] : -1;
-    if (v < 0) v = (can_tile && c >= kTiledCells) ? 2 : (c >= kBigCells ? 1 : 0);
-    if (v == 2 && !can_tile) v = 1;
-    if (v == 1 && T <= kTile * kNwPipe) v = 0;
-    if (v == 0 && S > kTile && T >= kRing) v = 1;
-    return v;
+    if (v < 0)
+        v = (can_tile && c >= kTiledCells) ? AF_TILED
+            : c >= (int64_t(1) << 17) ? AF_WARP8 : c >= (int64_t(1) << 16) ? AF_WARP4
+            : c >= (int64_t(1) << 15) ? AF_WARP2 : AF_WARP1;
+    if (v == AF_TILED && !can_tile) v = AF_WARP8;
+    if (v == AF_TILED) return v;
+    int g = form_warps(v);
+    const int ns = (S + 31) >> 5, tt = (T + 31) >> 5;
+    while (g > 1 && (g > ns || g > tt - 1)) g >>= 1;
+    if (g == 1 && S > kTile && T >= kRing) g = 2;
+    return g == 8 ? AF_WARP8 : g == 4 ? AF_WARP4 : g == 2 ? AF_WARP2 : AF_WARP1;
 }
 
 // Union of the selections of a batch mined in both directions (the second

@@ -154,8 +154,11 @@ extern "C" int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T
     b.pairs = reinterpret_cast<const PairPlan *>(plan);
     b.nw_items = reinterpret_cast<const NwItem *>(plan + sizeof(PairPlan));
     b.n_nw_items = 1;
-    const bool big = (int64_t)S * T >= kBigCells || (S > kTile && T >= kRing);
-    b.n_nw_big = big ? 1 : 0;
+    // the built-in alignment form of the pair (never tiles at these sizes)
+    int form = align_kind(nullptr, S, T);
+    if (form == AF_TILED) form = AF_WARP8;
+    const int g = form_warps(form);
+    b.n_nw_grp[g == 8 ? 0 : g == 4 ? 1 : g == 2 ? 2 : 3] = 1;
     const int32_t *set = reinterpret_cast<const int32_t *>(plan + sizeof(PairPlan) + sizeof(NwItem));
     b.set_gap = set;
     b.set_thr = set + 1;

@@ -110,7 +110,7 @@ struct Plan {
     std::vector<int32_t> set_gap, set_thr, gap_val;
     int64_t m_elems = 0, code_words = 0, match_words = 0, sel_cap = 0;
     int32_t R = 0;
-    int32_t n_big = 0;              // alignments [0, n_big) use a whole CTA
+    int32_t n_grp[kNwGroups] = {0, 0, 0, 0};   // alignments by pipelines of 8, 4, 2, 1 warps (from 0, in order)
     int64_t n_sent = 0, n_tok = 0;
 
     // empty again, keeping the vectors' storage (a plan reused call after
@@ -131,7 +131,7 @@ struct Plan {
         gap_val.clear();
         m_elems = code_words = match_words = sel_cap = 0;
         R = 0;
-        n_big = 0;
+        for (int k = 0; k < kNwGroups; ++k) n_grp[k] = 0;
         n_sent = n_tok = 0;
     }
 };
@@ -262,16 +262,16 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
             for (int c0 = 0; c0 < std::max(pp.T, 1); c0 += kScoreColChunk)
                 pl.sitems.push_back(ScoreItem{p, r0, c0, std::min(pp.T, c0 + kScoreColChunk)});
     }
-    // alignments: whole-CTA ones first, then one-warp ones, each longest
-    // first, then the tiled ones
+    // alignments: pipelines of 8, 4 and 2 warps, then one warp each, each
+    // longest first, then the tiled ones
     const std::vector<int> ord = order_by(bucketC);
-    const int kind_of_pass[3] = {1, 0, 2};
+    const int kind_of_pass[kNwGroups + 1] = {AF_WARP8, AF_WARP4, AF_WARP2, AF_WARP1, AF_TILED};
     std::vector<TileItem> tl;
     std::vector<int32_t> tdiag;
     int64_t n_items = 0;
     for (int p = 0; p < P; ++p) n_items += pl.pairs[p].ngap;
     pl.nitems.reserve(n_items);
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < kNwGroups + 1; ++pass) {
         for (int p : ord) {
             const PairPlan &pp = pl.pairs[p];
             if (kind[p] != kind_of_pass[pass]) continue;
@@ -285,7 +285,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
                 it.match_off = pl.match_words;
                 pl.match_words += std::min(pp.S, pp.T);
                 it.tb_off = -1;
-                if (pass == 2) {
+                if (pass == kNwGroups) {
                     const int64_t NR = tile_rows_of(pp.S), NC = tile_cols_of(pp.T);
                     it.tb_off = pl.tb_words;
                     pl.tb_words += align_up((NR - 1) * (pp.T + 1) + (NC - 1) * (pp.S + 1) + NR * NC, 4);
@@ -298,8 +298,12 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
                 pl.nitems.push_back(it);
             }
         }
-        if (pass == 0) pl.n_big = (int32_t)pl.nitems.size();
-        if (pass == 1) pl.n_tiled = -(int32_t)pl.nitems.size();
+        if (pass < kNwGroups) {
+            int32_t before = 0;
+            for (int k = 0; k < pass; ++k) before += pl.n_grp[k];
+            pl.n_grp[pass] = (int32_t)pl.nitems.size() - before;
+        }
+        if (pass == kNwGroups - 1) pl.n_tiled = -(int32_t)pl.nitems.size();
     }
     pl.n_tiled += (int32_t)pl.nitems.size();
     // tiles in order of their anti-diagonal: a tile's predecessors come first
@@ -371,7 +375,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     L.matches = take(4 * pl.match_words + 16);
     L.hfin = take(4 * (int64_t)pl.nitems.size() + 16);
     L.tbnd = take(4 * pl.tb_words + 16);
-    L.counters = take(4 * 16);
+    L.counters = take(4 * kCounters);
     L.nw = take(4 * (int64_t)pl.R);
     L.nsel = take(4 * (int64_t)pl.R);
     if (own_sel) L.sel = take(12 * pl.sel_cap + 16);
@@ -410,7 +414,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.n_score_items = (int32_t)pl.sitems.size();
     b.nw_items = reinterpret_cast<const NwItem *>(plan + L.o_nitems);
     b.n_nw_items = (int32_t)pl.nitems.size();
-    b.n_nw_big = pl.n_big;
+    for (int k = 0; k < kNwGroups; ++k) b.n_nw_grp[k] = pl.n_grp[k];
     b.n_nw_tiled = pl.n_tiled;
     b.tiles = reinterpret_cast<const TileItem *>(plan + L.o_tiles);
     b.n_tiles = (int32_t)pl.tiles.size();
@@ -702,7 +706,7 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
                     int64_t n_tok, bool scoring, cudaStream_t st, bool aligning = true)
 {
     int n = 0;
-    CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
+    CK(cudaMemsetAsync(b.counters, 0, 4 * kCounters, st));
     if (scoring) {
         n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
         BatchDev bd = b;
@@ -747,16 +751,16 @@ int64_t mine_launch_count(mine_ctx *ctx) { return ctx ? ctx->launches.load() : 0
 namespace {
 
 // Device time (ms, mean of three launches after a warm-up) of the alignment
-// kernel over P random side x side matrices, every pair aligned one warp
-// each (cta = 0) or by a whole CTA (cta = 1).
-int time_align(mine_ctx *ctx, int bin, int side, int32_t P, int cta, cudaEvent_t e0, cudaEvent_t e1,
+// kernel over P random side x side matrices, every pair aligned in form
+// `form` (AF_*).
+int time_align(mine_ctx *ctx, int bin, int side, int32_t P, int form, cudaEvent_t e0, cudaEvent_t e1,
                float &ms)
 {
     std::vector<int32_t> doc(2 * (size_t)P + 1);
     for (size_t k = 0; k < doc.size(); ++k) doc[k] = (int32_t)k * side;
     int8_t tab[kAlignBins];
     std::fill(tab, tab + kAlignBins, (int8_t)-1);
-    tab[bin] = (int8_t)cta;
+    tab[bin] = (int8_t)form;
     const Setting set(-65536, 0);
     Plan pl;
     int rc = build_plan(pl, P, doc.data(), (int64_t)doc.back(),
@@ -774,7 +778,7 @@ int time_align(mine_ctx *ctx, int bin, int side, int32_t P, int cta, cudaEvent_t
     BatchDev b = make_batchdev(pl, L, base, nullptr, nullptr, nullptr, ctx->recip, ctx->gscratch);
     launch_fill_scores(b.M, pl.m_elems, 0x5EEDu + (uint32_t)bin, st);
     for (int rep = 0; rep < 4; ++rep) {
-        CK(cudaMemsetAsync(b.counters, 0, 4 * 16, st));
+        CK(cudaMemsetAsync(b.counters, 0, 4 * kCounters, st));
         if (rep == 1) CK(cudaEventRecord(e0, st));
         ctx->launches += launch_align(b, ctx->num_sms, st);
         ctx->launches += launch_trace(b, ctx->num_sms, st);   // part of each form's cost
@@ -813,9 +817,23 @@ int mine_autotune(mine_ctx *ctx)
         while ((int64_t)(side + 1) * (side + 1) + 1 <= (int64_t(1) << bin)) ++side;
         const int64_t cells = (int64_t)side * side;
         const int32_t P = (int32_t)std::min<int64_t>(8192, std::max<int64_t>(64, (int64_t(1) << 23) / cells));
-        float t[2] = {0.f, 0.f};
-        for (int cta = 0; cta < 2 && rc == 0; ++cta) rc = time_align(ctx, bin, side, P, cta, e0, e1, t[cta]);
-        if (rc == 0) tab[bin] = t[1] < t[0] ? 1 : 0;
+        // pipelines of 1, 2, 4 and 8 warps (as far as the side allows)
+        const int forms[4] = {AF_WARP1, AF_WARP2, AF_WARP4, AF_WARP8};
+        float tbest = 0.f;
+        int fbest = -1;
+        for (int fi = 0; fi < 4 && rc == 0; ++fi) {
+            int8_t one[kAlignBins];
+            std::fill(one, one + kAlignBins, (int8_t)-1);
+            one[bin] = (int8_t)forms[fi];
+            if (align_kind(one, side, side) != forms[fi]) continue;
+            float t = 0.f;
+            rc = time_align(ctx, bin, side, P, forms[fi], e0, e1, t);
+            if (rc == 0 && (fbest < 0 || t < tbest)) {
+                tbest = t;
+                fbest = forms[fi];
+            }
+        }
+        if (rc == 0 && fbest >= 0) tab[bin] = (int8_t)fbest;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -898,7 +916,9 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
         BatchDev bq = make_batchdev(q, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
         for (int rep = 0; rep < 5; ++rep) {   // one untimed, four timed
-            CK(cudaMemsetAsync(bq.counters, 0, 4 * 8, st));   // queue heads; keeps the error word
+            // queue heads (the error word at index 8 is kept)
+            CK(cudaMemsetAsync(bq.counters, 0, 4 * 8, st));
+            CK(cudaMemsetAsync(bq.counters + 16, 0, 4 * (kCounters - 16), st));
             if (bq.n_tiles > 0) CK(cudaMemsetAsync(bq.tbnd, 0, 4 * bq.n_tbnd, st));
             if (rep == 1) CK(cudaEventRecord(e0, st));
             ctx->launches += launch_align(bq, ctx->num_sms, st);
@@ -919,32 +939,34 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
     // CTA pipelines its warps over 32-row stripes: for a pair of one stripe
     // seven of its eight warps would idle, so that form is tried only for
     // bins holding a pair of more rows.
+    // the forms open to some pair of each bin present in the batch (a form
+    // a pair cannot take is narrowed for it, so trying it would repeat
+    // another form's timing)
     bool present[kAlignBins] = {};
-    bool can[kAlignBins][3] = {};
+    bool can[kAlignBins][AF_FORMS] = {};
     for (const PairPlan &pp : pl.pairs) {
         const int64_t c = (int64_t)pp.S * pp.T;
         int bin = 0;
         while (bin < 63 && (int64_t(1) << bin) < c + 1) ++bin;
         if (bin >= kAlignBins) continue;
         present[bin] = true;
-        if (pp.S > kTile) can[bin][1] = true;
-        if (!(pp.S > kTile && pp.T >= kRing)) can[bin][0] = true;
-        if (pp.S > kAlignTileRows && pp.T > kAlignTileCols) can[bin][2] = true;
+        for (int f = 0; f < AF_FORMS; ++f) {
+            int8_t one[kAlignBins];
+            std::fill(one, one + kAlignBins, (int8_t)-1);
+            one[bin] = (int8_t)f;
+            if (align_kind(one, pp.S, pp.T) == f) can[bin][f] = true;
+        }
     }
     float best = 0.f;
     rc = time_with(tab, best);
+    const int order[AF_FORMS] = {AF_WARP1, AF_WARP2, AF_WARP4, AF_WARP8, AF_TILED};
     for (int bin = 0; bin < kAlignBins && rc == 0; ++bin) {
         if (!present[bin]) continue;
-        // the form the bin has now (the built-in rule decides for a pair of
-        // the bin's middle size when the entry is -1), then each other one
-        int now = tab[bin];
-        if (now < 0) {
-            const int64_t c_mid = bin > 0 ? (int64_t(1) << (bin - 1)) : 0;
-            now = (can[bin][2] && c_mid >= kTiledCells) ? 2 : (c_mid >= kBigCells ? 1 : 0);
-        }
-        int keep = now;
-        for (int f = 0; f < 3 && rc == 0; ++f) {
-            if (f == now || !can[bin][f]) continue;
+        // the entry the bin has now (-1: the built-in rule), then each form
+        int keep = tab[bin];
+        for (int fi = 0; fi < AF_FORMS && rc == 0; ++fi) {
+            const int f = order[fi];
+            if (f == tab[bin] || !can[bin][f]) continue;
             int8_t trial[kAlignBins];
             std::copy(tab, tab + kAlignBins, trial);
             trial[bin] = (int8_t)f;
@@ -972,7 +994,7 @@ int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get)
         std::copy(ctx->align_tab, ctx->align_tab + n, tab);
     } else {
         for (int k = 0; k < n; ++k)
-            if (tab[k] < -1 || tab[k] > 2) return fail(MINE_EINVAL, "strategy entries are -1, 0, 1 or 2");
+            if (tab[k] < -1 || tab[k] >= AF_FORMS) return fail(MINE_EINVAL, "strategy entries are -1 .. 4");
         std::copy(tab, tab + n, ctx->align_tab);
         ++ctx->arena_gen;   // cached graphs hold plans of the old table
     }

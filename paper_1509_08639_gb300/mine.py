@@ -395,8 +395,8 @@ class Context:
         return res
 
     def autotune(self):
-        """Time both alignment strategies per size bin on this GPU and keep
-        the faster; returns the strategy table."""
+        """Time the pipeline widths per size bin on this GPU and keep the
+        fastest; returns the strategy table."""
         _check(self.L.mine_autotune(self.h), self.L)
         return self.align_strategy()
 
@@ -416,8 +416,9 @@ class Context:
         return self.align_strategy()
 
     def align_strategy(self, table=None):
-        """Get (table None) or set the per-bin strategy table: 1 whole CTA,
-        0 one warp where allowed, -1 built-in rule."""
+        """Get (table None) or set the per-bin strategy table: 0 one warp, 3 / 4 / 1
+        pipelines of 2 / 4 / 8 warps, 2 tiles over many CTAs, -1 built-in rule
+        (each where the pair's shape allows, else the nearest form)."""
         t = np.full(ALIGN_BINS, -1, np.int8) if table is None else np.ascontiguousarray(table, np.int8)
         _check(self.L.mine_align_strategy(self.h, _ptr(t), int(t.shape[0]), 1 if table is None else 0),
                self.L)

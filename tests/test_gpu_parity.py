@@ -242,8 +242,9 @@ def _edge_batch(rng, d, sizes, vocab, lo=5, hi=30, empty_frac=0.0):
 
 
 def test_alignment_strategies_agree(ctx):
-    """Every pair aligned one warp each where allowed, then by a whole CTA
-    each, then by the autotuned table: the results never change."""
+    """Every pair aligned one warp each where allowed, then by pipelines of
+    2, 4 and 8 warps where the shape allows, then by the autotuned tables:
+    the results never change."""
     w = synth.workload(2, n_pairs=300)
     dh = ctx.dict_create(w.dictionary)
     want = oracle_results(w)
@@ -253,24 +254,25 @@ def test_alignment_strategies_agree(ctx):
     want_e = oracle_results(w, edge)
     old = ctx.align_strategy()
     try:
-        for tab in ([0] * mine.ALIGN_BINS, [1] * mine.ALIGN_BINS):
+        for tab in ([0] * mine.ALIGN_BINS, [3] * mine.ALIGN_BINS, [4] * mine.ALIGN_BINS,
+                    [1] * mine.ALIGN_BINS):
             ctx.align_strategy(tab)
             assert ctx.align_strategy() == tab
             assert_same(ctx.run_batch(dh, w.batch, w.settings), want, f"strategy {tab[0]}")
             assert_same(ctx.run_batch(dh, edge, w.settings), want_e, f"edge sizes, strategy {tab[0]}")
         ctx.align_strategy(old)
         tuned = ctx.autotune()
-        assert all(v in (0, 1) for v in tuned[6:18])
+        assert all(v in (0, 1, 3, 4) for v in tuned[6:18])
         assert tuned[:6] == old[:6] and tuned[18:] == old[18:]
         assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned")
         ctx.align_strategy(old)
         tuned = ctx.autotune_batch(dh, w.batch)
-        assert all(v in (-1, 0, 1) for v in tuned)
+        assert all(v in (-1, 0, 1, 3, 4) for v in tuned)
         assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned on the batch")
         # tuned with a sweep of settings (three distinct gaps per pair)
         sweep = w.settings + [(-16384, 16384), (0, 65536), (-16384, 40000)]
         tuned = ctx.autotune_batch(dh, w.batch, sweep)
-        assert all(v in (-1, 0, 1, 2) for v in tuned)
+        assert all(v in (-1, 0, 1, 2, 3, 4) for v in tuned)
         assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned on the batch and a sweep")
         with pytest.raises(mine.MineError):
             ctx.autotune_batch(dh, w.batch, [(1, 0)])            # gap > 0
