@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--plain-pairs", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=5000.0)
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
+                    help="seconds per offered load (30 s as config 5 states)")
+    ap.add_argument("--configs", default="1,3,4",
+                    help="other workloads measured after the benchmark batch (sub-records)")
     ap.add_argument("--serve-sweep", default="1000,20000",
                     help="further offered rates (pairs/s), 1.5 s each; empty for none")
     ap.add_argument("--only-device", action="store_true",
@@ -406,6 +409,91 @@ def extras_run(ctx, w, dh, reps=3):
     return bidi, tuning, best_match
 
 
+def config_record(ctx, cfg, reps=5, cpu_budget=8.0):
+    """One of the other workloads, measured the same way as the benchmark
+    batch: the strategy table tuned on it, the device-resident step (graph
+    replay, CUDA events), the host-buffer call end to end (pinned arrays,
+    one call at a time), and the oracle on a bounded sample."""
+    import torch
+    from paper_1509_08639_gb300 import mine, synth
+    t_gen = time.perf_counter()
+    w = synth.workload(cfg)
+    t_gen = time.perf_counter() - t_gen
+    b = w.batch
+    P = b.n_pairs
+    S, T = b.sizes()
+    n_set = len(w.settings)
+    n_gap = len({g for g, _ in w.settings})
+    cells = int((S.astype(np.int64) * T).sum())
+    dh = ctx.dict_create(w.dictionary)
+    old_tab = ctx.align_strategy()
+    t_tune = time.perf_counter()
+    table = ctx.autotune_batch(dh, b, w.settings)
+    t_tune = time.perf_counter() - t_tune
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sent = torch.from_numpy(b.sent_off).to(dev)
+    tok = torch.from_numpy(b.tokens).to(dev)
+    cap = max(int(n_set * np.minimum(S, T).astype(np.int64).sum()), 1)
+    nw = torch.zeros(P * n_set, dtype=torch.int32, device=dev)
+    ns = torch.zeros(P * n_set, dtype=torch.int32, device=dev)
+    sel = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    n_sent, n_tok = int(b.sent_off.shape[0] - 1), int(b.tokens.shape[0])
+
+    def step():
+        ctx.run_batch_device(dh, P, b.doc_off, sent, tok, n_sent, n_tok, w.settings, nw, ns, sel, cap, stream)
+
+    for _ in range(3):
+        step()
+    stream.synchronize()
+    ctx.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    ctx.profile(True)
+    ctx.profile_read()
+    step()
+    stream.synchronize()
+    prof = {k: v[0] for k, v in ctx.profile_read().items() if v[1]}
+    ctx.profile(False)
+    # end to end: pinned host arrays through mine_run_batch
+    pin_sent = torch.from_numpy(b.sent_off).pin_memory()
+    pin_tok = torch.from_numpy(b.tokens).pin_memory()
+    hdo = np.ascontiguousarray(b.doc_off)
+    g = np.asarray([x[0] for x in w.settings], np.int32)
+    th = np.asarray([x[1] for x in w.settings], np.int32)
+    bc = mine.BatchC(P, n_sent, n_tok, mine._ptr(hdo), pin_sent.data_ptr(), pin_tok.data_ptr())
+    sc = mine.SettingsC(n_set, mine._ptr(g), mine._ptr(th))
+    outs = (torch.zeros(P * n_set, dtype=torch.int32).pin_memory().numpy(),
+            torch.zeros(P * n_set, dtype=torch.int32).pin_memory().numpy(),
+            torch.zeros(P * n_set + 1, dtype=torch.int64).pin_memory().numpy(),
+            torch.zeros(cap * 3, dtype=torch.int32).pin_memory().numpy(), cap)
+    ctx.run_batch_raw(dh, bc, sc, outs)
+    io0 = ctx.io_bytes()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.run_batch_raw(dh, bc, sc, outs)
+    e2e_s = (time.perf_counter() - t0) / reps
+    io1 = ctx.io_bytes()
+    assert np.array_equal(outs[0], nw.cpu().numpy()) and np.array_equal(outs[1], ns.cpu().numpy())
+    cpu = cpu_baseline(w, budget_s=cpu_budget)
+    ctx.align_strategy(old_tab)
+    ctx.dict_destroy(dh)
+    return {"workload": w.name, "pairs": P, "cells": cells, "settings": n_set, "distinct_gaps": n_gap,
+            "tokens": n_tok, "ms_per_step": ms, "value": P / (ms / 1e3), "unit": UNIT,
+            "gcups": cells * n_gap / (ms / 1e3) / 1e9, "kernel_ms": prof,
+            "e2e": {"value": P / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                    "h2d_bytes_per_step": (io1[0] - io0[0]) // reps,
+                    "d2h_bytes_per_step": (io1[1] - io0[1]) // reps,
+                    "how": "mine_run_batch, pinned host inputs and outputs, one call at a time"},
+            "cpu_baseline": cpu, "generation_s": t_gen, "autotune_s": t_tune,
+            "autotune": {str(k): v for k, v in enumerate(table) if v >= 0}}
+
+
 def serving_run(ctx, dh, rate, seconds):
     """Poisson arrivals of 40x45 pairs with a 1% tail of 2000x2000 pairs."""
     from paper_1509_08639_gb300 import synth
@@ -602,10 +690,14 @@ def main():
     if not args.no_serving and rank == 0:
         serving = serving_run(ctx, dh, args.serve_rate, args.serve_seconds)
         rates = [float(r) for r in args.serve_sweep.split(",") if r.strip()]
-        serving["sweep"] = [serving_run(ctx, dh, r, 1.5) for r in rates]
+        serving["sweep"] = [serving_run(ctx, dh, r, args.serve_seconds) for r in rates]
     bidi = tuning = best_match = None
     if not args.no_extras and rank == 0:
         bidi, tuning, best_match = extras_run(ctx, w, dh)
+    configs = {}
+    if rank == 0 and not args.only_device:
+        for c in [int(x) for x in args.configs.split(",") if x.strip()]:
+            configs[str(c)] = config_record(ctx, c, cpu_budget=4.0 if args.no_cpu else 8.0)
 
     # ---- roofline of each stage, per SURVEY-style algorithmic units:
     # scoring (translate + set build + score matrix) is bounded by HBM: 4 B per
@@ -682,6 +774,7 @@ def main():
         "bidirectional": bidi,
         "tuning": tuning,
         "best_match": best_match,
+        "configs": configs,
         "roofline": roof,
         "roofline_kernels": rl,
         "kernel_ms_per_step": {k: v[0] for k, v in timed.items()},

@@ -91,10 +91,11 @@ __device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ bp, const i
         }
         const int32_t sv = (u < lane ? bp : bc)[u];
         const int32_t cd = up_prev + sv;
-        bool pu;
-        const int32_t m = __vibmax_s32(up_in, h, &pu);       // max(up, left), pu = up >= left
-        const int32_t best = __viaddmax_s32(m, g, cd);       // max(max(up, left) + g, diag + s)
-        const uint32_t code = best == cd ? DIR_DIAG : (pu ? DIR_UP : DIR_LEFT);
+        // the diagonal and the left cell do not wait for the shuffle: one
+        // fused add-then-max after it
+        const int32_t dl = __viaddmax_s32(h, g, cd);          // max(left + g, diag + s)
+        const int32_t best = __viaddmax_s32(up_in, g, dl);    // max(up + g, that)
+        const uint32_t code = best == cd ? DIR_DIAG : (up_in >= h ? DIR_UP : DIR_LEFT);
         word = __funnelshift_r(word, code, 2);
         h = best;
         up_prev = up_in;
@@ -111,11 +112,13 @@ __device__ __forceinline__ void nw_chunk(const int32_t *__restrict__ bp, const i
 
 // Wait (bounded) until every tile copy this warp has in flight has landed,
 // so that the CTA may end after an error.
+// tiles: the number of tiles this warp has issued so far; the j-th tile it
+// issued went into slot j % 3 and completes that slot's phase j / 3.
 template <int K>
-__device__ void nw_drain(NwSmem<K> &sm, int w, const uint32_t (&uses)[kNwSlots], int32_t *err)
+__device__ void nw_drain(NwSmem<K> &sm, int w, uint32_t tiles, int32_t *err)
 {
-    for (int k = 0; k < kNwSlots; ++k)
-        if (uses[k] > 0) mbar_wait(&sm.bar[w][k], (uses[k] - 1) & 1u, err);
+    for (uint32_t j = tiles > kNwSlots ? tiles - kNwSlots : 0; j < tiles; ++j)
+        mbar_wait(&sm.bar[w][j % kNwSlots], (j / kNwSlots) & 1u, err);
 }
 
 // Fill H for one alignment by warp wg of a pipeline of G warps (w = its
@@ -123,7 +126,7 @@ __device__ void nw_drain(NwSmem<K> &sm, int w, const uint32_t (&uses)[kNwSlots],
 // false when a bounded wait ran out (error word set).
 template <int K>
 __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, int lane, const NwItem &it,
-                       const PairPlan &pp, uint32_t (&uses)[kNwSlots], uint64_t pol)
+                       const PairPlan &pp, uint32_t &tiles, uint64_t pol)
 {
     const int S = pp.S, T = pp.T;
     const int TT = (T + 31) >> 5;           // column tiles; stripes are Tp = 32 TT wide
@@ -168,19 +171,21 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
     const int ntile = nq * TT;              // virtual tiles of this warp
     const int nchunks = ntile + 1;
 
-    // virtual tile k of this warp into slot k % 3: one 4 KB bulk copy
+    // virtual tile k of this warp (the warp's tile t0 + k) into slot
+    // (t0 + k) % 3: one 4 KB bulk copy
+    const uint32_t t0 = tiles;
     auto issue = [&](int k) {
         const int q = k / TT;
         const int C = k - q * TT;
         const int s = wg + q * G;
-        const int slot = k % kNwSlots;
+        const int slot = (int)((t0 + k) % kNwSlots);
         __syncwarp();
         if (lane == 0) {
             mbar_expect_tx(&sm.bar[w][slot], kTileElems * 4);
             bulk_g2s_once(sm.tile[w][slot], Mp + ((int64_t)s * TT + C) * kTileElems, kTileElems * 4,
                           &sm.bar[w][slot], pol);
         }
-        uses[slot]++;
+        tiles = t0 + k + 1;
     };
 
     int32_t h = 0, up_prev = 0;
@@ -188,10 +193,8 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
     issue(0);
     for (int c = 0; c < nchunks; ++c) {
         if (c + 1 < ntile) issue(c + 1);
-        if (c < ntile) {
-            const int slot = c % kNwSlots;
-            if (!mbar_wait(&sm.bar[w][slot], (uses[slot] - 1) & 1u, b.err)) return false;
-        }
+        const uint32_t tc = t0 + c;                   // the warp's tile of this chunk
+        if (c < ntile && !mbar_wait(&sm.bar[w][tc % kNwSlots], (tc / kNwSlots) & 1u, b.err)) return false;
         const int q = c / TT;                      // stripe (of this warp) lane 0 is in
         const int r = c - q * TT;
         const bool reset = r == 0 && q < nq;
@@ -214,8 +217,8 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
         }
         // lane k: key 32c + k, stored at slot key - 1
         const int32_t rv = xs == X_RING ? ring_in[(32 * c + lane - 1) & (kNwRing - 1)] : 0;
-        const int32_t *bp = sm.tile[w][(c + kNwSlots - 1) % kNwSlots] + lane * kTile + 32 - lane;
-        const int32_t *bc = sm.tile[w][c % kNwSlots] + lane * kTile - lane;
+        const int32_t *bp = sm.tile[w][(tc + kNwSlots - 1) % kNwSlots] + lane * kTile + 32 - lane;
+        const int32_t *bc = sm.tile[w][tc % kNwSlots] + lane * kTile - lane;
         int32_t *rw = ring_out + ((32 * c - 32 + off_out) & (kNwRing - 1));
         const int32_t xa = (32 * c + 1) * g;
         // the new stripe of a reset chunk, for the row of each lane
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(K * 32, 2) k_nw(BatchDev b)
         for (int k = 0; k < kNwSlots; ++k) mbar_init(&sm.bar[w][k], 1);
         fence_barrier_init();
     }
-    uint32_t uses[kNwSlots] = {0u, 0u, 0u};
+    uint32_t tiles = 0;                       // tiles this warp has issued
     const uint64_t pol = l2_evict_first();   // score tiles are read once per gap
     __syncthreads();
     if (*(volatile int32_t *)b.err) return;
@@ -325,11 +328,11 @@ __global__ void __launch_bounds__(K * 32, 2) k_nw(BatchDev b)
             // chunks: Ge < T'/32 keeps that dependency acyclic
             const int Ge = min(min(G, (pp.S + 31) >> 5), max(1, ((pp.T + 31) >> 5) - 1));
             bool ok = true;
-            if (pp.S > 0 && pp.T > 0 && wg < Ge) ok = nw_run<K>(b, sm, w, wg, Ge, lane, it, pp, uses, pol);
+            if (pp.S > 0 && pp.T > 0 && wg < Ge) ok = nw_run<K>(b, sm, w, wg, Ge, lane, it, pp, tiles, pol);
             if (!ok) atomicCAS(b.err, 0, ERR_TIMEOUT);
             group_sync(G, base_w);
             if (*(volatile int32_t *)b.err) {
-                nw_drain<K>(sm, w, uses, b.err);
+                nw_drain<K>(sm, w, tiles, b.err);
                 return;
             }
         }

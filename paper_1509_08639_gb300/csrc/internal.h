@@ -158,7 +158,7 @@ struct BatchDev {
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
-    int32_t *hfin;               // [n_nw_items] H[S][T] of each alignment
+    int32_t *hfin;               // [n_nw_items] H[S][T] of a tiled alignment (unused by the others)
     const uint64_t *recip;       // [kMaxSentTokens + 1]: ceil(2^48 / m), 0 for m = 0
     int2 *gscratch;              // per-warp tables for sentences longer than the shared ones
     int32_t f32;                 // score kernel writes single-precision scores (float bits) into M
@@ -210,10 +210,24 @@ inline int align_kind(const int8_t *tab, int32_t S, int32_t T)
             : c >= (int64_t(1) << 15) ? AF_WARP2 : AF_WARP1;
     if (v == AF_TILED && !can_tile) v = AF_WARP8;
     if (v == AF_TILED) return v;
-    int g = form_warps(v);
     const int ns = (S + 31) >> 5, tt = (T + 31) >> 5;
-    while (g > 1 && (g > ns || g > tt - 1)) g >>= 1;
-    if (g == 1 && S > kTile && T >= kRing) g = 2;
+    // a pipeline whose warps take several stripes each hands the rows of its
+    // last warp to its first one through rings of kRing entries: the first
+    // warp must get a whole row (tt tiles) ahead of the last one, which the
+    // ring space between the G - 1 links allows up to about 12 (G - 1) tiles.
+    // The kernel runs min(g, ns, tt - 1) warps of a pipeline of g.
+    auto feasible = [&](int g) {
+        const int ge = g < ns ? (g < tt - 1 ? g : tt - 1) : (ns < tt - 1 ? ns : tt - 1);
+        if (ge <= 1) return !(S > kTile && T >= kRing);
+        return ns <= ge || tt <= 12 * (ge - 1);
+    };
+    int g = form_warps(v);
+    while (g > 1 && (g > ns || g > tt - 1)) g >>= 1;   // no idle warps where a narrower one does
+    if (!feasible(g)) {
+        if (feasible(8)) g = 8;
+        else if (can_tile) return AF_TILED;
+        else g = 1;   // (a pair that reaches here has T <= 64)
+    }
     return g == 8 ? AF_WARP8 : g == 4 ? AF_WARP4 : g == 2 ? AF_WARP2 : AF_WARP1;
 }
 
