@@ -266,12 +266,12 @@ def cpu_baseline(w, budget_s=20.0):
     one_pairs, one_t, k1 = 0, 0.0, 0
     one_order = rng.permutation(w.batch.n_pairs)
     while one_t < budget_s / 4 and k1 < len(one_order):
-        idx = one_order[k1:k1 + 8]
+        idx = one_order[k1:k1 + 1]   # one pair at a time: a sample ends within one pair of its budget
         t0 = time.perf_counter()
         O.mine_batch(od, w.batch.subset(idx), w.settings, 1)
         one_t += time.perf_counter() - t0
         one_pairs += len(idx)
-        k1 += 8
+        k1 += 1
     cpu_model = ""
     try:
         with open("/proc/cpuinfo") as f:

@@ -546,6 +546,7 @@ struct HostCallOut {
     int64_t R = 0;                     // result rows (pairs x settings)
     int32_t *h_err = nullptr;          // pinned copy of the device error word
     int64_t h2d = 0, d2h = 0;          // bytes copied each way
+    const int32_t *d_sel = nullptr;    // packed triples left on the device (copied by the caller)
 };
 
 // One host-buffer batch call in flight (mine_run_batch_async): its own
@@ -1238,6 +1239,7 @@ struct HostCallRes {
     cudaEvent_t in_ready;    // recorded on cst after them when cst != st
     cudaStream_t ost;        // result copies (st itself for a synchronous call)
     cudaEvent_t packed;      // recorded on st after the packing when ost != st
+    bool exact_sel = false;  // leave the triples on the device: the caller copies exactly their total
 };
 
 // Enqueue one host-buffer batch call of P > 0 pairs: the inputs go first,
@@ -1326,12 +1328,14 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
     CKB(cudaMemcpyAsync(nw_score, b.nw_score, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
     CKB(cudaMemcpyAsync(n_sel, b.n_sel, 4 * (size_t)R, cudaMemcpyDeviceToHost, ost));
     CKB(cudaMemcpyAsync(sel_off, d_off, 8 * ((size_t)R + 1), cudaMemcpyDeviceToHost, ost));
-    if (cp > 0 && sel) CKB(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, ost));
+    if (cp > 0 && sel && !res.exact_sel)
+        CKB(cudaMemcpyAsync(sel, d_pk, 12 * (size_t)cp, cudaMemcpyDeviceToHost, ost));
     CKB(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, ost));
     out.R = R;
     out.h_err = h_err;
+    out.d_sel = res.exact_sel ? d_pk : nullptr;
     out.h2d = L.plan_bytes + 4 * (batch->n_sent + 1) + 4 * batch->n_tok;
-    out.d2h = 8 * (int64_t)R + 8 * ((int64_t)R + 1) + 4 + (sel ? 12 * cp : 0);
+    out.d2h = 8 * (int64_t)R + 8 * ((int64_t)R + 1) + 4 + (sel && !res.exact_sel ? 12 * cp : 0);
 #undef CKB
     return MINE_OK;
 }
@@ -1362,15 +1366,27 @@ int mine_run_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch
     ++ctx->arena_gen;
     sel_off[0] = 0;
     if (P == 0) return MINE_OK;
-    const HostCallRes res{&ctx->inbuf, &ctx->arena, &ctx->pin, &ctx->plan, ctx->gscratch, ctx->stream,
-                          ctx->stream, nullptr, ctx->stream, nullptr};
+    // synchronous: once the offsets are back, copy exactly the selected
+    // triples (a sweep's capacity, settings x min(S,T) per pair, is mostly
+    // unused)
+    HostCallRes res{&ctx->inbuf, &ctx->arena, &ctx->pin, &ctx->plan, ctx->gscratch, ctx->stream,
+                    ctx->stream, nullptr, ctx->stream, nullptr};
+    res.exact_sel = true;
     HostCallOut o;
     if ((rc = enqueue_host_batch(ctx, dict, batch, settings, nw_score, n_sel, sel_off, sel, sel_cap, res, o)))
         return rc;
-    ctx->h2d_bytes += o.h2d;
-    ctx->d2h_bytes += o.d2h;
     CK(cudaStreamSynchronize(ctx->stream));
-    return finish_host_batch(o, sel_off, sel, sel_cap);
+    if ((rc = finish_host_batch(o, sel_off, sel, sel_cap))) return rc;
+    const int64_t tot = sel_off[o.R];
+    if (tot > 0) {
+        const cudaError_t e = inject_cuda_error(ctx)
+                                  ? cudaErrorInvalidValue
+                                  : cudaMemcpy(sel, o.d_sel, 12 * (size_t)tot, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(MINE_ECUDA, std::string("selected pairs copy: ") + cudaGetErrorString(e));
+    }
+    ctx->h2d_bytes += o.h2d;
+    ctx->d2h_bytes += o.d2h + 12 * tot;
+    return MINE_OK;
 }
 
 int mine_run_batch_async(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
