@@ -41,7 +41,10 @@ constexpr int kScoreCtasPerSmScore = 6;     // its resident CTAs per SM
 constexpr int kBlkTokCap = 1024;            // tokens of one staged 32-column block at most
 constexpr int kPairPrepCtasPerSm = 2;       // CTAs (16 warps each) per SM of the pair preparation
 // per-warp global tables: enough for the largest grid of the three kernels using them
-constexpr int kGScratchWarpsPerSm = 40;
+constexpr int kGScratchWarpsPerSm = 72;
+// Target articles of more than this many sentences are prepared by the
+// wide-article launch (bigger tables, fewer CTAs per SM)
+constexpr int kWideArticleSent = 160;
 static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kGScratchWarpsPerSm &&
                   kScoreWarps * kScoreCtasPerSm <= kGScratchWarpsPerSm &&
                   16 * kPairPrepCtasPerSm <= kGScratchWarpsPerSm,
@@ -136,6 +139,8 @@ struct BatchDev {
     int32_t n_prep_items;
     const ScoreItem *score_items;    // 64 rows each
     int32_t n_score_items;
+    ScoreItem *wide_items;           // the items of the score launches for larger articles
+                                     // (built on the device; their count in counters[18])
     const NwItem *nw_items;
     int32_t n_nw_items;
     int32_t n_nw_grp[kNwGroups]; // items aligned by pipelines of 8, 4, 2 warps and by one warp, in that order from 0
@@ -153,7 +158,9 @@ struct BatchDev {
     int32_t *row_order;          // [n_sent] per pair, source rows by element count (longest first)
     uint16_t *tdoc;              // [n_tok + 32] document id of each target token
     int32_t *pdoc;               // [n_pairs] distinct target tokens D, or -1 (token-keyed path)
-    const int32_t *dorder;       // [n_pairs] pairs by article size, longest first
+    const int32_t *dorder;       // [n_pairs] pairs by article size, longest first: the n_dwide
+                                 // pairs of more than kWideArticleSent target sentences, then the rest
+    int32_t n_dwide;
     int32_t kmax;                // largest translation count of the dictionary
     int32_t *M;                  // tiled scores
     uint32_t *codes;             // directions

@@ -527,12 +527,15 @@ k_prep(BatchDev b, DevDict d)
 
 // ---------------------------------------------------------------- k_pairprep
 
-// Two launches: articles of at most kSmallArticleTok target tokens by CTAs of
-// 8 warps with a table of 2 kSmallArticleTok slots (five CTAs per SM, the
+// Two launches: target articles of at most kWideArticleSent sentences by
+// CTAs of 8 warps with a table of kSmallSlots slots (five CTAs per SM, the
 // most their shared memory allows, with registers capped to fit: more pairs
 // in flight and fewer warps waiting at a pair's barriers), the others by
-// CTAs of 16 warps with a table of 2 kDirect slots.
-constexpr int kSmallArticleTok = 4096;
+// CTAs of 16 warps with a table of 2 kDirect slots.  A small article stops
+// once it has more than kSmallIds distinct tokens (before its table fills)
+// and goes to the extra-wide launch.
+constexpr int kSmallSlots = 8192;
+constexpr int kSmallIds = 6144;
 constexpr int kRowSetBig = 2 * kMaxSentTokens;     // rows of > 64 tokens: per-warp table in global memory
 static_assert(kRowSetBig * 8 <= kScoreScratchPerWarp, "per-warp global table too small");
 
@@ -783,9 +786,9 @@ __device__ void prep_row_long(const BatchDev &b, const DevDict &d, const SM &sm,
     __syncwarp();
 }
 
-// Modes of the preparation launches: articles of more than kSmallArticleTok
-// target tokens (wide), the others (small), and the articles the wide launch
-// found to hold more than kDirect distinct tokens (extra wide: up to kDirectX
+// Modes of the preparation launches: target articles of more than
+// kWideArticleSent sentences (wide), the others (small), and the articles
+// those found to hold too many distinct tokens (extra wide: up to kDirectX
 // ids, a table of 2 kDirectX slots, one CTA per SM).
 constexpr int kModeWide = 0, kModeSmall = 1, kModeXWide = 2;
 
@@ -799,8 +802,8 @@ constexpr int kModeWide = 0, kModeSmall = 1, kModeXWide = 2;
 //     written as (id | FIRST | END) -- FIRST on the first copy of an id in the
 //     row, END on the last kept translation of each source token -- with
 //     (n_i, #kept, #kept FIRST) in sinfo.
-// A larger article gets pdoc[p] = -1 and is left to k_prep and the
-// token-keyed score path.
+// A larger article gets pdoc[p] = -1 and is left to the extra-wide launch,
+// then to k_prep and the token-keyed score path.
 template <int WARPS, int SLOTS, int CTAS, int MODE>
 __global__ void __launch_bounds__(WARPS * 32, CTAS)
 k_pairprep(BatchDev b, DevDict d)
@@ -808,7 +811,10 @@ k_pairprep(BatchDev b, DevDict d)
     constexpr bool SMALL = MODE == kModeSmall, XW = MODE == kModeXWide;
     constexpr int IDS = XW ? kDirectX : kDirect;
     constexpr int kPPWarps = WARPS, kPPThreads = WARPS * 32;
-    // nothing to do unless the wide launch left an article with too many ids
+    // the most distinct target tokens an article of this launch may have
+    constexpr int kCap = SMALL ? kSmallIds : IDS;
+    static_assert(kCap <= IDS && kCap + 4 * kPPThreads < SLOTS, "the target table never fills");
+    // nothing to do unless another launch left an article with too many ids
     if (XW && *(volatile int32_t *)&b.counters[9] == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairPrepSmem<WARPS, SLOTS, IDS> &sm = *reinterpret_cast<PairPrepSmem<WARPS, SLOTS, IDS> *>(smem_raw);
@@ -820,18 +826,19 @@ k_pairprep(BatchDev b, DevDict d)
     const int kmax = b.kmax;
     for (;;) {
         if (__syncthreads_or(*(volatile int32_t *)b.err != 0)) break;
+        // items: the wide launch takes dorder[0, n_dwide), the small one the
+        // rest, the extra-wide one every pair the others left
         if (tid == 0) {
-            sm.item = atomicAdd(&b.counters[SMALL ? 5 : (XW ? 11 : 10)], 1);
+            sm.item = atomicAdd(&b.counters[SMALL ? 5 : (XW ? 11 : 10)], 1) + (SMALL ? b.n_dwide : 0);
             sm.nd = 0;
         }
         __syncthreads();
         const int item = sm.item;
-        if (item >= b.n_pairs) break;
+        if (item >= (MODE == kModeWide ? b.n_dwide : b.n_pairs)) break;
         const int p = b.dorder[item];
         if (XW && b.pdoc[p] != -1) continue;    // prepared by one of the other launches
         const PairPlan pp = b.pairs[p];
         const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
-        if (!XW && (tb - ta <= kSmallArticleTok) != SMALL) continue;   // the other launch's pair
         // at most a quarter of the slots used where the table allows (the
         // probes of absent translations, the common case, end sooner)
         const int lg = min(max(ceil_log2(4 * max(tb - ta, 1)), 10), SMALL ? 13 : (XW ? 15 : 14));
@@ -840,12 +847,11 @@ k_pairprep(BatchDev b, DevDict d)
         for (int k = tid; k < NS / 4; k += kPPThreads) kz[k] = make_int4(-1, -1, -1, -1);
         __syncthreads();
         // 1. distinct target tokens; four loads in flight per thread; the
-        //    warp adds its new tokens to the count at once; a wide article
-        //    stops once its tokens cannot all get ids (before its table fills:
-        //    at most 4 kPPThreads more insertions than IDS < SLOTS)
-        static_assert(SMALL || IDS + 4 * kPPThreads < SLOTS, "table of a wide article");
+        //    warp adds its new tokens to the count at once; an article stops
+        //    once its tokens cannot all get ids (before its table fills: at
+        //    most 4 kPPThreads more insertions than kCap)
         for (int32_t kw = ta + (tid & ~31); kw < tb; kw += 4 * kPPThreads) {   // warp-uniform
-            if (!SMALL && __shfl_sync(kFull, *(volatile int32_t *)&sm.nd, 0) > IDS) break;
+            if (__shfl_sync(kFull, *(volatile int32_t *)&sm.nd, 0) > kCap) break;
             const int32_t k = kw + lane;
             int32_t tk[4];
 #pragma unroll
@@ -876,16 +882,17 @@ k_pairprep(BatchDev b, DevDict d)
         const int D = sm.nd;
         if (tid == 0) {
             if (!XW) {
-                b.pdoc[p] = D <= IDS ? D : -1;
-                if (D > IDS) atomicExch(&b.counters[9], 1);   // the extra-wide launch has work
-            } else if (D <= IDS) {
+                b.pdoc[p] = D <= kCap ? D : -1;
+                if (D > kCap) atomicExch(&b.counters[9], 1);   // the extra-wide launch has work
+            } else if (D <= kCap) {
                 b.pdoc[p] = D;
-                atomicExch(&b.counters[13], 1);   // so has the extra-wide score launch
+                // so has the extra-wide score launch, unless another one takes it
+                if (D > kDirect) atomicExch(&b.counters[13], 1);
             } else {
                 atomicExch(&b.counters[14], 1);   // k_prep has work (pdoc stays -1)
             }
         }
-        if (D > IDS) continue;
+        if (D > kCap) continue;
         const int NW = NS >> 5;
         for (int w = wib; w < NW; w += kPPWarps)
             sm.occ[w] = __ballot_sync(kFull, sm.key[32 * w + lane] != -1);
@@ -961,9 +968,15 @@ k_pairprep(BatchDev b, DevDict d)
 
 // ---------------------------------------------------------------- k_order
 
+// Score launches: articles of at most kDirectSmall distinct target tokens
+// (from the plan's item list), and the others (from a list k_order builds).
+constexpr int kDirectSmall = 4096;
+
 // Per pair, the source rows sorted by element count, longest first (counting
 // sort on min(count, 1023); ties in any order), written to row_order[s0 ..
-// s0+S).  One warp per pair.
+// s0+S); and the score items of the pairs with more than kDirectSmall
+// distinct target tokens (or the token-keyed path) appended to wide_items.
+// One warp per pair.
 __global__ void __launch_bounds__(256)
 k_order(BatchDev b)
 {
@@ -975,6 +988,19 @@ k_order(BatchDev b)
     for (int p = (blockIdx.x * 8 + wib); p < b.n_pairs; p += gridDim.x * 8) {
         const PairPlan pp = b.pairs[p];
         const int S = pp.S;
+        const int D = b.pdoc[p];
+        if (D < 0 || D > kDirectSmall) {
+            // the pair's score items, for the launches of larger articles
+            // (as the plan cuts them: 64 rows by kScoreColChunk columns)
+            const int nc = (max(pp.T, 1) + kScoreColChunk - 1) / kScoreColChunk, n = ((S + 63) / 64) * nc;
+            int base = 0;
+            if (lane == 0 && n > 0) base = atomicAdd(&b.counters[18], n);
+            base = __shfl_sync(kFull, base, 0);
+            for (int k = lane; k < n; k += 32) {
+                const int c0 = kScoreColChunk * (k % nc);
+                b.wide_items[base + k] = ScoreItem{p, 64 * (k / nc), c0, min(pp.T, c0 + kScoreColChunk)};
+            }
+        }
         int32_t *ord = b.row_order + pp.s0;
         if (S <= 32) {
             if (lane < S) ord[lane] = lane;
@@ -1056,7 +1082,6 @@ struct alignas(16) ScoreSmem {
 
 // The two score launches: articles with at most kDirectSmall distinct target
 // tokens (small mask array, more CTAs per SM), and all others.
-constexpr int kDirectSmall = 4096;
 
 __device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b,
                                     uint32_t c)
@@ -1617,8 +1642,10 @@ k_score(BatchDev b)
         if (tid == 0) S.item = atomicAdd(&b.counters[KEYED ? 6 : (XW ? 12 : 1)], 1);
         __syncthreads();
         const int item = S.item;
-        if (item >= b.n_score_items) break;
-        const ScoreItem si = b.score_items[item];
+        // the larger articles' launches take the list k_order built
+        constexpr bool kWideList = KEYED || XW;
+        if (item >= (kWideList ? b.counters[18] : b.n_score_items)) break;
+        const ScoreItem si = kWideList ? b.wide_items[item] : b.score_items[item];
         const int D = b.pdoc[si.pair];
         if (KEYED ? (D >= 0 && (D <= kDirectSmall || D > kDirect))
                   : (XW ? (D <= kDirect || D > kDirectX) : (D < 0 || D > kDirectSmall)))
@@ -2099,18 +2126,24 @@ int launch_pairprep_one(const BatchDev &b, const DevDict &d, int num_sms, cudaSt
     return 1;
 }
 
-static_assert(16 * 2 <= kGScratchWarpsPerSm && 8 * 5 <= kGScratchWarpsPerSm, "per-warp global tables");
+// per-warp global tables (rows of more than 64 tokens): the small-article
+// launch takes the first 40 per SM, the wide-article launch, which may run
+// beside it, the next 32; the extra-wide launch runs after both
+constexpr int kSmallPrepScratchWarps = 8 * 5;
+static_assert(kSmallPrepScratchWarps + 16 * 2 <= kGScratchWarpsPerSm, "per-warp global tables");
 
 int launch_pairprep_wide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    return launch_pairprep_one<16, 2 * kDirect, 2, kModeWide>(b, d, num_sms, st);
+    BatchDev bw = b;
+    bw.gscratch += (int64_t)num_sms * kSmallPrepScratchWarps * kGTabSlots;
+    return launch_pairprep_one<16, 2 * kDirect, 2, kModeWide>(bw, d, num_sms, st);
 }
 
 int launch_pairprep(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)
 {
     if (b.n_pairs <= 0) return 0;
-    return launch_pairprep_one<8, 2 * kSmallArticleTok, 5, kModeSmall>(b, d, num_sms, st);
+    return launch_pairprep_one<8, kSmallSlots, 5, kModeSmall>(b, d, num_sms, st);
 }
 
 int launch_pairprep_xwide(const BatchDev &b, const DevDict &d, int num_sms, cudaStream_t st)

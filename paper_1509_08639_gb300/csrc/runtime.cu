@@ -102,7 +102,8 @@ struct Plan {
     std::vector<PairPlan> pairs;
     std::vector<ScoreItem> pitems;  // 32-row items of the preparation kernel
     std::vector<ScoreItem> sitems;  // 64-row items of the score kernel
-    std::vector<int32_t> dorder;    // pairs by sentence count, longest first
+    std::vector<int32_t> dorder;    // pairs by sentence count, longest first; wide targets first
+    int32_t n_dwide = 0;            // pairs of more than kWideArticleSent target sentences
     std::vector<NwItem> nitems;
     std::vector<TileItem> tiles;    // of the tiled alignments (the last n_tiled items)
     int32_t n_tiled = 0;
@@ -122,6 +123,7 @@ struct Plan {
         pitems.clear();
         sitems.clear();
         dorder.clear();
+        n_dwide = 0;
         nitems.clear();
         tiles.clear();
         n_tiled = 0;
@@ -255,6 +257,10 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         return ord;
     };
     pl.dorder = order_by(bucketD);
+    // the pairs of the wide-article preparation first, each part longest first
+    pl.n_dwide = (int32_t)(std::stable_partition(pl.dorder.begin(), pl.dorder.end(),
+                                                 [&](int p) { return pl.pairs[p].T > kWideArticleSent; }) -
+                           pl.dorder.begin());
     for (int p : order_by(bucketS)) {
         const PairPlan &pp = pl.pairs[p];
         for (int r0 = 0; r0 < pp.S; r0 += 32) pl.pitems.push_back(ScoreItem{p, r0, 0, 0});
@@ -319,7 +325,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
 struct Layout {
     int64_t plan = 0, plan_bytes = 0;
     int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
-    int64_t elems = 0, sinfo = 0, order = 0, tdoc = 0, pdoc = 0;
+    int64_t elems = 0, sinfo = 0, order = 0, tdoc = 0, pdoc = 0, witems = 0;
     int64_t M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
@@ -364,6 +370,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
         L.order = take(4 * pl.n_sent + 16);
         L.tdoc = take(2 * pl.n_tok + 64);   // bulk copies round up past the end
         L.pdoc = take(4 * (int64_t)pl.P + 16);
+        L.witems = take(sizeof(ScoreItem) * (pl.sitems.size() + 1));
     } else {
         // a caller-supplied row-major matrix is copied here, then tiled
         int64_t rows = 0;
@@ -407,6 +414,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.tokens = tokens;
     b.n_tok = pl.n_tok;
     b.n_pairs = pl.P;
+    b.n_dwide = pl.n_dwide;
     b.pairs = reinterpret_cast<const PairPlan *>(plan + L.o_pairs);
     b.prep_items = reinterpret_cast<const ScoreItem *>(plan + L.o_pitems);
     b.n_prep_items = (int32_t)pl.pitems.size();
@@ -428,6 +436,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.row_order = reinterpret_cast<int32_t *>(base + L.order);
     b.tdoc = reinterpret_cast<uint16_t *>(base + L.tdoc);
     b.pdoc = reinterpret_cast<int32_t *>(base + L.pdoc);
+    b.wide_items = reinterpret_cast<ScoreItem *>(base + L.witems);
     b.dorder = reinterpret_cast<const int32_t *>(plan + L.o_dorder);
     b.M = reinterpret_cast<int32_t *>(base + L.M);
     b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
@@ -527,8 +536,34 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit;
 };
 
+// A second stream beside a launch stream: the wide-article launches of a
+// batch run on it next to the others (fork and join by events), so that their
+// few long pairs do not hold up the rest of the GPU.
+struct Fork {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+int fork_create(Fork &f)
+{
+    if (cudaStreamCreateWithFlags(&f.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(MINE_ECUDA, "stream or event creation failed");
+    return 0;
+}
+
+void fork_destroy(Fork &f)
+{
+    if (f.st) cudaStreamDestroy(f.st);
+    if (f.fork) cudaEventDestroy(f.fork);
+    if (f.join) cudaEventDestroy(f.join);
+    f = Fork{};
+}
+
 struct Slot {
     cudaStream_t st = nullptr;
+    Fork fork;                         // beside st
     cudaEvent_t ev = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;   // timed: before the first copy, after the last
     bool busy = false;
@@ -575,6 +610,7 @@ struct mine_ctx {
     int device = 0;
     int num_sms = 0;
     cudaStream_t stream = nullptr;
+    Fork fork;                         // beside stream
     std::mutex api_mu;                 // synchronous calls
     DevBuf arena;                      // scratch of the synchronous calls
     DevBuf inbuf;                      // inputs of the host-buffer batch call
@@ -703,8 +739,13 @@ int timed_launch(mine_ctx *ctx, int kid, cudaStream_t st, F fn)
 }
 
 // Enqueue the kernels of one batch whose plan is already on the device.
+// With a fork stream, the wide-article preparation and score launches run on
+// it beside the small-article ones (launched first: their long pairs start
+// early and finish while the others run); each pair of launches is joined
+// before the next step.
 int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int64_t n_sent,
-                    int64_t n_tok, bool scoring, cudaStream_t st, bool aligning = true)
+                    int64_t n_tok, bool scoring, cudaStream_t st, bool aligning = true,
+                    const Fork *fk = nullptr)
 {
     int n = 0;
     CK(cudaMemsetAsync(b.counters, 0, 4 * kCounters, st));
@@ -712,14 +753,32 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
         BatchDev bd = b;
         bd.kmax = dict->d.kmax;
-        n += timed_launch(ctx, KID_DOC_WIDE, st, [&] { return launch_pairprep_wide(bd, dict->d, ctx->num_sms, st); });
+        const bool par = fk && fk->st;
+        const cudaStream_t sw = par ? fk->st : st;
+        if (par) {
+            CK(cudaEventRecord(fk->fork, st));
+            CK(cudaStreamWaitEvent(sw, fk->fork, 0));
+        }
+        n += timed_launch(ctx, KID_DOC_WIDE, sw, [&] { return launch_pairprep_wide(bd, dict->d, ctx->num_sms, sw); });
         n += timed_launch(ctx, KID_DOC, st, [&] { return launch_pairprep(bd, dict->d, ctx->num_sms, st); });
+        if (par) {
+            CK(cudaEventRecord(fk->join, sw));
+            CK(cudaStreamWaitEvent(st, fk->join, 0));
+        }
         n += timed_launch(ctx, KID_DOC_XWIDE, st, [&] { return launch_pairprep_xwide(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_PREP, st, [&] { return launch_prep(bd, dict->d, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_ORDER, st, [&] { return launch_order(bd, ctx->num_sms, st); });
-        n += timed_launch(ctx, KID_SCORE_WIDE, st, [&] { return launch_score_wide(bd, ctx->num_sms, st); });
+        if (par) {
+            CK(cudaEventRecord(fk->fork, st));
+            CK(cudaStreamWaitEvent(sw, fk->fork, 0));
+        }
+        n += timed_launch(ctx, KID_SCORE_WIDE, sw, [&] { return launch_score_wide(bd, ctx->num_sms, sw); });
         n += timed_launch(ctx, KID_SCORE, st, [&] { return launch_score(bd, ctx->num_sms, st); });
         n += timed_launch(ctx, KID_SCORE_XWIDE, st, [&] { return launch_score_xwide(bd, ctx->num_sms, st); });
+        if (par) {
+            CK(cudaEventRecord(fk->join, sw));
+            CK(cudaStreamWaitEvent(st, fk->join, 0));
+        }
     }
     if (aligning) {
         if (b.n_tiles > 0) CK(cudaMemsetAsync(b.tbnd, 0, 4 * b.n_tbnd, st));
@@ -899,7 +958,7 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
     // the batch's score matrices, once
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false, &ctx->fork))) return rc;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1024,6 +1083,7 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     CK(cudaSetDevice(ctx->device));
     CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
     CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    if (int frc = fork_create(ctx->fork)) return frc;
     CK(cudaMalloc(&ctx->pool_mem, (size_t)c.device_budget_bytes));
     {
         // exact fixed-point reciprocals: floor(x * 65536 / m) == (x * K[m]) >> 32
@@ -1044,6 +1104,7 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     for (int k = 0; k < c.max_inflight; ++k) {
         std::unique_ptr<Slot> s(new Slot());
         CK(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+        if (int frc = fork_create(s->fork)) return frc;
         CK(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
         CK(cudaEventCreate(&s->t0));
         CK(cudaEventCreate(&s->t1));
@@ -1090,6 +1151,7 @@ int mine_close(mine_ctx *ctx)
     }
     for (auto &s : ctx->slots) {
         cudaStreamDestroy(s->st);
+        fork_destroy(s->fork);
         cudaEventDestroy(s->ev);
         if (s->t0) cudaEventDestroy(s->t0);
         if (s->t1) cudaEventDestroy(s->t1);
@@ -1107,6 +1169,7 @@ int mine_close(mine_ctx *ctx)
     cudaFree(ctx->pool_mem);
     cudaFree(ctx->recip);
     cudaStreamDestroy(ctx->stream);
+    fork_destroy(ctx->fork);
     delete ctx;
     return MINE_OK;
 }
@@ -1312,7 +1375,8 @@ static int enqueue_host_batch(mine_ctx *ctx, const mine_dict *dict, const mine_b
         b.test_withhold = 1;
         b.wait_spins = kTestWaitSpins;
     }
-    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return bail(rc);
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, true, &ctx->fork)))
+        return bail(rc);
     int64_t *d_off = reinterpret_cast<int64_t *>(base + o_off);
     int32_t *d_pk = reinterpret_cast<int32_t *>(base + o_pk);
     int32_t *d_bs = reinterpret_cast<int32_t *>(base + o_bs);
@@ -1511,7 +1575,7 @@ static int score_matrices(mine_ctx *ctx, const mine_dict *dict, const mine_batch
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
     b.f32 = f32;
-    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false, &ctx->fork))) return rc;
     int32_t *h_err = reinterpret_cast<int32_t *>(hp + align_up(L.plan_bytes, 64));
     const int32_t *h_m = h_err + 16;
     CK(cudaMemcpyAsync(h_err, b.err, 4, cudaMemcpyDeviceToHost, st));
@@ -1605,8 +1669,8 @@ int mine_run_batch_bidi(mine_ctx *ctx, const mine_dict *fwd, const mine_dict *bw
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
     BatchDev bf = make_batchdev(pf, Lf, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
     BatchDev bb = make_batchdev(pb, Lb, base + ob, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-    if ((rc = enqueue_kernels(ctx, bf, fwd, batch->n_sent, batch->n_tok, true, st))) return rc;
-    if ((rc = enqueue_kernels(ctx, bb, bwd, batch->n_sent, batch->n_tok, true, st))) return rc;
+    if ((rc = enqueue_kernels(ctx, bf, fwd, batch->n_sent, batch->n_tok, true, st, true, &ctx->fork))) return rc;
+    if ((rc = enqueue_kernels(ctx, bb, bwd, batch->n_sent, batch->n_tok, true, st, true, &ctx->fork))) return rc;
     UnionDev u;
     u.fwd = bf.pairs;
     u.bwd = bb.pairs;
@@ -1715,7 +1779,7 @@ int mine_tune_f1(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batch,
     CK(cudaMemcpyAsync(d_truth, truth, 4 * batch->n_sent, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(d_acc, 0, acc_bytes, st));
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st))) return rc;
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, true, &ctx->fork))) return rc;
     F1Dev f;
     f.pairs = b.pairs;
     f.n_pairs = P;
@@ -1787,7 +1851,7 @@ int mine_best_match(mine_ctx *ctx, const mine_dict *dict, const mine_batch *batc
         CK(cudaMemcpyAsync(d_tok, batch->tokens, 4 * batch->n_tok, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(base + o_bits, 0, 8 * words, st));
     BatchDev b = make_batchdev(pl, L, base, d_sent, d_tok, nullptr, ctx->recip, ctx->gscratch);
-    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false))) return rc;
+    if ((rc = enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, false, &ctx->fork))) return rc;
     BestDev d;
     d.pairs = b.pairs;
     d.n_pairs = P;
@@ -1887,7 +1951,7 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
     ctx->err_off = L.counters + 4 * 8;
     if (ctx->prof_on) {   // per-kernel events: plain launches
         CK(cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st));
-        return enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st);
+        return enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, true, &ctx->fork);
     }
     // capture the plan upload and the kernels as one graph, then launch it
     if (G.exec) {
@@ -1897,7 +1961,7 @@ int mine_run_batch_device(mine_ctx *ctx, const mine_dict *dict, const mine_batch
     const int64_t before = ctx->launches.load();
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     cudaError_t ce = cudaMemcpyAsync(base + L.plan, hp, L.plan_bytes, cudaMemcpyHostToDevice, st);
-    rc = ce == cudaSuccess ? enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st)
+    rc = ce == cudaSuccess ? enqueue_kernels(ctx, b, dict, batch->n_sent, batch->n_tok, true, st, true, &ctx->fork)
                            : fail(MINE_ECUDA, cudaGetErrorString(ce));
     cudaGraph_t graph = nullptr;
     ce = cudaStreamEndCapture(st, &graph);
@@ -2303,7 +2367,7 @@ int launch_slot(mine_ctx *ctx, Slot &s)
     CK(cudaMemcpyAsync(d_sent, h_sent, 4 * (n_sent + 1), cudaMemcpyHostToDevice, s.st));
     if (n_tok > 0) CK(cudaMemcpyAsync(d_tok, h_tok, 4 * n_tok, cudaMemcpyHostToDevice, s.st));
     BatchDev b = make_batchdev(s.plan, L, base, d_sent, d_tok, nullptr, ctx->recip, s.gscratch);
-    if ((rc = enqueue_kernels(ctx, b, dict, n_sent, n_tok, true, s.st))) return rc;
+    if ((rc = enqueue_kernels(ctx, b, dict, n_sent, n_tok, true, s.st, true, &s.fork))) return rc;
     char *ho = static_cast<char *>(s.pin_out.p);
     CK(cudaMemcpyAsync(ho + s.out_nw, b.nw_score, 4 * s.plan.R, cudaMemcpyDeviceToHost, s.st));
     CK(cudaMemcpyAsync(ho + s.out_nsel, b.n_sel, 4 * s.plan.R, cudaMemcpyDeviceToHost, s.st));
