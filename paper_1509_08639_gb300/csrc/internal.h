@@ -78,11 +78,14 @@ struct DevDict {
 };
 constexpr int kInlineTrans = 6;
 
-struct PairPlan {       // 48 bytes
+struct PairPlan {       // 56 bytes
     int32_t s0, S;      // source sentences [s0, s0+S) (global sentence index)
     int32_t t0, T;      // target sentences [t0, t0+T)
-    int32_t set0, nset; // settings rows [set0, set0+nset)
-    int32_t gap0, ngap; // distinct gaps [gap0, gap0+ngap) of this pair
+    int32_t set0, nset; // settings rows [set0, set0+nset) (the outputs)
+    int32_t gap0, ngap; // distinct gaps [gap0, gap0+ngap) of this pair (shared by the pairs
+                        // with the same settings list)
+    int32_t slist0;     // its settings: set_gap / set_thr [slist0, slist0+nset) (shared too)
+    int32_t pad_;
     int64_t m_off;      // int32 offset of M: ceil(S/32) x ceil(T/32) tiles of 32 x 32
     int64_t sel_base;   // mine_pair offset of the selection block (nset * min(S,T))
 };
@@ -149,8 +152,8 @@ struct BatchDev {
     int32_t n_tiles;
     int32_t *tbnd;               // tile boundaries and flags (zeroed per batch)
     int64_t n_tbnd;              // their int32 count
-    const int32_t *set_gap;      // [R] global gap index of each setting row
-    const int32_t *set_thr;      // [R]
+    const int32_t *set_gap;      // settings lists (PairPlan::slist0): each setting's gap as an
+    const int32_t *set_thr;      // index among its pair's distinct gaps, and its threshold
     const int32_t *gap_val;      // [G]
     // scratch
     uint32_t *elems;             // source elements (see elem_base)

@@ -1816,8 +1816,8 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
     const int32_t H = sum + b.gap_val[gap_idx] * (pp.S + pp.T - 2 * nm);
     for (int k = 0; k < pp.nset; ++k) {
         const int row = pp.set0 + k;
-        if (b.set_gap[row] != gap_idx) continue;
-        const int32_t thr = b.set_thr[row];
+        if (b.set_gap[pp.slist0 + k] != gap_idx - pp.gap0) continue;
+        const int32_t thr = b.set_thr[pp.slist0 + k];
         int32_t *out = b.sel + 3 * (pp.sel_base + (int64_t)k * cap);
         int cnt = 0;
         for (int c = 0; c < nm; c += 32) {

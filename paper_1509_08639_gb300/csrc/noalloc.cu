@@ -58,6 +58,8 @@ __global__ void k_noalloc_setup(int32_t *scratch, int32_t S, int32_t T, int32_t 
     pp->nset = 1;
     pp->gap0 = 0;
     pp->ngap = 1;
+    pp->slist0 = 0;
+    pp->pad_ = 0;
     pp->m_off = kOffM;
     pp->sel_base = 0;
     it->pair = 0;

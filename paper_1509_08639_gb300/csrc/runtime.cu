@@ -140,19 +140,23 @@ struct Plan {
 
 // A pair's settings list, checked once for every pair that has the same
 // list: each setting's gap as an index into the list's distinct gaps (in
-// order of first appearance) and the largest |gap|.
+// order of first appearance) and the largest |gap|; where the list sits in
+// the plan (every pair with the same list shares it).
 struct SettingsSeen {
     std::vector<Setting> list;
     std::vector<int32_t> local, thr, gaps;
     int64_t max_g = 0;
+    int32_t gap0 = 0, slist0 = 0;
     bool valid = false;
 };
 
-// Validate a pair's settings and add them to the plan; returns the number of
-// distinct gaps (their indices start at gap0).  `seen` keeps the last list
-// checked: a pair with the same list only has its size bound checked.
+// Validate a pair's settings and add them to the plan: the list's distinct
+// gaps (their indices start at gap0) and its settings, each as (its gap's
+// index among them, θ), from slist0.  `seen` keeps the last list checked: a
+// pair with the same list only has its size bound checked and shares the
+// list's place in the plan.
 int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_t S, int32_t T,
-                 int64_t max_abs_s, bool mined, int32_t &gap0, int32_t &ngap)
+                 int64_t max_abs_s, bool mined, int32_t &gap0, int32_t &ngap, int32_t &slist0)
 {
     if (n < 1 || n > 256) return fail(MINE_EINVAL, "settings count must be in [1, 256]");
     if (!seen.valid || (int)seen.list.size() != n || !std::equal(set, set + n, seen.list.begin())) {
@@ -173,19 +177,19 @@ int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_
             if (it == seen.gaps.end()) seen.gaps.push_back(g);
             seen.max_g = std::max(seen.max_g, -(int64_t)g);
         }
+        seen.gap0 = (int32_t)pl.gap_val.size();
+        pl.gap_val.insert(pl.gap_val.end(), seen.gaps.begin(), seen.gaps.end());
+        seen.slist0 = (int32_t)pl.set_gap.size();
+        pl.set_gap.insert(pl.set_gap.end(), seen.local.begin(), seen.local.end());
+        pl.set_thr.insert(pl.set_thr.end(), seen.thr.begin(), seen.thr.end());
         seen.valid = true;
     }
     // the bound grows with |gap|: the largest decides for every setting
     const int64_t bound = (int64_t)(S + T) * seen.max_g + (int64_t)std::min(S, T) * max_abs_s;
     if (bound >= (int64_t(1) << 31))
         return fail(MINE_EOVERFLOW, "(S+T)*|gap| + min(S,T)*max|s| reaches 2^31");
-    gap0 = (int32_t)pl.gap_val.size();
-    pl.gap_val.insert(pl.gap_val.end(), seen.gaps.begin(), seen.gaps.end());
-    const size_t at = pl.set_gap.size();
-    pl.set_gap.resize(at + n);
-    pl.set_thr.insert(pl.set_thr.end(), seen.thr.begin(), seen.thr.end());
-    int32_t *sg = pl.set_gap.data() + at;
-    for (int k = 0; k < n; ++k) sg[k] = gap0 + seen.local[k];
+    gap0 = seen.gap0;
+    slist0 = seen.slist0;
     ngap = (int32_t)seen.gaps.size();
     return 0;
 }
@@ -228,11 +232,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         settings_of(p, set, n);
         pp.set0 = pl.R;
         pp.nset = n;
-        if (p == 0) {   // the first pair's count as a guess for every pair
-            pl.set_gap.reserve((size_t)P * n);
-            pl.set_thr.reserve((size_t)P * n);
-        }
-        int rc = add_settings(pl, seen, set, n, pp.S, pp.T, max_abs_s, mined, pp.gap0, pp.ngap);
+        int rc = add_settings(pl, seen, set, n, pp.S, pp.T, max_abs_s, mined, pp.gap0, pp.ngap, pp.slist0);
         if (rc) return rc;
         pl.R += n;
         pp.m_off = pl.m_elems;
@@ -753,7 +753,13 @@ int enqueue_kernels(mine_ctx *ctx, const BatchDev &b, const mine_dict *dict, int
         n += timed_launch(ctx, KID_VALIDATE, st, [&] { return launch_validate(b.sent_off, n_sent, n_tok, b.err, st); });
         BatchDev bd = b;
         bd.kmax = dict->d.kmax;
-        const bool par = fk && fk->st;
+        // (with per-kernel events every launch runs alone: its time is its own)
+        bool prof = false;
+        {
+            std::lock_guard<std::mutex> g(ctx->prof_mu);
+            prof = ctx->prof_on;
+        }
+        const bool par = fk && fk->st && !prof;
         const cudaStream_t sw = par ? fk->st : st;
         if (par) {
             CK(cudaEventRecord(fk->fork, st));
