@@ -172,18 +172,21 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
     const int nchunks = ntile + 1;
 
     // virtual tile k of this warp (the warp's tile t0 + k) into slot
-    // (t0 + k) % 3: one 4 KB bulk copy
+    // (t0 + k) % 3: one bulk copy of the tile's rows inside the pair (4 KB
+    // but in the last stripe; the lanes past the last row read stale rows,
+    // and rows never feed the rows above them)
     const uint32_t t0 = tiles;
     auto issue = [&](int k) {
         const int q = k / TT;
         const int C = k - q * TT;
         const int s = wg + q * G;
         const int slot = (int)((t0 + k) % kNwSlots);
+        const uint32_t bytes = (uint32_t)min(kTile, pp.S - kTile * s) * (kTile * 4);
         __syncwarp();
         if (lane == 0) {
-            mbar_expect_tx(&sm.bar[w][slot], kTileElems * 4);
-            bulk_g2s_once(sm.tile[w][slot], Mp + ((int64_t)s * TT + C) * kTileElems, kTileElems * 4,
-                          &sm.bar[w][slot], pol);
+            mbar_expect_tx(&sm.bar[w][slot], bytes);
+            bulk_g2s_once(sm.tile[w][slot], Mp + ((int64_t)s * TT + C) * kTileElems, bytes, &sm.bar[w][slot],
+                          pol);
         }
         tiles = t0 + k + 1;
     };
