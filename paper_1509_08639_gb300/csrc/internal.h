@@ -45,6 +45,8 @@ constexpr int kGScratchWarpsPerSm = 72;
 // Target articles of more than this many sentences are prepared by the
 // wide-article launch (bigger tables, fewer CTAs per SM)
 constexpr int kWideArticleSent = 160;
+// floor(x * 65536 / m) == umulhi(x << 17, ceil(2^31 / m)) for 0 <= x <= m <= this
+constexpr int kRecip31Max = 181;
 static_assert(kScoreWarpsScore * kScoreCtasPerSmScore <= kGScratchWarpsPerSm &&
                   kScoreWarps * kScoreCtasPerSm <= kGScratchWarpsPerSm &&
                   16 * kPairPrepCtasPerSm <= kGScratchWarpsPerSm,
@@ -170,6 +172,7 @@ struct BatchDev {
     uint32_t *matches;           // traceback matches (i << 16 | j), decreasing i
     int32_t *hfin;               // [n_nw_items] H[S][T] of a tiled alignment (unused by the others)
     const uint64_t *recip;       // [kMaxSentTokens + 1]: ceil(2^48 / m), 0 for m = 0
+    const uint32_t *recip31;     // [kMaxSentTokens + 1]: ceil(2^31 / m), 0 for m = 0 (after recip)
     int2 *gscratch;              // per-warp tables for sentences longer than the shared ones
     int32_t f32;                 // score kernel writes single-precision scores (float bits) into M
     int32_t *counters;           // [8] work-queue heads

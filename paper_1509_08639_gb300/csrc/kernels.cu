@@ -1064,6 +1064,8 @@ struct alignas(16) DirectCta {
     uint64_t KL[32];
     int32_t Lt[32];
     int32_t Mj[32];          // m_j (single-precision scores)
+    uint32_t Rm[32];         // the 32-bit reciprocals of m_j and L'_j (kRecip31Max at most)
+    uint32_t RL[32];
 };
 
 // Shared memory of one k_score CTA (kSWS warps).  The mbarriers stay outside
@@ -1135,6 +1137,22 @@ __device__ __forceinline__ int32_t cell_score(uint32_t a, uint32_t bb, uint64_t 
     }
     const uint32_t h = (q_t + q_s) >> 1;
     // (49152 * h + 16384 * q_l) >> 16 == (3h + q_l) >> 2
+    return (int32_t)((3u * h + q_l) >> 2);
+}
+
+// The same score with 32-bit reciprocals, for counts and lengths of at most
+// kRecip31Max: R = ceil(2^31 / m) = 2^31 / m + e (0 <= e < 1), so
+// (x 2^17) R / 2^32 = x 2^16 / m + x e / 2^15, and x e / 2^15 < m / 2^15 < 1 / m
+// when m^2 < 2^15 (m <= 181): below the distance from x 2^16 / m to the next
+// integer, so the high word is the floor (m = 0: R = 0 and x = 0).
+__device__ __forceinline__ int32_t cell_score32(uint32_t a, uint32_t bb, uint32_t Rm, uint32_t Rs, int Ls,
+                                                int Lt, uint32_t RLs, uint32_t RLt)
+{
+    const uint32_t q_t = __umulhi(a << 17, Rm);
+    const uint32_t q_s = __umulhi(bb << 17, Rs);
+    const uint32_t q_l = (Ls == 0 && Lt == 0) ? 65536u
+                                              : __umulhi((uint32_t)min(Ls, Lt) << 17, Ls >= Lt ? RLs : RLt);
+    const uint32_t h = (q_t + q_s) >> 1;
     return (int32_t)((3u * h + q_l) >> 2);
 }
 
@@ -1302,6 +1320,42 @@ __device__ __forceinline__ void emit_row(const uint32_t (&A)[NPL], const uint32_
     }
 }
 
+// emit_row (NPL = 8, fixed point) with the 32-bit reciprocals of cell_score32
+__device__ __forceinline__ void emit_row32(const uint32_t (&A)[8], const uint32_t (&B)[8], const uint32_t *Rm,
+                                           const uint32_t *RL, const int32_t *Lt, uint32_t Rs, uint32_t RLs,
+                                           int Ls, int ncols, int32_t *mrow, int c0)
+{
+    const bool whole = ncols == 32 && (c0 & 31) == 0;   // one whole row of one tile
+#pragma unroll 1
+    for (int m = 0; m < 4 && 8 * m < ncols; ++m) {
+        uint32_t alo, ahi, blo, bhi;
+        planes_to_bytes(A, m, alo, ahi);
+        planes_to_bytes(B, m, blo, bhi);
+        int32_t v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int jj = 8 * m + c;
+            const uint32_t a = ((c < 4 ? alo : ahi) >> (8 * (c & 3))) & 0xffu;
+            const uint32_t bb = ((c < 4 ? blo : bhi) >> (8 * (c & 3))) & 0xffu;
+            v[c] = cell_score32(a, bb, Rm[jj], Rs, Ls, Lt[jj], RLs, RL[jj]);
+        }
+        if (whole) {
+            int4 *dst = reinterpret_cast<int4 *>(mrow + (int64_t)(c0 >> 5) * kTileElems + 8 * m);
+            dst[0] = make_int4(v[0], v[1], v[2], v[3]);
+            dst[1] = make_int4(v[4], v[5], v[6], v[7]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int jj = 8 * m + c;
+                if (jj < ncols) {
+                    const int col = c0 + jj;
+                    mrow[(int64_t)(col >> 5) * kTileElems + (col & 31)] = v[c];
+                }
+            }
+        }
+    }
+}
+
 // Add eight 32-lane bit vectors to the bit-sliced counter P (planes 0..2 are
 // the ones / twos / fours of a carry-save tree; the weight-8 carry ripples
 // into the planes above).
@@ -1400,6 +1454,9 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
                                   uint64_t KLs, int Ls, int32_t *mrow, int cbeg, int cend)
 {
     const int maxH = (int)__reduce_max_sync(kFull, (unsigned)n_h);   // this warp's rows
+    // this warp's rows short enough for the 32-bit reciprocals (n_i <= Ls)
+    const bool rows32 = __all_sync(kFull, !row_ok || Ls <= kRecip31Max);
+    const uint32_t Rs = b.recip31[min(n_i, kRecip31Max)], RLs = b.recip31[min(Ls, kRecip31Max)];
     const int nIt = (maxH + 7) >> 3;
     uint4 f0 = make_uint4(0u, 0u, 0u, 0u), f1 = f0;
     if (0 < n_h) {
@@ -1446,8 +1503,11 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
             sd.KL[col] = __ldg(&b.recip[e - a]);
             sd.Lt[col] = e - a;
             sd.Mj[col] = m;
+            sd.Rm[col] = __ldg(&b.recip31[min(m, kRecip31Max)]);
+            sd.RL[col] = __ldg(&b.recip31[min(e - a, kRecip31Max)]);
         }
-        __syncthreads();
+        // every column of the block short enough for the 32-bit reciprocals (m_j <= L'_j)
+        const bool cols32 = __syncthreads_and(half != 0 || col >= ncols || e - a <= kRecip31Max);
         // the ids are in the masks now: stage the next block's
         if (more) {
             k0 = k1;
@@ -1459,9 +1519,12 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
             if (maxH < 256) {
                 uint32_t A[8], B[8];
                 direct_counts<8, DIRECT>(sd.mask, hl, n_h, nIt, f0, f1, A, B);
-                if (row_ok)
+                if (rows32 && cols32 && !b.f32) {
+                    if (row_ok) emit_row32(A, B, sd.Rm, sd.RL, sd.Lt, Rs, RLs, Ls, ncols, mrow, c0);
+                } else if (row_ok) {
                     emit_row_any<8>(A, B, sd.Km, sd.KL, sd.Lt, Ks, KLs, Ls, ncols, mrow, c0, b.f32 != 0,
                                     sd.Mj, n_i);
+                }
             } else {
                 uint32_t A[11], B[11];
                 direct_counts<11, DIRECT>(sd.mask, hl, n_h, nIt, f0, f1, A, B);

@@ -408,6 +408,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
 {
     BatchDev b{};
     b.recip = recip;
+    b.recip31 = recip ? reinterpret_cast<const uint32_t *>(recip + kMaxSentTokens + 1) : nullptr;
     b.gscratch = static_cast<int2 *>(gscratch);
     char *plan = base + L.plan;
     b.sent_off = sent_off;
@@ -1094,10 +1095,15 @@ int mine_open(const mine_config *cfg, mine_ctx **out)
     {
         // exact fixed-point reciprocals: floor(x * 65536 / m) == (x * K[m]) >> 32
         // for 0 <= x <= m <= kMaxSentTokens (error of K below 1/m)
+        // and the 32-bit form floor(x * 65536 / m) == umulhi(x << 17, R[m]),
+        // R[m] = ceil(2^31 / m), for m <= kRecip31Max (after K in the same block)
         std::vector<uint64_t> K(kMaxSentTokens + 1, 0);
         for (int m = 1; m <= kMaxSentTokens; ++m) K[m] = ((uint64_t(1) << 48) + m - 1) / m;
-        CK(cudaMalloc(&ctx->recip, sizeof(uint64_t) * K.size()));
+        std::vector<uint32_t> R(kMaxSentTokens + 1, 0);
+        for (int m = 1; m <= kMaxSentTokens; ++m) R[m] = (uint32_t)(((uint64_t(1) << 31) + m - 1) / m);
+        CK(cudaMalloc(&ctx->recip, sizeof(uint64_t) * K.size() + sizeof(uint32_t) * R.size()));
         CK(cudaMemcpy(ctx->recip, K.data(), sizeof(uint64_t) * K.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->recip + K.size(), R.data(), sizeof(uint32_t) * R.size(), cudaMemcpyHostToDevice));
     }
     ctx->pool.base = static_cast<char *>(ctx->pool_mem);
     ctx->pool.size = c.device_budget_bytes;
