@@ -88,7 +88,8 @@ def test_q16_score_matrices_cell_by_cell(ctx):
     """Every cell of the fixed-point score matrix M against the oracle's: 300
     lognormal pairs, tile-edge sizes, empty sentences, sentences of up to 1024
     tokens, a target article of 8,192-16,384 distinct tokens (the extra-wide
-    launches) and one with more (the token-keyed path)."""
+    launches), one with more (the token-keyed path) and a short one with
+    4,097-6,144."""
     rng = np.random.default_rng(316)
     w = synth.workload(2, n_pairs=300)
     d = w.dictionary
@@ -104,7 +105,11 @@ def test_q16_score_matrices_cell_by_cell(ctx):
         np.cumsum(lens, out=off[1:])
         return off, rng.integers(0, 200000, int(off[-1])).astype(np.int32)
     wide = synth.pack_docs([rand_doc(120, 5, 40), rand_doc(700, 15, 25),     # ~14,000 distinct
-                            rand_doc(60, 5, 40), rand_doc(1000, 25, 35)])    # ~28,000: token-keyed
+                            rand_doc(60, 5, 40), rand_doc(1000, 25, 35),     # ~28,000: token-keyed
+                            # at most 160 target sentences with 4,097-6,144 distinct
+                            # tokens: the small-article preparation, the score launch
+                            # of larger articles (from k_order's list)
+                            rand_doc(40, 5, 40), rand_doc(100, 50, 60)])     # ~5,400
     dh = ctx.dict_create(d)
     od = O.OracleDict(d)
     for name, b in (("lognormal", w.batch), ("edges", edge), ("empties", empties), ("long", longs),
