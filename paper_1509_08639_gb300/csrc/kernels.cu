@@ -971,6 +971,7 @@ k_pairprep(BatchDev b, DevDict d)
 // Score launches: articles of at most kDirectSmall distinct target tokens
 // (from the plan's item list), and the others (from a list k_order builds).
 constexpr int kDirectSmall = 4096;
+constexpr int kScoreWarpsX = 8;   // warps per CTA of the extra-wide score launch
 
 // Per pair, the source rows sorted by element count, longest first (counting
 // sort on min(count, 1023); ties in any order), written to row_order[s0 ..
@@ -990,15 +991,17 @@ k_order(BatchDev b)
         const int S = pp.S;
         const int D = b.pdoc[p];
         if (D < 0 || D > kDirectSmall) {
-            // the pair's score items, for the launches of larger articles
-            // (as the plan cuts them: 64 rows by kScoreColChunk columns)
-            const int nc = (max(pp.T, 1) + kScoreColChunk - 1) / kScoreColChunk, n = ((S + 63) / 64) * nc;
+            // the pair's score items, for the launches of larger articles:
+            // 32 rows per warp of the launch that takes them (64, or 32
+            // kScoreWarpsX for the extra-wide ones) by kScoreColChunk columns
+            const int rows = D > kDirect ? 32 * kScoreWarpsX : 64;
+            const int nc = (max(pp.T, 1) + kScoreColChunk - 1) / kScoreColChunk, n = ((S + rows - 1) / rows) * nc;
             int base = 0;
             if (lane == 0 && n > 0) base = atomicAdd(&b.counters[18], n);
             base = __shfl_sync(kFull, base, 0);
             for (int k = lane; k < n; k += 32) {
                 const int c0 = kScoreColChunk * (k % nc);
-                b.wide_items[base + k] = ScoreItem{p, 64 * (k / nc), c0, min(pp.T, c0 + kScoreColChunk)};
+                b.wide_items[base + k] = ScoreItem{p, rows * (k / nc), c0, min(pp.T, c0 + kScoreColChunk)};
             }
         }
         int32_t *ord = b.row_order + pp.s0;
@@ -1068,16 +1071,16 @@ struct alignas(16) DirectCta {
     uint32_t RL[32];
 };
 
-// Shared memory of one k_score CTA (kSWS warps).  The mbarriers stay outside
+// Shared memory of one k_score CTA (W warps).  The mbarriers stay outside
 // the union: both paths write it with generic stores.  Without the
 // token-keyed path (KEYED false) the per-warp buffers are not needed.
-template <int DIRECT, bool KEYED>
+template <int DIRECT, bool KEYED, int W>
 struct alignas(16) ScoreSmem {
     union {
-        KeyedWarp kw[KEYED ? kSWS : 1];
+        KeyedWarp kw[KEYED ? W : 1];
         DirectCta<DIRECT> d;
     };
-    unsigned long long bar[kSWS][2];   // token-keyed path, per warp
+    unsigned long long bar[W][2];      // token-keyed path, per warp
     unsigned long long dbar;           // document-id path
     int32_t item;
 };
@@ -1447,7 +1450,7 @@ __device__ __forceinline__ int stage_ids(const BatchDev &b, uint16_t *ids, unsig
 // its 32 rows and scores their cells; the masks of ids [0, D) are cleared
 // again.  A block with more than kBlkTokCap tokens reads its ids from global
 // memory.  Returns false (on every thread) when a bounded wait ran out.
-template <int DIRECT>
+template <int DIRECT, int W>
 __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsigned long long *dbar,
                                   uint32_t &dparity, const PairPlan &pp, int D, int tid, int nrows,
                                   bool row_ok, const uint32_t *hl, int n_h, int n_i, uint64_t Ks,
@@ -1463,7 +1466,8 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
         f0 = *reinterpret_cast<const uint4 *>(hl);
         f1 = *reinterpret_cast<const uint4 *>(hl + 4);
     }
-    const int col = tid >> 1, half = tid & 1;
+    // W threads per target column of the block (tid = W col + part)
+    const int col = tid / W, part = tid % W;
     const int64_t t0 = pp.t0;
     int32_t k0 = b.sent_off[t0 + cbeg], k1 = b.sent_off[t0 + cbeg + max(0, min(32, cend - cbeg))];
     // a copy is issued only for a block the loop below consumes (and waits for)
@@ -1491,14 +1495,15 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
         int m = 0;
         if (staged) {
             const uint16_t *ids = sd.ids + lead - k0;
-            for (int32_t k = a + half; k < e; k += 2)
+            for (int32_t k = a + part; k < e; k += W)
                 m += (atomicOr(&sd.mask[min((uint32_t)ids[k], (uint32_t)DIRECT - 1)], bit) & bit) ? 0 : 1;
         } else {
-            for (int32_t k = a + half; k < e; k += 2)
+            for (int32_t k = a + part; k < e; k += W)
                 m += (atomicOr(&sd.mask[min((uint32_t)b.tdoc[k], (uint32_t)DIRECT - 1)], bit) & bit) ? 0 : 1;
         }
-        m += __shfl_xor_sync(kFull, m, 1);
-        if (half == 0 && col < ncols) {
+#pragma unroll
+        for (int o = 1; o < W; o <<= 1) m += __shfl_xor_sync(kFull, m, o);
+        if (part == 0 && col < ncols) {
             sd.Km[col] = __ldg(&b.recip[m]);
             sd.KL[col] = __ldg(&b.recip[e - a]);
             sd.Lt[col] = e - a;
@@ -1507,7 +1512,7 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
             sd.RL[col] = __ldg(&b.recip31[min(e - a, kRecip31Max)]);
         }
         // every column of the block short enough for the 32-bit reciprocals (m_j <= L'_j)
-        const bool cols32 = __syncthreads_and(half != 0 || col >= ncols || e - a <= kRecip31Max);
+        const bool cols32 = __syncthreads_and(part != 0 || col >= ncols || e - a <= kRecip31Max);
         // the ids are in the masks now: stage the next block's
         if (more) {
             k0 = k1;
@@ -1535,7 +1540,7 @@ __device__ bool score_item_direct(const BatchDev &b, DirectCta<DIRECT> &sd, unsi
         }
         __syncthreads();
         uint4 *mz = reinterpret_cast<uint4 *>(sd.mask);
-        for (int k = tid; k < (D + 3) >> 2; k += kSWS * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
+        for (int k = tid; k < (D + 3) >> 2; k += W * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
     }
     return true;
@@ -1671,20 +1676,23 @@ __device__ __forceinline__ int plan_block(const BatchDev &b, KeyedWarp &sm, unsi
 // target tokens (queue counters[1]); DIRECT = kDirectX: articles with more
 // than kDirect and at most kDirectX (queue counters[12]); DIRECT = kDirect
 // with KEYED: all other items, document-id or token-keyed (queue counters[6]).
-template <int DIRECT, bool KEYED>
-__global__ void __launch_bounds__(kSWS * 32, KEYED ? 1 : 11)   // small launch: 11 CTAs per SM fit
+// W warps per CTA, 32 rows each: 2 (items of 64 rows), or kScoreWarpsX for
+// the extra-wide articles, whose 64 KB mask array leaves room for 3 CTAs per
+// SM (items of 32 kScoreWarpsX rows, from k_order's list).
+template <int DIRECT, bool KEYED, int W>
+__global__ void __launch_bounds__(W * 32, KEYED ? 1 : (W == 2 ? 11 : 3))   // 11 small-launch CTAs per SM fit
 k_score(BatchDev b)
 {
     constexpr bool XW = !KEYED && DIRECT == kDirectX;
     if (XW && *(volatile int32_t *)&b.counters[13] == 0) return;   // no such article
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScoreSmem<DIRECT, KEYED> &S = *reinterpret_cast<ScoreSmem<DIRECT, KEYED> *>(smem_raw);
+    ScoreSmem<DIRECT, KEYED, W> &S = *reinterpret_cast<ScoreSmem<DIRECT, KEYED, W> *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int wib = tid >> 5;
     KeyedWarp &kw = S.kw[wib];
     unsigned long long *kbar = S.bar[wib];
-    int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * kSWS + wib) * kGTabSlots;
+    int2 *gtab = b.gscratch + (int64_t)(blockIdx.x * W + wib) * kGTabSlots;
     const uint64_t *recip = b.recip;
     const int kmax = b.kmax;
     if (lane == 0) {
@@ -1741,14 +1749,14 @@ k_score(BatchDev b)
             if (!mask_clean) {
                 // the token-keyed path wrote these bytes with generic stores
                 uint4 *mz = reinterpret_cast<uint4 *>(S.d.mask);
-                for (int k = tid; k < (DIRECT + 16) / 4; k += kSWS * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
+                for (int k = tid; k < (DIRECT + 16) / 4; k += W * 32) mz[k] = make_uint4(0u, 0u, 0u, 0u);
                 fence_proxy_async();
                 __syncthreads();
                 mask_clean = true;
             }
             // generic stores now cover the keyed staging buffers: fence before their next copy
             generic[0] = generic[1] = true;
-            ok = score_item_direct<DIRECT>(b, S.d, &S.dbar, dparity, pp, D, tid, nrows, row_ok, el,
+            ok = score_item_direct<DIRECT, W>(b, S.d, &S.dbar, dparity, pp, D, tid, nrows, row_ok, el,
                                            n_elem, n_i, Ks, KLs, Ls, mrow, si.c0, si.c1);
             continue;
         }
@@ -2223,40 +2231,40 @@ int launch_order(const BatchDev &b, int num_sms, cudaStream_t st)
     return 1;
 }
 
-template <int DIRECT, bool KEYED>
+template <int DIRECT, bool KEYED, int W>
 int launch_score_one(const BatchDev &b, int num_sms, cudaStream_t st)
 {
-    const size_t smem = sizeof(ScoreSmem<DIRECT, KEYED>);
+    const size_t smem = sizeof(ScoreSmem<DIRECT, KEYED, W>);
     static int per_sm = 0;   // resident CTAs per SM of this variant (queried once)
     if (per_sm == 0) {
-        cudaFuncSetAttribute(k_score<DIRECT, KEYED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_score<DIRECT, KEYED, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<DIRECT, KEYED>, kSWS * 32, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<DIRECT, KEYED, W>, W * 32, smem) !=
                 cudaSuccess || n < 1)
             n = 1;
-        per_sm = std::min(n, kGScratchWarpsPerSm / kSWS);
+        per_sm = std::min(n, kGScratchWarpsPerSm / W);
     }
     const int grid = std::max(1, std::min(num_sms * per_sm, b.n_score_items));
-    k_score<DIRECT, KEYED><<<grid, kSWS * 32, smem, st>>>(b);
+    k_score<DIRECT, KEYED, W><<<grid, W * 32, smem, st>>>(b);
     return 1;
 }
 
 int launch_score(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
-    return launch_score_one<kDirectSmall, false>(b, num_sms, st);
+    return launch_score_one<kDirectSmall, false, kSWS>(b, num_sms, st);
 }
 
 int launch_score_wide(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
-    return launch_score_one<kDirect, true>(b, num_sms, st);
+    return launch_score_one<kDirect, true, kSWS>(b, num_sms, st);
 }
 
 int launch_score_xwide(const BatchDev &b, int num_sms, cudaStream_t st)
 {
     if (b.n_score_items <= 0) return 0;
-    return launch_score_one<kDirectX, false>(b, num_sms, st);
+    return launch_score_one<kDirectX, false, kScoreWarpsX>(b, num_sms, st);
 }
 
 int launch_align_tiled(const BatchDev &b, int num_sms, cudaStream_t st)
