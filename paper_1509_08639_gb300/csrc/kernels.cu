@@ -6,35 +6,40 @@
 // (monotone paths: "cannot go upward or leftward"), the traceback, and the
 // selection of aligned pairs whose score passes the threshold.
 //
-// Kernels, in launch order:
+// Kernels, in launch order (the wide-article preparation and score launches
+// run on a second stream beside the small-article ones):
 //   k_dict_build  once per dictionary: bucketed table (8 slots per 64-byte
-//                 bucket) of key -> (offset, count) of its translations
+//                 bucket) of key -> (offset, count) of its translations, and
+//                 the inline table (two keys with their first translations)
 //   k_validate    sentence offsets are sane (later kernels trust them)
-//   k_pairprep    one CTA per pair, largest first: the target article's
-//                 distinct tokens get dense ids (ranks of occupied slots of a
-//                 shared table); every target token's id; one warp per source
-//                 row: distinct tokens, dictionary lookups, and the
-//                 translations the target article holds written as (id |
+//   k_pairprep    one CTA per pair, largest first, three launches (target
+//                 articles of at most / more than 160 sentences, then the
+//                 ones with too many distinct tokens for those): the target
+//                 article's distinct tokens get dense ids (ranks of occupied
+//                 slots of a shared table); every target token's id; one warp
+//                 per source row: distinct tokens, dictionary lookups, and
+//                 the translations the target article holds written as (id |
 //                 FIRST | END) -- the only ones that can overlap
-//   k_prep        the same for articles with more than 8192 distinct target
+//   k_prep        the same for articles with more than 16384 distinct target
 //                 tokens, keeping every translation (token-keyed path)
-//   k_order       per pair, source rows by list length
-//   k_score       two launches (articles with at most 4096 / more distinct
-//                 target tokens): per item of 64 source rows and one range of
-//                 target columns, block by block of 32 target sentences, a
-//                 column mask per id (direct-indexed shared array, block ids
-//                 TMA-staged), every lane adds the masks of its row's kept
-//                 ids into bit-sliced carry-save counters, 8 x 8 bit
-//                 transposes give the counts, exact reciprocal multiplies the
-//                 ratios; 32 x 32 tiles of M.  Articles beyond 8192 ids use a
-//                 per-block hashed token -> column mask table instead.
-//   k_align       persistent; per size bin (autotuned) a pair is aligned by
-//                 one warp or by a whole CTA (8 warps pipelined over stripes
-//                 of 32 rows, the boundary row through a shared-memory ring
-//                 with bounded flag waits).  Inside a stripe: anti-diagonal
-//                 wavefront, lane = row, the cell above by __shfl_up_sync,
-//                 score tiles by TMA bulk copies three deep, 2-bit directions
-//                 packed 16 per word.
+//   k_order       per pair, source rows by list length; the score items of
+//                 the larger articles, listed for their launches
+//   k_score       three launches (articles with at most 4096 distinct target
+//                 tokens, from the plan's items; more, from k_order's list;
+//                 8193-16384, by CTAs of 8 warps): per item of 64 (256)
+//                 source rows and one range of target columns, block by block
+//                 of 32 target sentences, a column mask per id
+//                 (direct-indexed shared array, block ids TMA-staged), every
+//                 lane adds the masks of its row's kept ids into bit-sliced
+//                 carry-save counters, 8 x 8 bit transposes give the counts,
+//                 exact reciprocal multiplies the ratios; 32 x 32 tiles of M.
+//                 Articles beyond 16384 ids use a per-block hashed token ->
+//                 column mask table instead.
+//   k_nw          (align.cu) persistent wavefront fill: a pair by one warp or
+//                 by a pipeline of 2, 4 or 8 warps over its 32-row stripes
+//   k_align_tiled very large pairs: 256 x 512-cell tiles over many CTAs, in
+//                 anti-diagonal order with bounded flag waits on the tiles
+//                 above and on the left
 //   k_trace       one warp per alignment: traceback over the packed codes and
 //                 the threshold selection of every setting that shares the gap
 #include "internal.h"
@@ -1443,10 +1448,10 @@ __device__ __forceinline__ int stage_ids(const BatchDev &b, uint16_t *ids, unsig
     return k0 - a0;
 }
 
-// One score item (up to 64 source rows) on the document-id path, block by
+// One score item (up to 32 W source rows) on the document-id path, block by
 // block (32 columns), by the whole CTA: the block's ids are staged by TMA
-// (one block ahead); threads 2j and 2j+1 set bit j in the mask of every id of
-// target sentence j and count m_j on the way; every warp counts the hits of
+// (one block ahead); threads W j .. W j + W - 1 set bit j in the mask of
+// every id of target sentence j and count m_j on the way; every warp counts the hits of
 // its 32 rows and scores their cells; the masks of ids [0, D) are cleared
 // again.  A block with more than kBlkTokCap tokens reads its ids from global
 // memory.  Returns false (on every thread) when a bounded wait ran out.
