@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--configs", default="1,3,4",
                     help="other workloads measured after the benchmark batch (sub-records)")
     ap.add_argument("--serve-sweep", default="1000,20000",
-                    help="further offered rates (pairs/s), 1.5 s each; empty for none")
+                    help="further offered rates (pairs/s), --serve-seconds each; empty for none")
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident path (for profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
@@ -100,7 +100,7 @@ class ClockSampler:
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    INTERVAL_MS = 50
+    INTERVAL_MS = 10
     TS_FORMAT = "%Y/%m/%d %H:%M:%S.%f"
 
     def __init__(self, index):
