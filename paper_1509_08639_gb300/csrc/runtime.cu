@@ -143,6 +143,7 @@ struct Plan {
 // order of first appearance) and the largest |gap|; where the list sits in
 // the plan (every pair with the same list shares it).
 struct SettingsSeen {
+    const Setting *last = nullptr;   // the array the list was last read from
     std::vector<Setting> list;
     std::vector<int32_t> local, thr, gaps;
     int64_t max_g = 0;
@@ -159,7 +160,9 @@ int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_
                  int64_t max_abs_s, bool mined, int32_t &gap0, int32_t &ngap, int32_t &slist0)
 {
     if (n < 1 || n > 256) return fail(MINE_EINVAL, "settings count must be in [1, 256]");
-    if (!seen.valid || (int)seen.list.size() != n || !std::equal(set, set + n, seen.list.begin())) {
+    // (the same array as the pair before: the same list, not compared again)
+    if (!seen.valid || (int)seen.list.size() != n ||
+        (set != seen.last && !std::equal(set, set + n, seen.list.begin()))) {
         seen.valid = false;
         seen.list.assign(set, set + n);
         seen.local.resize(n);
@@ -184,6 +187,7 @@ int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_
         pl.set_thr.insert(pl.set_thr.end(), seen.thr.begin(), seen.thr.end());
         seen.valid = true;
     }
+    seen.last = set;
     // the bound grows with |gap|: the largest decides for every setting
     const int64_t bound = (int64_t)(S + T) * seen.max_g + (int64_t)std::min(S, T) * max_abs_s;
     if (bound >= (int64_t(1) << 31))
@@ -194,8 +198,10 @@ int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_
     return 0;
 }
 
-// settings_of(p) -> (pointer, count) of pair p's settings; swap: every
-// pair's two articles exchange roles (the target article is the source)
+// settings_of(p) -> (pointer, count) of pair p's settings (arrays that stay
+// unchanged during the call: pairs given the same array share one list);
+// swap: every pair's two articles exchange roles (the target article is the
+// source)
 template <class F>
 int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F settings_of,
                int64_t max_abs_s, bool mined, const int8_t *align_tab = nullptr, bool swap = false)
