@@ -163,6 +163,7 @@ struct BatchDev {
     int32_t *row_order;          // [n_sent] per pair, source rows by element count (longest first)
     uint16_t *tdoc;              // [n_tok + 32] document id of each target token
     int32_t *pdoc;               // [n_pairs] distinct target tokens D, or -1 (token-keyed path)
+    int32_t *xw_list;            // [n_pairs] pairs left to the extra-wide preparation (counters[21])
     const int32_t *dorder;       // [n_pairs] pairs by article size, longest first: the n_dwide
                                  // pairs of more than kWideArticleSent target sentences, then the rest
     int32_t n_dwide;

@@ -820,6 +820,7 @@ k_pairprep(BatchDev b, DevDict d)
     constexpr int kCap = SMALL ? kSmallIds : IDS;
     static_assert(kCap <= IDS && kCap + 4 * kPPThreads < SLOTS, "the target table never fills");
     // nothing to do unless another launch left an article with too many ids
+    // (their pairs listed in xw_list, counters[21] of them)
     if (XW && *(volatile int32_t *)&b.counters[9] == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairPrepSmem<WARPS, SLOTS, IDS> &sm = *reinterpret_cast<PairPrepSmem<WARPS, SLOTS, IDS> *>(smem_raw);
@@ -839,8 +840,8 @@ k_pairprep(BatchDev b, DevDict d)
         }
         __syncthreads();
         const int item = sm.item;
-        if (item >= (MODE == kModeWide ? b.n_dwide : b.n_pairs)) break;
-        const int p = b.dorder[item];
+        if (item >= (MODE == kModeWide ? b.n_dwide : (XW ? b.counters[21] : b.n_pairs))) break;
+        const int p = XW ? b.xw_list[item] : b.dorder[item];
         if (XW && b.pdoc[p] != -1) continue;    // prepared by one of the other launches
         const PairPlan pp = b.pairs[p];
         const int32_t ta = b.sent_off[pp.t0], tb = b.sent_off[pp.t0 + pp.T];
@@ -888,7 +889,10 @@ k_pairprep(BatchDev b, DevDict d)
         if (tid == 0) {
             if (!XW) {
                 b.pdoc[p] = D <= kCap ? D : -1;
-                if (D > kCap) atomicExch(&b.counters[9], 1);   // the extra-wide launch has work
+                if (D > kCap) {   // the extra-wide launch has work: this pair
+                    b.xw_list[atomicAdd(&b.counters[21], 1)] = p;
+                    atomicExch(&b.counters[9], 1);
+                }
             } else if (D <= kCap) {
                 b.pdoc[p] = D;
                 // so has the extra-wide score launch, unless another one takes it
