@@ -164,6 +164,7 @@ struct BatchDev {
     uint16_t *tdoc;              // [n_tok + 32] document id of each target token
     int32_t *pdoc;               // [n_pairs] distinct target tokens D, or -1 (token-keyed path)
     int32_t *xw_list;            // [n_pairs] pairs left to the extra-wide preparation (counters[21])
+    ScoreItem *keyed_items;      // [n_prep_items] 32-row groups left to k_prep (counters[22])
     const int32_t *dorder;       // [n_pairs] pairs by article size, longest first: the n_dwide
                                  // pairs of more than kWideArticleSent target sentences, then the rest
     int32_t n_dwide;

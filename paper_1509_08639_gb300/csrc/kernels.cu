@@ -378,8 +378,9 @@ k_prep(BatchDev b, DevDict d)
         int item = 0;
         if (lane == 0) item = atomicAdd(&b.counters[0], 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= b.n_prep_items) break;
-        const ScoreItem si = b.prep_items[item];
+        // the 32-row groups of the pairs the extra-wide preparation listed
+        if (item >= b.counters[22]) break;
+        const ScoreItem si = b.keyed_items[item];
         if (b.pdoc[si.pair] >= 0) continue;   // prepared by k_pairprep
         const PairPlan pp = b.pairs[si.pair];
         const int nrows = min(32, pp.S - si.row0);
@@ -898,7 +899,11 @@ k_pairprep(BatchDev b, DevDict d)
                 // so has the extra-wide score launch, unless another one takes it
                 if (D > kDirect) atomicExch(&b.counters[13], 1);
             } else {
-                atomicExch(&b.counters[14], 1);   // k_prep has work (pdoc stays -1)
+                // k_prep has work (pdoc stays -1): this pair's 32-row groups
+                const int n = (pp.S + 31) >> 5;
+                const int at = atomicAdd(&b.counters[22], n);
+                for (int k = 0; k < n; ++k) b.keyed_items[at + k] = ScoreItem{p, 32 * k, 0, 0};
+                atomicExch(&b.counters[14], 1);
             }
         }
         if (D > kCap) continue;

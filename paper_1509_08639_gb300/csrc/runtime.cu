@@ -331,7 +331,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
 struct Layout {
     int64_t plan = 0, plan_bytes = 0;
     int64_t sent_off = 0, tokens = 0;           // only when the inputs are copied in
-    int64_t elems = 0, sinfo = 0, order = 0, tdoc = 0, pdoc = 0, witems = 0, xwl = 0;
+    int64_t elems = 0, sinfo = 0, order = 0, tdoc = 0, pdoc = 0, witems = 0, xwl = 0, kitems = 0;
     int64_t M = 0, Mrow = 0, codes = 0, matches = 0, hfin = 0;
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
@@ -378,6 +378,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
         L.pdoc = take(4 * (int64_t)pl.P + 16);
         L.witems = take(sizeof(ScoreItem) * (pl.sitems.size() + 1));
         L.xwl = take(4 * (int64_t)pl.P + 16);
+        L.kitems = take(sizeof(ScoreItem) * (pl.pitems.size() + 1));
     } else {
         // a caller-supplied row-major matrix is copied here, then tiled
         int64_t rows = 0;
@@ -446,6 +447,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.pdoc = reinterpret_cast<int32_t *>(base + L.pdoc);
     b.wide_items = reinterpret_cast<ScoreItem *>(base + L.witems);
     b.xw_list = reinterpret_cast<int32_t *>(base + L.xwl);
+    b.keyed_items = reinterpret_cast<ScoreItem *>(base + L.kitems);
     b.dorder = reinterpret_cast<const int32_t *>(plan + L.o_dorder);
     b.M = reinterpret_cast<int32_t *>(base + L.M);
     b.codes = reinterpret_cast<uint32_t *>(base + L.codes);
