@@ -157,6 +157,8 @@ struct BatchDev {
     const int32_t *set_gap;      // settings lists (PairPlan::slist0): each setting's gap as an
     const int32_t *set_thr;      // index among its pair's distinct gaps, and its threshold
     const int32_t *gap_val;      // [G]
+    const int32_t *set_perm;     // per settings list, its settings ordered by gap (stable)
+    const int32_t *gap_sfirst;   // [G] where a gap's settings start in set_perm (list-relative)
     // scratch
     uint32_t *elems;             // source elements (see elem_base)
     int4 *sinfo;                 // [n_sent] (n_i, #elements, |U_i|, 0) of source sentences

@@ -1892,16 +1892,36 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
 {
     const int cap = min(pp.S, pp.T);
     const int TT = (pp.T + 31) >> 5;
-    int32_t sum = 0;
-    for (int q = lane; q < nm; q += 32) {
-        const uint32_t ij = matches[q];
+    // the first 64 matches in increasing-i order (lane and lane + 32), kept
+    // in registers for every setting of the gap
+    int i0 = 0, j0 = 0, i1 = 0, j1 = 0;
+    int32_t s0 = 0, s1 = 0;
+    if (lane < nm) {
+        const uint32_t ij = matches[nm - 1 - lane];
+        i0 = (int)(ij >> 16);
+        j0 = (int)(ij & 0xffffu);
+        s0 = b.M[m_cell(pp.m_off, TT, i0 - 1, j0 - 1)];
+    }
+    if (32 + lane < nm) {
+        const uint32_t ij = matches[nm - 33 - lane];
+        i1 = (int)(ij >> 16);
+        j1 = (int)(ij & 0xffffu);
+        s1 = b.M[m_cell(pp.m_off, TT, i1 - 1, j1 - 1)];
+    }
+    int32_t sum = s0 + s1;
+    for (int q = 64 + lane; q < nm; q += 32) {
+        const uint32_t ij = matches[nm - 1 - q];
         sum += b.M[m_cell(pp.m_off, TT, (int)(ij >> 16) - 1, (int)(ij & 0xffffu) - 1)];
     }
     sum = (int32_t)__reduce_add_sync(kFull, (uint32_t)sum);
     const int32_t H = sum + b.gap_val[gap_idx] * (pp.S + pp.T - 2 * nm);
-    for (int k = 0; k < pp.nset; ++k) {
+    // the settings of this gap: set_perm[slist0 + first .. slist0 + last)
+    const int lg = gap_idx - pp.gap0;
+    const int first = b.gap_sfirst[gap_idx];
+    const int last = lg + 1 < pp.ngap ? b.gap_sfirst[gap_idx + 1] : pp.nset;
+    for (int f = first; f < last; ++f) {
+        const int k = b.set_perm[pp.slist0 + f];
         const int row = pp.set0 + k;
-        if (b.set_gap[pp.slist0 + k] != gap_idx - pp.gap0) continue;
         const int32_t thr = b.set_thr[pp.slist0 + k];
         int32_t *out = b.sel + 3 * (pp.sel_base + (int64_t)k * cap);
         int cnt = 0;
@@ -1910,7 +1930,12 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
             bool take = false;
             int i = 0, j = 0;
             int32_t sc = 0;
-            if (q < nm) {
+            if (c < 64) {   // (c warp-uniform)
+                i = c == 0 ? i0 : i1;
+                j = c == 0 ? j0 : j1;
+                sc = c == 0 ? s0 : s1;
+                take = q < nm && sc > thr;
+            } else if (q < nm) {
                 const uint32_t ij = matches[nm - 1 - q];
                 i = (int)(ij >> 16);
                 j = (int)(ij & 0xffffu);

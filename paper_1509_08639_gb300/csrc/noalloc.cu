@@ -36,7 +36,7 @@ static_assert(kOffMrow % 64 == 0 && kOffCodes % 64 == 0 && kOffMatch % 64 == 0 &
                   kOffSel % 64 == 0 && kOffOut % 64 == 0 && kOffPlan % 64 == 0 &&
                   kOffCounters % 64 == 0,
               "scratch regions must stay 256-byte aligned");
-static_assert(sizeof(PairPlan) + sizeof(NwItem) + 12 <= 64 * 4, "plan region too small");
+static_assert(sizeof(PairPlan) + sizeof(NwItem) + 20 <= 64 * 4, "plan region too small");
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchWords];
 
@@ -69,6 +69,8 @@ __global__ void k_noalloc_setup(int32_t *scratch, int32_t S, int32_t T, int32_t 
     set[0] = 0;     // set_gap
     set[1] = thr;   // set_thr
     set[2] = gap;   // gap_val
+    set[3] = 0;     // set_perm
+    set[4] = 0;     // gap_sfirst
     for (int k = 0; k < 64; ++k) scratch[kOffCounters + k] = 0;
     scratch[kOffOut] = 0;
     scratch[kOffOut + 1] = 0;
@@ -165,6 +167,8 @@ extern "C" int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T
     b.set_gap = set;
     b.set_thr = set + 1;
     b.gap_val = set + 2;
+    b.set_perm = set + 3;
+    b.gap_sfirst = set + 4;
     b.M = sc + kOffM;
     b.codes = reinterpret_cast<uint32_t *>(sc + kOffCodes);
     b.matches = reinterpret_cast<uint32_t *>(sc + kOffMatch);

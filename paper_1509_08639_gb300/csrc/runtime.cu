@@ -109,6 +109,7 @@ struct Plan {
     int32_t n_tiled = 0;
     int64_t tb_words = 0;
     std::vector<int32_t> set_gap, set_thr, gap_val;
+    std::vector<int32_t> set_perm, gap_sfirst;   // each list's settings by gap; where each gap's start
     int64_t m_elems = 0, code_words = 0, match_words = 0, sel_cap = 0;
     int32_t R = 0;
     int32_t n_grp[kNwGroups] = {0, 0, 0, 0};   // alignments by pipelines of 8, 4, 2, 1 warps (from 0, in order)
@@ -129,6 +130,8 @@ struct Plan {
         n_tiled = 0;
         tb_words = 0;
         set_gap.clear();
+        set_perm.clear();
+        gap_sfirst.clear();
         set_thr.clear();
         gap_val.clear();
         m_elems = code_words = match_words = sel_cap = 0;
@@ -185,6 +188,15 @@ int add_settings(Plan &pl, SettingsSeen &seen, const Setting *set, int n, int32_
         seen.slist0 = (int32_t)pl.set_gap.size();
         pl.set_gap.insert(pl.set_gap.end(), seen.local.begin(), seen.local.end());
         pl.set_thr.insert(pl.set_thr.end(), seen.thr.begin(), seen.thr.end());
+        // the settings by gap (a counting sort, stable), and where each gap's start
+        const int ng = (int)seen.gaps.size();
+        std::vector<int32_t> start(ng + 1, 0);
+        for (int k = 0; k < n; ++k) ++start[seen.local[k] + 1];
+        for (int g = 0; g < ng; ++g) start[g + 1] += start[g];
+        pl.gap_sfirst.insert(pl.gap_sfirst.end(), start.begin(), start.begin() + ng);
+        const size_t at = pl.set_perm.size();
+        pl.set_perm.resize(at + n);
+        for (int k = 0; k < n; ++k) pl.set_perm[at + start[seen.local[k]]++] = k;
         seen.valid = true;
     }
     seen.last = set;
@@ -337,6 +349,7 @@ struct Layout {
     int64_t total = 0;
     // offsets inside the plan blob
     int64_t o_pairs = 0, o_sitems = 0, o_nitems = 0, o_setgap = 0, o_setthr = 0, o_gapval = 0;
+    int64_t o_setperm = 0, o_gapsfirst = 0;
     int64_t o_dorder = 0, o_pitems = 0, o_tiles = 0, tbnd = 0;
 };
 
@@ -361,6 +374,8 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
     L.o_setgap = sub(4 * pl.set_gap.size());
     L.o_setthr = sub(4 * pl.set_thr.size());
     L.o_gapval = sub(4 * pl.gap_val.size());
+    L.o_setperm = sub(4 * pl.set_perm.size());
+    L.o_gapsfirst = sub(4 * pl.gap_sfirst.size());
     L.o_dorder = sub(4 * pl.dorder.size());
     L.o_pitems = sub(sizeof(ScoreItem) * pl.pitems.size());
     L.o_tiles = sub(sizeof(TileItem) * pl.tiles.size());
@@ -406,6 +421,8 @@ void pack_plan(const Plan &pl, const Layout &L, char *dst)
     std::memcpy(dst + L.o_setgap, pl.set_gap.data(), 4 * pl.set_gap.size());
     std::memcpy(dst + L.o_setthr, pl.set_thr.data(), 4 * pl.set_thr.size());
     std::memcpy(dst + L.o_gapval, pl.gap_val.data(), 4 * pl.gap_val.size());
+    std::memcpy(dst + L.o_setperm, pl.set_perm.data(), 4 * pl.set_perm.size());
+    std::memcpy(dst + L.o_gapsfirst, pl.gap_sfirst.data(), 4 * pl.gap_sfirst.size());
     std::memcpy(dst + L.o_dorder, pl.dorder.data(), 4 * pl.dorder.size());
     std::memcpy(dst + L.o_pitems, pl.pitems.data(), sizeof(ScoreItem) * pl.pitems.size());
     std::memcpy(dst + L.o_tiles, pl.tiles.data(), sizeof(TileItem) * pl.tiles.size());
@@ -440,6 +457,8 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.set_gap = reinterpret_cast<const int32_t *>(plan + L.o_setgap);
     b.set_thr = reinterpret_cast<const int32_t *>(plan + L.o_setthr);
     b.gap_val = reinterpret_cast<const int32_t *>(plan + L.o_gapval);
+    b.set_perm = reinterpret_cast<const int32_t *>(plan + L.o_setperm);
+    b.gap_sfirst = reinterpret_cast<const int32_t *>(plan + L.o_gapsfirst);
     b.elems = reinterpret_cast<uint32_t *>(base + L.elems);
     b.sinfo = reinterpret_cast<int4 *>(base + L.sinfo);
     b.row_order = reinterpret_cast<int32_t *>(base + L.order);
