@@ -743,7 +743,7 @@ def main():
         for c in [int(x) for x in args.configs.split(",") if x.strip()]:
             configs[str(c)] = config_record(ctx, c, cpu_budget=4.0 if args.no_cpu else 8.0)
 
-    # ---- roofline of each stage, per SURVEY-style algorithmic units:
+    # ---- roofline of each stage, in algorithmic units:
     # scoring (translate + set build + score matrix) is bounded by HBM: 4 B per
     # score cell written + 4 B per token read, over all its launches together;
     # the alignment is bounded by int32 add/max issue: 4 ops per DP cell
