@@ -146,7 +146,7 @@ __device__ bool nw_run(const BatchDev &b, NwSmem<K> &sm, int w, int wg, int G, i
     const int nq = (NS - wg + G - 1) / G;   // stripes of this warp: wg, wg + G, ...
     const int32_t g = b.gap_val[it.gap];
     const int CW = (T + 15) >> 4;
-    uint32_t *codes = b.codes + it.code_off;
+    uint32_t *codes = b.codes + item_codes(b.pbases[it.pair].codes, pp, it.gap);
     const int32_t *Mp = b.M + pp.m_off;
     const int base_w = w - wg;
     const int pw = self ? w : base_w + (wg == 0 ? G - 1 : wg - 1);

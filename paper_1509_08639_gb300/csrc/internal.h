@@ -92,18 +92,24 @@ struct PairPlan {       // 56 bytes
     int64_t sel_base;   // mine_pair offset of the selection block (nset * min(S,T))
 };
 
+// Where a pair's alignment buffers start (read by the alignment kernels only)
+struct PairBases {
+    int64_t codes;      // uint32 offset of the direction codes of its first gap (then one
+                        // block of S rows x ceil(T/16) words per gap, in gap order)
+    int64_t matches;    // uint32 offset of its match lists (min(S,T) entries per gap)
+    int64_t tb;         // tiled alignments: int32 offset of the tile boundaries and flags
+                        // of its first gap (tb_words_of(S, T) per gap)
+};
+
 // Offset of cell (r, c) (0-based) of a tiled score matrix with TT column tiles.
 __host__ __device__ __forceinline__ int64_t m_cell(int64_t m_off, int TT, int r, int c)
 {
     return m_off + ((int64_t)(r >> 5) * TT + (c >> 5)) * kTileElems + (r & 31) * kTile + (c & 31);
 }
 
-struct NwItem {         // one alignment: (pair, gap)
+struct NwItem {         // one alignment: (pair, gap); its buffers follow from the pair's PairBases
     int32_t pair;
     int32_t gap;        // global gap index
-    int64_t code_off;   // uint32 offset of the direction codes (S rows x ceil(T/16) words)
-    int64_t match_off;  // uint32 offset of the match list (min(S,T) entries)
-    int64_t tb_off;     // tiled alignments: int32 offset of the tile boundaries and flags
 };
 
 // A tiled alignment is cut into tiles of kAlignTileRows x kAlignTileCols
@@ -121,6 +127,28 @@ struct TileItem {
 // (NC-1) x (S+1), flags NR x NC (int32 each)
 __host__ __device__ inline int64_t tile_rows_of(int32_t S) { return (S + kAlignTileRows - 1) / kAlignTileRows; }
 __host__ __device__ inline int64_t tile_cols_of(int32_t T) { return (T + kAlignTileCols - 1) / kAlignTileCols; }
+// int32 words of one tiled alignment's boundaries and flags: the last row of
+// every tile row but the last ((NR-1) x (T+1)), the last column of every tile
+// column but the last ((NC-1) x (S+1)), a done flag per tile; a multiple of 4
+__host__ __device__ inline int64_t tb_words_of(int32_t S, int32_t T)
+{
+    const int64_t NR = tile_rows_of(S), NC = tile_cols_of(T);
+    return ((NR - 1) * (T + 1) + (NC - 1) * (S + 1) + NR * NC + 3) & ~int64_t(3);
+}
+// Offsets of the buffers of alignment (pair pp, global gap index gap), from
+// the pair's base of that buffer
+__host__ __device__ inline int64_t item_codes(int64_t base, const PairPlan &pp, int32_t gap)
+{
+    return base + (int64_t)(gap - pp.gap0) * pp.S * ((pp.T + 15) >> 4);
+}
+__host__ __device__ inline int64_t item_matches(int64_t base, const PairPlan &pp, int32_t gap)
+{
+    return base + (int64_t)(gap - pp.gap0) * (pp.S < pp.T ? pp.S : pp.T);
+}
+__host__ __device__ inline int64_t item_tb(int64_t base, const PairPlan &pp, int32_t gap)
+{
+    return base + (int64_t)(gap - pp.gap0) * tb_words_of(pp.S, pp.T);
+}
 
 struct ScoreItem {      // 32 (preparation) or 64 (scoring) source rows of one pair
     int32_t pair;
@@ -140,6 +168,7 @@ struct BatchDev {
     int32_t n_pairs;
     // plan
     const PairPlan *pairs;
+    const PairBases *pbases;         // [n_pairs] where each pair's alignment buffers start
     const ScoreItem *prep_items;     // 32 rows each
     int32_t n_prep_items;
     const ScoreItem *score_items;    // 64 rows each

@@ -1963,8 +1963,9 @@ __device__ __forceinline__ void select_and_emit(const BatchDev &b, const PairPla
 __device__ void trace_and_select(const BatchDev &b, const NwItem &it, const PairPlan &pp, int lane)
 {
     const int S = pp.S, T = pp.T;
-    uint32_t *matches = b.matches + it.match_off;
-    const uint32_t *codes = b.codes + it.code_off;
+    const PairBases pb = b.pbases[it.pair];
+    uint32_t *matches = b.matches + item_matches(pb.matches, pp, it.gap);
+    const uint32_t *codes = b.codes + item_codes(pb.codes, pp, it.gap);
     const int CW = (T + 15) >> 4;
     int i = S, j = T, nm = 0;
     while (i > 0 && j > 0) {
@@ -2019,7 +2020,7 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
     const int S = pp.S, T = pp.T;
     const int R = ti.R, C = ti.C;
     const int NR = (int)tile_rows_of(S), NC = (int)tile_cols_of(T);
-    int32_t *hb = b.tbnd + it.tb_off;                              // rows: (NR-1) x (T+1)
+    int32_t *hb = b.tbnd + item_tb(b.pbases[it.pair].tb, pp, it.gap);   // rows: (NR-1) x (T+1)
     int32_t *vb = hb + (int64_t)(NR - 1) * (T + 1);                 // columns: (NC-1) x (S+1)
     int32_t *fl = vb + (int64_t)(NC - 1) * (S + 1);                 // flags: NR x NC
     // wait for the tiles above and on the left
@@ -2043,7 +2044,7 @@ __device__ bool align_tile(const BatchDev &b, AlignSmem &sm, int wib, int lane, 
     const int cb = clo >> 5, ce = (chi + 31) >> 5;           // score tiles of the columns
     const int s = (kAlignTileRows / 32) * R + wib;            // this warp's stripe
     if (s < TS) {
-        uint32_t *codes = b.codes + it.code_off;
+        uint32_t *codes = b.codes + item_codes(b.pbases[it.pair].codes, pp, it.gap);
         const int32_t *Mp = b.M + pp.m_off;
         const int mlo = clo >> 4, mhi = (chi + 15) >> 4;   // code words of the tile's columns
         const int i0 = 32 * s;

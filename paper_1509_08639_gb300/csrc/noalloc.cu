@@ -29,14 +29,16 @@ constexpr int64_t kOffCodes = kOffMrow + (int64_t)kNoAllocMaxDim * kNoAllocMaxDi
 constexpr int64_t kOffMatch = kOffCodes + (int64_t)kNoAllocMaxDim * (kNoAllocMaxDim / 16);
 constexpr int64_t kOffSel = kOffMatch + kNoAllocMaxDim;
 constexpr int64_t kOffOut = kOffSel + 3 * kNoAllocMaxDim;                 // nw_score, n_sel, hfin
-constexpr int64_t kOffPlan = kOffOut + 64;                                // PairPlan, NwItem, settings
+constexpr int64_t kOffPlan = kOffOut + 64;                                // PairPlan, NwItem, settings, PairBases
+constexpr int kPlanBasesAt = 128;                                         // byte offset of PairBases in the plan region
 constexpr int64_t kOffCounters = kOffPlan + 64;
 constexpr int64_t kScratchWords = kOffCounters + 64;
 static_assert(kOffMrow % 64 == 0 && kOffCodes % 64 == 0 && kOffMatch % 64 == 0 &&
                   kOffSel % 64 == 0 && kOffOut % 64 == 0 && kOffPlan % 64 == 0 &&
                   kOffCounters % 64 == 0,
               "scratch regions must stay 256-byte aligned");
-static_assert(sizeof(PairPlan) + sizeof(NwItem) + 20 <= 64 * 4, "plan region too small");
+static_assert(sizeof(PairPlan) + sizeof(NwItem) + 20 <= kPlanBasesAt && kPlanBasesAt + sizeof(PairBases) <= 64 * 4,
+              "plan region too small");
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchWords];
 
@@ -50,6 +52,7 @@ __global__ void k_noalloc_setup(int32_t *scratch, int32_t S, int32_t T, int32_t 
     PairPlan *pp = reinterpret_cast<PairPlan *>(plan);
     NwItem *it = reinterpret_cast<NwItem *>(plan + sizeof(PairPlan));
     int32_t *set = reinterpret_cast<int32_t *>(plan + sizeof(PairPlan) + sizeof(NwItem));
+    *reinterpret_cast<PairBases *>(plan + kPlanBasesAt) = PairBases{0, 0, 0};
     pp->s0 = 0;
     pp->S = S;
     pp->t0 = S;
@@ -64,8 +67,6 @@ __global__ void k_noalloc_setup(int32_t *scratch, int32_t S, int32_t T, int32_t 
     pp->sel_base = 0;
     it->pair = 0;
     it->gap = 0;
-    it->code_off = 0;
-    it->match_off = 0;
     set[0] = 0;     // set_gap
     set[1] = thr;   // set_thr
     set[2] = gap;   // gap_val
@@ -157,6 +158,7 @@ extern "C" int mine_align_matrix_noalloc(const mine_q16 *M, int32_t S, int32_t T
     b.n_pairs = 1;
     b.pairs = reinterpret_cast<const PairPlan *>(plan);
     b.nw_items = reinterpret_cast<const NwItem *>(plan + sizeof(PairPlan));
+    b.pbases = reinterpret_cast<const PairBases *>(plan + kPlanBasesAt);
     b.n_nw_items = 1;
     // the built-in alignment form of the pair (never tiles at these sizes)
     int form = align_kind(nullptr, S, T);

@@ -100,6 +100,7 @@ using Setting = std::pair<int32_t, int32_t>;   // (gap, threshold)
 struct Plan {
     int32_t P = 0;
     std::vector<PairPlan> pairs;
+    std::vector<PairBases> pbases;  // per pair: where its alignment buffers start
     std::vector<ScoreItem> pitems;  // 32-row items of the preparation kernel
     std::vector<ScoreItem> sitems;  // 64-row items of the score kernel
     std::vector<int32_t> dorder;    // pairs by sentence count, longest first; wide targets first
@@ -121,6 +122,7 @@ struct Plan {
     {
         P = 0;
         pairs.clear();
+        pbases.clear();
         pitems.clear();
         sitems.clear();
         dorder.clear();
@@ -231,6 +233,7 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
     if ((int64_t)doc_off[2 * (int64_t)P] != n_sent)
         return fail(MINE_EINVAL, "doc_off[2P] must equal n_sent");
     pl.pairs.resize(P);
+    pl.pbases.assign(P, PairBases{0, 0, 0});
     SettingsSeen seen;
     std::vector<int> bucketS(P), bucketC(P), bucketD(P);
     std::vector<int8_t> kind(P);
@@ -299,27 +302,28 @@ int build_plan(Plan &pl, int32_t P, const int32_t *doc_off, int64_t n_sent, F se
         for (int p : ord) {
             const PairPlan &pp = pl.pairs[p];
             if (kind[p] != kind_of_pass[pass]) continue;
+            // the pair's gaps one after another in each buffer
+            PairBases &pb = pl.pbases[p];
             const int64_t CW = (pp.T + 15) >> 4;
+            pb.codes = pl.code_words;
+            pl.code_words += pp.ngap * (int64_t)pp.S * CW;
+            pb.matches = pl.match_words;
+            pl.match_words += pp.ngap * (int64_t)std::min(pp.S, pp.T);
+            pb.tb = 0;
+            if (pass == kNwGroups) {
+                pb.tb = pl.tb_words;
+                pl.tb_words += pp.ngap * tb_words_of(pp.S, pp.T);
+            }
             for (int g = 0; g < pp.ngap; ++g) {
-                NwItem it;
-                it.pair = p;
-                it.gap = pp.gap0 + g;
-                it.code_off = pl.code_words;
-                pl.code_words += (int64_t)pp.S * CW;
-                it.match_off = pl.match_words;
-                pl.match_words += std::min(pp.S, pp.T);
-                it.tb_off = -1;
                 if (pass == kNwGroups) {
                     const int64_t NR = tile_rows_of(pp.S), NC = tile_cols_of(pp.T);
-                    it.tb_off = pl.tb_words;
-                    pl.tb_words += align_up((NR - 1) * (pp.T + 1) + (NC - 1) * (pp.S + 1) + NR * NC, 4);
                     for (int R = 0; R < NR; ++R)
                         for (int C = 0; C < NC; ++C) {
                             tl.push_back(TileItem{(int32_t)pl.nitems.size(), (int16_t)R, (int16_t)C});
                             tdiag.push_back(R + C);
                         }
                 }
-                pl.nitems.push_back(it);
+                pl.nitems.push_back(NwItem{p, pp.gap0 + g});
             }
         }
         if (pass < kNwGroups) {
@@ -348,7 +352,7 @@ struct Layout {
     int64_t counters = 0, nw = 0, nsel = 0, sel = 0;
     int64_t total = 0;
     // offsets inside the plan blob
-    int64_t o_pairs = 0, o_sitems = 0, o_nitems = 0, o_setgap = 0, o_setthr = 0, o_gapval = 0;
+    int64_t o_pairs = 0, o_pbases = 0, o_sitems = 0, o_nitems = 0, o_setgap = 0, o_setthr = 0, o_gapval = 0;
     int64_t o_setperm = 0, o_gapsfirst = 0;
     int64_t o_dorder = 0, o_pitems = 0, o_tiles = 0, tbnd = 0;
 };
@@ -369,6 +373,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
         return at;
     };
     L.o_pairs = sub(sizeof(PairPlan) * pl.pairs.size());
+    L.o_pbases = sub(sizeof(PairBases) * pl.pbases.size());
     L.o_sitems = sub(sizeof(ScoreItem) * pl.sitems.size());
     L.o_nitems = sub(sizeof(NwItem) * pl.nitems.size());
     L.o_setgap = sub(4 * pl.set_gap.size());
@@ -416,6 +421,7 @@ Layout make_layout(const Plan &pl, int32_t kmax, bool copy_inputs, bool own_sel,
 void pack_plan(const Plan &pl, const Layout &L, char *dst)
 {
     std::memcpy(dst + L.o_pairs, pl.pairs.data(), sizeof(PairPlan) * pl.pairs.size());
+    std::memcpy(dst + L.o_pbases, pl.pbases.data(), sizeof(PairBases) * pl.pbases.size());
     std::memcpy(dst + L.o_sitems, pl.sitems.data(), sizeof(ScoreItem) * pl.sitems.size());
     std::memcpy(dst + L.o_nitems, pl.nitems.data(), sizeof(NwItem) * pl.nitems.size());
     std::memcpy(dst + L.o_setgap, pl.set_gap.data(), 4 * pl.set_gap.size());
@@ -442,6 +448,7 @@ BatchDev make_batchdev(const Plan &pl, const Layout &L, char *base, const int32_
     b.n_pairs = pl.P;
     b.n_dwide = pl.n_dwide;
     b.pairs = reinterpret_cast<const PairPlan *>(plan + L.o_pairs);
+    b.pbases = reinterpret_cast<const PairBases *>(plan + L.o_pbases);
     b.prep_items = reinterpret_cast<const ScoreItem *>(plan + L.o_pitems);
     b.n_prep_items = (int32_t)pl.pitems.size();
     b.score_items = reinterpret_cast<const ScoreItem *>(plan + L.o_sitems);
