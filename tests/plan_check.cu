@@ -49,21 +49,25 @@ void check_tiling(std::vector<std::pair<int64_t, int64_t>> iv, int64_t total, co
     EXPECT(at == total, "%s: regions end at %lld, total %lld", what, (long long)at, (long long)total);
 }
 
-// A batch: pair sizes (S, T) and each pair's settings array.
+// A batch: pair sizes (S, T) and each pair's settings array; optionally the
+// two articles' roles exchanged (the other mining direction) and a
+// strategy table of alignment forms per size bin.
 struct Case {
     const char *name;
     std::vector<std::pair<int, int>> st;
     std::vector<std::vector<Setting>> lists;   // distinct arrays
     std::vector<int> list_of;                  // per pair: index into lists
+    bool swap = false;
+    std::vector<int8_t> tab;                   // empty: the built-in rule
 };
 
 void check_case(const Case &cs)
 {
     const int32_t P = (int32_t)cs.st.size();
     std::vector<int32_t> doc(2 * (size_t)P + 1, 0);
-    for (int p = 0; p < P; ++p) {
-        doc[2 * p + 1] = doc[2 * p] + cs.st[p].first;
-        doc[2 * p + 2] = doc[2 * p + 1] + cs.st[p].second;
+    for (int p = 0; p < P; ++p) {   // (with swap, the target article comes first in doc)
+        doc[2 * p + 1] = doc[2 * p] + (cs.swap ? cs.st[p].second : cs.st[p].first);
+        doc[2 * p + 2] = doc[2 * p + 1] + (cs.swap ? cs.st[p].first : cs.st[p].second);
     }
     Plan pl;
     const int rc = build_plan(pl, P, doc.data(), (int64_t)doc.back(),
@@ -72,7 +76,7 @@ void check_case(const Case &cs)
                                   s = l.data();
                                   n = (int)l.size();
                               },
-                              65536, true, nullptr);
+                              65536, true, cs.tab.empty() ? nullptr : cs.tab.data(), cs.swap);
     EXPECT(rc == 0, "%s: build_plan returned %d (%s)", cs.name, rc, g_err.c_str());
     EXPECT((int32_t)pl.pairs.size() == P && (int32_t)pl.pbases.size() == P, "%s: pair tables", cs.name);
 
@@ -83,7 +87,8 @@ void check_case(const Case &cs)
     for (int p = 0; p < P; ++p) {
         const PairPlan &pp = pl.pairs[p];
         const int S = cs.st[p].first, T = cs.st[p].second;
-        EXPECT(pp.s0 == doc[2 * p] && pp.S == S && pp.t0 == doc[2 * p + 1] && pp.T == T, "%s: pair %d", cs.name, p);
+        const int32_t s0 = cs.swap ? doc[2 * p + 1] : doc[2 * p], t0 = cs.swap ? doc[2 * p] : doc[2 * p + 1];
+        EXPECT(pp.s0 == s0 && pp.S == S && pp.t0 == t0 && pp.T == T, "%s: pair %d", cs.name, p);
         const auto &l = cs.lists[cs.list_of[p]];
         EXPECT(pp.set0 == rows && pp.nset == (int)l.size(), "%s: settings rows of pair %d", cs.name, p);
         rows += pp.nset;
@@ -269,6 +274,23 @@ int main()
             c.list_of.push_back(p < 40 ? 0 : p < 80 ? 1 : (p / 7) % 4);
         }
         cases.push_back(c);
+    }
+    // the other direction (each pair's articles exchanged), and a strategy
+    // table that sends some size bins to other forms
+    {
+        Case c = cases[1];
+        c.name = "sweep-swapped";
+        c.swap = true;
+        cases.push_back(c);
+        Case d = cases[1];
+        d.name = "sweep-table";
+        d.tab.assign(kAlignBins, (int8_t)-1);
+        d.tab[7] = AF_WARP1;
+        d.tab[12] = AF_WARP2;
+        d.tab[16] = AF_WARP8;
+        d.tab[18] = AF_WARP4;
+        d.tab[20] = AF_TILED;
+        cases.push_back(d);
     }
     for (const Case &c : cases) {
         check_case(c);
