@@ -1,11 +1,15 @@
-// Host-only check of the batch plan (built on the CPU, no GPU needed): the
-// runtime translation unit is compiled into this program, which builds plans
-// for seeded synthetic batches and checks their invariants -- every buffer
-// region of every pair and alignment in place and disjoint, every (pair, gap)
-// aligned once, the settings lists and their by-gap index, the tiles of the
-// tiled alignments, the preparation order and the byte layout of the device
-// region.  Exit status 0 and "ok" when every check holds; otherwise the first
-// failed check is printed and the status is 1.
+// Host-only checks of the runtime's host logic (no GPU needed): the runtime
+// translation unit is compiled into this program.
+//  - The batch plan: plans for seeded synthetic batches, and their invariants
+//    -- every buffer region of every pair and alignment in place and
+//    disjoint, every (pair, gap) aligned once, the settings lists and their
+//    by-gap index, the tiles of the tiled alignments, the preparation order
+//    and the byte layout of the device region.
+//  - The serving budget's first-fit pool: seeded alloc / release sequences
+//    against a plain model of the region (256-byte units), checking each
+//    offset (the first fit), the used count and that free blocks are merged.
+// Exit status 0 and "ok" when every check holds; otherwise the first failed
+// check is printed and the status is 1.
 #include "runtime.cu"
 
 #include <cstdio>
@@ -231,10 +235,77 @@ void check_case(const Case &cs)
            "%s: plan blob sizes", cs.name);
 }
 
+// The first-fit pool against a model: a byte per 256-byte unit (1 = taken).
+void check_pool(int64_t units, int steps)
+{
+    Pool pool;
+    pool.size = units * 256;
+    pool.free_[0] = pool.size;
+    std::vector<char> model(units, 0);
+    std::vector<std::pair<int64_t, int64_t>> live;   // (offset, bytes asked)
+    int64_t used = 0;
+    for (int it = 0; it < steps; ++it) {
+        if (live.empty() || rnd(3) != 0) {
+            // ask for 1 .. units/4 units' worth, not always a multiple of 256
+            const int64_t bytes = 1 + rnd((int)(units * 64));
+            const int64_t need = (bytes + 255) / 256;
+            int64_t want = -1;   // the model's first fit
+            for (int64_t u = 0, run = 0; u < units; ++u) {
+                run = model[u] ? 0 : run + 1;
+                if (run == need) {
+                    want = (u + 1 - need) * 256;
+                    break;
+                }
+            }
+            const int64_t off = pool.alloc(bytes);
+            EXPECT(off == want, "pool step %d: %lld bytes at %lld, the first fit is %lld", it, (long long)bytes,
+                   (long long)off, (long long)want);
+            if (off >= 0) {
+                for (int64_t u = off / 256; u < off / 256 + need; ++u) model[u] = 1;
+                live.push_back({off, bytes});
+                used += need * 256;
+            }
+        } else {
+            const int k = rnd((int)live.size());
+            const auto x = live[k];
+            live.erase(live.begin() + k);
+            pool.release(x.first, x.second);
+            for (int64_t u = x.first / 256; u < x.first / 256 + (x.second + 255) / 256; ++u) model[u] = 0;
+            used -= (x.second + 255) / 256 * 256;
+        }
+        EXPECT(pool.used == used, "pool step %d: used %lld, want %lld", it, (long long)pool.used, (long long)used);
+        // the free list is the model's free runs, each merged with its neighbours
+        int64_t at = -1;
+        for (const auto &f : pool.free_) {
+            EXPECT(f.first > at && f.second > 0 && f.first + f.second <= pool.size, "pool step %d: free block", it);
+            EXPECT(f.first == 0 || model[f.first / 256 - 1], "pool step %d: free block at %lld not merged", it,
+                   (long long)f.first);
+            for (int64_t u = f.first / 256; u < (f.first + f.second) / 256; ++u)
+                EXPECT(!model[u], "pool step %d: free block over a taken unit", it);
+            EXPECT(f.first + f.second == pool.size || model[(f.first + f.second) / 256], "pool step %d: free run cut",
+                   it);
+            at = f.first + f.second;
+        }
+        int64_t free_units = 0;
+        for (char m : model) free_units += !m;
+        int64_t listed = 0;
+        for (const auto &f : pool.free_) listed += f.second / 256;
+        EXPECT(listed == free_units, "pool step %d: %lld free units listed, %lld free", it, (long long)listed,
+               (long long)free_units);
+    }
+    for (const auto &x : live) pool.release(x.first, x.second);
+    EXPECT(pool.used == 0 && pool.free_.size() == 1 && pool.free_.begin()->first == 0 &&
+               pool.free_.begin()->second == pool.size,
+           "pool: not one free block after every release");
+}
+
 }  // namespace
 
 int main()
 {
+    check_pool(64, 4000);
+    check_pool(1000, 4000);
+    if (g_fail) return 1;
     std::vector<Case> cases;
     // edge sizes, one shared list of one setting
     {
