@@ -5,6 +5,8 @@
 //    disjoint, every (pair, gap) aligned once, the settings lists and their
 //    by-gap index, the tiles of the tiled alignments, the preparation order
 //    and the byte layout of the device region.
+//  - The plan's input checks: malformed batches and settings refused with
+//    their ABI codes, the int32 overflow bound exactly at its edge.
 //  - The serving budget's first-fit pool: seeded alloc / release sequences
 //    against a plain model of the region (256-byte units), checking each
 //    offset (the first fit), the used count and that free blocks are merged.
@@ -235,6 +237,53 @@ void check_case(const Case &cs)
            "%s: plan blob sizes", cs.name);
 }
 
+// The plan's input checks: each malformed batch or settings list is refused
+// with its ABI code, and the overflow bound (S+T)|g| + min(S,T) max|s| < 2^31
+// holds exactly at its edge.
+int plan_rc(std::vector<int32_t> doc, int64_t n_sent, std::vector<Setting> set, bool mined = true)
+{
+    Plan pl;
+    const int32_t P = doc.size() > 1 ? (int32_t)(doc.size() - 1) / 2 : 0;
+    return build_plan(pl, P, doc.data(), n_sent,
+                      [&](int32_t, const Setting *&s, int &n) {
+                          s = set.data();
+                          n = (int)set.size();
+                      },
+                      65536, mined, nullptr);
+}
+
+void check_errors()
+{
+    const std::vector<Setting> one{Setting(-65536, 32768)};
+    EXPECT(plan_rc({0, 3, 7}, 7, one) == MINE_OK, "a valid batch");
+    EXPECT(plan_rc({0}, 0, one) == MINE_OK, "no pairs");
+    EXPECT(plan_rc({1, 3, 7}, 7, one) == MINE_EINVAL, "doc_off[0] != 0");
+    EXPECT(plan_rc({0, 3, 2}, 2, one) == MINE_EINVAL, "decreasing doc_off");
+    EXPECT(plan_rc({0, 3, 7}, 8, one) == MINE_EINVAL, "doc_off[2P] != n_sent");
+    // (a gap of -1/65536: the overflow bound allows these sizes)
+    const std::vector<Setting> tiny{Setting(-1, 32768)};
+    EXPECT(plan_rc({0, MINE_MAX_SENTENCES, MINE_MAX_SENTENCES + 1}, MINE_MAX_SENTENCES + 1, tiny) == MINE_OK,
+           "the largest article");
+    EXPECT(plan_rc({0, MINE_MAX_SENTENCES + 1, MINE_MAX_SENTENCES + 2}, MINE_MAX_SENTENCES + 2, tiny) ==
+               MINE_EINVAL,
+           "an article above the largest");
+    EXPECT(plan_rc({0, MINE_MAX_SENTENCES, MINE_MAX_SENTENCES + 1}, MINE_MAX_SENTENCES + 1, one) == MINE_EOVERFLOW,
+           "the largest article at gap -1: (S+T)|g| reaches 2^32");
+    EXPECT(plan_rc({0, 3, 7}, 7, {}) == MINE_EINVAL, "no settings");
+    EXPECT(plan_rc({0, 3, 7}, 7, std::vector<Setting>(256, Setting(-1, 0))) == MINE_OK, "256 settings");
+    EXPECT(plan_rc({0, 3, 7}, 7, std::vector<Setting>(257, Setting(-1, 0))) == MINE_EINVAL, "257 settings");
+    EXPECT(plan_rc({0, 3, 7}, 7, {Setting(1, 0)}) == MINE_EINVAL, "a positive gap");
+    EXPECT(plan_rc({0, 3, 7}, 7, {Setting(0, 0), Setting(0, 65536)}) == MINE_OK, "gap 0, thresholds 0 and 1");
+    EXPECT(plan_rc({0, 3, 7}, 7, {Setting(-1, -1)}) == MINE_EINVAL, "a negative threshold");
+    EXPECT(plan_rc({0, 3, 7}, 7, {Setting(-1, 65537)}) == MINE_EINVAL, "a threshold above 1");
+    EXPECT(plan_rc({0, 3, 7}, 7, {Setting(-1, 65537)}, false) == MINE_OK, "thresholds unused: not checked");
+    // S = 1, T = 2: the bound is 3 |g| + 65536
+    EXPECT(plan_rc({0, 1, 3}, 3, {Setting(-715806037, 0)}) == MINE_OK, "bound 2^31 - 1");
+    EXPECT(plan_rc({0, 1, 3}, 3, {Setting(-715806038, 0)}) == MINE_EOVERFLOW, "bound 2^31 + 2");
+    // the largest |gap| decides for every setting of the list
+    EXPECT(plan_rc({0, 1, 3}, 3, {Setting(-1, 0), Setting(-715806038, 0)}) == MINE_EOVERFLOW, "a list's largest gap");
+}
+
 // The first-fit pool against a model: a byte per 256-byte unit (1 = taken).
 void check_pool(int64_t units, int steps)
 {
@@ -303,6 +352,8 @@ void check_pool(int64_t units, int steps)
 
 int main()
 {
+    check_errors();
+    if (g_fail) return 1;
     check_pool(64, 4000);
     check_pool(1000, 4000);
     if (g_fail) return 1;
