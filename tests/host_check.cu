@@ -5,6 +5,8 @@
 //    disjoint, every (pair, gap) aligned once, the settings lists and their
 //    by-gap index, the tiles of the tiled alignments, the preparation order
 //    and the byte layout of the device region.
+//  - The alignment forms: every pair shape under every strategy-table entry
+//    gets a form the kernels can run.
 //  - The plan's input checks: malformed batches and settings refused with
 //    their ABI codes, the int32 overflow bound exactly at its edge.
 //  - The serving budget's first-fit pool: seeded alloc / release sequences
@@ -284,6 +286,40 @@ void check_errors()
     EXPECT(plan_rc({0, 1, 3}, 3, {Setting(-1, 0), Setting(-715806038, 0)}) == MINE_EOVERFLOW, "a list's largest gap");
 }
 
+// The alignment form of every pair shape under every table entry is one the
+// kernels can run: tiles only where there are several tile rows and columns;
+// one warp only where its own ring holds a row (T < kRing, or one stripe);
+// a pipeline only where its first warp can get a whole row ahead of its last
+// (every warp one stripe at most, or the row within the rings of the links:
+// about 12 tiles of 32 columns per link).
+void check_forms()
+{
+    std::vector<int> sides;
+    for (int v : {0, 1, 2, 31, 32, 33, 63, 64, 65, 95, 96, 97, 128, 200, 255, 256, 257, 300, 384, 511, 512, 513,
+                  600, 800, 1000, 1023, 1024, 1025, 2000, 2048, 4000, 8192})
+        sides.push_back(v);
+    std::vector<int8_t> tab(kAlignBins, (int8_t)-1);
+    for (int entry = -1; entry < AF_FORMS; ++entry) {
+        for (int b = 0; b < kAlignBins; ++b) tab[b] = (int8_t)entry;
+        for (int S : sides)
+            for (int T : sides) {
+                const int f = align_kind(entry < 0 ? nullptr : tab.data(), S, T);
+                EXPECT(f == AF_WARP1 || f == AF_WARP2 || f == AF_WARP4 || f == AF_WARP8 || f == AF_TILED,
+                       "form %d for %d x %d", f, S, T);
+                if (f == AF_TILED) {
+                    EXPECT(S > kAlignTileRows && T > kAlignTileCols, "tiles for %d x %d", S, T);
+                    continue;
+                }
+                const int g = form_warps(f), ns = (S + 31) / 32, tt = (T + 31) / 32;
+                const int ge = std::max(1, std::min(std::min(g, ns), std::max(1, tt - 1)));
+                if (ge == 1)
+                    EXPECT(ns <= 1 || T < kRing, "one warp for %d x %d (table entry %d)", S, T, entry);
+                else
+                    EXPECT(ns <= ge || tt <= 12 * (ge - 1), "%d warps for %d x %d (table entry %d)", ge, S, T, entry);
+            }
+    }
+}
+
 // The first-fit pool against a model: a byte per 256-byte unit (1 = taken).
 void check_pool(int64_t units, int steps)
 {
@@ -353,6 +389,8 @@ void check_pool(int64_t units, int steps)
 int main()
 {
     check_errors();
+    if (g_fail) return 1;
+    check_forms();
     if (g_fail) return 1;
     check_pool(64, 4000);
     check_pool(1000, 4000);

@@ -7,6 +7,8 @@ runtime translation unit into a host program (no GPU involved) that
    aligned once, the settings lists and their by-gap index are right, the
    tiled alignments' tiles come in anti-diagonal order, and the device
    region's byte layout is aligned and disjoint;
+ - checks that every pair shape under every strategy-table entry gets an
+   alignment form the kernels can run;
  - checks that malformed batches and settings lists are refused with their
    ABI codes and that the int32 overflow bound holds exactly at its edge;
  - runs the serving budget's first-fit pool through seeded alloc / release
