@@ -1,8 +1,10 @@
 """Host-side logic of the benchmark, on the CPU: the count of kept
 translations (the entries the preparation kernel writes, part of its
 algorithmic bytes), computed with numpy in bench.py, against a direct loop
-over pairs, sentences, distinct tokens and dictionary entries; and the clock
-sampler's choice of the samples taken during the timed region."""
+over pairs, sentences, distinct tokens and dictionary entries; the clock
+sampler's choice of the samples taken during the timed region; the committed
+DRAM traffic used only while it describes the kernel source; and the
+whole-job rate and per-rank seeds of the multi-GPU run."""
 import os
 import sys
 import time
@@ -105,3 +107,38 @@ def test_clock_sampler_without_readable_timestamps(tmp_path, monkeypatch):
         clk.mark_end()
     s = clk.summary()
     assert s["window"] == "whole sampler run" and s["samples"] >= 3 and s["sm_mhz"] == 1000.0
+
+
+def test_traffic_is_kept_only_while_it_describes_the_kernel_source(tmp_path, monkeypatch):
+    # a stand-in tree: the three kernel sources and a committed summary keyed by their hash
+    csrc = tmp_path / "paper_1509_08639_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("kernels.cu", "align.cu", "internal.h"):
+        (csrc / f).write_text("// " + f + "\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    import json
+    summary = {"source_hash": bench.kernel_source_hash(),
+               "kernels": {"scoring": {"dram_bytes_per_launch_full_workload": 123},
+                           "alignment": {"dram_bytes_per_launch_full_workload": 45}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(summary))
+    assert bench.committed_traffic("scoring") == 123
+    assert bench.committed_traffic("alignment") == 45
+    assert bench.committed_traffic("other") is None
+    # any change to a kernel source: the counters no longer describe it
+    (csrc / "align.cu").write_text("// align.cu, changed\n")
+    assert bench.committed_traffic("scoring") is None
+    # no summary at all
+    (tmp_path / "profiles" / "traffic.json").unlink()
+    assert bench.committed_traffic("scoring") is None
+
+
+def test_whole_job_rate_and_rank_seeds():
+    # units of all ranks over the slowest rank's time
+    assert bench.whole_job_rate(10000, 1, 0.002) == 5e6
+    assert bench.whole_job_rate(10000, 4, 0.004) == 1e7
+    # rank 0 mines the standard batch; other ranks batches of their own, distinct per rank
+    assert bench.rank_seed(2, 0) is None
+    seeds = {bench.rank_seed(2, r) for r in range(1, 8)}
+    assert len(seeds) == 7 and all(s != 1508 + 2 for s in seeds)
+    assert bench.max_over_ranks(3.5, 1) == 3.5
