@@ -428,6 +428,17 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
  * warps in place of tiles for a pair of one tile row or column. */
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get);
 
+/* The autotuner's result kept across processes: write the context's strategy
+ * table to the file `path` as a small JSON document,
+ *   {"format": "mine-align-strategy", "bins": [t0, ..., t39]}
+ * (MINE_ALIGN_BINS entries, values as in mine_align_strategy), and read such
+ * a file back into a context (as mine_align_strategy with get = 0; a table is
+ * tuned for one kind of GPU).  MINE_EINVAL for a null argument, a file that
+ * cannot be opened or written, or content of any other form (the context's
+ * table is then unchanged).  Host only. */
+int mine_align_strategy_save(mine_ctx *ctx, const char *path);
+int mine_align_strategy_load(mine_ctx *ctx, const char *path);
+
 /* The roofline of the alignment: the measured rate of int32 add and max
  * operations of a device (device < 0: the current one).  Every thread of a
  * full grid runs independent chains of max(x + g, y) in three forms (plain C,

@@ -1089,6 +1089,99 @@ int mine_autotune_batch(mine_ctx *ctx, const mine_dict *dict, const mine_batch *
     return MINE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The strategy table as a small JSON document,
+//   {"format": "mine-align-strategy", "bins": [t0, t1, ..., t39]},
+// entries -1 .. AF_FORMS - 1 as in mine_align_strategy.
+std::string strategy_json(const int8_t *tab)
+{
+    std::string s = "{\"format\": \"mine-align-strategy\", \"bins\": [";
+    for (int b = 0; b < kAlignBins; ++b) {
+        if (b) s += ", ";
+        s += std::to_string((int)tab[b]);
+    }
+    s += "]}\n";
+    return s;
+}
+
+// Parse a document of that form (any white space between its tokens) into
+// tab; false, with tab unchanged, for anything else.
+bool strategy_parse(const std::string &t, int8_t *tab)
+{
+    size_t i = 0;
+    auto ws = [&] {
+        while (i < t.size() && (t[i] == ' ' || t[i] == '\t' || t[i] == '\n' || t[i] == '\r')) ++i;
+    };
+    auto lit = [&](const char *x) {
+        ws();
+        const size_t n = std::strlen(x);
+        if (t.compare(i, n, x) != 0) return false;
+        i += n;
+        return true;
+    };
+    int8_t v[kAlignBins];
+    if (!lit("{") || !lit("\"format\"") || !lit(":") || !lit("\"mine-align-strategy\"") || !lit(",") ||
+        !lit("\"bins\"") || !lit(":") || !lit("["))
+        return false;
+    for (int n = 0;; ++n) {
+        ws();
+        const bool neg = i < t.size() && t[i] == '-';
+        if (neg) ++i;
+        int x = 0, digits = 0;
+        while (i < t.size() && t[i] >= '0' && t[i] <= '9' && digits < 3) x = 10 * x + (t[i++] - '0'), ++digits;
+        if (digits == 0 || n >= kAlignBins) return false;
+        x = neg ? -x : x;
+        if (x < -1 || x >= AF_FORMS) return false;
+        v[n] = (int8_t)x;
+        if (lit(",")) continue;
+        if (!lit("]") || n + 1 != kAlignBins) return false;
+        break;
+    }
+    if (!lit("}")) return false;
+    ws();
+    if (i != t.size()) return false;
+    std::copy(v, v + kAlignBins, tab);
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mine_align_strategy_save(mine_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(MINE_EINVAL, "null context or path");
+    int8_t tab[kAlignBins];
+    {
+        std::lock_guard<std::mutex> lk(ctx->api_mu);
+        std::copy(ctx->align_tab, ctx->align_tab + kAlignBins, tab);
+    }
+    const std::string s = strategy_json(tab);
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(MINE_EINVAL, std::string("cannot open ") + path);
+    const size_t w = std::fwrite(s.data(), 1, s.size(), f);
+    if (std::fclose(f) != 0 || w != s.size()) return fail(MINE_EINVAL, std::string("cannot write ") + path);
+    return MINE_OK;
+}
+
+int mine_align_strategy_load(mine_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return fail(MINE_EINVAL, "null context or path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(MINE_EINVAL, std::string("cannot open ") + path);
+    std::string t;
+    char buf[4096];
+    size_t r;
+    while ((r = std::fread(buf, 1, sizeof buf, f)) > 0 && t.size() < (1u << 16)) t.append(buf, r);
+    std::fclose(f);
+    int8_t tab[kAlignBins];
+    if (!strategy_parse(t, tab)) return fail(MINE_EINVAL, std::string("not a strategy table: ") + path);
+    return mine_align_strategy(ctx, tab, kAlignBins, 0);
+}
+
 int mine_align_strategy(mine_ctx *ctx, int8_t *tab, int32_t n, int32_t get)
 {
     if (!ctx || !tab || n < 0 || n > kAlignBins) return fail(MINE_EINVAL, "bad argument");

@@ -101,6 +101,8 @@ SIGNATURES = {
     "mine_serving_stats": (_I, [_P, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "mine_int_peak": (_I, [_I, ctypes.POINTER(ctypes.c_double), _P, _I]),
     "mine_align_strategy": (_I, [_P, _P, _I, _I]),
+    "mine_align_strategy_save": (_I, [_P, ctypes.c_char_p]),
+    "mine_align_strategy_load": (_I, [_P, ctypes.c_char_p]),
     "mine_run_batch_bidi": (_I, [_P, _P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P,
                                  _P, _P, _P, _P, _L]),
     "mine_tune_f1": (_I, [_P, _P, ctypes.POINTER(BatchC), ctypes.POINTER(SettingsC), _P, _P, _P,
@@ -423,6 +425,15 @@ class Context:
         _check(self.L.mine_align_strategy(self.h, _ptr(t), int(t.shape[0]), 1 if table is None else 0),
                self.L)
         return [int(v) for v in t]
+
+    def align_strategy_save(self, path):
+        """Write the strategy table to a JSON file (mine_align_strategy_save)."""
+        _check(self.L.mine_align_strategy_save(self.h, os.fsencode(path)), self.L)
+
+    def align_strategy_load(self, path):
+        """Read a table written by align_strategy_save into this context; returns it."""
+        _check(self.L.mine_align_strategy_load(self.h, os.fsencode(path)), self.L)
+        return self.align_strategy()
 
     def profile_read(self):
         """{kernel name: (total device ms, timed launches)} since the last read."""

@@ -9,6 +9,8 @@
 //    gets a form the kernels can run.
 //  - The plan's input checks: malformed batches and settings refused with
 //    their ABI codes, the int32 overflow bound exactly at its edge.
+//  - The strategy table's file: save / load round trips through a context
+//    built on the host, and malformed documents refused.
 //  - The serving budget's first-fit pool: seeded alloc / release sequences
 //    against a plain model of the region (256-byte units), checking each
 //    offset (the first fit), the used count and that free blocks are merged.
@@ -320,6 +322,58 @@ void check_forms()
     }
 }
 
+// The strategy table's file: written and read back through a context (one
+// built on the host: no device is touched), every table a round trip; the
+// documents of any other form refused with the table unchanged.
+void check_strategy_file(const char *dir)
+{
+    const std::string path = std::string(dir) + "/strategy.json";
+    mine_ctx ctx;
+    for (int rep = 0; rep < 50; ++rep) {
+        int8_t tab[kAlignBins], back[kAlignBins];
+        for (int b = 0; b < kAlignBins; ++b) tab[b] = (int8_t)(rnd(AF_FORMS + 1) - 1);
+        EXPECT(mine_align_strategy(&ctx, tab, kAlignBins, 0) == MINE_OK, "set");
+        EXPECT(mine_align_strategy_save(&ctx, path.c_str()) == MINE_OK, "save: %s", mine_last_error());
+        int8_t other[kAlignBins];
+        std::fill(other, other + kAlignBins, (int8_t)-1);
+        EXPECT(mine_align_strategy(&ctx, other, kAlignBins, 0) == MINE_OK, "reset");
+        EXPECT(mine_align_strategy_load(&ctx, path.c_str()) == MINE_OK, "load: %s", mine_last_error());
+        EXPECT(mine_align_strategy(&ctx, back, kAlignBins, 1) == MINE_OK, "get");
+        EXPECT(std::equal(tab, tab + kAlignBins, back), "round trip %d", rep);
+    }
+    int8_t before[kAlignBins], after[kAlignBins];
+    EXPECT(mine_align_strategy(&ctx, before, kAlignBins, 1) == MINE_OK, "get");
+    std::string good = strategy_json(before);
+    std::string spaced = good;   // white space anywhere between tokens
+    for (size_t k = 0; k < spaced.size(); ++k)
+        if (spaced[k] == ',' || spaced[k] == ':' || spaced[k] == '[') spaced.insert(++k, "\n\t ");
+    std::string list = "";
+    for (int b = 0; b < kAlignBins; ++b) list += (b ? ", " : "") + std::to_string((int)before[b]);
+    const std::string head = "{\"format\": \"mine-align-strategy\", \"bins\": [";
+    const char *bad[] = {"", "{}", "not json", "{\"format\": \"other\", \"bins\": []}"};
+    std::vector<std::string> docs(bad, bad + 4);
+    docs.push_back(head + list + ", 0]}");                          // 41 entries
+    docs.push_back(head + list.substr(0, list.rfind(',')) + "]}");  // 39 entries
+    docs.push_back(head + "5" + list.substr(list.find(',')) + "]}");   // a value above the forms
+    docs.push_back(head + "-2" + list.substr(list.find(',')) + "]}");  // below -1
+    docs.push_back(head + list + ",]}");                            // a trailing comma
+    docs.push_back(head + list + "]} x");                           // text after the document
+    docs.push_back(good.substr(0, good.size() / 2));                // cut short
+    for (size_t k = 0; k <= docs.size(); ++k) {
+        const std::string &d = k < docs.size() ? docs[k] : spaced;
+        FILE *f = std::fopen(path.c_str(), "wb");
+        EXPECT(f && std::fwrite(d.data(), 1, d.size(), f) == d.size() && std::fclose(f) == 0, "write");
+        const int rc = mine_align_strategy_load(&ctx, path.c_str());
+        EXPECT(rc == (k < docs.size() ? MINE_EINVAL : MINE_OK), "document %zu: rc %d", k, rc);
+        EXPECT(mine_align_strategy(&ctx, after, kAlignBins, 1) == MINE_OK, "get");
+        EXPECT(std::equal(before, before + kAlignBins, after), "document %zu changed the table", k);
+    }
+    EXPECT(mine_align_strategy_load(&ctx, (path + ".missing").c_str()) == MINE_EINVAL, "a missing file");
+    EXPECT(mine_align_strategy_save(&ctx, (std::string(dir) + "/no/such/dir/s.json").c_str()) == MINE_EINVAL,
+           "an unwritable path");
+    std::remove(path.c_str());
+}
+
 // The first-fit pool against a model: a byte per 256-byte unit (1 = taken).
 void check_pool(int64_t units, int steps)
 {
@@ -386,8 +440,10 @@ void check_pool(int64_t units, int steps)
 
 }  // namespace
 
-int main()
+int main(int argc, char **argv)
 {
+    check_strategy_file(argc > 1 ? argv[1] : ".");
+    if (g_fail) return 1;
     check_errors();
     if (g_fail) return 1;
     check_forms();

@@ -75,3 +75,5 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.mine_run_batch_async(None, None, None, None, None, None, None, None, 0, None) == -1
     assert lib.mine_batch_wait(None, 1) == -1
     assert lib.mine_check(None) == -1
+    assert lib.mine_align_strategy_save(None, None) == -1
+    assert lib.mine_align_strategy_load(None, None) == -1

@@ -5,6 +5,7 @@ source rows x 32 target columns per score tile, 32-row alignment stripes,
 16-column direction words) and ragged tails; the full-size batch of 10,000
 lognormal pairs is run in the benchmark's launch configuration and sampled.
 """
+import json
 import os
 
 import numpy as np
@@ -281,6 +282,26 @@ def test_alignment_strategies_agree(ctx):
         assert_same(ctx.run_batch(dh, w.batch, w.settings), want, "tuned on the batch and a sweep")
         with pytest.raises(mine.MineError):
             ctx.autotune_batch(dh, w.batch, [(1, 0)])            # gap > 0
+    finally:
+        ctx.align_strategy(old)
+
+
+def test_strategy_table_file(ctx, tmp_path):
+    """The tuned table kept across processes: saved to a JSON file and loaded
+    back into a context; a malformed file is refused and changes nothing."""
+    old = ctx.align_strategy()
+    try:
+        tab = [(-1, 0, 1, 2, 3, 4)[k % 6] for k in range(mine.ALIGN_BINS)]
+        ctx.align_strategy(tab)
+        path = tmp_path / "strategy.json"
+        ctx.align_strategy_save(path)
+        assert json.loads(path.read_text()) == {"format": "mine-align-strategy", "bins": tab}
+        ctx.align_strategy(old)
+        assert ctx.align_strategy_load(path) == tab
+        path.write_text('{"format": "mine-align-strategy", "bins": [9]}')
+        with pytest.raises(mine.MineError):
+            ctx.align_strategy_load(path)
+        assert ctx.align_strategy() == tab
     finally:
         ctx.align_strategy(old)
 

@@ -11,6 +11,8 @@ runtime translation unit into a host program (no GPU involved) that
    alignment form the kernels can run;
  - checks that malformed batches and settings lists are refused with their
    ABI codes and that the int32 overflow bound holds exactly at its edge;
+ - saves and loads the strategy table's file through a context built on the
+   host (round trips; malformed documents refused, the table unchanged);
  - runs the serving budget's first-fit pool through seeded alloc / release
    sequences against a plain model of the region."""
 import os
@@ -35,5 +37,5 @@ def test_host_logic(tmp_path):
                                    os.path.join(HERE, "host_check.cu")] + objs + ["-lpthread"])
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
-    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    r = subprocess.run([exe, str(tmp_path)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
